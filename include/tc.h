@@ -1,0 +1,190 @@
+/*
+ * tc.h -- C ABI of the GB300 streaming triangle-count library (libtc.so).
+ *
+ * Implements the bulk update of r neighborhood-sampling estimators of
+ * Tangwongsan, Pavan and Tirthapura, "Parallel Triangle Counting in Massive
+ * Streaming Graphs" (CIKM'13, arXiv:1308.2166): each estimator keeps the
+ * tuple (f1, f2, f3, chi) of Invariant 3.1 (Sec. 3.1); a batch W of edges is
+ * folded in by Steps 1-3 of Sec. 4 (procedure bulkUpdateAll, Thm. 4.1); the
+ * estimate is the mean of the per-estimator values of Lemma 3.1.
+ *
+ * Conventions shared by every call:
+ *   - Edges are uint64 keys (u << 32) | v with u < v (undirected, packed
+ *     smaller id first).  Vertex ids are < 2^vertex_bits.  The order of an
+ *     edge array is arrival order (Sec. 2: the stream's total order).
+ *   - Every call returns 0 (TC_OK) or a negative TC_ERR_* code; no C++
+ *     exception crosses the ABI.  tc_strerror() names a code.
+ *   - Randomness is Philox4x32-10 keyed by (seed, stream id, estimator,
+ *     batch, slot): the same inputs, seed and batch boundaries give the same
+ *     state bit for bit, on any launch configuration.
+ *   - Device memory for the estimator state and all per-batch scratch is
+ *     owned by the library (cudaMalloc on the device that is current when
+ *     the context is created).  Input arrays are borrowed for the duration
+ *     of the call (or, for *_async calls, until the given CUDA stream
+ *     reaches that point).
+ *   - A rejected batch (TC_ERR_INPUT) leaves the estimator state, |E| and
+ *     the batch counter unchanged: validation results are checked on the
+ *     device before any state is written.
+ */
+#ifndef TC_H
+#define TC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TC_OK 0
+#define TC_ERR_INVAL (-1)   /* bad argument: null pointer, r == 0, bad sizes */
+#define TC_ERR_NOMEM (-2)   /* device or host allocation failed */
+#define TC_ERR_INPUT (-3)   /* batch breaks the stream model: self-loop, key
+                               not (min,max), id >= 2^vertex_bits, or an edge
+                               repeated inside the batch */
+#define TC_ERR_CUDA (-4)    /* a CUDA runtime call failed */
+#define TC_ERR_TIMEOUT (-5) /* a bounded device-side wait gave up */
+
+/* Empty level-1 / level-2 edge in tc_get_state output. */
+#define TC_EMPTY_EDGE 0xFFFFFFFFFFFFFFFFull
+/* Bit 0 of a state flag word: the wedge (f1, f2) is closed (f3 present). */
+#define TC_FLAG_CLOSED 1u
+
+typedef struct tc_ctx tc_ctx;
+
+/* Result of tc_estimate (Lemma 3.1 aggregated by the plain mean).
+ *   S = sum of chi over the estimators whose wedge is closed (128-bit),
+ *   N = |E| * S (128-bit, exact), tau_hat = N / r as a double computed as
+ *   q + rem / r with q = N div r. */
+typedef struct {
+    uint64_t sum_lo, sum_hi;   /* S */
+    uint64_t num_lo, num_hi;   /* N = m * S */
+    uint64_t r;                /* estimators */
+    uint64_t m;                /* |E|: edges folded in so far */
+    uint64_t n_closed;         /* estimators with a closed wedge */
+    uint64_t batches;          /* batches folded in so far */
+    double tau_hat;            /* N / r (display value; N is exact) */
+} tc_estimate_t;
+
+/* Create a stream of r >= 1 estimators (Sec. 4.1: est_1..est_r), all empty,
+ * |E| = 0, stream id 0, 32-bit vertex ids, scratch for batches of up to
+ * 2^22 edges (grown on demand by tc_process_batch).  *out receives the
+ * context.  Errors: TC_ERR_INVAL (r == 0, out == NULL), TC_ERR_NOMEM,
+ * TC_ERR_CUDA. */
+int tc_create(uint64_t r, uint64_t seed, tc_ctx **out);
+
+/* As tc_create with explicit stream id (part of the Philox counter, so
+ * independent streams may share a seed), maximum batch size w_max >= 1
+ * (scratch is sized for it up front) and vertex_bits in [1, 32] (a promise
+ * that every id is < 2^vertex_bits; it shortens the radix-sort keys).
+ * r must be < 2^32 (the estimator index is a 32-bit Philox counter word). */
+int tc_create_ex(uint64_t r, uint64_t seed, uint32_t stream_id, uint64_t w_max,
+                 uint32_t vertex_bits, tc_ctx **out);
+
+/* bulkUpdateAll (Sec. 4, Thm. 4.1): fold the batch edges[0..w) into every
+ * estimator -- Step 1 level-1 reservoir (Sec. 4.2), Step 2 rankAll, chi+
+ * and level-2 rank-select (Sec. 4.3, Lemma 4.3, Def. 4.2), Step 3 closing
+ * edges (Sec. 4.4) -- then |E| += w.  `edges` may be a host pointer (copied
+ * to the device inside the call) or a device pointer.  Synchronous: returns
+ * once the update is complete.  w == 0 is a no-op (no batch is counted).
+ * w above 2^28 is TC_ERR_INVAL.  Errors: TC_ERR_INPUT (state unchanged),
+ * TC_ERR_INVAL, TC_ERR_NOMEM, TC_ERR_CUDA, TC_ERR_TIMEOUT. */
+int tc_process_batch(tc_ctx *c, const uint64_t *edges, uint64_t w);
+
+/* Enqueue the same update on `cuda_stream` (a cudaStream_t; NULL = the
+ * legacy default stream) for a DEVICE array d_edges, without waiting.
+ * w must not exceed the context's current scratch capacity (w_max of
+ * tc_create_ex, or the largest w seen by tc_process_batch), else
+ * TC_ERR_INVAL.  Device-side errors (a rejected batch, a timeout) are
+ * reported by the next tc_sync / tc_estimate on this context; a rejected
+ * batch leaves the state unchanged and later batches proceed. */
+int tc_process_batch_async(tc_ctx *c, const uint64_t *d_edges, uint64_t w,
+                           void *cuda_stream);
+
+/* Wait for all work enqueued on the context and return the first
+ * device-side error recorded since the last tc_sync (then clear it). */
+int tc_sync(tc_ctx *c);
+
+/* The estimate of Lemma 3.1 averaged over the r estimators: one device
+ * reduction of S in 128-bit integers, then N = m * S exactly.  Synchronises
+ * (returns a pending device-side error first, as tc_sync). */
+int tc_estimate(tc_ctx *c, tc_estimate_t *out);
+
+/* Enqueue the reduction of tc_estimate on `cuda_stream` without waiting:
+ * writes four uint64 to the DEVICE array d_out -- S low word, S high word,
+ * the closed count, and |E| -- once the stream reaches it (N = |E| * S and
+ * tau_hat = N / r are then formed by the caller).  d_out is borrowed until
+ * the stream passes this point.  Errors: TC_ERR_INVAL, TC_ERR_CUDA. */
+int tc_estimate_async(tc_ctx *c, uint64_t *d_out, void *cuda_stream);
+
+/* Median-of-means aggregate (Sec. 3.1; the paper's implementation, Sec. 5):
+ * estimators are split into g contiguous groups, group k holding indices
+ * [k*r/g, (k+1)*r/g); each group's exact mean m * S_k / |group k| is formed
+ * and the lower median of the g means is returned as the exact fraction
+ * num / den (num 128-bit, den = that group's size) and as a double.
+ * Requires 1 <= g <= r.  Synchronises. */
+int tc_estimate_mom(tc_ctx *c, uint32_t g, uint64_t *num_lo, uint64_t *num_hi,
+                    uint64_t *den, double *value);
+
+/* Copy the estimator state to HOST arrays of r entries each (any may be
+ * NULL): f1, f2 as packed keys (TC_EMPTY_EDGE when empty), chi, and flags
+ * (TC_FLAG_CLOSED).  Synchronises. */
+int tc_get_state(tc_ctx *c, uint64_t *f1, uint64_t *f2, uint64_t *chi,
+                 uint32_t *flags);
+
+/* Counters: r, |E| and batches folded in so far.  Synchronises. */
+int tc_get_counters(tc_ctx *c, uint64_t *r, uint64_t *m, uint64_t *batches);
+
+/* Per-stage device time of the update (the paper's time breakdown of
+ * Sec. 5, Fig. 6: sort vs. multisearch vs. the rest).  Between
+ * tc_profile_begin and tc_profile_end every batch and estimate enqueued on
+ * this context records CUDA events around each stage on the stream it runs
+ * on; tc_profile_end waits for them and returns the sums.  `launches` counts
+ * the library kernels launched in that window; `sort_pass_bytes` is the
+ * algorithmic traffic of the onesweep digit passes (each launched pass reads
+ * and writes its n keys and values once).  Errors: TC_ERR_INVAL,
+ * TC_ERR_CUDA. */
+typedef struct {
+    uint64_t batches;             /* batches recorded */
+    uint64_t launches;            /* library kernels launched */
+    uint64_t sort_pass_launches;  /* onesweep digit-pass launches */
+    uint64_t sort_pass_bytes;     /* algorithmic bytes of those launches */
+    uint64_t sort_pass_skipped;   /* passes that found one digit value and did no work */
+    uint64_t overflow;            /* 1 if events ran out and some stages went unrecorded */
+    double ms_prep;               /* key build, histograms, validation, sort plans */
+    double ms_arc_sort;           /* rankAll digit passes (Lemma 4.3) */
+    double ms_edge_sort;          /* Step-3 `edges` digit passes (Sec. 4.4) */
+    double ms_dups;               /* in-batch repeat check */
+    double ms_sweep;              /* fused Steps 1-3 per estimator (searches) */
+    double ms_finish;             /* batch bookkeeping */
+    double ms_estimate;           /* tc_estimate / tc_estimate_async reductions */
+} tc_profile_t;
+
+int tc_profile_begin(tc_ctx *c);
+int tc_profile_end(tc_ctx *c, tc_profile_t *out);
+
+/* Free the context and its device memory (NULL is a no-op). */
+void tc_destroy(tc_ctx *c);
+
+/* Static description of an error code. */
+const char *tc_strerror(int code);
+
+/* rankAll (Lemma 4.3, Fig. 2) as a standalone call: for the DEVICE batch
+ * d_edges[0..w), write the 2w arcs ordered by src ascending then pos
+ * descending into DEVICE arrays of 2w uint32 each: src, dst, pos (0-based
+ * arrival index) and rank = rank(src -> dst) of Def. 4.2 (the number of
+ * batch edges on src that arrive after this one).  Work runs on
+ * `cuda_stream` and the call returns once it is complete.  Scratch (about
+ * 16 bytes per arc) is taken from and returned to the stream-ordered
+ * allocator inside the call.  The batch is not validated: its edges must be
+ * distinct (min,max) keys without self-loops and ids < 2^vertex_bits, and
+ * w <= 2^28.  Errors: TC_ERR_INVAL, TC_ERR_NOMEM, TC_ERR_CUDA,
+ * TC_ERR_TIMEOUT. */
+int tc_rank_all(const uint64_t *d_edges, uint64_t w, uint32_t vertex_bits,
+                uint32_t *d_src, uint32_t *d_dst, uint32_t *d_pos,
+                uint32_t *d_rank, void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TC_H */

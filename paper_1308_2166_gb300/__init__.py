@@ -1,0 +1,262 @@
+"""Thin Python binding of libtc.so (the C ABI in include/tc.h).
+
+Argument marshalling only: every step of the estimator update runs in the
+library's CUDA kernels.  Functions carry the C names; arrays may be numpy
+arrays (host) or torch tensors (host or CUDA, int64/uint64 holding the packed
+edge keys' bit patterns).  Errors raise ``TcError``.  If the compiled library
+is missing this module raises on first use -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libtc.so")
+
+TC_OK = 0
+TC_ERR_INVAL = -1
+TC_ERR_NOMEM = -2
+TC_ERR_INPUT = -3
+TC_ERR_CUDA = -4
+TC_ERR_TIMEOUT = -5
+TC_EMPTY_EDGE = (1 << 64) - 1
+TC_FLAG_CLOSED = 1
+
+# Every symbol include/tc.h declares (checked by tests/test_abi.py).
+EXPORTS = (
+    "tc_create", "tc_create_ex", "tc_process_batch", "tc_process_batch_async",
+    "tc_sync", "tc_estimate", "tc_estimate_async", "tc_estimate_mom", "tc_get_state",
+    "tc_get_counters", "tc_profile_begin", "tc_profile_end", "tc_destroy", "tc_strerror",
+    "tc_rank_all",
+)
+
+
+class TcError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {tc_strerror(code)} ({code})")
+
+
+class tc_estimate_t(ctypes.Structure):
+    _fields_ = [("sum_lo", ctypes.c_uint64), ("sum_hi", ctypes.c_uint64),
+                ("num_lo", ctypes.c_uint64), ("num_hi", ctypes.c_uint64),
+                ("r", ctypes.c_uint64), ("m", ctypes.c_uint64),
+                ("n_closed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
+                ("tau_hat", ctypes.c_double)]
+
+
+class tc_profile_t(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_uint64), ("launches", ctypes.c_uint64),
+                ("sort_pass_launches", ctypes.c_uint64), ("sort_pass_bytes", ctypes.c_uint64),
+                ("sort_pass_skipped", ctypes.c_uint64), ("overflow", ctypes.c_uint64),
+                ("ms_prep", ctypes.c_double), ("ms_arc_sort", ctypes.c_double),
+                ("ms_edge_sort", ctypes.c_double), ("ms_dups", ctypes.c_double),
+                ("ms_sweep", ctypes.c_double), ("ms_finish", ctypes.c_double),
+                ("ms_estimate", ctypes.c_double)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libtc.so (built by ``paper_1308_2166_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtc.so not built ({path}); run paper_1308_2166_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    P, U64, U32, I = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int
+    sig = {
+        "tc_create": (I, [U64, U64, ctypes.POINTER(P)]),
+        "tc_create_ex": (I, [U64, U64, U32, U64, U32, ctypes.POINTER(P)]),
+        "tc_process_batch": (I, [P, P, U64]),
+        "tc_process_batch_async": (I, [P, P, U64, P]),
+        "tc_sync": (I, [P]),
+        "tc_estimate": (I, [P, ctypes.POINTER(tc_estimate_t)]),
+        "tc_estimate_async": (I, [P, P, P]),
+        "tc_profile_begin": (I, [P]),
+        "tc_profile_end": (I, [P, ctypes.POINTER(tc_profile_t)]),
+        "tc_estimate_mom": (I, [P, U32, ctypes.POINTER(U64), ctypes.POINTER(U64),
+                                ctypes.POINTER(U64), ctypes.POINTER(ctypes.c_double)]),
+        "tc_get_state": (I, [P, P, P, P, P]),
+        "tc_get_counters": (I, [P, ctypes.POINTER(U64), ctypes.POINTER(U64), ctypes.POINTER(U64)]),
+        "tc_destroy": (None, [P]),
+        "tc_strerror": (ctypes.c_char_p, [I]),
+        "tc_rank_all": (I, [P, U64, U32, P, P, P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != TC_OK:
+        raise TcError(rc, where)
+
+
+def _ptr(a) -> int:
+    """Address of a numpy array or torch tensor (contiguous)."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _len(a) -> int:
+    return a.numel() if hasattr(a, "numel") else a.size
+
+
+def tc_strerror(code: int) -> str:
+    return load().tc_strerror(code).decode()
+
+
+def tc_create(r: int, seed: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load().tc_create(r, seed, ctypes.byref(h)), "tc_create")
+    return h.value
+
+
+def tc_create_ex(r: int, seed: int, stream_id: int = 0, w_max: int = 1 << 22,
+                 vertex_bits: int = 32) -> int:
+    h = ctypes.c_void_p()
+    _check(load().tc_create_ex(r, seed, stream_id, w_max, vertex_bits, ctypes.byref(h)),
+           "tc_create_ex")
+    return h.value
+
+
+def tc_process_batch(ctx: int, edges, w: int | None = None) -> None:
+    w = _len(edges) if w is None else w
+    _check(load().tc_process_batch(ctx, _ptr(edges) if w else None, w), "tc_process_batch")
+
+
+def tc_process_batch_async(ctx: int, d_edges, w: int | None = None, stream: int = 0) -> None:
+    w = _len(d_edges) if w is None else w
+    _check(load().tc_process_batch_async(ctx, _ptr(d_edges) if w else None, w, stream or None),
+           "tc_process_batch_async")
+
+
+def tc_sync(ctx: int) -> None:
+    _check(load().tc_sync(ctx), "tc_sync")
+
+
+def tc_estimate(ctx: int) -> dict:
+    out = tc_estimate_t()
+    _check(load().tc_estimate(ctx, ctypes.byref(out)), "tc_estimate")
+    return {"S": out.sum_lo | (out.sum_hi << 64), "N": out.num_lo | (out.num_hi << 64),
+            "r": out.r, "m": out.m, "n_closed": out.n_closed, "batches": out.batches,
+            "tau_hat": out.tau_hat}
+
+
+def tc_estimate_async(ctx: int, d_out, stream: int = 0) -> None:
+    """Enqueue the reduction; d_out: device array of 4 uint64 (S lo, S hi, closed, m)."""
+    _check(load().tc_estimate_async(ctx, _ptr(d_out), stream or None), "tc_estimate_async")
+
+
+def estimate_from_words(words, r: int) -> dict:
+    """Host-side finish of tc_estimate_async's four words (N = m * S exactly)."""
+    S = int(words[0]) | (int(words[1]) << 64)
+    m = int(words[3])
+    N = m * S
+    q, rem = divmod(N, r)
+    return {"S": S, "N": N, "n_closed": int(words[2]), "m": m, "tau_hat": q + rem / r}
+
+
+def tc_profile_begin(ctx: int) -> None:
+    _check(load().tc_profile_begin(ctx), "tc_profile_begin")
+
+
+def tc_profile_end(ctx: int) -> dict:
+    out = tc_profile_t()
+    _check(load().tc_profile_end(ctx, ctypes.byref(out)), "tc_profile_end")
+    return {name: getattr(out, name) for name, _ in tc_profile_t._fields_}
+
+
+def tc_estimate_mom(ctx: int, g: int) -> dict:
+    lo, hi, den = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    val = ctypes.c_double()
+    _check(load().tc_estimate_mom(ctx, g, ctypes.byref(lo), ctypes.byref(hi), ctypes.byref(den),
+                                  ctypes.byref(val)), "tc_estimate_mom")
+    return {"num": lo.value | (hi.value << 64), "den": den.value, "value": val.value}
+
+
+def tc_get_state(ctx: int):
+    """(f1, f2, chi, flags) as numpy uint64/uint32 arrays of length r."""
+    import numpy as np
+    r, _, _ = tc_get_counters(ctx)
+    f1 = np.empty(r, dtype=np.uint64)
+    f2 = np.empty(r, dtype=np.uint64)
+    chi = np.empty(r, dtype=np.uint64)
+    fl = np.empty(r, dtype=np.uint32)
+    _check(load().tc_get_state(ctx, f1.ctypes.data, f2.ctypes.data, chi.ctypes.data,
+                               fl.ctypes.data), "tc_get_state")
+    return f1, f2, chi, fl
+
+
+def tc_get_counters(ctx: int):
+    r, m, b = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().tc_get_counters(ctx, ctypes.byref(r), ctypes.byref(m), ctypes.byref(b)),
+           "tc_get_counters")
+    return r.value, m.value, b.value
+
+
+def tc_destroy(ctx: int) -> None:
+    if ctx:
+        load().tc_destroy(ctx)
+
+
+def tc_rank_all(d_edges, w: int, vertex_bits: int, d_src, d_dst, d_pos, d_rank,
+                stream: int = 0) -> None:
+    _check(load().tc_rank_all(_ptr(d_edges), w, vertex_bits, _ptr(d_src), _ptr(d_dst),
+                              _ptr(d_pos), _ptr(d_rank), stream or None), "tc_rank_all")
+
+
+class TriangleStream:
+    """Owning wrapper around one tc_ctx (same calls, Python lifetime)."""
+
+    def __init__(self, r: int, seed: int = 1, stream_id: int = 0, w_max: int = 1 << 22,
+                 vertex_bits: int = 32):
+        self.ctx = tc_create_ex(r, seed, stream_id, w_max, vertex_bits)
+        self.r = r
+
+    def process_batch(self, edges, w=None):
+        tc_process_batch(self.ctx, edges, w)
+
+    def process_batch_async(self, d_edges, w=None, stream=0):
+        tc_process_batch_async(self.ctx, d_edges, w, stream)
+
+    def sync(self):
+        tc_sync(self.ctx)
+
+    def estimate(self):
+        return tc_estimate(self.ctx)
+
+    def estimate_mom(self, g):
+        return tc_estimate_mom(self.ctx, g)
+
+    def state(self):
+        return tc_get_state(self.ctx)
+
+    def counters(self):
+        return tc_get_counters(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            tc_destroy(self.ctx)
+            self.ctx = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

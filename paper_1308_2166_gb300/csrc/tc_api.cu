@@ -1,0 +1,577 @@
+// Host side of the C ABI declared in include/tc.h: context lifetime, the
+// per-batch launch sequence of bulkUpdateAll (Sec. 4), the estimate of
+// Lemma 3.1, stage timing and the standalone rankAll (Lemma 4.3).
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tc_kernels.cuh"
+
+using namespace tc;
+
+static cudaError_t &last_cuda_error() {
+    static thread_local cudaError_t e = cudaSuccess;
+    return e;
+}
+
+#define TC_CUDA(call)                \
+    do {                             \
+        cudaError_t e_ = (call);     \
+        if (e_ != cudaSuccess) {     \
+            last_cuda_error() = e_;  \
+            return TC_ERR_CUDA;      \
+        }                            \
+    } while (0)
+
+namespace {
+
+constexpr u64 kMaxBatch = 1ull << 28;
+constexpr u64 kDefaultWMax = 1ull << 22;
+constexpr size_t kEventPool = 8192;
+
+enum Stage { kStart = -1, kPrep = 0, kArcSort, kEdgeSort, kDups, kSweep, kFinish, kEstimate,
+             kStages };
+
+size_t onesweep_smem(bool values) {
+    return values ? sizeof(OnesweepSmem<true>) : sizeof(OnesweepSmem<false>);
+}
+
+int configure_kernels() {
+    static bool done[64] = {false};
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && done[dev]) return TC_OK;
+    TC_CUDA(cudaFuncSetAttribute(onesweep_pass_kernel<false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)onesweep_smem(false)));
+    TC_CUDA(cudaFuncSetAttribute(onesweep_pass_kernel<true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)onesweep_smem(true)));
+    if (dev < 64) done[dev] = true;
+    return TC_OK;
+}
+
+BatchShape make_shape(u64 w, u32 B) {
+    BatchShape s{};
+    s.w = (u32)w;
+    s.bw = bits_for(w - 1);
+    s.B = B;
+    s.sha = s.bw + 1;
+    s.npa = (int)((B + kRadixBits - 1) / kRadixBits);
+    s.ekeys_only = (2 * B + s.bw <= 64) ? 1u : 0u;
+    s.she = s.ekeys_only ? s.bw : 0u;
+    s.npe = (int)((2 * B + kRadixBits - 1) / kRadixBits);
+    return s;
+}
+
+u64 tiles_of(u64 n) { return (n + kSortTile - 1) / kSortTile; }
+
+// Words of look-back status for one batch of w edges.
+u64 lookback_words(const BatchShape &s, bool edges) {
+    u64 words = (u64)s.npa * tiles_of(2ull * s.w) * kRadix;
+    if (edges) words += (u64)s.npe * tiles_of(s.w) * kRadix;
+    return words;
+}
+
+}  // namespace
+
+struct tc_ctx {
+    int device = 0;
+    u64 r = 0, seed = 0;
+    u32 stream_id = 0, vertex_bits = 32;
+    u64 cap_w = 0;  // scratch capacity in edges
+    cudaStream_t own = nullptr;
+    // estimator state (structure of arrays)
+    u64 *f1 = nullptr, *f2 = nullptr, *chi = nullptr;
+    u32 *flags = nullptr;
+    Control *ctl = nullptr;
+    // per-batch scratch
+    u64 *arcs[2] = {nullptr, nullptr};
+    u64 *ekeys[2] = {nullptr, nullptr};
+    u32 *evals[2] = {nullptr, nullptr};
+    u64 *staging = nullptr;
+    unsigned char *zeroed = nullptr;  // SortPlan[2] followed by look-back words
+    u64 *red = nullptr;               // reduction output (device, 4 words)
+    // host side
+    Mailbox *mbox = nullptr;  // mapped pinned, written by finish_kernel
+    Mailbox *mbox_dev = nullptr;
+    u64 *h_red = nullptr;     // pinned
+    // launch accounting and stage timing
+    u64 launches = 0;
+    bool prof = false;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    struct Stamp {
+        cudaEvent_t ev;
+        int stage;  // stage that ends here; kStart opens a sequence
+    };
+    std::vector<Stamp> stamps;
+    u64 prof_launch0 = 0, prof_batches = 0, prof_sort_launches = 0, prof_sort_bytes = 0;
+    u64 prof_skip0 = 0, prof_skipbytes0 = 0;
+    bool prof_overflow = false;
+};
+
+static void stamp(tc_ctx *c, cudaStream_t st, int stage) {
+    if (!c->prof) return;
+    if (c->pool_used >= c->pool.size()) {
+        c->prof_overflow = true;
+        return;
+    }
+    cudaEvent_t ev = c->pool[c->pool_used++];
+    cudaEventRecord(ev, st);
+    c->stamps.push_back({ev, stage});
+}
+
+static void free_scratch(tc_ctx *c) {
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(c->arcs[k]);
+        cudaFree(c->ekeys[k]);
+        cudaFree(c->evals[k]);
+        c->arcs[k] = c->ekeys[k] = nullptr;
+        c->evals[k] = nullptr;
+    }
+    cudaFree(c->staging);
+    cudaFree(c->zeroed);
+    c->staging = nullptr;
+    c->zeroed = nullptr;
+    c->cap_w = 0;
+}
+
+static int ensure_scratch(tc_ctx *c, u64 w) {
+    if (w <= c->cap_w) return TC_OK;
+    TC_CUDA(cudaDeviceSynchronize());
+    free_scratch(c);
+    const BatchShape s = make_shape(w, c->vertex_bits);
+    const u64 zb = 2 * sizeof(SortPlan) + lookback_words(s, true) * sizeof(u32);
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k) {
+        ok &= cudaMalloc(&c->arcs[k], 2 * w * sizeof(u64)) == cudaSuccess;
+        ok &= ok && cudaMalloc(&c->ekeys[k], w * sizeof(u64)) == cudaSuccess;
+        ok &= ok && cudaMalloc(&c->evals[k], w * sizeof(u32)) == cudaSuccess;
+    }
+    ok &= ok && cudaMalloc(&c->staging, w * sizeof(u64)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&c->zeroed, zb) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_scratch(c);
+        return TC_ERR_NOMEM;
+    }
+    c->cap_w = w;
+    return TC_OK;
+}
+
+static int map_device_error(u32 e) {
+    if (e == kErrInput) return TC_ERR_INPUT;
+    if (e == kErrTimeout) return TC_ERR_TIMEOUT;
+    return e ? TC_ERR_CUDA : TC_OK;
+}
+
+// Enqueue one batch on `st`.  W is a device pointer; w in [1, cap_w].
+static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
+    const BatchShape s = make_shape(w, c->vertex_bits);
+    SortPlan *plans = reinterpret_cast<SortPlan *>(c->zeroed);
+    u32 *lb = reinterpret_cast<u32 *>(c->zeroed + 2 * sizeof(SortPlan));
+    const u64 used = 2 * sizeof(SortPlan) + lookback_words(s, true) * sizeof(u32);
+    stamp(c, st, kStart);
+    TC_CUDA(cudaMemsetAsync(c->zeroed, 0, used, st));
+
+    const u64 prep_blocks = std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
+    prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, 0, st>>>(W, s, c->arcs[0], c->ekeys[0],
+                                                                 c->evals[0], plans, &c->ctl->err, 1);
+    sort_plan_kernel<<<2, kSortThreads, 0, st>>>(plans, s.npa, (u32)(2 * w), s.npe, (u32)w);
+    stamp(c, st, kPrep);
+    const u64 ta = tiles_of(2 * w), te = tiles_of(w);
+    for (int p = 0; p < s.npa; ++p) {
+        onesweep_pass_kernel<false><<<(unsigned)ta, kSortThreads, onesweep_smem(false), st>>>(
+            c->arcs[0], c->arcs[1], nullptr, nullptr, (u32)(2 * w), s.sha + p * kRadixBits, p,
+            &plans[0], lb + (u64)p * ta * kRadix, &c->ctl->err, c->ctl);
+    }
+    stamp(c, st, kArcSort);
+    u32 *lbe = lb + (u64)s.npa * ta * kRadix;
+    for (int p = 0; p < s.npe; ++p) {
+        u32 *lbp = lbe + (u64)p * te * kRadix;
+        if (s.ekeys_only)
+            onesweep_pass_kernel<false><<<(unsigned)te, kSortThreads, onesweep_smem(false), st>>>(
+                c->ekeys[0], c->ekeys[1], nullptr, nullptr, (u32)w, s.she + p * kRadixBits, p,
+                &plans[1], lbp, &c->ctl->err, c->ctl);
+        else
+            onesweep_pass_kernel<true><<<(unsigned)te, kSortThreads, onesweep_smem(true), st>>>(
+                c->ekeys[0], c->ekeys[1], c->evals[0], c->evals[1], (u32)w,
+                s.she + p * kRadixBits, p, &plans[1], lbp, &c->ctl->err, c->ctl);
+    }
+    stamp(c, st, kEdgeSort);
+    const u64 dup_blocks = std::min<u64>((w + 255) / 256, 1216);
+    dups_kernel<<<(unsigned)dup_blocks, 256, 0, st>>>(c->ekeys[0], c->ekeys[1], plans, s,
+                                                      &c->ctl->err);
+    stamp(c, st, kDups);
+    SweepArgs a{};
+    a.W = W;
+    a.f1 = c->f1;
+    a.f2 = c->f2;
+    a.chi = c->chi;
+    a.flags = c->flags;
+    a.r = c->r;
+    a.arcs0 = c->arcs[0];
+    a.arcs1 = c->arcs[1];
+    a.ekeys0 = c->ekeys[0];
+    a.ekeys1 = c->ekeys[1];
+    a.evals0 = c->evals[0];
+    a.evals1 = c->evals[1];
+    a.plans = plans;
+    a.ctl = c->ctl;
+    a.s = s;
+    a.key = make_uint2((u32)(c->seed & 0xFFFFFFFFu), (u32)(c->seed >> 32));
+    a.stream = c->stream_id;
+    const u64 sweep_blocks = (c->r + kSweepThreads - 1) / kSweepThreads;
+    sweep_kernel<<<(unsigned)sweep_blocks, kSweepThreads, 0, st>>>(a);
+    stamp(c, st, kSweep);
+    finish_kernel<<<1, 1, 0, st>>>(c->ctl, c->mbox_dev, w);
+    stamp(c, st, kFinish);
+    TC_CUDA(cudaGetLastError());
+    c->launches += 5 + (u64)s.npa + (u64)s.npe;
+    if (c->prof) {
+        c->prof_batches += 1;
+        c->prof_sort_launches += (u64)s.npa + (u64)s.npe;
+        c->prof_sort_bytes += (u64)s.npa * 2 * w * 16 + (u64)s.npe * w * (s.ekeys_only ? 16 : 24);
+    }
+    return TC_OK;
+}
+
+static int enqueue_estimate(tc_ctx *c, u64 *d_out, cudaStream_t st) {
+    stamp(c, st, kStart);
+    TC_CUDA(cudaMemsetAsync(d_out, 0, 3 * sizeof(u64), st));
+    const u64 blocks = std::min<u64>((c->r + kReduceThreads - 1) / kReduceThreads, 1216);
+    estimate_kernel<<<(unsigned)blocks, kReduceThreads, 0, st>>>(c->chi, c->flags, c->r, c->ctl,
+                                                                 d_out);
+    stamp(c, st, kEstimate);
+    TC_CUDA(cudaGetLastError());
+    c->launches += 1;
+    return TC_OK;
+}
+
+// Read and clear the device-side error after the context's work is done.
+static int collect_error(tc_ctx *c) {
+    const u32 e = c->mbox->err;
+    if (e) {
+        c->mbox->err = 0;
+        TC_CUDA(cudaMemsetAsync(&c->ctl->sticky, 0, sizeof(u32), c->own));
+        TC_CUDA(cudaStreamSynchronize(c->own));
+    }
+    return map_device_error(e);
+}
+
+extern "C" {
+
+const char *tc_strerror(int code) {
+    switch (code) {
+        case TC_OK: return "ok";
+        case TC_ERR_INVAL: return "invalid argument";
+        case TC_ERR_NOMEM: return "out of memory";
+        case TC_ERR_INPUT:
+            return "batch breaks the stream model (self-loop, bad key, id range or repeated edge)";
+        case TC_ERR_CUDA: return "CUDA runtime error";
+        case TC_ERR_TIMEOUT: return "bounded device wait timed out";
+        default: return "unknown error";
+    }
+}
+
+int tc_create_ex(uint64_t r, uint64_t seed, uint32_t stream_id, uint64_t w_max,
+                 uint32_t vertex_bits, tc_ctx **out) {
+    if (!out || r == 0 || r > 0xFFFFFFFFull || w_max == 0 || w_max > kMaxBatch ||
+        vertex_bits < 1 || vertex_bits > 32)
+        return TC_ERR_INVAL;
+    *out = nullptr;
+    int rc = configure_kernels();
+    if (rc) return rc;
+    tc_ctx *c = new (std::nothrow) tc_ctx();
+    if (!c) return TC_ERR_NOMEM;
+    c->r = r;
+    c->seed = seed;
+    c->stream_id = stream_id;
+    c->vertex_bits = vertex_bits;
+    bool ok = cudaGetDevice(&c->device) == cudaSuccess;
+    ok &= ok && cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) == cudaSuccess;
+    ok &= ok && cudaMalloc(&c->f1, r * sizeof(u64)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&c->f2, r * sizeof(u64)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&c->chi, r * sizeof(u64)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&c->flags, r * sizeof(u32)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&c->ctl, sizeof(Control)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&c->red, 4 * sizeof(u64)) == cudaSuccess;
+    ok &= ok && cudaHostAlloc(&c->mbox, sizeof(Mailbox), cudaHostAllocMapped) == cudaSuccess;
+    ok &= ok && cudaHostGetDevicePointer((void **)&c->mbox_dev, c->mbox, 0) == cudaSuccess;
+    ok &= ok && cudaHostAlloc(&c->h_red, 4 * sizeof(u64), cudaHostAllocDefault) == cudaSuccess;
+    if (ok) {
+        std::memset(c->mbox, 0, sizeof(Mailbox));
+        ok &= cudaMemsetAsync(c->f1, 0xFF, r * sizeof(u64), c->own) == cudaSuccess;
+        ok &= cudaMemsetAsync(c->f2, 0xFF, r * sizeof(u64), c->own) == cudaSuccess;
+        ok &= cudaMemsetAsync(c->chi, 0, r * sizeof(u64), c->own) == cudaSuccess;
+        ok &= cudaMemsetAsync(c->flags, 0, r * sizeof(u32), c->own) == cudaSuccess;
+        ok &= cudaMemsetAsync(c->ctl, 0, sizeof(Control), c->own) == cudaSuccess;
+    }
+    if (ok) {
+        int rc2 = ensure_scratch(c, w_max);
+        if (rc2) {
+            tc_destroy(c);
+            return rc2;
+        }
+        ok &= cudaStreamSynchronize(c->own) == cudaSuccess;
+    }
+    if (!ok) {
+        cudaError_t e = cudaGetLastError();
+        tc_destroy(c);
+        return e == cudaErrorMemoryAllocation ? TC_ERR_NOMEM : TC_ERR_CUDA;
+    }
+    *out = c;
+    return TC_OK;
+}
+
+int tc_create(uint64_t r, uint64_t seed, tc_ctx **out) {
+    return tc_create_ex(r, seed, 0, kDefaultWMax, 32, out);
+}
+
+void tc_destroy(tc_ctx *c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    free_scratch(c);
+    cudaFree(c->f1);
+    cudaFree(c->f2);
+    cudaFree(c->chi);
+    cudaFree(c->flags);
+    cudaFree(c->ctl);
+    cudaFree(c->red);
+    if (c->mbox) cudaFreeHost(c->mbox);
+    if (c->h_red) cudaFreeHost(c->h_red);
+    for (cudaEvent_t ev : c->pool) cudaEventDestroy(ev);
+    if (c->own) cudaStreamDestroy(c->own);
+    delete c;
+}
+
+int tc_process_batch_async(tc_ctx *c, const uint64_t *d_edges, uint64_t w, void *cuda_stream) {
+    if (!c || (w && !d_edges) || w > kMaxBatch) return TC_ERR_INVAL;
+    if (w == 0) return TC_OK;
+    if (w > c->cap_w) return TC_ERR_INVAL;
+    return enqueue_batch(c, d_edges, w, (cudaStream_t)cuda_stream);
+}
+
+int tc_process_batch(tc_ctx *c, const uint64_t *edges, uint64_t w) {
+    if (!c || (w && !edges) || w > kMaxBatch) return TC_ERR_INVAL;
+    if (w == 0) return TC_OK;
+    int rc = ensure_scratch(c, w);
+    if (rc) return rc;
+    cudaPointerAttributes attr{};
+    TC_CUDA(cudaPointerGetAttributes(&attr, edges));
+    const u64 *W = edges;
+    if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
+        TC_CUDA(cudaMemcpyAsync(c->staging, edges, w * sizeof(u64), cudaMemcpyHostToDevice,
+                                c->own));
+        W = c->staging;
+    }
+    rc = enqueue_batch(c, W, w, c->own);
+    if (rc) return rc;
+    TC_CUDA(cudaStreamSynchronize(c->own));
+    return collect_error(c);
+}
+
+int tc_sync(tc_ctx *c) {
+    if (!c) return TC_ERR_INVAL;
+    TC_CUDA(cudaDeviceSynchronize());
+    return collect_error(c);
+}
+
+int tc_get_counters(tc_ctx *c, uint64_t *r, uint64_t *m, uint64_t *batches) {
+    if (!c) return TC_ERR_INVAL;
+    TC_CUDA(cudaDeviceSynchronize());
+    if (r) *r = c->r;
+    if (m) *m = c->mbox->m;
+    if (batches) *batches = c->mbox->batches;
+    return TC_OK;
+}
+
+int tc_estimate_async(tc_ctx *c, uint64_t *d_out, void *cuda_stream) {
+    if (!c || !d_out) return TC_ERR_INVAL;
+    return enqueue_estimate(c, d_out, (cudaStream_t)cuda_stream);
+}
+
+int tc_estimate(tc_ctx *c, tc_estimate_t *out) {
+    if (!c || !out) return TC_ERR_INVAL;
+    int rc = tc_sync(c);
+    if (rc) return rc;
+    rc = enqueue_estimate(c, c->red, c->own);
+    if (rc) return rc;
+    TC_CUDA(cudaMemcpyAsync(c->h_red, c->red, 4 * sizeof(u64), cudaMemcpyDeviceToHost, c->own));
+    TC_CUDA(cudaStreamSynchronize(c->own));
+    using u128 = unsigned __int128;
+    const u128 S = ((u128)c->h_red[1] << 64) | c->h_red[0];
+    const u64 m = c->h_red[3];
+    const u128 N = S * (u128)m;
+    out->sum_lo = (u64)S;
+    out->sum_hi = (u64)(S >> 64);
+    out->num_lo = (u64)N;
+    out->num_hi = (u64)(N >> 64);
+    out->r = c->r;
+    out->m = m;
+    out->n_closed = c->h_red[2];
+    out->batches = c->mbox->batches;
+    const u128 q = N / c->r, rem = N % c->r;
+    out->tau_hat = (double)q + (double)rem / (double)c->r;
+    return TC_OK;
+}
+
+int tc_estimate_mom(tc_ctx *c, uint32_t g, uint64_t *num_lo, uint64_t *num_hi, uint64_t *den,
+                    double *value) {
+    if (!c || g == 0 || g > c->r) return TC_ERR_INVAL;
+    int rc = tc_sync(c);
+    if (rc) return rc;
+    u64 *d_out = nullptr;
+    TC_CUDA(cudaMallocAsync(&d_out, 2ull * g * sizeof(u64), c->own));
+    group_sum_kernel<<<g, kReduceThreads, 0, c->own>>>(c->chi, c->flags, c->r, g, d_out);
+    c->launches += 1;
+    std::vector<u64> h(2ull * g);
+    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e2 =
+        cudaMemcpyAsync(h.data(), d_out, 2ull * g * sizeof(u64), cudaMemcpyDeviceToHost, c->own);
+    cudaError_t e3 = cudaFreeAsync(d_out, c->own);
+    cudaError_t e4 = cudaStreamSynchronize(c->own);
+    if (e1 || e2 || e3 || e4) return TC_ERR_CUDA;
+    using u128 = unsigned __int128;
+    struct G {
+        u128 s;
+        u64 size;
+    };
+    std::vector<G> gs(g);
+    for (u32 k = 0; k < g; ++k) {
+        const u64 lo = (u64)(((u128)k * c->r) / g), hi = (u64)(((u128)(k + 1) * c->r) / g);
+        gs[k].s = ((u128)h[2 * k + 1] << 64) | h[2 * k];
+        gs[k].size = hi - lo;
+    }
+    // order the means S_k / size_k exactly (the common factor m drops out)
+    std::sort(gs.begin(), gs.end(),
+              [](const G &a, const G &b) { return a.s * (u128)b.size < b.s * (u128)a.size; });
+    const G &med = gs[(g - 1) / 2];
+    const u128 num = med.s * (u128)c->mbox->m;
+    if (num_lo) *num_lo = (u64)num;
+    if (num_hi) *num_hi = (u64)(num >> 64);
+    if (den) *den = med.size;
+    if (value) *value = (double)(num / med.size) + (double)(num % med.size) / (double)med.size;
+    return TC_OK;
+}
+
+int tc_get_state(tc_ctx *c, uint64_t *f1, uint64_t *f2, uint64_t *chi, uint32_t *flags) {
+    if (!c) return TC_ERR_INVAL;
+    TC_CUDA(cudaDeviceSynchronize());
+    if (f1) TC_CUDA(cudaMemcpy(f1, c->f1, c->r * sizeof(u64), cudaMemcpyDeviceToHost));
+    if (f2) TC_CUDA(cudaMemcpy(f2, c->f2, c->r * sizeof(u64), cudaMemcpyDeviceToHost));
+    if (chi) TC_CUDA(cudaMemcpy(chi, c->chi, c->r * sizeof(u64), cudaMemcpyDeviceToHost));
+    if (flags) TC_CUDA(cudaMemcpy(flags, c->flags, c->r * sizeof(u32), cudaMemcpyDeviceToHost));
+    return TC_OK;
+}
+
+int tc_profile_begin(tc_ctx *c) {
+    if (!c) return TC_ERR_INVAL;
+    TC_CUDA(cudaDeviceSynchronize());
+    while (c->pool.size() < kEventPool) {
+        cudaEvent_t ev;
+        TC_CUDA(cudaEventCreate(&ev));
+        c->pool.push_back(ev);
+    }
+    Control h{};
+    TC_CUDA(cudaMemcpy(&h, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost));
+    c->prof_skip0 = h.skipped_passes;
+    c->prof_skipbytes0 = h.skipped_bytes;
+    c->pool_used = 0;
+    c->stamps.clear();
+    c->prof = true;
+    c->prof_overflow = false;
+    c->prof_launch0 = c->launches;
+    c->prof_batches = c->prof_sort_launches = c->prof_sort_bytes = 0;
+    return TC_OK;
+}
+
+int tc_profile_end(tc_ctx *c, tc_profile_t *out) {
+    if (!c || !out) return TC_ERR_INVAL;
+    TC_CUDA(cudaDeviceSynchronize());
+    std::memset(out, 0, sizeof(*out));
+    double ms[kStages] = {0};
+    for (size_t k = 1; k < c->stamps.size(); ++k) {
+        const int stg = c->stamps[k].stage;
+        if (stg < 0) continue;
+        float t = 0.f;
+        TC_CUDA(cudaEventElapsedTime(&t, c->stamps[k - 1].ev, c->stamps[k].ev));
+        ms[stg] += t;
+    }
+    Control h{};
+    TC_CUDA(cudaMemcpy(&h, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost));
+    out->batches = c->prof_batches;
+    out->launches = c->launches - c->prof_launch0;
+    out->sort_pass_launches = c->prof_sort_launches;
+    out->sort_pass_skipped = h.skipped_passes - c->prof_skip0;
+    out->sort_pass_bytes = c->prof_sort_bytes - (h.skipped_bytes - c->prof_skipbytes0);
+    out->overflow = c->prof_overflow ? 1 : 0;
+    out->ms_prep = ms[kPrep];
+    out->ms_arc_sort = ms[kArcSort];
+    out->ms_edge_sort = ms[kEdgeSort];
+    out->ms_dups = ms[kDups];
+    out->ms_sweep = ms[kSweep];
+    out->ms_finish = ms[kFinish];
+    out->ms_estimate = ms[kEstimate];
+    c->prof = false;
+    c->stamps.clear();
+    c->pool_used = 0;
+    return TC_OK;
+}
+
+int tc_rank_all(const uint64_t *d_edges, uint64_t w, uint32_t vertex_bits, uint32_t *d_src,
+                uint32_t *d_dst, uint32_t *d_pos, uint32_t *d_rank, void *cuda_stream) {
+    if (w > kMaxBatch || vertex_bits < 1 || vertex_bits > 32) return TC_ERR_INVAL;
+    if (w == 0) return TC_OK;
+    if (!d_edges || !d_src || !d_dst || !d_pos || !d_rank) return TC_ERR_INVAL;
+    int rc = configure_kernels();
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const BatchShape s = make_shape(w, vertex_bits);
+    const u64 ta = tiles_of(2 * w);
+    const u64 zb = sizeof(SortPlan) * 2 + lookback_words(s, false) * sizeof(u32) + 16;
+    unsigned char *z = nullptr;
+    u64 *a0 = nullptr, *a1 = nullptr;
+    if (cudaMallocAsync(&z, zb, st) != cudaSuccess ||
+        cudaMallocAsync(&a0, 2 * w * sizeof(u64), st) != cudaSuccess ||
+        cudaMallocAsync(&a1, 2 * w * sizeof(u64), st) != cudaSuccess) {
+        cudaGetLastError();
+        if (z) cudaFreeAsync(z, st);
+        if (a0) cudaFreeAsync(a0, st);
+        cudaStreamSynchronize(st);
+        return TC_ERR_NOMEM;
+    }
+    SortPlan *plans = reinterpret_cast<SortPlan *>(z);
+    u32 *lb = reinterpret_cast<u32 *>(z + 2 * sizeof(SortPlan));
+    u32 *err = reinterpret_cast<u32 *>(z + zb - 16);
+    cudaMemsetAsync(z, 0, zb, st);
+    const u64 prep_blocks = std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
+    prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, 0, st>>>(d_edges, s, a0, nullptr, nullptr,
+                                                                 plans, err, 0);
+    sort_plan_kernel<<<1, kSortThreads, 0, st>>>(plans, s.npa, (u32)(2 * w), 0, 0);
+    for (int p = 0; p < s.npa; ++p)
+        onesweep_pass_kernel<false><<<(unsigned)ta, kSortThreads, onesweep_smem(false), st>>>(
+            a0, a1, nullptr, nullptr, (u32)(2 * w), s.sha + p * kRadixBits, p, &plans[0],
+            lb + (u64)p * ta * kRadix, err, nullptr);
+    const u64 rb = (2 * w + kRankTile - 1) / kRankTile;
+    rank_out_kernel<<<(unsigned)rb, kRankThreads, 0, st>>>(d_edges, a0, a1, &plans[0], s, d_src,
+                                                           d_dst, d_pos, d_rank);
+    u32 h_err = 0;
+    cudaError_t e1 = cudaGetLastError();
+    cudaError_t e2 = cudaMemcpyAsync(&h_err, err, sizeof(u32), cudaMemcpyDeviceToHost, st);
+    cudaFreeAsync(a1, st);
+    cudaFreeAsync(a0, st);
+    cudaFreeAsync(z, st);
+    cudaError_t e3 = cudaStreamSynchronize(st);
+    if (e1 || e2 || e3) {
+        last_cuda_error() = e1 ? e1 : (e2 ? e2 : e3);
+        return TC_ERR_CUDA;
+    }
+    return map_device_error(h_err & kErrTimeout);
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+// Shared device helpers for the streaming triangle-count kernels.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "tc.h"
+
+namespace tc {
+
+using u32 = uint32_t;
+using u64 = uint64_t;
+
+constexpr u64 kEmpty = TC_EMPTY_EDGE;
+constexpr u32 kMask32 = 0xFFFFFFFFu;
+
+// Device-side error bits (the first nonzero code wins, see set_error).
+enum : u32 {
+    kErrNone = 0,
+    kErrInput = 1,    // batch breaks the stream model
+    kErrTimeout = 2,  // a bounded spin wait gave up
+};
+
+// Per-context control block in device memory.  `err` is cleared at the start
+// of every batch; `sticky` keeps the first error of any batch until the host
+// reads it.
+struct Control {
+    u64 m;        // |E|: edges folded in so far
+    u64 batches;  // batch counter b (part of the Philox counter)
+    u32 err;      // error of the batch in flight
+    u32 sticky;   // first error since the host last looked
+    u64 skipped_passes;  // sort digit passes that found a single digit value
+    u64 skipped_bytes;   // their algorithmic bytes (not moved)
+};
+
+__device__ __forceinline__ void set_error(u32 *err, u32 code) {
+    atomicCAS(err, 0u, code);
+}
+
+// Relaxed loads/stores at GPU scope: bypass L1 so that flags written by other
+// CTAs of the same kernel become visible.
+__device__ __forceinline__ u32 ld_relaxed(const u32 *p) {
+    u32 v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(u32 *p, u32 v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// First index i in [0, n) with a[i] >= key (n if none).  The loop count
+// depends only on n, so a warp's lanes stay converged.
+__device__ __forceinline__ u64 lower_bound_u64(const u64 *__restrict__ a, u64 n, u64 key) {
+    const u64 *base = a;
+    u64 len = n;
+    while (len > 1) {
+        u64 half = len >> 1;
+        base = (__ldg(base + half - 1) < key) ? base + half : base;
+        len -= half;
+    }
+    return (u64)(base - a) + ((len == 1 && __ldg(base) < key) ? 1 : 0);
+}
+
+// Same, restricted to [lo, hi).
+__device__ __forceinline__ u64 lower_bound_range(const u64 *__restrict__ a, u64 lo, u64 hi,
+                                                 u64 key) {
+    return lo + lower_bound_u64(a + lo, hi - lo, key);
+}
+
+__host__ __device__ __forceinline__ u32 bits_for(u64 x) {
+    // number of bits needed to hold values 0..x (at least 1)
+    u32 b = 1;
+    while (b < 64 && (x >> b) != 0) ++b;
+    return b;
+}
+
+}  // namespace tc

@@ -1,0 +1,401 @@
+// Kernels of one batch update (bulkUpdateAll, Sec. 4 of Tangwongsan, Pavan,
+// Tirthapura, "Parallel Triangle Counting in Massive Streaming Graphs").
+//
+// Data layout in HBM (per stream context):
+//   estimator state, structure of arrays over i = 0..r-1:
+//     f1[i], f2[i]  uint64 packed edges (min << 32) | max, kEmpty if empty
+//     chi[i]        uint64 |Gamma(f1)|
+//     flags[i]      uint32, bit 0 = closed (f3 present)
+//   per-batch scratch:
+//     arcs[2][2w]   uint64 arc keys  src << (bw+1) | (w-1-pos) << 1 | side
+//                   (side 0: src is the smaller endpoint).  Written in
+//                   decreasing pos order and sorted stably on the src bits
+//                   only, which yields Lemma 4.3's order (src asc, pos desc)
+//                   and makes the arc's rank its offset in the src segment.
+//     ekeys[2][w]   uint64 Step-3 keys, sorted on (src, dst):
+//                   keys-only form  u << (B+bw) | v << bw | pos  when
+//                   2B + bw <= 64, else  u << B | v  with evals[2][w] = pos.
+//   bw = bits of w-1, B = vertex id bits.
+#pragma once
+
+#include "tc_common.cuh"
+#include "tc_onesweep.cuh"
+#include "tc_philox.cuh"
+
+namespace tc {
+
+// Host-computed shape of one batch.
+struct BatchShape {
+    u32 w;          // batch size
+    u32 bw;         // bits of w-1
+    u32 B;          // vertex id bits
+    u32 sha;        // arc key: src shift = bw + 1
+    u32 she;        // edge key: sort bits start (bw keys-only, 0 with values)
+    u32 ekeys_only; // 1: pos packed in the edge key
+    int npa;        // arc sort passes
+    int npe;        // edge sort passes
+};
+
+// ---------------------------------------------------------------------------
+// Key build + all digit histograms (one pass over the batch).
+// Validates the stream model (Sec. 2): u < v and v < 2^B.
+// ---------------------------------------------------------------------------
+constexpr int kPrepThreads = 256;
+
+__global__ void __launch_bounds__(kPrepThreads) prep_kernel(
+    const u64 *__restrict__ W, BatchShape s, u64 *__restrict__ arcs0, u64 *__restrict__ ekeys0,
+    u32 *__restrict__ evals0, SortPlan *plans, u32 *err, int build_edges) {
+    __shared__ u32 h[2 * kMaxPasses][kRadix];
+    for (int k = threadIdx.x; k < 2 * kMaxPasses * kRadix; k += kPrepThreads) (&h[0][0])[k] = 0;
+    __syncthreads();
+    const u64 id_lim = (s.B >= 32) ? (1ull << 32) : (1ull << s.B);
+    const u32 wm1 = s.w - 1;
+    bool bad = false;
+    for (u64 j = (u64)blockIdx.x * kPrepThreads + threadIdx.x; j < s.w;
+         j += (u64)gridDim.x * kPrepThreads) {
+        const u64 e = W[j];
+        const u64 u = e >> 32, v = e & kMask32;
+        bad |= !(u < v) || v >= id_lim;
+        const u64 rpos = (u64)(wm1 - (u32)j) << 1;
+        const u64 au = (u << s.sha) | rpos;
+        const u64 av = (v << s.sha) | rpos | 1ull;
+        reinterpret_cast<ulonglong2 *>(arcs0)[wm1 - (u32)j] = make_ulonglong2(au, av);
+        for (int p = 0; p < s.npa; ++p) {
+            atomicAdd(&h[p][digit_of(au, s.sha + p * kRadixBits)], 1u);
+            atomicAdd(&h[p][digit_of(av, s.sha + p * kRadixBits)], 1u);
+        }
+        if (build_edges) {
+            u64 ek;
+            if (s.ekeys_only) {
+                ek = (u << (s.B + s.bw)) | (v << s.bw) | j;
+            } else {
+                ek = (u << s.B) | v;
+                evals0[j] = (u32)j;
+            }
+            ekeys0[j] = ek;
+            for (int p = 0; p < s.npe; ++p)
+                atomicAdd(&h[kMaxPasses + p][digit_of(ek, s.she + p * kRadixBits)], 1u);
+        }
+    }
+    if (bad) set_error(err, kErrInput);
+    __syncthreads();
+    for (int k = threadIdx.x; k < kRadix; k += kPrepThreads) {
+        for (int p = 0; p < s.npa; ++p)
+            if (h[p][k]) atomicAdd(&plans[0].counts[p][k], h[p][k]);
+        if (build_edges)
+            for (int p = 0; p < s.npe; ++p)
+                if (h[kMaxPasses + p][k]) atomicAdd(&plans[1].counts[p][k], h[kMaxPasses + p][k]);
+    }
+}
+
+// In-batch repeats are adjacent after the Step-3 sort.
+__global__ void dups_kernel(const u64 *ekeys0, const u64 *ekeys1, const SortPlan *plans,
+                            BatchShape s, u32 *err) {
+    const u64 *E = plans[1].sel[kMaxPasses] ? ekeys1 : ekeys0;
+    const u32 drop = s.ekeys_only ? s.bw : 0;
+    for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x + 1; k < s.w;
+         k += (u64)gridDim.x * blockDim.x) {
+        if ((E[k] >> drop) == (E[k - 1] >> drop)) {
+            set_error(err, kErrInput);
+            return;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused Steps 1-3 per estimator.
+// ---------------------------------------------------------------------------
+struct SweepArgs {
+    const u64 *W;
+    u64 *f1, *f2, *chi;
+    u32 *flags;
+    u64 r;
+    const u64 *arcs0, *arcs1;
+    const u64 *ekeys0, *ekeys1;
+    const u32 *evals0, *evals1;
+    const SortPlan *plans;
+    Control *ctl;
+    BatchShape s;
+    uint2 key;
+    u32 stream;
+};
+
+// Segment [start, end) of src x in the sorted arcs.
+__device__ __forceinline__ void arc_segment(const u64 *arcs, u64 n, u32 sha, u64 x, u64 &start,
+                                            u64 &end) {
+    start = lower_bound_u64(arcs, n, x << sha);
+    const u64 next = (x + 1) << sha;
+    end = (next == 0) ? n : lower_bound_range(arcs, start, n, next);
+}
+
+constexpr int kSweepThreads = 256;
+
+__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(SweepArgs a) {
+    if (ld_relaxed(&a.ctl->err)) return;  // rejected batch: state stays as it was
+    const u64 i = (u64)blockIdx.x * kSweepThreads + threadIdx.x;
+    if (i >= a.r) return;
+    const BatchShape s = a.s;
+    const u64 m = a.ctl->m;
+    const DrawKey dk{a.key, (u32)a.ctl->batches, a.stream};
+    const u64 *__restrict__ arcs = a.plans[0].sel[kMaxPasses] ? a.arcs1 : a.arcs0;
+    const bool e_sel = a.plans[1].sel[kMaxPasses] != 0;
+    const u64 *__restrict__ E = e_sel ? a.ekeys1 : a.ekeys0;
+    const u32 *__restrict__ EV = e_sel ? a.evals1 : a.evals0;
+    const u64 n_arcs = 2ull * s.w;
+    const u32 wm1 = s.w - 1;
+    const u64 wmask = (1ull << s.bw) - 1;
+
+    u64 f1 = a.f1[i], f2 = a.f2[i], chi = a.chi[i];
+    u32 fl = a.flags[i];
+
+    // ---- Step 1 (Sec. 4.2): level-1 reservoir over E u W
+    const u64 x = draw_bounded(dk, (u32)i, kStep1, m + s.w);
+    const bool new1 = x >= m;
+    u32 p1 = 0;
+    if (new1) {
+        p1 = (u32)(x - m);
+        f1 = __ldg(a.W + p1);
+        chi = 0;
+        f2 = kEmpty;
+        fl = 0;
+    }
+
+    // ---- Step 2 (Sec. 4.3): chi+ = rank(u->v) + rank(v->u), coin, rank-select
+    const u64 u = f1 >> 32, v = f1 & kMask32;
+    u64 su, eu, sv, ev;
+    arc_segment(arcs, n_arcs, s.sha, u, su, eu);
+    arc_segment(arcs, n_arcs, s.sha, v, sv, ev);
+    u64 ld, rd;
+    if (new1) {
+        // rank of the arc (x, p1): its offset inside the src segment
+        const u64 rp = (u64)(wm1 - p1) << 1;
+        ld = lower_bound_range(arcs, su, eu, (u << s.sha) | rp) - su;
+        rd = lower_bound_range(arcs, sv, ev, (v << s.sha) | rp) - sv;
+    } else {
+        ld = eu - su;  // deg_W(u): Def. 4.2 for a pair outside W
+        rd = ev - sv;
+    }
+    const u64 chi_plus = ld + rd;
+    bool new2 = false;
+    u32 p2 = 0;
+    if (chi_plus > 0) {
+        const u64 y = draw_bounded(dk, (u32)i, kStep2, chi + chi_plus);
+        if (y >= chi) {
+            const u64 phi = y - chi;
+            const u64 k = (phi < ld) ? su + phi : sv + (phi - ld);
+            const u64 akey = __ldg(arcs + k);
+            p2 = wm1 - (u32)((akey >> 1) & wmask);
+            f2 = __ldg(a.W + p2);
+            fl &= ~TC_FLAG_CLOSED;
+            new2 = true;
+        }
+    }
+    chi += chi_plus;
+
+    // ---- Step 3 (Sec. 4.4): closing edge after f2
+    if (f2 != kEmpty && !(fl & TC_FLAG_CLOSED)) {
+        const u64 a1 = f1 >> 32, b1 = f1 & kMask32, a2 = f2 >> 32, b2 = f2 & kMask32;
+        const u64 x1 = (a1 == a2 || a1 == b2) ? b1 : a1;
+        const u64 x2 = (a2 == a1 || a2 == b1) ? b2 : a2;
+        const u64 gu = x1 < x2 ? x1 : x2, gv = x1 < x2 ? x2 : x1;
+        bool found;
+        u32 q;
+        if (s.ekeys_only) {
+            const u64 probe = (gu << (s.B + s.bw)) | (gv << s.bw);
+            const u64 k = lower_bound_u64(E, s.w, probe);
+            const u64 ek = k < s.w ? __ldg(E + k) : ~0ull;
+            found = k < s.w && (ek >> s.bw) == (probe >> s.bw);
+            q = (u32)(ek & wmask);
+        } else {
+            const u64 probe = (gu << s.B) | gv;
+            const u64 k = lower_bound_u64(E, s.w, probe);
+            found = k < s.w && __ldg(E + k) == probe;
+            q = found ? __ldg(EV + k) : 0u;
+        }
+        if (found && (!new2 || q > p2)) fl |= TC_FLAG_CLOSED;
+    }
+
+    a.f1[i] = f1;
+    a.f2[i] = f2;
+    a.chi[i] = chi;
+    a.flags[i] = fl;
+}
+
+// Close the batch: count it if accepted, record the error otherwise.
+struct Mailbox {
+    u32 err;      // first device-side error since the host last cleared it
+    u32 pad;
+    u64 m;
+    u64 batches;
+};
+
+__global__ void finish_kernel(Control *ctl, Mailbox *mbox, u64 w) {
+    const u32 e = ctl->err;
+    if (e) {
+        if (!ctl->sticky) ctl->sticky = e;
+    } else {
+        ctl->m += w;
+        ctl->batches += 1;
+    }
+    ctl->err = 0;
+    mbox->err = ctl->sticky;
+    mbox->m = ctl->m;
+    mbox->batches = ctl->batches;
+}
+
+// ---------------------------------------------------------------------------
+// Estimate (Lemma 3.1): S = sum of chi over closed estimators, in 128 bits.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void add_u128(u64 *dst_lo_hi, u64 lo, u64 hi) {
+    const u64 old = atomicAdd((unsigned long long *)dst_lo_hi, (unsigned long long)lo);
+    const u64 carry = (old + lo < old) ? 1ull : 0ull;
+    if (hi + carry) atomicAdd((unsigned long long *)(dst_lo_hi + 1), (unsigned long long)(hi + carry));
+}
+
+// Sum a per-thread (lo, hi) pair over the CTA; result valid in thread 0.
+__device__ __forceinline__ void block_sum_u128(u64 &lo, u64 &hi, u64 *s_lo, u64 *s_hi) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const u64 l2 = __shfl_down_sync(0xFFFFFFFFu, lo, o);
+        const u64 h2 = __shfl_down_sync(0xFFFFFFFFu, hi, o);
+        const u64 s = lo + l2;
+        hi += h2 + (s < lo ? 1 : 0);
+        lo = s;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_lo[warp] = lo;
+        s_hi[warp] = hi;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        lo = 0;
+        hi = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            const u64 s = lo + s_lo[k];
+            hi += s_hi[k] + (s < lo ? 1 : 0);
+            lo = s;
+        }
+    }
+}
+
+constexpr int kReduceThreads = 256;
+
+// out[0..1] = S (lo, hi), out[2] = closed count (out[0..2] zeroed before).
+// out[3] = |E| (read from the control block).
+__global__ void __launch_bounds__(kReduceThreads) estimate_kernel(const u64 *chi, const u32 *flags,
+                                                                  u64 r, const Control *ctl,
+                                                                  u64 *out) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[3] = ctl->m;
+    __shared__ u64 s_lo[kReduceThreads / 32], s_hi[kReduceThreads / 32];
+    u64 lo = 0, hi = 0, nc = 0;
+    for (u64 i = (u64)blockIdx.x * kReduceThreads + threadIdx.x; i < r;
+         i += (u64)gridDim.x * kReduceThreads) {
+        if (flags[i] & TC_FLAG_CLOSED) {
+            const u64 c = chi[i];
+            const u64 s = lo + c;
+            hi += (s < lo) ? 1 : 0;
+            lo = s;
+            ++nc;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) nc += __shfl_down_sync(0xFFFFFFFFu, nc, o);
+    __shared__ u64 s_nc[kReduceThreads / 32];
+    if ((threadIdx.x & 31) == 0) s_nc[threadIdx.x >> 5] = nc;
+    block_sum_u128(lo, hi, s_lo, s_hi);
+    if (threadIdx.x == 0) {
+        u64 t = 0;
+        for (int k = 0; k < kReduceThreads / 32; ++k) t += s_nc[k];
+        add_u128(out, lo, hi);
+        if (t) atomicAdd((unsigned long long *)(out + 2), (unsigned long long)t);
+    }
+}
+
+// Median-of-means groups: CTA k sums group k = [k*r/g, (k+1)*r/g) into
+// out[2k], out[2k+1] (128-bit).
+__global__ void __launch_bounds__(kReduceThreads) group_sum_kernel(const u64 *chi, const u32 *flags,
+                                                                   u64 r, u32 g, u64 *out) {
+    __shared__ u64 s_lo[kReduceThreads / 32], s_hi[kReduceThreads / 32];
+    const u64 k = blockIdx.x;
+    const u64 lo_i = (u64)(((unsigned __int128)k * r) / g);
+    const u64 hi_i = (u64)(((unsigned __int128)(k + 1) * r) / g);
+    u64 lo = 0, hi = 0;
+    for (u64 i = lo_i + threadIdx.x; i < hi_i; i += kReduceThreads) {
+        if (flags[i] & TC_FLAG_CLOSED) {
+            const u64 s = lo + chi[i];
+            hi += (s < lo) ? 1 : 0;
+            lo = s;
+        }
+    }
+    block_sum_u128(lo, hi, s_lo, s_hi);
+    if (threadIdx.x == 0) {
+        out[2 * k] = lo;
+        out[2 * k + 1] = hi;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// rankAll output (Lemma 4.3, Fig. 2): (src, dst, pos, rank) per sorted arc.
+// rank = index - start of the src segment: a scan with resets (App. B) done
+// as a CTA-wide running maximum of segment-head indices, seeded by one
+// binary search for the segment that the tile starts in.
+// ---------------------------------------------------------------------------
+constexpr int kRankThreads = 256;
+constexpr int kRankItems = 4;
+constexpr int kRankTile = kRankThreads * kRankItems;
+
+__global__ void __launch_bounds__(kRankThreads) rank_out_kernel(
+    const u64 *W, const u64 *arcs0, const u64 *arcs1, const SortPlan *plan, BatchShape s,
+    u32 *src_out, u32 *dst_out, u32 *pos_out, u32 *rank_out) {
+    __shared__ u64 s_seed;
+    __shared__ u64 s_wmax[kRankThreads / 32];
+    const u64 *arcs = plan->sel[kMaxPasses] ? arcs1 : arcs0;
+    const u64 n = 2ull * s.w;
+    const u64 t0 = (u64)blockIdx.x * kRankTile;
+    const u32 wm1 = s.w - 1;
+    const u64 wmask = (1ull << s.bw) - 1;
+    if (threadIdx.x == 0) s_seed = lower_bound_u64(arcs, n, (arcs[t0] >> s.sha) << s.sha);
+    __syncthreads();
+    const u64 k0 = t0 + (u64)threadIdx.x * kRankItems;
+    u64 heads[kRankItems];
+    u64 run = s_seed;
+#pragma unroll
+    for (int j = 0; j < kRankItems; ++j) {
+        const u64 k = k0 + j;
+        heads[j] = 0;
+        if (k < n) {
+            const bool head = (k == 0) || ((arcs[k] >> s.sha) != (arcs[k - 1] >> s.sha));
+            if (head) heads[j] = k;
+        }
+        run = max(run, heads[j]);
+    }
+    // exclusive running max over threads
+    u64 inc = run;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        const u64 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        if (lane >= o) inc = max(inc, t);
+    }
+    if (lane == 31) s_wmax[warp] = inc;
+    __syncthreads();
+    u64 excl = s_seed;
+    for (int w2 = 0; w2 < warp; ++w2) excl = max(excl, s_wmax[w2]);
+    const u64 prev_lane = __shfl_up_sync(0xFFFFFFFFu, inc, 1);
+    if (lane > 0) excl = max(excl, prev_lane);
+    u64 seg = excl;
+#pragma unroll
+    for (int j = 0; j < kRankItems; ++j) {
+        const u64 k = k0 + j;
+        if (k >= n) break;
+        seg = max(seg, heads[j]);
+        const u64 key = arcs[k];
+        u32 pos = wm1 - (u32)((key >> 1) & wmask);
+        if (pos > wm1) pos = wm1;  // only keys left by a timed-out sort can get here
+        const u64 e = W[pos];
+        src_out[k] = (u32)(key >> s.sha);
+        dst_out[k] = (key & 1) ? (u32)(e >> 32) : (u32)(e & kMask32);
+        pos_out[k] = pos;
+        rank_out[k] = (u32)(k - seg);
+    }
+}
+
+}  // namespace tc
