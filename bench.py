@@ -222,7 +222,11 @@ def run_gpu(args, rank, world, local_rank):
     dev_batches = [torch.from_numpy(b.view(np.int64)).cuda() for b in host_batches]
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
+    from paper_1308_2166_gb300 import autotune
+    tuning, tune_table = autotune.tune(dev_batches, r, cfg["vertex_bits"], seed=cfg["seed"] + 99,
+                                       reps=1, stream=sh)
     ctx = tc.tc_create_ex(r, cfg["seed"], rank, w, cfg["vertex_bits"])
+    tc.tc_tune(ctx, *tuning)
     est_words = torch.zeros(4, dtype=torch.int64, device="cuda")
     nb = len(dev_batches)
 
@@ -343,6 +347,10 @@ def run_gpu(args, rank, world, local_rank):
         "config": {
             "workload": f"{args.workload}: {cfg['graph']}, m={cfg['m']}, r={r}, w={w}",
             "r": r, "w": w, "m": cfg["m"], "vertex_bits": B, "parallelism": f"replicas{world}",
+            "sort_tuning": {"arc_digit_bits": tuning[0], "edge_digit_bits": tuning[1],
+                            "ranking": autotune.RANKINGS[tuning[2]],
+                            "table_ms": {f"{a}/{b}/{autotune.RANKINGS[c]}": round(v, 4)
+                                         for (a, b, c), v in sorted(tune_table.items())}},
             "l2": "working set per step (batch 32 MB, arcs 2x64 MB, edge keys 2x32 MB, state "
                   "28 MB) exceeds the 126 MB L2; each step reads a batch untouched for the "
                   "previous 3 steps",

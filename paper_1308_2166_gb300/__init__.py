@@ -27,8 +27,8 @@ TC_FLAG_CLOSED = 1
 EXPORTS = (
     "tc_create", "tc_create_ex", "tc_process_batch", "tc_process_batch_async",
     "tc_sync", "tc_estimate", "tc_estimate_async", "tc_estimate_mom", "tc_get_state",
-    "tc_get_counters", "tc_profile_begin", "tc_profile_end", "tc_destroy", "tc_strerror",
-    "tc_rank_all",
+    "tc_get_counters", "tc_profile_begin", "tc_profile_end", "tc_tune", "tc_destroy",
+    "tc_strerror", "tc_rank_all",
 )
 
 
@@ -79,6 +79,7 @@ def load(path: str | None = None):
         "tc_estimate_async": (I, [P, P, P]),
         "tc_profile_begin": (I, [P]),
         "tc_profile_end": (I, [P, ctypes.POINTER(tc_profile_t)]),
+        "tc_tune": (I, [P, U32, U32, U32]),
         "tc_estimate_mom": (I, [P, U32, ctypes.POINTER(U64), ctypes.POINTER(U64),
                                 ctypes.POINTER(U64), ctypes.POINTER(ctypes.c_double)]),
         "tc_get_state": (I, [P, P, P, P, P]),
@@ -180,6 +181,10 @@ def tc_profile_end(ctx: int) -> dict:
     out = tc_profile_t()
     _check(load().tc_profile_end(ctx, ctypes.byref(out)), "tc_profile_end")
     return {name: getattr(out, name) for name, _ in tc_profile_t._fields_}
+
+
+def tc_tune(ctx: int, arc_digit_bits: int = 0, edge_digit_bits: int = 0, ranking: int = 0) -> None:
+    _check(load().tc_tune(ctx, arc_digit_bits, edge_digit_bits, ranking), "tc_tune")
 
 
 def tc_estimate_mom(ctx: int, g: int) -> dict:

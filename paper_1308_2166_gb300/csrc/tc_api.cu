@@ -35,35 +35,83 @@ constexpr size_t kEventPool = 8192;
 enum Stage { kStart = -1, kPrep = 0, kArcSort, kEdgeSort, kDups, kSweep, kFinish, kEstimate,
              kStages };
 
-size_t onesweep_smem(bool values) {
-    return values ? sizeof(OnesweepSmem<true>) : sizeof(OnesweepSmem<false>);
+using PassFn = void (*)(u64 *, u64 *, u32 *, u32 *, u32, u32, int, SortPlan *, u32 *, u32 *,
+                        Control *);
+
+template <int kBits, bool kValues, bool kMatch>
+void pass_variant(PassFn &fn, size_t &smem) {
+    fn = onesweep_pass_kernel<kBits, kValues, kMatch>;
+    smem = sizeof(OnesweepSmem<kBits, kValues>);
 }
+
+// The onesweep instantiation for a digit width, value payload and ranking.
+void select_pass(u32 bits, bool values, bool match, PassFn &fn, size_t &smem) {
+#define TC_PASS_CASE(B)                                                     \
+    case B:                                                                 \
+        if (values) {                                                       \
+            if (match) pass_variant<B, true, true>(fn, smem);               \
+            else pass_variant<B, true, false>(fn, smem);                    \
+        } else {                                                            \
+            if (match) pass_variant<B, false, true>(fn, smem);              \
+            else pass_variant<B, false, false>(fn, smem);                   \
+        }                                                                   \
+        return;
+    switch (bits) {
+        TC_PASS_CASE(8)
+        TC_PASS_CASE(10)
+        default:
+        TC_PASS_CASE(11)
+    }
+#undef TC_PASS_CASE
+}
+
+constexpr u32 kDigitChoices[3] = {8, 10, 11};
 
 int configure_kernels() {
     static bool done[64] = {false};
     int dev = 0;
     TC_CUDA(cudaGetDevice(&dev));
     if (dev < 64 && done[dev]) return TC_OK;
-    TC_CUDA(cudaFuncSetAttribute(onesweep_pass_kernel<false>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)onesweep_smem(false)));
-    TC_CUDA(cudaFuncSetAttribute(onesweep_pass_kernel<true>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)onesweep_smem(true)));
+    for (u32 bits : kDigitChoices)
+        for (int v = 0; v < 2; ++v)
+            for (int mt = 0; mt < 2; ++mt) {
+                PassFn fn;
+                size_t smem;
+                select_pass(bits, v, mt, fn, smem);
+                TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+            }
+    TC_CUDA(cudaFuncSetAttribute(prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
     if (dev < 64) done[dev] = true;
     return TC_OK;
 }
 
-BatchShape make_shape(u64 w, u32 B) {
+// Digit width and pass count for `live` key bits: fewest passes with digits
+// of at most 11 bits, then the narrowest compiled width giving that count
+// (or the width forced by tc_tune).
+u32 pick_digits(u32 live, u32 forced, int &passes) {
+    if (forced) {
+        passes = (int)((live + forced - 1) / forced);
+        return forced;
+    }
+    passes = (int)((live + 10) / 11);
+    if (passes < 1) passes = 1;
+    for (u32 b : kDigitChoices)
+        if (b * (u32)passes >= live) return b;
+    return 11;
+}
+
+BatchShape make_shape(u64 w, u32 B, u32 force_a = 0, u32 force_e = 0) {
     BatchShape s{};
     s.w = (u32)w;
     s.bw = bits_for(w - 1);
     s.B = B;
     s.sha = s.bw + 1;
-    s.npa = (int)((B + kRadixBits - 1) / kRadixBits);
     s.ekeys_only = (2 * B + s.bw <= 64) ? 1u : 0u;
     s.she = s.ekeys_only ? s.bw : 0u;
-    s.npe = (int)((2 * B + kRadixBits - 1) / kRadixBits);
+    s.bits_a = pick_digits(B, force_a, s.npa);
+    s.bits_e = pick_digits(2 * B, force_e, s.npe);
     return s;
 }
 
@@ -71,9 +119,21 @@ u64 tiles_of(u64 n) { return (n + kSortTile - 1) / kSortTile; }
 
 // Words of look-back status for one batch of w edges.
 u64 lookback_words(const BatchShape &s, bool edges) {
-    u64 words = (u64)s.npa * tiles_of(2ull * s.w) * kRadix;
-    if (edges) words += (u64)s.npe * tiles_of(s.w) * kRadix;
+    u64 words = ((u64)s.npa * tiles_of(2ull * s.w)) << s.bits_a;
+    if (edges) words += ((u64)s.npe * tiles_of(s.w)) << s.bits_e;
     return words;
+}
+
+// Largest look-back need over every digit width a context may use.
+u64 lookback_words_max(u64 w, u32 B) {
+    u64 best = 0;
+    for (u32 ba : kDigitChoices)
+        for (u32 be : kDigitChoices) best = std::max(best, lookback_words(make_shape(w, B, ba, be), true));
+    return std::max(best, lookback_words(make_shape(w, B), true));
+}
+
+size_t prep_smem(const BatchShape &s, bool edges) {
+    return (((size_t)s.npa << s.bits_a) + (edges ? ((size_t)s.npe << s.bits_e) : 0)) * sizeof(u32);
 }
 
 }  // namespace
@@ -83,6 +143,8 @@ struct tc_ctx {
     u64 r = 0, seed = 0;
     u32 stream_id = 0, vertex_bits = 32;
     u64 cap_w = 0;  // scratch capacity in edges
+    u32 force_bits_a = 0, force_bits_e = 0;  // tc_tune digit widths (0 = automatic)
+    bool match_rank = true;                  // tc_tune ranking (match.any vs ballots)
     cudaStream_t own = nullptr;
     // estimator state (structure of arrays)
     u64 *f1 = nullptr, *f2 = nullptr, *chi = nullptr;
@@ -95,6 +157,8 @@ struct tc_ctx {
     u64 *staging = nullptr;
     unsigned char *zeroed = nullptr;  // SortPlan[2] followed by look-back words
     u64 *red = nullptr;               // reduction output (device, 4 words)
+    DirEntry *adir = nullptr;         // per-vertex directories (ids < 2^kDirMaxBits)
+    DirEntry *edir = nullptr;
     // host side
     Mailbox *mbox = nullptr;  // mapped pinned, written by finish_kernel
     Mailbox *mbox_dev = nullptr;
@@ -144,8 +208,7 @@ static int ensure_scratch(tc_ctx *c, u64 w) {
     if (w <= c->cap_w) return TC_OK;
     TC_CUDA(cudaDeviceSynchronize());
     free_scratch(c);
-    const BatchShape s = make_shape(w, c->vertex_bits);
-    const u64 zb = 2 * sizeof(SortPlan) + lookback_words(s, true) * sizeof(u32);
+    const u64 zb = 2 * sizeof(SortPlan) + lookback_words_max(w, c->vertex_bits) * sizeof(u32);
     bool ok = true;
     for (int k = 0; k < 2 && ok; ++k) {
         ok &= cudaMalloc(&c->arcs[k], 2 * w * sizeof(u64)) == cudaSuccess;
@@ -171,7 +234,7 @@ static int map_device_error(u32 e) {
 
 // Enqueue one batch on `st`.  W is a device pointer; w in [1, cap_w].
 static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
-    const BatchShape s = make_shape(w, c->vertex_bits);
+    const BatchShape s = make_shape(w, c->vertex_bits, c->force_bits_a, c->force_bits_e);
     SortPlan *plans = reinterpret_cast<SortPlan *>(c->zeroed);
     u32 *lb = reinterpret_cast<u32 *>(c->zeroed + 2 * sizeof(SortPlan));
     const u64 used = 2 * sizeof(SortPlan) + lookback_words(s, true) * sizeof(u32);
@@ -179,33 +242,39 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
     TC_CUDA(cudaMemsetAsync(c->zeroed, 0, used, st));
 
     const u64 prep_blocks = std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
-    prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, 0, st>>>(W, s, c->arcs[0], c->ekeys[0],
-                                                                 c->evals[0], plans, &c->ctl->err, 1);
-    sort_plan_kernel<<<2, kSortThreads, 0, st>>>(plans, s.npa, (u32)(2 * w), s.npe, (u32)w);
+    prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, prep_smem(s, true), st>>>(
+        W, s, c->arcs[0], c->ekeys[0], c->evals[0], plans, &c->ctl->err, 1);
+    sort_plan_kernel<<<2, kSortThreads, 0, st>>>(plans, s.npa, (u32)(2 * w), s.bits_a, s.npe,
+                                                 (u32)w, s.bits_e);
     stamp(c, st, kPrep);
     const u64 ta = tiles_of(2 * w), te = tiles_of(w);
-    for (int p = 0; p < s.npa; ++p) {
-        onesweep_pass_kernel<false><<<(unsigned)ta, kSortThreads, onesweep_smem(false), st>>>(
-            c->arcs[0], c->arcs[1], nullptr, nullptr, (u32)(2 * w), s.sha + p * kRadixBits, p,
-            &plans[0], lb + (u64)p * ta * kRadix, &c->ctl->err, c->ctl);
-    }
+    PassFn fa, fe;
+    size_t sma, sme;
+    select_pass(s.bits_a, false, c->match_rank, fa, sma);
+    select_pass(s.bits_e, !s.ekeys_only, c->match_rank, fe, sme);
+    for (int p = 0; p < s.npa; ++p)
+        fa<<<(unsigned)ta, kSortThreads, sma, st>>>(c->arcs[0], c->arcs[1], nullptr, nullptr,
+                                                    (u32)(2 * w), s.sha + p * s.bits_a, p,
+                                                    &plans[0], lb + ((u64)p * ta << s.bits_a),
+                                                    &c->ctl->err, c->ctl);
     stamp(c, st, kArcSort);
-    u32 *lbe = lb + (u64)s.npa * ta * kRadix;
-    for (int p = 0; p < s.npe; ++p) {
-        u32 *lbp = lbe + (u64)p * te * kRadix;
-        if (s.ekeys_only)
-            onesweep_pass_kernel<false><<<(unsigned)te, kSortThreads, onesweep_smem(false), st>>>(
-                c->ekeys[0], c->ekeys[1], nullptr, nullptr, (u32)w, s.she + p * kRadixBits, p,
-                &plans[1], lbp, &c->ctl->err, c->ctl);
-        else
-            onesweep_pass_kernel<true><<<(unsigned)te, kSortThreads, onesweep_smem(true), st>>>(
-                c->ekeys[0], c->ekeys[1], c->evals[0], c->evals[1], (u32)w,
-                s.she + p * kRadixBits, p, &plans[1], lbp, &c->ctl->err, c->ctl);
-    }
+    u32 *lbe = lb + ((u64)s.npa * ta << s.bits_a);
+    for (int p = 0; p < s.npe; ++p)
+        fe<<<(unsigned)te, kSortThreads, sme, st>>>(c->ekeys[0], c->ekeys[1], c->evals[0],
+                                                    c->evals[1], (u32)w, s.she + p * s.bits_e, p,
+                                                    &plans[1], lbe + ((u64)p * te << s.bits_e),
+                                                    &c->ctl->err, c->ctl);
     stamp(c, st, kEdgeSort);
-    const u64 dup_blocks = std::min<u64>((w + 255) / 256, 1216);
-    dups_kernel<<<(unsigned)dup_blocks, 256, 0, st>>>(c->ekeys[0], c->ekeys[1], plans, s,
-                                                      &c->ctl->err);
+    if (c->adir) {
+        const u64 idx_blocks = std::min<u64>((3 * w + 255) / 256, 152 * 16);
+        index_kernel<<<(unsigned)idx_blocks, 256, 0, st>>>(c->arcs[0], c->arcs[1], c->ekeys[0],
+                                                           c->ekeys[1], plans, s, c->adir,
+                                                           c->edir, c->ctl, &c->ctl->err);
+    } else {
+        const u64 dup_blocks = std::min<u64>((w + 255) / 256, 1216);
+        dups_kernel<<<(unsigned)dup_blocks, 256, 0, st>>>(c->ekeys[0], c->ekeys[1], plans, s,
+                                                          &c->ctl->err);
+    }
     stamp(c, st, kDups);
     SweepArgs a{};
     a.W = W;
@@ -221,12 +290,17 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
     a.evals0 = c->evals[0];
     a.evals1 = c->evals[1];
     a.plans = plans;
+    a.adir = c->adir;
+    a.edir = c->edir;
     a.ctl = c->ctl;
     a.s = s;
     a.key = make_uint2((u32)(c->seed & 0xFFFFFFFFu), (u32)(c->seed >> 32));
     a.stream = c->stream_id;
     const u64 sweep_blocks = (c->r + kSweepThreads - 1) / kSweepThreads;
-    sweep_kernel<<<(unsigned)sweep_blocks, kSweepThreads, 0, st>>>(a);
+    if (c->adir)
+        sweep_kernel<true><<<(unsigned)sweep_blocks, kSweepThreads, 0, st>>>(a);
+    else
+        sweep_kernel<false><<<(unsigned)sweep_blocks, kSweepThreads, 0, st>>>(a);
     stamp(c, st, kSweep);
     finish_kernel<<<1, 1, 0, st>>>(c->ctl, c->mbox_dev, w);
     stamp(c, st, kFinish);
@@ -300,6 +374,13 @@ int tc_create_ex(uint64_t r, uint64_t seed, uint32_t stream_id, uint64_t w_max,
     ok &= ok && cudaMalloc(&c->flags, r * sizeof(u32)) == cudaSuccess;
     ok &= ok && cudaMalloc(&c->ctl, sizeof(Control)) == cudaSuccess;
     ok &= ok && cudaMalloc(&c->red, 4 * sizeof(u64)) == cudaSuccess;
+    const u64 nverts = 1ull << vertex_bits;
+    if (ok && vertex_bits <= kDirMaxBits) {
+        ok &= cudaMalloc(&c->adir, nverts * sizeof(DirEntry)) == cudaSuccess;
+        ok &= ok && cudaMalloc(&c->edir, nverts * sizeof(DirEntry)) == cudaSuccess;
+        ok &= ok && cudaMemsetAsync(c->adir, 0, nverts * sizeof(DirEntry), c->own) == cudaSuccess;
+        ok &= ok && cudaMemsetAsync(c->edir, 0, nverts * sizeof(DirEntry), c->own) == cudaSuccess;
+    }
     ok &= ok && cudaHostAlloc(&c->mbox, sizeof(Mailbox), cudaHostAllocMapped) == cudaSuccess;
     ok &= ok && cudaHostGetDevicePointer((void **)&c->mbox_dev, c->mbox, 0) == cudaSuccess;
     ok &= ok && cudaHostAlloc(&c->h_red, 4 * sizeof(u64), cudaHostAllocDefault) == cudaSuccess;
@@ -342,6 +423,8 @@ void tc_destroy(tc_ctx *c) {
     cudaFree(c->flags);
     cudaFree(c->ctl);
     cudaFree(c->red);
+    cudaFree(c->adir);
+    cudaFree(c->edir);
     if (c->mbox) cudaFreeHost(c->mbox);
     if (c->h_red) cudaFreeHost(c->h_red);
     for (cudaEvent_t ev : c->pool) cudaEventDestroy(ev);
@@ -469,6 +552,16 @@ int tc_get_state(tc_ctx *c, uint64_t *f1, uint64_t *f2, uint64_t *chi, uint32_t 
     return TC_OK;
 }
 
+int tc_tune(tc_ctx *c, uint32_t arc_digit_bits, uint32_t edge_digit_bits, uint32_t ranking) {
+    auto ok_bits = [](uint32_t b) { return b == 0 || b == 8 || b == 10 || b == 11; };
+    if (!c || !ok_bits(arc_digit_bits) || !ok_bits(edge_digit_bits) || ranking > 2)
+        return TC_ERR_INVAL;
+    c->force_bits_a = arc_digit_bits;
+    c->force_bits_e = edge_digit_bits;
+    c->match_rank = ranking != 2;
+    return TC_OK;
+}
+
 int tc_profile_begin(tc_ctx *c) {
     if (!c) return TC_ERR_INVAL;
     TC_CUDA(cudaDeviceSynchronize());
@@ -533,6 +626,9 @@ int tc_rank_all(const uint64_t *d_edges, uint64_t w, uint32_t vertex_bits, uint3
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const BatchShape s = make_shape(w, vertex_bits);
     const u64 ta = tiles_of(2 * w);
+    PassFn fa;
+    size_t sma;
+    select_pass(s.bits_a, false, true, fa, sma);
     const u64 zb = sizeof(SortPlan) * 2 + lookback_words(s, false) * sizeof(u32) + 16;
     unsigned char *z = nullptr;
     u64 *a0 = nullptr, *a1 = nullptr;
@@ -550,13 +646,13 @@ int tc_rank_all(const uint64_t *d_edges, uint64_t w, uint32_t vertex_bits, uint3
     u32 *err = reinterpret_cast<u32 *>(z + zb - 16);
     cudaMemsetAsync(z, 0, zb, st);
     const u64 prep_blocks = std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
-    prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, 0, st>>>(d_edges, s, a0, nullptr, nullptr,
-                                                                 plans, err, 0);
-    sort_plan_kernel<<<1, kSortThreads, 0, st>>>(plans, s.npa, (u32)(2 * w), 0, 0);
+    prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, prep_smem(s, false), st>>>(
+        d_edges, s, a0, nullptr, nullptr, plans, err, 0);
+    sort_plan_kernel<<<1, kSortThreads, 0, st>>>(plans, s.npa, (u32)(2 * w), s.bits_a, 0, 0, 8);
     for (int p = 0; p < s.npa; ++p)
-        onesweep_pass_kernel<false><<<(unsigned)ta, kSortThreads, onesweep_smem(false), st>>>(
-            a0, a1, nullptr, nullptr, (u32)(2 * w), s.sha + p * kRadixBits, p, &plans[0],
-            lb + (u64)p * ta * kRadix, err, nullptr);
+        fa<<<(unsigned)ta, kSortThreads, sma, st>>>(a0, a1, nullptr, nullptr, (u32)(2 * w),
+                                                    s.sha + p * s.bits_a, p, &plans[0],
+                                                    lb + ((u64)p * ta << s.bits_a), err, nullptr);
     const u64 rb = (2 * w + kRankTile - 1) / kRankTile;
     rank_out_kernel<<<(unsigned)rb, kRankThreads, 0, st>>>(d_edges, a0, a1, &plans[0], s, d_src,
                                                            d_dst, d_pos, d_rank);

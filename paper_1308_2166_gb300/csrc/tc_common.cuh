@@ -31,6 +31,18 @@ struct Control {
     u32 sticky;   // first error since the host last looked
     u64 skipped_passes;  // sort digit passes that found a single digit value
     u64 skipped_bytes;   // their algorithmic bytes (not moved)
+    u32 epoch;           // batches enqueued (accepted or not); tags directory entries
+    u32 pad;
+};
+
+// Per-vertex segment directory entry: the run [start, end) of vertex x in a
+// sorted array, valid only when `epoch` equals the batch's epoch (entries of
+// earlier batches are stale without being cleared).
+struct __align__(16) DirEntry {
+    u32 epoch;
+    u32 start;
+    u32 end;
+    u32 pad;
 };
 
 __device__ __forceinline__ void set_error(u32 *err, u32 code) {

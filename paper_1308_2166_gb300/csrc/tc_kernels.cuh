@@ -34,19 +34,28 @@ struct BatchShape {
     u32 ekeys_only; // 1: pos packed in the edge key
     int npa;        // arc sort passes
     int npe;        // edge sort passes
+    u32 bits_a;     // arc sort digit width
+    u32 bits_e;     // edge sort digit width
 };
 
 // ---------------------------------------------------------------------------
 // Key build + all digit histograms (one pass over the batch).
 // Validates the stream model (Sec. 2): u < v and v < 2^B.
+// Dynamic shared memory: npa << bits_a arc counters, then npe << bits_e edge
+// counters.
 // ---------------------------------------------------------------------------
 constexpr int kPrepThreads = 256;
 
 __global__ void __launch_bounds__(kPrepThreads) prep_kernel(
     const u64 *__restrict__ W, BatchShape s, u64 *__restrict__ arcs0, u64 *__restrict__ ekeys0,
     u32 *__restrict__ evals0, SortPlan *plans, u32 *err, int build_edges) {
-    __shared__ u32 h[2 * kMaxPasses][kRadix];
-    for (int k = threadIdx.x; k < 2 * kMaxPasses * kRadix; k += kPrepThreads) (&h[0][0])[k] = 0;
+    extern __shared__ u32 h[];
+    const u32 ra = 1u << s.bits_a, re = 1u << s.bits_e;
+    const u32 ma = ra - 1, me = re - 1;
+    const u32 na = (u32)s.npa * ra;
+    const u32 nh = na + (build_edges ? (u32)s.npe * re : 0u);
+    u32 *he = h + na;
+    for (u32 k = threadIdx.x; k < nh; k += kPrepThreads) h[k] = 0;
     __syncthreads();
     const u64 id_lim = (s.B >= 32) ? (1ull << 32) : (1ull << s.B);
     const u32 wm1 = s.w - 1;
@@ -61,8 +70,8 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(
         const u64 av = (v << s.sha) | rpos | 1ull;
         reinterpret_cast<ulonglong2 *>(arcs0)[wm1 - (u32)j] = make_ulonglong2(au, av);
         for (int p = 0; p < s.npa; ++p) {
-            atomicAdd(&h[p][digit_of(au, s.sha + p * kRadixBits)], 1u);
-            atomicAdd(&h[p][digit_of(av, s.sha + p * kRadixBits)], 1u);
+            atomicAdd(&h[p * ra + digit_bits(au, s.sha + p * s.bits_a, ma)], 1u);
+            atomicAdd(&h[p * ra + digit_bits(av, s.sha + p * s.bits_a, ma)], 1u);
         }
         if (build_edges) {
             u64 ek;
@@ -74,17 +83,16 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(
             }
             ekeys0[j] = ek;
             for (int p = 0; p < s.npe; ++p)
-                atomicAdd(&h[kMaxPasses + p][digit_of(ek, s.she + p * kRadixBits)], 1u);
+                atomicAdd(&he[p * re + digit_bits(ek, s.she + p * s.bits_e, me)], 1u);
         }
     }
     if (bad) set_error(err, kErrInput);
     __syncthreads();
-    for (int k = threadIdx.x; k < kRadix; k += kPrepThreads) {
-        for (int p = 0; p < s.npa; ++p)
-            if (h[p][k]) atomicAdd(&plans[0].counts[p][k], h[p][k]);
-        if (build_edges)
-            for (int p = 0; p < s.npe; ++p)
-                if (h[kMaxPasses + p][k]) atomicAdd(&plans[1].counts[p][k], h[kMaxPasses + p][k]);
+    for (u32 k = threadIdx.x; k < nh; k += kPrepThreads) {
+        const u32 c = h[k];
+        if (!c) continue;
+        if (k < na) atomicAdd(&plans[0].counts[k / ra][k % ra], c);
+        else atomicAdd(&plans[1].counts[(k - na) / re][(k - na) % re], c);
     }
 }
 
@@ -114,13 +122,16 @@ struct SweepArgs {
     const u64 *ekeys0, *ekeys1;
     const u32 *evals0, *evals1;
     const SortPlan *plans;
+    const DirEntry *adir, *edir;  // null unless vertex ids < 2^kDirMaxBits
     Control *ctl;
     BatchShape s;
     uint2 key;
     u32 stream;
 };
 
-// Segment [start, end) of src x in the sorted arcs.
+constexpr u32 kDirMaxBits = 26;
+
+// Segment [start, end) of src x in the sorted arcs, by binary search.
 __device__ __forceinline__ void arc_segment(const u64 *arcs, u64 n, u32 sha, u64 x, u64 &start,
                                             u64 &end) {
     start = lower_bound_u64(arcs, n, x << sha);
@@ -128,14 +139,71 @@ __device__ __forceinline__ void arc_segment(const u64 *arcs, u64 n, u32 sha, u64
     end = (next == 0) ? n : lower_bound_range(arcs, start, n, next);
 }
 
+// Segment [start, end) of vertex x from a directory (empty if x is absent).
+__device__ __forceinline__ void dir_segment(const DirEntry *dir, u32 epoch, u64 x, u64 &start,
+                                            u64 &end) {
+    const uint4 e = __ldg(reinterpret_cast<const uint4 *>(dir + x));
+    const bool hit = e.x == epoch;
+    start = hit ? e.y : 0;
+    end = hit ? e.z : 0;
+}
+
+// ---------------------------------------------------------------------------
+// Directories over the two sorted arrays, plus the in-batch repeat check.
+// For the arcs, x = src; for the Step-3 keys, x = the smaller endpoint.  The
+// first element of a run writes (epoch, start), the last one writes end.
+// ---------------------------------------------------------------------------
+__global__ void index_kernel(const u64 *arcs0, const u64 *arcs1, const u64 *ekeys0,
+                             const u64 *ekeys1, const SortPlan *plans, BatchShape s,
+                             DirEntry *adir, DirEntry *edir, const Control *ctl, u32 *err) {
+    const u64 *__restrict__ arcs = plans[0].sel[kMaxPasses] ? arcs1 : arcs0;
+    const u64 *__restrict__ E = plans[1].sel[kMaxPasses] ? ekeys1 : ekeys0;
+    const u32 epoch = ctl->epoch + 1;
+    const u64 n_a = 2ull * s.w, n_e = s.w;
+    const u64 nverts = 1ull << s.B;
+    const u32 esh = s.ekeys_only ? s.B + s.bw : s.B;  // edge key -> smaller endpoint
+    const u32 drop = s.ekeys_only ? s.bw : 0;          // edge key -> (u, v)
+    bool dup = false;
+    for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x; k < n_a + n_e;
+         k += (u64)gridDim.x * blockDim.x) {
+        if (k < n_a) {
+            const u64 x = __ldg(arcs + k) >> s.sha;
+            const u64 prev = k ? __ldg(arcs + k - 1) >> s.sha : ~0ull;
+            const u64 next = k + 1 < n_a ? __ldg(arcs + k + 1) >> s.sha : ~0ull;
+            if (x >= nverts) continue;  // invalid batch (already flagged by the key build)
+            if (x != prev)
+                *reinterpret_cast<u64 *>(&adir[x].epoch) = ((u64)k << 32) | epoch;
+            if (x != next) adir[x].end = (u32)(k + 1);
+        } else {
+            const u64 j = k - n_a;
+            const u64 ek = __ldg(E + j);
+            const u64 x = ek >> esh;
+            const u64 pk = j ? __ldg(E + j - 1) : ~0ull;
+            const u64 prev = j ? pk >> esh : ~0ull;
+            const u64 next = j + 1 < n_e ? __ldg(E + j + 1) >> esh : ~0ull;
+            dup |= j && (ek >> drop) == (pk >> drop);
+            if (x >= nverts) continue;
+            if (x != prev)
+                *reinterpret_cast<u64 *>(&edir[x].epoch) = ((u64)j << 32) | epoch;
+            if (x != next) edir[x].end = (u32)(j + 1);
+        }
+    }
+    if (dup) set_error(err, kErrInput);
+}
+
 constexpr int kSweepThreads = 256;
 
+// Fused Steps 1-3 for one estimator per thread.  kDir: segment lookups from
+// the directories (vertex ids < 2^26), else binary search on the sorted
+// arrays.
+template <bool kDir>
 __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(SweepArgs a) {
     if (ld_relaxed(&a.ctl->err)) return;  // rejected batch: state stays as it was
     const u64 i = (u64)blockIdx.x * kSweepThreads + threadIdx.x;
     if (i >= a.r) return;
     const BatchShape s = a.s;
     const u64 m = a.ctl->m;
+    const u32 epoch = a.ctl->epoch + 1;
     const DrawKey dk{a.key, (u32)a.ctl->batches, a.stream};
     const u64 *__restrict__ arcs = a.plans[0].sel[kMaxPasses] ? a.arcs1 : a.arcs0;
     const bool e_sel = a.plans[1].sel[kMaxPasses] != 0;
@@ -163,8 +231,13 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(SweepArgs a) {
     // ---- Step 2 (Sec. 4.3): chi+ = rank(u->v) + rank(v->u), coin, rank-select
     const u64 u = f1 >> 32, v = f1 & kMask32;
     u64 su, eu, sv, ev;
-    arc_segment(arcs, n_arcs, s.sha, u, su, eu);
-    arc_segment(arcs, n_arcs, s.sha, v, sv, ev);
+    if constexpr (kDir) {
+        dir_segment(a.adir, epoch, u, su, eu);
+        dir_segment(a.adir, epoch, v, sv, ev);
+    } else {
+        arc_segment(arcs, n_arcs, s.sha, u, su, eu);
+        arc_segment(arcs, n_arcs, s.sha, v, sv, ev);
+    }
     u64 ld, rd;
     if (new1) {
         // rank of the arc (x, p1): its offset inside the src segment
@@ -198,18 +271,20 @@ __global__ void __launch_bounds__(kSweepThreads) sweep_kernel(SweepArgs a) {
         const u64 x1 = (a1 == a2 || a1 == b2) ? b1 : a1;
         const u64 x2 = (a2 == a1 || a2 == b1) ? b2 : a2;
         const u64 gu = x1 < x2 ? x1 : x2, gv = x1 < x2 ? x2 : x1;
+        u64 lo = 0, hi = s.w;
+        if constexpr (kDir) dir_segment(a.edir, epoch, gu, lo, hi);
         bool found;
         u32 q;
         if (s.ekeys_only) {
             const u64 probe = (gu << (s.B + s.bw)) | (gv << s.bw);
-            const u64 k = lower_bound_u64(E, s.w, probe);
-            const u64 ek = k < s.w ? __ldg(E + k) : ~0ull;
-            found = k < s.w && (ek >> s.bw) == (probe >> s.bw);
+            const u64 k = lower_bound_range(E, lo, hi, probe);
+            const u64 ek = k < hi ? __ldg(E + k) : ~0ull;
+            found = k < hi && (ek >> s.bw) == (probe >> s.bw);
             q = (u32)(ek & wmask);
         } else {
             const u64 probe = (gu << s.B) | gv;
-            const u64 k = lower_bound_u64(E, s.w, probe);
-            found = k < s.w && __ldg(E + k) == probe;
+            const u64 k = lower_bound_range(E, lo, hi, probe);
+            found = k < hi && __ldg(E + k) == probe;
             q = found ? __ldg(EV + k) : 0u;
         }
         if (found && (!new2 || q > p2)) fl |= TC_FLAG_CLOSED;
@@ -237,6 +312,7 @@ __global__ void finish_kernel(Control *ctl, Mailbox *mbox, u64 w) {
         ctl->m += w;
         ctl->batches += 1;
     }
+    ctl->epoch += 1;
     ctl->err = 0;
     mbox->err = ctl->sticky;
     mbox->m = ctl->m;

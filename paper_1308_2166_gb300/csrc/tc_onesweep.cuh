@@ -9,16 +9,18 @@
 //     that builds the keys (no separate upsweep per digit);
 //   * one kernel per digit: each CTA takes the next tile id from an atomic
 //     counter (so it only ever waits on tiles that already run), ranks its
-//     keys per warp with 8 ballots per key (peers with equal digits), adds
-//     the warp histograms up, publishes its per-digit tile count and walks
-//     back over earlier tiles' published counts / inclusive prefixes
-//     (decoupled look-back) to find where its keys go;
+//     keys per warp -- peers with equal digits found by warp votes, either
+//     one ballot per digit bit or one match.any -- adds the warp histograms
+//     up, publishes its per-digit tile counts and walks back over earlier
+//     tiles' published counts / inclusive prefixes (decoupled look-back);
 //   * keys are re-ordered by digit in shared memory first so that the scatter
 //     to global memory writes runs of consecutive addresses;
 //   * a pass whose digit is the same for every key is an identity
 //     permutation and is skipped (decided on the device from the
 //     histogram); ping-pong buffer selection follows on the device, so the
 //     host never needs the histogram.
+// Digit width (8, 10 or 11 bits) is a template parameter; the host picks the
+// width that needs the fewest passes over the live key bits.
 // Look-back waits are bounded: after kSpinLimit polls the CTA records
 // kErrTimeout and proceeds (the batch is then rejected, never hung).
 #pragma once
@@ -27,90 +29,99 @@
 
 namespace tc {
 
-constexpr int kRadixBits = 8;
-constexpr int kRadix = 1 << kRadixBits;
-constexpr int kSortThreads = 256;  // one thread per digit in the per-digit phases
+constexpr int kMaxRadixBits = 11;
+constexpr int kMaxRadix = 1 << kMaxRadixBits;
+constexpr int kMaxPasses = 8;
+constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 16;
 constexpr int kSortTile = kSortThreads * kSortItems;
-constexpr int kMaxPasses = 8;
 constexpr u32 kSpinLimit = 1u << 21;
 
-constexpr u32 kFlagAgg = 1u << 30;   // tile count published
-constexpr u32 kFlagPre = 2u << 30;   // inclusive prefix published
+constexpr u32 kFlagAgg = 1u << 30;  // tile count published
+constexpr u32 kFlagPre = 2u << 30;  // inclusive prefix published
 constexpr u32 kFlagMask = 3u << 30;
 constexpr u32 kValMask = (1u << 30) - 1;
 
-static_assert(kSortThreads == kRadix, "per-digit phases use one thread per digit");
-
-// Sort plan in device memory (one per sort and batch).
+// Sort plan in device memory (one per sort and batch; zeroed per batch).
 struct SortPlan {
-    u32 counts[kMaxPasses][kRadix];   // digit histograms (filled by the key build)
-    u32 offsets[kMaxPasses][kRadix];  // exclusive bucket offsets
-    u32 skip[kMaxPasses];             // 1 if every key has the same digit
-    u32 sel[kMaxPasses + 1];          // ping-pong buffer holding keys before pass p
+    u32 counts[kMaxPasses][kMaxRadix];   // digit histograms (filled by the key build)
+    u32 offsets[kMaxPasses][kMaxRadix];  // exclusive bucket offsets
+    u32 skip[kMaxPasses];                // 1 if every key has the same digit
+    u32 sel[kMaxPasses + 1];             // ping-pong buffer holding keys before pass p
     u32 tile_counter[kMaxPasses];
-    u32 pad[8];
+    u32 pad[7];
 };
 
-__device__ __forceinline__ u32 digit_of(u64 key, u32 shift) {
-    return (u32)(key >> shift) & (kRadix - 1);
+__device__ __forceinline__ u32 digit_bits(u64 key, u32 shift, u32 mask) {
+    return (u32)(key >> shift) & mask;
 }
 
-// Exclusive prefix over the kSortThreads values `x` of a CTA.  `s_tmp` must
-// hold kSortWarps words.  Must be called by all threads.
-__device__ __forceinline__ u32 block_exclusive_sum(u32 x, u32 *s_tmp, u32 *total) {
+// Exclusive prefix over the values `x` of the kThreads threads of a CTA.
+// `s_tmp` holds kThreads/32 words.  Must be called by all threads.
+template <int kThreads>
+__device__ __forceinline__ u32 block_exclusive_sum(u32 x, u32 *s_tmp) {
+    constexpr int kWarps = kThreads / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     u32 inc = x;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+        const u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
         if (lane >= o) inc += t;
     }
     if (lane == 31) s_tmp[warp] = inc;
     __syncthreads();
-    u32 before = 0, all = 0;
+    u32 before = 0;
 #pragma unroll
-    for (int w2 = 0; w2 < kSortWarps; ++w2) {
-        u32 s = s_tmp[w2];
-        if (w2 < warp) before += s;
-        all += s;
-    }
-    if (total) *total = all;
+    for (int w2 = 0; w2 < kWarps; ++w2)
+        if (w2 < warp) before += s_tmp[w2];
     __syncthreads();
     return before + inc - x;
 }
 
-// Turn the histograms of `npass` passes over `n` keys into bucket offsets,
-// skip flags and buffer selections.  One CTA of kSortThreads per plan.
+// Turn the histograms of `npass` passes over `n` keys (digit width `bits`)
+// into bucket offsets, skip flags and buffer selections.  One CTA of
+// kSortThreads per plan; blockIdx.x selects the plan.
 __global__ void __launch_bounds__(kSortThreads) sort_plan_kernel(SortPlan *plans, int npass0,
-                                                                  u32 n0, int npass1, u32 n1) {
+                                                                  u32 n0, u32 bits0, int npass1,
+                                                                  u32 n1, u32 bits1) {
     __shared__ u32 s_tmp[kSortWarps];
     SortPlan *plan = plans + blockIdx.x;
     const int npass = blockIdx.x == 0 ? npass0 : npass1;
     const u32 n = blockIdx.x == 0 ? n0 : n1;
-    const int d = threadIdx.x;
+    const u32 radix = 1u << (blockIdx.x == 0 ? bits0 : bits1);
+    const u32 per = (radix + kSortThreads - 1) / kSortThreads;  // digits per thread
+    const u32 d0 = threadIdx.x * per;
     for (int p = 0; p < npass; ++p) {
-        u32 c = plan->counts[p][d];
-        plan->offsets[p][d] = block_exclusive_sum(c, s_tmp, nullptr);
-        int single = __syncthreads_or(c == n);
-        if (d == 0) plan->skip[p] = single ? 1u : 0u;
+        u32 local = 0;
+        bool single = false;
+        for (u32 k = 0; k < per; ++k) {
+            const u32 c = d0 + k < radix ? plan->counts[p][d0 + k] : 0u;
+            local += c;
+            single |= (c == n);
+        }
+        u32 run = block_exclusive_sum<kSortThreads>(local, s_tmp);
+        for (u32 k = 0; k < per && d0 + k < radix; ++k) {
+            plan->offsets[p][d0 + k] = run;
+            run += plan->counts[p][d0 + k];
+        }
+        const int any_single = __syncthreads_or(single);
+        if (threadIdx.x == 0) plan->skip[p] = any_single ? 1u : 0u;
     }
     __syncthreads();
-    if (d == 0) {
+    if (threadIdx.x == 0) {
         u32 sel = 0;
         for (int p = 0; p < kMaxPasses; ++p) {
             plan->sel[p] = sel;
             if (p < npass && !plan->skip[p]) sel ^= 1u;
         }
-        plan->sel[kMaxPasses] = sel;
-        // passes beyond npass are never launched; make the final selection
-        // readable at a fixed index
+        plan->sel[kMaxPasses] = sel;  // where the sorted keys end up
     }
 }
 
-template <bool kHasValues>
+template <int kBits, bool kHasValues>
 struct OnesweepSmem {
+    static constexpr int kRadix = 1 << kBits;
     u32 warp_hist[kSortWarps][kRadix];
     u32 tile_excl[kRadix];
     u32 base[kRadix];
@@ -121,12 +132,16 @@ struct OnesweepSmem {
 };
 
 // One digit pass.  keys/vals ping-pong between buffers 0 and 1 as selected
-// by plan->sel[pass]; `lookback` holds this pass's [tiles][kRadix] status
-// words, zeroed before the pass.
-template <bool kHasValues>
-__global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
+// by plan->sel[pass]; `lookback` holds this pass's [tiles][2^kBits] status
+// words, zeroed before the pass.  kMatch: peers found with one match.any
+// per key; otherwise with one ballot per digit bit.
+template <int kBits, bool kHasValues, bool kMatch>
+__global__ void __launch_bounds__(kSortThreads, (kBits <= 10 ? 3 : 2)) onesweep_pass_kernel(
     u64 *keys0, u64 *keys1, u32 *vals0, u32 *vals1, u32 n, u32 shift, int pass,
     SortPlan *plan, u32 *lookback, u32 *err, Control *ctl) {
+    constexpr int kRadix = 1 << kBits;
+    constexpr u32 kMask = kRadix - 1;
+    constexpr int kDPT = (kRadix + kSortThreads - 1) / kSortThreads;  // digits per thread
     if (plan->skip[pass]) {
         if (blockIdx.x == 0 && threadIdx.x == 0 && ctl) {
             atomicAdd((unsigned long long *)&ctl->skipped_passes, 1ull);
@@ -136,7 +151,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
         return;
     }
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto &S = *reinterpret_cast<OnesweepSmem<kHasValues> *>(smem_raw);
+    auto &S = *reinterpret_cast<OnesweepSmem<kBits, kHasValues> *>(smem_raw);
 
     const u32 sel = plan->sel[pass];
     const u64 *__restrict__ kin = sel ? keys1 : keys0;
@@ -162,64 +177,107 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
         if constexpr (kHasValues) vals[j] = idx < n ? vin[idx] : 0u;
     }
 
-    // -- warp-ballot ranking: peers = lanes holding the same digit
+    // -- warp-level ranking: peers = lanes of this warp holding the same digit
     const u32 lt_mask = (1u << lane) - 1u;
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const bool valid = warp_base + (u64)j * 32 + lane < n;
-        const u32 d = digit_of(keys[j], shift);
-        u32 peers = __ballot_sync(0xFFFFFFFFu, valid);
+        const u32 d = digit_bits(keys[j], shift, kMask);
+        u32 peers;
+        if constexpr (kMatch) {
+            peers = __match_any_sync(0xFFFFFFFFu, valid ? d : (u32)kRadix + lane);
+        } else {
+            peers = __ballot_sync(0xFFFFFFFFu, valid);
 #pragma unroll
-        for (int b = 0; b < kRadixBits; ++b) {
-            const bool bit = (d >> b) & 1u;
-            const u32 vote = __ballot_sync(0xFFFFFFFFu, bit);
-            peers &= bit ? vote : ~vote;
+            for (int b = 0; b < kBits; ++b) {
+                const bool bit = (d >> b) & 1u;
+                const u32 vote = __ballot_sync(0xFFFFFFFFu, bit);
+                peers &= bit ? vote : ~vote;
+            }
         }
+        const int leader = 31 - __clz(peers);
         u32 before = 0;
-        if (valid) before = S.warp_hist[warp][d];
-        __syncwarp();
-        if (valid && lane == 31 - __clz(peers)) S.warp_hist[warp][d] = before + __popc(peers);
-        __syncwarp();
+        if (valid && lane == leader) {
+            before = S.warp_hist[warp][d];
+            S.warp_hist[warp][d] = before + __popc(peers);
+        }
+        before = __shfl_sync(0xFFFFFFFFu, before, leader);
         ranks[j] = before + __popc(peers & lt_mask);
+        __syncwarp();
     }
     __syncthreads();
 
-    // -- per digit: warp-exclusive offsets and the tile count
-    const int d = tid;
-    u32 count = 0;
+    // -- per digit: warp-exclusive offsets and the tile count; publish counts
+    static_assert(kRadix % kSortThreads == 0, "whole digits per thread");
+    u32 count[kDPT];
+    u32 local = 0;
 #pragma unroll
-    for (int w2 = 0; w2 < kSortWarps; ++w2) {
-        const u32 t = S.warp_hist[w2][d];
-        S.warp_hist[w2][d] = count;
-        count += t;
+    for (int q = 0; q < kDPT; ++q) {
+        const int d = tid * kDPT + q;
+        u32 c = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < kSortWarps; ++w2) {
+            const u32 t = S.warp_hist[w2][d];
+            S.warp_hist[w2][d] = c;
+            c += t;
+        }
+        st_relaxed(lookback + (u64)tile * kRadix + d, (tile == 0 ? kFlagPre : kFlagAgg) | c);
+        count[q] = c;
+        local += c;
     }
-    u32 *my_status = lookback + (u64)tile * kRadix + d;
-    st_relaxed(my_status, (tile == 0 ? kFlagPre : kFlagAgg) | count);
-    S.tile_excl[d] = block_exclusive_sum(count, S.scan_tmp, nullptr);
+    u32 run = block_exclusive_sum<kSortThreads>(local, S.scan_tmp);
 
-    // -- decoupled look-back over earlier tiles, one thread per digit
-    u32 excl = 0;
+    // -- decoupled look-back over earlier tiles; the thread's digits walk back
+    //    in lockstep so their status loads overlap
+    u32 excl[kDPT];
     if (tile > 0) {
-        long k = (long)tile - 1;
+        long k[kDPT];
+        u32 pending = 0;
+#pragma unroll
+        for (int q = 0; q < kDPT; ++q) {
+            excl[q] = 0;
+            k[q] = (long)tile - 1;
+            pending |= 1u << q;
+        }
         u32 spins = 0;
-        while (k >= 0) {
-            const u32 s = ld_relaxed(lookback + (u64)k * kRadix + d);
-            const u32 flag = s & kFlagMask;
-            if (flag == 0) {
+        while (pending) {
+            bool waited = false;
+#pragma unroll
+            for (int q = 0; q < kDPT; ++q) {
+                if (!(pending & (1u << q))) continue;
+                const u32 s = ld_relaxed(lookback + (u64)k[q] * kRadix + tid * kDPT + q);
+                const u32 flag = s & kFlagMask;
+                if (flag == 0) {
+                    waited = true;
+                    continue;
+                }
+                excl[q] += s & kValMask;
+                if (flag == kFlagPre) pending &= ~(1u << q);
+                else --k[q];  // tile 0 always publishes a prefix, so k stays >= 0
+            }
+            if (waited && pending) {
                 if (++spins > kSpinLimit) {
                     set_error(err, kErrTimeout);
                     break;
                 }
                 if (spins > 32) __nanosleep(64);
-                continue;
             }
-            excl += s & kValMask;
-            if (flag == kFlagPre) break;
-            --k;
         }
-        st_relaxed(my_status, kFlagPre | ((excl + count) & kValMask));
+#pragma unroll
+        for (int q = 0; q < kDPT; ++q)
+            st_relaxed(lookback + (u64)tile * kRadix + tid * kDPT + q,
+                       kFlagPre | ((excl[q] + count[q]) & kValMask));
+    } else {
+#pragma unroll
+        for (int q = 0; q < kDPT; ++q) excl[q] = 0;
     }
-    S.base[d] = plan->offsets[pass][d] + excl - S.tile_excl[d];
+#pragma unroll
+    for (int q = 0; q < kDPT; ++q) {
+        const int d = tid * kDPT + q;
+        S.tile_excl[d] = run;
+        S.base[d] = plan->offsets[pass][d] + excl[q] - run;
+        run += count[q];
+    }
     __syncthreads();
 
     // -- stage in shared memory in digit order
@@ -227,7 +285,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
     for (int j = 0; j < kSortItems; ++j) {
         const bool valid = warp_base + (u64)j * 32 + lane < n;
         if (valid) {
-            const u32 dj = digit_of(keys[j], shift);
+            const u32 dj = digit_bits(keys[j], shift, kMask);
             const u32 lp = S.tile_excl[dj] + S.warp_hist[warp][dj] + ranks[j];
             S.keys[lp] = keys[j];
             if constexpr (kHasValues) S.vals[lp] = vals[j];
@@ -241,7 +299,7 @@ __global__ void __launch_bounds__(kSortThreads) onesweep_pass_kernel(
     const u32 tile_n = left < (u64)kSortTile ? (u32)left : (u32)kSortTile;
     for (u32 i = tid; i < tile_n; i += kSortThreads) {
         const u64 key = S.keys[i];
-        const u32 pos = S.base[digit_of(key, shift)] + i;
+        const u32 pos = S.base[digit_bits(key, shift, kMask)] + i;
         if (pos < n) {  // only a timed-out look-back can make it larger
             kout[pos] = key;
             if constexpr (kHasValues) vout[pos] = S.vals[i];

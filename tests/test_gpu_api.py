@@ -124,7 +124,7 @@ def test_rank_all_worked_example_fig2():
     assert got == ex["rankall"]
 
 
-@pytest.mark.parametrize("w,vertex_bits", [(1, 4), (4095, 12), (50000, 12), (70001, 32)])
+@pytest.mark.parametrize("w,vertex_bits", [(1, 12), (2, 13), (4095, 12), (50000, 12), (70001, 32)])
 def test_rank_all_matches_oracle(w, vertex_bits):
     keys = synth.tiny_chung_lu(gen_seed=11) if w <= 32768 else \
         synth.finish(synth.chung_lu(1 << 12, 2.3, 40.0, w, seed=12), 1 << 12, seed=13)

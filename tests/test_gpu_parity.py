@@ -84,3 +84,25 @@ def test_rmat20_full_size():
     ws = [min(w, keys.size - i) for i in range(0, keys.size, w)]
     est = _run_pair(keys, 1 << 20, ws, seed=1, vertex_bits=20, check_every=False)
     assert est["m"] == keys.size
+
+
+@pytest.mark.parametrize("vertex_bits", [12, 20, 32])
+def test_every_sort_tuning_gives_identical_states(vertex_bits):
+    """Digit widths 8/10/11 and both warp rankings: same states as the oracle."""
+    from paper_1308_2166_gb300 import autotune
+    keys = synth.tiny_chung_lu(gen_seed=21)
+    r, w = 777, 5000
+    ref = nbsi_bulk.BulkStream(r, seed=3, vertex_bits=vertex_bits)
+    for W in synth.batches(keys, w):
+        ref.process_batch(W)
+    exp = ref.state_arrays()
+    dev = [to_device(W) for W in synth.batches(keys, w)]
+    for cand in autotune.candidates(vertex_bits) + [(0, 0, 0)]:
+        ctx = tc.tc_create_ex(r, 3, 0, w, vertex_bits)
+        try:
+            tc.tc_tune(ctx, *cand)
+            for d in dev:
+                tc.tc_process_batch(ctx, d)
+            assert_state_equal(tc.tc_get_state(ctx), exp, f"tuning {cand}")
+        finally:
+            tc.tc_destroy(ctx)
