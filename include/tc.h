@@ -164,9 +164,11 @@ int tc_profile_end(tc_ctx *c, tc_profile_t *out);
 
 /* Launch tuning of the two radix sorts (rankAll's arcs, Lemma 4.3; Step 3's
  * edges, Sec. 4.4).  arc_digit_bits / edge_digit_bits: 0 (automatic: the
- * fewest passes over the live key bits), 8, 10 or 11.  ranking: 0 or 1 =
- * one warp match.any per key, 2 = one warp ballot per digit bit.  Results
- * do not depend on the tuning.  Applies to batches enqueued afterwards.
+ * fewest passes over the live key bits), 8, 10 or 11.  ranking (how a warp
+ * finds the lanes holding equal digits): 1 = one match.any per key, 2 = one
+ * ballot per digit bit, 0 or 3 = lanes OR their bit into a shared-memory
+ * word per (warp, digit).  Results do not depend on the tuning.  Applies to
+ * batches enqueued afterwards.
  * Errors: TC_ERR_INVAL for other values. */
 int tc_tune(tc_ctx *c, uint32_t arc_digit_bits, uint32_t edge_digit_bits, uint32_t ranking);
 

@@ -15,7 +15,7 @@ from . import (tc_create_ex, tc_destroy, tc_process_batch_async, tc_profile_begi
                tc_profile_end, tc_sync, tc_tune)
 
 DIGITS = (8, 10, 11)
-RANKINGS = {1: "match", 2: "ballot"}
+RANKINGS = {1: "match", 2: "ballot", 3: "atomic-or"}
 
 
 def candidates(vertex_bits: int):

@@ -38,24 +38,36 @@ enum Stage { kStart = -1, kPrep = 0, kArcSort, kEdgeSort, kDups, kSweep, kFinish
 using PassFn = void (*)(u64 *, u64 *, u32 *, u32 *, u32, u32, int, SortPlan *, u32 *, u32 *,
                         Control *);
 
-template <int kBits, bool kValues, bool kMatch>
-void pass_variant(PassFn &fn, size_t &smem) {
-    fn = onesweep_pass_kernel<kBits, kValues, kMatch>;
-    smem = sizeof(OnesweepSmem<kBits, kValues>);
+struct PassKernel {
+    PassFn fn;
+    size_t smem;
+    int threads;
+};
+
+template <int kBits, bool kValues, int kRank>
+void pass_variant(PassKernel &k) {
+    k.fn = onesweep_pass_kernel<kBits, kValues, kRank>;
+    k.smem = sizeof(OnesweepSmem<kBits, kValues, kRank>);
+    k.threads = OnesweepShape<kBits>::kThreads;
 }
 
 // The onesweep instantiation for a digit width, value payload and ranking.
-void select_pass(u32 bits, bool values, bool match, PassFn &fn, size_t &smem) {
+// Atomic-or ranking keeps a mask word per (warp, digit) twice over, which
+// only fits shared memory for 8-bit digits; wider digits use match.any.
+PassKernel select_pass(u32 bits, bool values, int rank) {
+    PassKernel k{};
+#define TC_PASS_RANK(B, V)                                                  \
+    if (rank == kRankBallot) pass_variant<B, V, kRankBallot>(k);            \
+    else if (rank == kRankMatch || B > 8) pass_variant<B, V, kRankMatch>(k); \
+    else pass_variant<B, V, (B > 8 ? kRankMatch : kRankAtomicOr)>(k);
 #define TC_PASS_CASE(B)                                                     \
     case B:                                                                 \
         if (values) {                                                       \
-            if (match) pass_variant<B, true, true>(fn, smem);               \
-            else pass_variant<B, true, false>(fn, smem);                    \
+            TC_PASS_RANK(B, true)                                           \
         } else {                                                            \
-            if (match) pass_variant<B, false, true>(fn, smem);              \
-            else pass_variant<B, false, false>(fn, smem);                   \
+            TC_PASS_RANK(B, false)                                          \
         }                                                                   \
-        return;
+        return k;
     switch (bits) {
         TC_PASS_CASE(8)
         TC_PASS_CASE(10)
@@ -63,6 +75,7 @@ void select_pass(u32 bits, bool values, bool match, PassFn &fn, size_t &smem) {
         TC_PASS_CASE(11)
     }
 #undef TC_PASS_CASE
+#undef TC_PASS_RANK
 }
 
 constexpr u32 kDigitChoices[3] = {8, 10, 11};
@@ -74,12 +87,10 @@ int configure_kernels() {
     if (dev < 64 && done[dev]) return TC_OK;
     for (u32 bits : kDigitChoices)
         for (int v = 0; v < 2; ++v)
-            for (int mt = 0; mt < 2; ++mt) {
-                PassFn fn;
-                size_t smem;
-                select_pass(bits, v, mt, fn, smem);
-                TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem));
+            for (int mt = 0; mt < 3; ++mt) {
+                const PassKernel k = select_pass(bits, v, mt);
+                TC_CUDA(cudaFuncSetAttribute(k.fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)k.smem));
             }
     TC_CUDA(cudaFuncSetAttribute(prep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024));
@@ -117,10 +128,16 @@ BatchShape make_shape(u64 w, u32 B, u32 force_a = 0, u32 force_e = 0) {
 
 u64 tiles_of(u64 n) { return (n + kSortTile - 1) / kSortTile; }
 
+// Look-back words of one digit pass over n keys with `bits`-bit digits
+// (digit-major rows of lookback_stride(tiles) words).
+u64 pass_lookback_words(u64 n, u32 bits) {
+    return (u64)lookback_stride((u32)tiles_of(n)) << bits;
+}
+
 // Words of look-back status for one batch of w edges.
 u64 lookback_words(const BatchShape &s, bool edges) {
-    u64 words = ((u64)s.npa * tiles_of(2ull * s.w)) << s.bits_a;
-    if (edges) words += ((u64)s.npe * tiles_of(s.w)) << s.bits_e;
+    u64 words = (u64)s.npa * pass_lookback_words(2ull * s.w, s.bits_a);
+    if (edges) words += (u64)s.npe * pass_lookback_words(s.w, s.bits_e);
     return words;
 }
 
@@ -144,7 +161,7 @@ struct tc_ctx {
     u32 stream_id = 0, vertex_bits = 32;
     u64 cap_w = 0;  // scratch capacity in edges
     u32 force_bits_a = 0, force_bits_e = 0;  // tc_tune digit widths (0 = automatic)
-    bool match_rank = true;                  // tc_tune ranking (match.any vs ballots)
+    int rank_method = kRankAtomicOr;         // tc_tune warp ranking method
     cudaStream_t own = nullptr;
     // estimator state (structure of arrays)
     u64 *f1 = nullptr, *f2 = nullptr, *chi = nullptr;
@@ -244,26 +261,23 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
     const u64 prep_blocks = std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
     prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, prep_smem(s, true), st>>>(
         W, s, c->arcs[0], c->ekeys[0], c->evals[0], plans, &c->ctl->err, 1);
-    sort_plan_kernel<<<2, kSortThreads, 0, st>>>(plans, s.npa, (u32)(2 * w), s.bits_a, s.npe,
-                                                 (u32)w, s.bits_e);
+    sort_plan_kernel<<<2, 256, 0, st>>>(plans, s.npa, (u32)(2 * w), s.bits_a, s.npe, (u32)w,
+                                        s.bits_e);
     stamp(c, st, kPrep);
     const u64 ta = tiles_of(2 * w), te = tiles_of(w);
-    PassFn fa, fe;
-    size_t sma, sme;
-    select_pass(s.bits_a, false, c->match_rank, fa, sma);
-    select_pass(s.bits_e, !s.ekeys_only, c->match_rank, fe, sme);
+    const u64 la = pass_lookback_words(2 * w, s.bits_a), le = pass_lookback_words(w, s.bits_e);
+    const PassKernel ka = select_pass(s.bits_a, false, c->rank_method);
+    const PassKernel ke = select_pass(s.bits_e, !s.ekeys_only, c->rank_method);
     for (int p = 0; p < s.npa; ++p)
-        fa<<<(unsigned)ta, kSortThreads, sma, st>>>(c->arcs[0], c->arcs[1], nullptr, nullptr,
-                                                    (u32)(2 * w), s.sha + p * s.bits_a, p,
-                                                    &plans[0], lb + ((u64)p * ta << s.bits_a),
-                                                    &c->ctl->err, c->ctl);
+        ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(
+            c->arcs[0], c->arcs[1], nullptr, nullptr, (u32)(2 * w), s.sha + p * s.bits_a, p,
+            &plans[0], lb + (u64)p * la, &c->ctl->err, c->ctl);
     stamp(c, st, kArcSort);
-    u32 *lbe = lb + ((u64)s.npa * ta << s.bits_a);
+    u32 *lbe = lb + (u64)s.npa * la;
     for (int p = 0; p < s.npe; ++p)
-        fe<<<(unsigned)te, kSortThreads, sme, st>>>(c->ekeys[0], c->ekeys[1], c->evals[0],
-                                                    c->evals[1], (u32)w, s.she + p * s.bits_e, p,
-                                                    &plans[1], lbe + ((u64)p * te << s.bits_e),
-                                                    &c->ctl->err, c->ctl);
+        ke.fn<<<(unsigned)te, ke.threads, ke.smem, st>>>(
+            c->ekeys[0], c->ekeys[1], c->evals[0], c->evals[1], (u32)w, s.she + p * s.bits_e, p,
+            &plans[1], lbe + (u64)p * le, &c->ctl->err, c->ctl);
     stamp(c, st, kEdgeSort);
     if (c->adir) {
         const u64 idx_blocks = std::min<u64>((3 * w + 255) / 256, 152 * 16);
@@ -554,11 +568,11 @@ int tc_get_state(tc_ctx *c, uint64_t *f1, uint64_t *f2, uint64_t *chi, uint32_t 
 
 int tc_tune(tc_ctx *c, uint32_t arc_digit_bits, uint32_t edge_digit_bits, uint32_t ranking) {
     auto ok_bits = [](uint32_t b) { return b == 0 || b == 8 || b == 10 || b == 11; };
-    if (!c || !ok_bits(arc_digit_bits) || !ok_bits(edge_digit_bits) || ranking > 2)
+    if (!c || !ok_bits(arc_digit_bits) || !ok_bits(edge_digit_bits) || ranking > 3)
         return TC_ERR_INVAL;
     c->force_bits_a = arc_digit_bits;
     c->force_bits_e = edge_digit_bits;
-    c->match_rank = ranking != 2;
+    c->rank_method = ranking == 1 ? kRankMatch : ranking == 2 ? kRankBallot : kRankAtomicOr;
     return TC_OK;
 }
 
@@ -626,9 +640,8 @@ int tc_rank_all(const uint64_t *d_edges, uint64_t w, uint32_t vertex_bits, uint3
     cudaStream_t st = (cudaStream_t)cuda_stream;
     const BatchShape s = make_shape(w, vertex_bits);
     const u64 ta = tiles_of(2 * w);
-    PassFn fa;
-    size_t sma;
-    select_pass(s.bits_a, false, true, fa, sma);
+    const u64 la = pass_lookback_words(2 * w, s.bits_a);
+    const PassKernel ka = select_pass(s.bits_a, false, kRankBallot);
     const u64 zb = sizeof(SortPlan) * 2 + lookback_words(s, false) * sizeof(u32) + 16;
     unsigned char *z = nullptr;
     u64 *a0 = nullptr, *a1 = nullptr;
@@ -648,11 +661,11 @@ int tc_rank_all(const uint64_t *d_edges, uint64_t w, uint32_t vertex_bits, uint3
     const u64 prep_blocks = std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
     prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, prep_smem(s, false), st>>>(
         d_edges, s, a0, nullptr, nullptr, plans, err, 0);
-    sort_plan_kernel<<<1, kSortThreads, 0, st>>>(plans, s.npa, (u32)(2 * w), s.bits_a, 0, 0, 8);
+    sort_plan_kernel<<<1, 256, 0, st>>>(plans, s.npa, (u32)(2 * w), s.bits_a, 0, 0, 8);
     for (int p = 0; p < s.npa; ++p)
-        fa<<<(unsigned)ta, kSortThreads, sma, st>>>(a0, a1, nullptr, nullptr, (u32)(2 * w),
-                                                    s.sha + p * s.bits_a, p, &plans[0],
-                                                    lb + ((u64)p * ta << s.bits_a), err, nullptr);
+        ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(a0, a1, nullptr, nullptr, (u32)(2 * w),
+                                                         s.sha + p * s.bits_a, p, &plans[0],
+                                                         lb + (u64)p * la, err, nullptr);
     const u64 rb = (2 * w + kRankTile - 1) / kRankTile;
     rank_out_kernel<<<(unsigned)rb, kRankThreads, 0, st>>>(d_edges, a0, a1, &plans[0], s, d_src,
                                                            d_dst, d_pos, d_rank);

@@ -8,21 +8,26 @@
 //   * all digit histograms of a sort are counted up front, in the same pass
 //     that builds the keys (no separate upsweep per digit);
 //   * one kernel per digit: each CTA takes the next tile id from an atomic
-//     counter (so it only ever waits on tiles that already run), ranks its
-//     keys per warp -- peers with equal digits found by warp votes, either
-//     one ballot per digit bit or one match.any -- adds the warp histograms
-//     up, publishes its per-digit tile counts and walks back over earlier
-//     tiles' published counts / inclusive prefixes (decoupled look-back);
-//   * keys are re-ordered by digit in shared memory first so that the scatter
-//     to global memory writes runs of consecutive addresses;
+//     counter (so it only ever waits on tiles that already run), counts its
+//     digits and publishes the counts at once, ranks its keys stably inside
+//     each warp (peers with equal digits found by warp votes: one ballot per
+//     digit bit, one match.any, or lanes OR-ing their bit into a shared
+//     word) and writes them to a digit-ordered staging area;
+//   * then each thread walks back, for its digits, over earlier tiles'
+//     published counts / inclusive prefixes (decoupled look-back).  Status
+//     words are stored tile-major, so a warp's loads of one tile's statuses
+//     are coalesced; after the nearest predecessor, up to eight predecessors
+//     are loaded per round trip;
+//   * the staged keys are scattered in digit order, so each digit's keys go
+//     to consecutive global addresses;
 //   * a pass whose digit is the same for every key is an identity
 //     permutation and is skipped (decided on the device from the
 //     histogram); ping-pong buffer selection follows on the device, so the
 //     host never needs the histogram.
-// Digit width (8, 10 or 11 bits) is a template parameter; the host picks the
-// width that needs the fewest passes over the live key bits.
-// Look-back waits are bounded: after kSpinLimit polls the CTA records
-// kErrTimeout and proceeds (the batch is then rejected, never hung).
+// Digit width (8, 10 or 11 bits) is a template parameter.
+// Look-back waits are bounded: after kSpinLimit rounds without progress the
+// CTA records kErrTimeout and proceeds (the batch is then rejected, never
+// hung).
 #pragma once
 
 #include "tc_common.cuh"
@@ -32,10 +37,11 @@ namespace tc {
 constexpr int kMaxRadixBits = 11;
 constexpr int kMaxRadix = 1 << kMaxRadixBits;
 constexpr int kMaxPasses = 8;
-constexpr int kSortThreads = 256;
-constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kRankThreads8 = 256;  // ranking warps x 32
+constexpr int kSortWarps = kRankThreads8 / 32;
 constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;
+constexpr int kSortTile = kRankThreads8 * kSortItems;
+constexpr int kLookWin = 8;  // predecessors per look-back load group
 constexpr u32 kSpinLimit = 1u << 21;
 
 constexpr u32 kFlagAgg = 1u << 30;  // tile count published
@@ -53,12 +59,19 @@ struct SortPlan {
     u32 pad[7];
 };
 
+// Tiles whose look-back statuses one pass keeps (rounded up to whole
+// groups of kLookWin).
+__host__ __device__ __forceinline__ u32 lookback_stride(u32 tiles) {
+    return (tiles + kLookWin - 1) / kLookWin * kLookWin;
+}
+
 __device__ __forceinline__ u32 digit_bits(u64 key, u32 shift, u32 mask) {
     return (u32)(key >> shift) & mask;
 }
 
-// Exclusive prefix over the values `x` of the kThreads threads of a CTA.
-// `s_tmp` holds kThreads/32 words.  Must be called by all threads.
+// Exclusive prefix over the values `x` of threads [0, kThreads) of a CTA.
+// `s_tmp` holds kThreads/32 words.  Must be reached by every thread of the
+// CTA; threads at or beyond kThreads contribute nothing.
 template <int kThreads>
 __device__ __forceinline__ u32 block_exclusive_sum(u32 x, u32 *s_tmp) {
     constexpr int kWarps = kThreads / 32;
@@ -69,7 +82,7 @@ __device__ __forceinline__ u32 block_exclusive_sum(u32 x, u32 *s_tmp) {
         const u32 t = __shfl_up_sync(0xFFFFFFFFu, inc, o);
         if (lane >= o) inc += t;
     }
-    if (lane == 31) s_tmp[warp] = inc;
+    if (lane == 31 && warp < kWarps) s_tmp[warp] = inc;
     __syncthreads();
     u32 before = 0;
 #pragma unroll
@@ -80,17 +93,17 @@ __device__ __forceinline__ u32 block_exclusive_sum(u32 x, u32 *s_tmp) {
 }
 
 // Turn the histograms of `npass` passes over `n` keys (digit width `bits`)
-// into bucket offsets, skip flags and buffer selections.  One CTA of
-// kSortThreads per plan; blockIdx.x selects the plan.
-__global__ void __launch_bounds__(kSortThreads) sort_plan_kernel(SortPlan *plans, int npass0,
-                                                                  u32 n0, u32 bits0, int npass1,
-                                                                  u32 n1, u32 bits1) {
-    __shared__ u32 s_tmp[kSortWarps];
+// into bucket offsets, skip flags and buffer selections.  One CTA of 256
+// threads per plan; blockIdx.x selects the plan.
+__global__ void __launch_bounds__(256) sort_plan_kernel(SortPlan *plans, int npass0, u32 n0,
+                                                         u32 bits0, int npass1, u32 n1,
+                                                         u32 bits1) {
+    __shared__ u32 s_tmp[8];
     SortPlan *plan = plans + blockIdx.x;
     const int npass = blockIdx.x == 0 ? npass0 : npass1;
     const u32 n = blockIdx.x == 0 ? n0 : n1;
     const u32 radix = 1u << (blockIdx.x == 0 ? bits0 : bits1);
-    const u32 per = (radix + kSortThreads - 1) / kSortThreads;  // digits per thread
+    const u32 per = (radix + 255) / 256;  // digits per thread
     const u32 d0 = threadIdx.x * per;
     for (int p = 0; p < npass; ++p) {
         u32 local = 0;
@@ -100,7 +113,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_plan_kernel(SortPlan *plans
             local += c;
             single |= (c == n);
         }
-        u32 run = block_exclusive_sum<kSortThreads>(local, s_tmp);
+        u32 run = block_exclusive_sum<256>(local, s_tmp);
         for (u32 k = 0; k < per && d0 + k < radix; ++k) {
             plan->offsets[p][d0 + k] = run;
             run += plan->counts[p][d0 + k];
@@ -119,29 +132,50 @@ __global__ void __launch_bounds__(kSortThreads) sort_plan_kernel(SortPlan *plans
     }
 }
 
-template <int kBits, bool kHasValues>
+// Warp ranking methods: how a warp finds the lanes holding the same digit.
+enum RankMethod : int {
+    kRankBallot = 0,    // one ballot per digit bit
+    kRankMatch = 1,     // one match.any per key
+    kRankAtomicOr = 2,  // lanes OR their bit into a per-(warp, digit) word
+};
+
+// Launch shape of a digit pass: every thread ranks keys, then walks back for
+// its kDPT digits.
+template <int kBits>
+struct OnesweepShape {
+    static constexpr int kRadix = 1 << kBits;
+    static constexpr int kThreads = kRankThreads8;
+    static constexpr int kDPT = kRadix / kRankThreads8;  // digits per thread
+};
+
+template <int kBits, bool kHasValues, int kRank>
 struct OnesweepSmem {
     static constexpr int kRadix = 1 << kBits;
-    u32 warp_hist[kSortWarps][kRadix];
+    static constexpr int kPeerWords = kRank == kRankAtomicOr ? kRadix : 1;
+    u32 cursor[kSortWarps][kRadix];        // per-warp counts, then running local slots
+    u32 peers[2][kSortWarps][kPeerWords];  // atomic-or ranking masks (double-buffered)
     u32 tile_excl[kRadix];
+    u32 count[kRadix];
     u32 base[kRadix];
-    u32 scan_tmp[kSortWarps];
+    u32 scan_tmp[kSortWarps + 8];
     u32 tile;
     u64 keys[kSortTile];
     u32 vals[kHasValues ? kSortTile : 1];
 };
 
 // One digit pass.  keys/vals ping-pong between buffers 0 and 1 as selected
-// by plan->sel[pass]; `lookback` holds this pass's [tiles][2^kBits] status
-// words, zeroed before the pass.  kMatch: peers found with one match.any
-// per key; otherwise with one ballot per digit bit.
-template <int kBits, bool kHasValues, bool kMatch>
-__global__ void __launch_bounds__(kSortThreads, (kBits <= 10 ? 3 : 2)) onesweep_pass_kernel(
-    u64 *keys0, u64 *keys1, u32 *vals0, u32 *vals1, u32 n, u32 shift, int pass,
-    SortPlan *plan, u32 *lookback, u32 *err, Control *ctl) {
-    constexpr int kRadix = 1 << kBits;
+// by plan->sel[pass]; `lookback` holds this pass's status words, tile-major
+// ([tiles][2^kBits]), zeroed before the pass.
+template <int kBits, bool kHasValues, int kRank>
+__global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits <= 8 ? 4 : 3))
+    onesweep_pass_kernel(u64 *keys0, u64 *keys1, u32 *vals0, u32 *vals1, u32 n, u32 shift,
+                         int pass, SortPlan *plan, u32 *lookback, u32 *err, Control *ctl) {
+    using Shape = OnesweepShape<kBits>;
+    constexpr int kRadix = Shape::kRadix;
     constexpr u32 kMask = kRadix - 1;
-    constexpr int kDPT = (kRadix + kSortThreads - 1) / kSortThreads;  // digits per thread
+    constexpr int kDPT = Shape::kDPT;
+    static_assert(kRadix % kRankThreads8 == 0, "whole digits per thread");
+    static_assert(kDPT <= 32, "pending bits per thread");
     if (plan->skip[pass]) {
         if (blockIdx.x == 0 && threadIdx.x == 0 && ctl) {
             atomicAdd((unsigned long long *)&ctl->skipped_passes, 1ull);
@@ -151,7 +185,7 @@ __global__ void __launch_bounds__(kSortThreads, (kBits <= 10 ? 3 : 2)) onesweep_
         return;
     }
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    auto &S = *reinterpret_cast<OnesweepSmem<kBits, kHasValues> *>(smem_raw);
+    auto &S = *reinterpret_cast<OnesweepSmem<kBits, kHasValues, kRank> *>(smem_raw);
 
     const u32 sel = plan->sel[pass];
     const u64 *__restrict__ kin = sel ? keys1 : keys0;
@@ -160,135 +194,170 @@ __global__ void __launch_bounds__(kSortThreads, (kBits <= 10 ? 3 : 2)) onesweep_
     u32 *__restrict__ vout = sel ? vals0 : vals1;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool ranker = true;  // every warp ranks keys
     if (tid == 0) S.tile = atomicAdd(&plan->tile_counter[pass], 1u);
-    for (int k = tid; k < kSortWarps * kRadix; k += kSortThreads) (&S.warp_hist[0][0])[k] = 0;
+    for (int k = tid; k < kSortWarps * kRadix; k += Shape::kThreads) (&S.cursor[0][0])[k] = 0;
+    if constexpr (kRank == kRankAtomicOr)
+        for (int k = tid; k < 2 * kSortWarps * kRadix; k += Shape::kThreads)
+            (&S.peers[0][0][0])[k] = 0;
     __syncthreads();
     const u32 tile = S.tile;
     const u64 tile_base = (u64)tile * kSortTile;
     const u64 warp_base = tile_base + (u64)warp * 32 * kSortItems;
+    // items of a ranking thread: warp_base + j*32 + lane, valid while < n
+    const u32 nvalid = (!ranker || warp_base >= n)
+                           ? 0u
+                           : (u32)min((u64)kSortItems * 32, (u64)n - warp_base);
 
     u64 keys[kSortItems];
     u32 vals[kHasValues ? kSortItems : 1];
-    u32 ranks[kSortItems];
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
-        const u64 idx = warp_base + (u64)j * 32 + lane;
-        keys[j] = idx < n ? kin[idx] : ~0ull;
-        if constexpr (kHasValues) vals[j] = idx < n ? vin[idx] : 0u;
+        const bool valid = (u32)(j * 32 + lane) < nvalid;
+        keys[j] = valid ? kin[warp_base + j * 32 + lane] : ~0ull;
+        if constexpr (kHasValues) vals[j] = valid ? vin[warp_base + j * 32 + lane] : 0u;
     }
 
-    // -- warp-level ranking: peers = lanes of this warp holding the same digit
-    const u32 lt_mask = (1u << lane) - 1u;
+    // -- early digit counts per warp (order-free)
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        const bool valid = warp_base + (u64)j * 32 + lane < n;
-        const u32 d = digit_bits(keys[j], shift, kMask);
-        u32 peers;
-        if constexpr (kMatch) {
-            peers = __match_any_sync(0xFFFFFFFFu, valid ? d : (u32)kRadix + lane);
-        } else {
-            peers = __ballot_sync(0xFFFFFFFFu, valid);
+    for (int j = 0; j < kSortItems; ++j)
+        if ((u32)(j * 32 + lane) < nvalid)
+            atomicAdd(&S.cursor[warp][digit_bits(keys[j], shift, kMask)], 1u);
+    __syncthreads();
+
+    // -- per digit: tile count, publish it, turn warp counts into slots
+    u32 local = 0;
+    if (ranker) {
 #pragma unroll
-            for (int b = 0; b < kBits; ++b) {
-                const bool bit = (d >> b) & 1u;
-                const u32 vote = __ballot_sync(0xFFFFFFFFu, bit);
-                peers &= bit ? vote : ~vote;
+        for (int q = 0; q < kDPT; ++q) {
+            const int d = tid * kDPT + q;
+            u32 c = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < kSortWarps; ++w2) c += S.cursor[w2][d];
+            st_relaxed(lookback + (u64)tile * kRadix + d, (tile == 0 ? kFlagPre : kFlagAgg) | c);
+            S.count[d] = c;
+            local += c;
+        }
+    }
+    u32 run = block_exclusive_sum<kRankThreads8>(local, S.scan_tmp);
+    if (ranker) {
+#pragma unroll
+        for (int q = 0; q < kDPT; ++q) {
+            const int d = tid * kDPT + q;
+            S.tile_excl[d] = run;
+            u32 slot = run;
+#pragma unroll
+            for (int w2 = 0; w2 < kSortWarps; ++w2) {
+                const u32 t = S.cursor[w2][d];
+                S.cursor[w2][d] = slot;
+                slot += t;
             }
+            run += S.count[d];
         }
-        const int leader = 31 - __clz(peers);
-        u32 before = 0;
-        if (valid && lane == leader) {
-            before = S.warp_hist[warp][d];
-            S.warp_hist[warp][d] = before + __popc(peers);
-        }
-        before = __shfl_sync(0xFFFFFFFFu, before, leader);
-        ranks[j] = before + __popc(peers & lt_mask);
-        __syncwarp();
     }
     __syncthreads();
 
-    // -- per digit: warp-exclusive offsets and the tile count; publish counts
-    static_assert(kRadix % kSortThreads == 0, "whole digits per thread");
-    u32 count[kDPT];
-    u32 local = 0;
+    if (ranker) {
+        // -- stable ranking inside each warp, written straight to the staging area
+        const u32 lt_mask = (1u << lane) - 1u;
 #pragma unroll
-    for (int q = 0; q < kDPT; ++q) {
-        const int d = tid * kDPT + q;
-        u32 c = 0;
+        for (int j = 0; j < kSortItems; ++j) {
+            const bool valid = (u32)(j * 32 + lane) < nvalid;
+            const u32 d = digit_bits(keys[j], shift, kMask);
+            u32 peers;
+            if constexpr (kRank == kRankMatch) {
+                peers = __match_any_sync(0xFFFFFFFFu, valid ? d : (u32)kRadix + lane);
+            } else if constexpr (kRank == kRankBallot) {
+                peers = __ballot_sync(0xFFFFFFFFu, valid);
 #pragma unroll
-        for (int w2 = 0; w2 < kSortWarps; ++w2) {
-            const u32 t = S.warp_hist[w2][d];
-            S.warp_hist[w2][d] = c;
-            c += t;
+                for (int b = 0; b < kBits; ++b) {
+                    const bool bit = (d >> b) & 1u;
+                    const u32 vote = __ballot_sync(0xFFFFFFFFu, bit);
+                    peers &= bit ? vote : ~vote;
+                }
+            } else {
+                u32 *word = &S.peers[j & 1][warp][d];
+                if (valid) atomicOr(word, 1u << lane);
+                __syncwarp();
+                peers = valid ? *word : (1u << lane);
+            }
+            const int leader = 31 - __clz(peers);
+            u32 slot = 0;
+            if (valid && lane == leader) {
+                slot = S.cursor[warp][d];
+                S.cursor[warp][d] = slot + __popc(peers);
+            }
+            if constexpr (kRank == kRankAtomicOr) {
+                // every lane has read this iteration's mask before its leader
+                // clears it; the buffer is next OR-ed two iterations later
+                __syncwarp();
+                if (valid && lane == leader) S.peers[j & 1][warp][d] = 0;
+            }
+            slot = __shfl_sync(0xFFFFFFFFu, slot, leader) + __popc(peers & lt_mask);
+            if (valid) {
+                S.keys[slot] = keys[j];
+                if constexpr (kHasValues) S.vals[slot] = vals[j];
+            }
+            __syncwarp();
         }
-        st_relaxed(lookback + (u64)tile * kRadix + d, (tile == 0 ? kFlagPre : kFlagAgg) | c);
-        count[q] = c;
-        local += c;
     }
-    u32 run = block_exclusive_sum<kSortThreads>(local, S.scan_tmp);
-
-    // -- decoupled look-back over earlier tiles; the thread's digits walk back
-    //    in lockstep so their status loads overlap
-    u32 excl[kDPT];
-    if (tile > 0) {
-        long k[kDPT];
+    {
+        // -- look-back: each thread walks back for its kDPT digits, in aligned
+        //    groups of kLookWin predecessors per round trip (earlier tiles
+        //    have had the ranking time to publish)
+        u32 sum[kDPT];
+        long next[kDPT];  // next predecessor tile to examine
         u32 pending = 0;
 #pragma unroll
         for (int q = 0; q < kDPT; ++q) {
-            excl[q] = 0;
-            k[q] = (long)tile - 1;
-            pending |= 1u << q;
+            sum[q] = 0;
+            next[q] = (long)tile - 1;
+            if (tile > 0) pending |= 1u << q;
         }
-        u32 spins = 0;
+        u32 idle = 0;
+        int window = 1;  // the nearest predecessor usually holds a prefix already
         while (pending) {
-            bool waited = false;
+            bool progress = false;
 #pragma unroll
             for (int q = 0; q < kDPT; ++q) {
                 if (!(pending & (1u << q))) continue;
-                const u32 s = ld_relaxed(lookback + (u64)k[q] * kRadix + tid * kDPT + q);
-                const u32 flag = s & kFlagMask;
-                if (flag == 0) {
-                    waited = true;
-                    continue;
+                const int d = tid * kDPT + q;
+                // statuses of tiles next, next-1, ...: independent loads, each
+                // coalesced across the warp's consecutive digits
+                u32 st[kLookWin];
+#pragma unroll
+                for (int t = 0; t < kLookWin; ++t)
+                    st[t] = (t < window && next[q] - t >= 0)
+                                ? ld_relaxed(lookback + (u64)(next[q] - t) * kRadix + d)
+                                : 0u;
+#pragma unroll
+                for (int t = 0; t < kLookWin; ++t) {
+                    if (t >= window || !(pending & (1u << q))) break;
+                    const u32 s = st[t];
+                    const u32 flag = s & kFlagMask;
+                    if (flag == 0) break;  // not published yet: retry this tile
+                    sum[q] += s & kValMask;
+                    progress = true;
+                    if (flag == kFlagPre) pending &= ~(1u << q);
+                    else --next[q];  // tile 0 always publishes a prefix
                 }
-                excl[q] += s & kValMask;
-                if (flag == kFlagPre) pending &= ~(1u << q);
-                else --k[q];  // tile 0 always publishes a prefix, so k stays >= 0
             }
-            if (waited && pending) {
-                if (++spins > kSpinLimit) {
+            window = kLookWin;
+            if (!progress && pending) {
+                if (++idle > kSpinLimit) {
                     set_error(err, kErrTimeout);
                     break;
                 }
-                if (spins > 32) __nanosleep(64);
+                if (idle > 16) __nanosleep(64);
             }
         }
 #pragma unroll
-        for (int q = 0; q < kDPT; ++q)
-            st_relaxed(lookback + (u64)tile * kRadix + tid * kDPT + q,
-                       kFlagPre | ((excl[q] + count[q]) & kValMask));
-    } else {
-#pragma unroll
-        for (int q = 0; q < kDPT; ++q) excl[q] = 0;
-    }
-#pragma unroll
-    for (int q = 0; q < kDPT; ++q) {
-        const int d = tid * kDPT + q;
-        S.tile_excl[d] = run;
-        S.base[d] = plan->offsets[pass][d] + excl[q] - run;
-        run += count[q];
-    }
-    __syncthreads();
-
-    // -- stage in shared memory in digit order
-#pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        const bool valid = warp_base + (u64)j * 32 + lane < n;
-        if (valid) {
-            const u32 dj = digit_bits(keys[j], shift, kMask);
-            const u32 lp = S.tile_excl[dj] + S.warp_hist[warp][dj] + ranks[j];
-            S.keys[lp] = keys[j];
-            if constexpr (kHasValues) S.vals[lp] = vals[j];
+        for (int q = 0; q < kDPT; ++q) {
+            const int d = tid * kDPT + q;
+            if (tile > 0)
+                st_relaxed(lookback + (u64)tile * kRadix + d,
+                           kFlagPre | ((sum[q] + S.count[d]) & kValMask));
+            S.base[d] = plan->offsets[pass][d] + sum[q] - S.tile_excl[d];
         }
     }
     __syncthreads();
@@ -297,7 +366,7 @@ __global__ void __launch_bounds__(kSortThreads, (kBits <= 10 ? 3 : 2)) onesweep_
     //    global slots
     const u64 left = (u64)n - tile_base;
     const u32 tile_n = left < (u64)kSortTile ? (u32)left : (u32)kSortTile;
-    for (u32 i = tid; i < tile_n; i += kSortThreads) {
+    for (u32 i = tid; i < tile_n; i += Shape::kThreads) {
         const u64 key = S.keys[i];
         const u32 pos = S.base[digit_bits(key, shift, kMask)] + i;
         if (pos < n) {  // only a timed-out look-back can make it larger
