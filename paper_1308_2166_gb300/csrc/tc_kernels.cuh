@@ -150,9 +150,9 @@ __device__ __forceinline__ void dir_segment(const DirEntry *dir, u32 epoch, u64 
 
 // ---------------------------------------------------------------------------
 // Directories over the two sorted arrays, plus the in-batch repeat check.
-// For the arcs, x = src; for the Step-3 keys, x = the smaller endpoint.  The
-// first element of a run writes (epoch, start), the last one writes end.
+// For the arcs, x = src; for the Step-3 keys, x = the smaller endpoint.
 // ---------------------------------------------------------------------------
+// The first element of a run writes (epoch, start), the last one writes end.
 __global__ void index_kernel(const u64 *arcs0, const u64 *arcs1, const u64 *ekeys0,
                              const u64 *ekeys1, const SortPlan *plans, BatchShape s,
                              DirEntry *adir, DirEntry *edir, const Control *ctl, u32 *err) {
@@ -197,7 +197,7 @@ constexpr int kSweepThreads = 256;
 // the directories (vertex ids < 2^26), else binary search on the sorted
 // arrays.
 template <bool kDir>
-__global__ void __launch_bounds__(kSweepThreads) sweep_kernel(SweepArgs a) {
+__global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArgs a) {
     if (ld_relaxed(&a.ctl->err)) return;  // rejected batch: state stays as it was
     const u64 i = (u64)blockIdx.x * kSweepThreads + threadIdx.x;
     if (i >= a.r) return;
