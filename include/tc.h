@@ -43,6 +43,7 @@ extern "C" {
                                repeated inside the batch */
 #define TC_ERR_CUDA (-4)    /* a CUDA runtime call failed */
 #define TC_ERR_TIMEOUT (-5) /* a bounded device-side wait gave up */
+#define TC_ERR_RANGE (-6)   /* size beyond the fixed maximum of tc_rank_all_noalloc */
 
 /* Empty level-1 / level-2 edge in tc_get_state output. */
 #define TC_EMPTY_EDGE 0xFFFFFFFFFFFFFFFFull
@@ -192,6 +193,31 @@ const char *tc_strerror(int code);
 int tc_rank_all(const uint64_t *d_edges, uint64_t w, uint32_t vertex_bits,
                 uint32_t *d_src, uint32_t *d_dst, uint32_t *d_pos,
                 uint32_t *d_rank, void *cuda_stream);
+
+/* Largest batch tc_rank_all_noalloc accepts. */
+#define TC_NOALLOC_MAX_EDGES (1u << 18)
+
+/* tc_rank_all without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * when they need rankAll -- a process whose HBM another allocator already
+ * owns, a latency-critical loop where cudaMalloc/cudaFree would synchronise
+ * the device or could fail with out-of-memory halfway through, or code that
+ * must not run out of memory once started.  Same arguments and output as
+ * tc_rank_all, for batches of at most TC_NOALLOC_MAX_EDGES edges (larger w
+ * returns TC_ERR_RANGE before any GPU work).  Its scratch (about 12.3 MB) is
+ * a fixed array in the library's device image, so every GPU that loads
+ * libtc.so holds it from module load until the process exits; no call
+ * allocates or frees anything.  The first call on a device looks the
+ * array's device address up (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one array and each clears what must start at zero, but calls whose
+ * work overlaps on the GPU (other streams, other host threads) race on it:
+ * issue them one after another.  Returns after the work on `cuda_stream` is
+ * complete.  Errors: TC_ERR_INVAL, TC_ERR_RANGE, TC_ERR_CUDA,
+ * TC_ERR_TIMEOUT. */
+int tc_rank_all_noalloc(const uint64_t *d_edges, uint64_t w, uint32_t vertex_bits,
+                        uint32_t *d_src, uint32_t *d_dst, uint32_t *d_pos,
+                        uint32_t *d_rank, void *cuda_stream);
 
 #ifdef __cplusplus
 }

@@ -20,6 +20,8 @@ TC_ERR_NOMEM = -2
 TC_ERR_INPUT = -3
 TC_ERR_CUDA = -4
 TC_ERR_TIMEOUT = -5
+TC_ERR_RANGE = -6
+TC_NOALLOC_MAX_EDGES = 1 << 18
 TC_EMPTY_EDGE = (1 << 64) - 1
 TC_FLAG_CLOSED = 1
 
@@ -28,7 +30,7 @@ EXPORTS = (
     "tc_create", "tc_create_ex", "tc_process_batch", "tc_process_batch_async",
     "tc_sync", "tc_estimate", "tc_estimate_async", "tc_estimate_mom", "tc_get_state",
     "tc_get_counters", "tc_profile_begin", "tc_profile_end", "tc_tune", "tc_destroy",
-    "tc_strerror", "tc_rank_all",
+    "tc_strerror", "tc_rank_all", "tc_rank_all_noalloc",
 )
 
 
@@ -87,6 +89,7 @@ def load(path: str | None = None):
         "tc_destroy": (None, [P]),
         "tc_strerror": (ctypes.c_char_p, [I]),
         "tc_rank_all": (I, [P, U64, U32, P, P, P, P, P]),
+        "tc_rank_all_noalloc": (I, [P, U64, U32, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -265,3 +268,17 @@ class TriangleStream:
             self.close()
         except Exception:
             pass
+
+
+def tc_rank_all_noalloc(d_edges, w: int, vertex_bits: int, d_src, d_dst, d_pos, d_rank,
+                        stream: int = 0) -> None:
+    """tc_rank_all for callers that cannot allocate device memory at call time.
+
+    Same outputs as ``tc_rank_all``; the scratch is a fixed array inside the
+    library's device image (held by every GPU that loads the library until
+    the process exits), so nothing is allocated or freed.  At most
+    ``TC_NOALLOC_MAX_EDGES`` edges; calls must not overlap on the GPU.
+    """
+    _check(load().tc_rank_all_noalloc(_ptr(d_edges), w, vertex_bits, _ptr(d_src), _ptr(d_dst),
+                                      _ptr(d_pos), _ptr(d_rank), stream or None),
+           "tc_rank_all_noalloc")

@@ -362,6 +362,7 @@ const char *tc_strerror(int code) {
             return "batch breaks the stream model (self-loop, bad key, id range or repeated edge)";
         case TC_ERR_CUDA: return "CUDA runtime error";
         case TC_ERR_TIMEOUT: return "bounded device wait timed out";
+        case TC_ERR_RANGE: return "size exceeds the fixed maximum of this entry point";
         default: return "unknown error";
     }
 }
@@ -684,3 +685,102 @@ int tc_rank_all(const uint64_t *d_edges, uint64_t w, uint32_t vertex_bits, uint3
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// rankAll without any device allocation.
+//
+// Some callers cannot allocate device memory at the point where they need
+// rankAll: a process whose HBM is already handed out to another allocator
+// (a framework's caching allocator that reserved nearly all of it), a
+// latency-critical loop where cudaMalloc / cudaFree would synchronise the
+// device or fail with out-of-memory halfway through, or code that must not
+// fail for lack of memory once it has started.  tc_rank_all_noalloc serves
+// them with scratch that lives in a fixed array in the library's own device
+// image: every GPU that loads libtc.so holds these kNoAllocScratchBytes
+// (about 12.3 MB) from module load until the process exits, and batches are
+// limited to TC_NOALLOC_MAX_EDGES edges.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr u64 kNoAllocArcs = 2ull * TC_NOALLOC_MAX_EDGES;
+constexpr u64 kNoAllocPlanBytes = 2 * sizeof(SortPlan);
+// Look-back words for any vertex width: at most 3 passes of <= 11-bit digits
+// over the arcs (reserved for 4).
+constexpr u64 kNoAllocLookbackWords =
+    4ull * ((kNoAllocArcs / kSortTile + kLookWin - 1) / kLookWin * kLookWin) * kMaxRadix;
+constexpr u64 align256(u64 x) { return (x + 255) / 256 * 256; }
+constexpr u64 kNoAllocOffLookback = align256(kNoAllocPlanBytes);
+constexpr u64 kNoAllocOffErr = kNoAllocOffLookback + align256(kNoAllocLookbackWords * sizeof(u32));
+constexpr u64 kNoAllocOffArcs0 = kNoAllocOffErr + 256;
+constexpr u64 kNoAllocOffArcs1 = kNoAllocOffArcs0 + align256(kNoAllocArcs * sizeof(u64));
+constexpr u64 kNoAllocScratchBytes = kNoAllocOffArcs1 + align256(kNoAllocArcs * sizeof(u64));
+
+// The scratch itself.  In host code this name is only a stand-in for the
+// device array: its device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+unsigned char *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch on the current device (looked up once per
+// device, on that device's first call).
+int noalloc_scratch(unsigned char **out) {
+    int dev = 0;
+    TC_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return TC_ERR_INVAL;
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        TC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[dev] = static_cast<unsigned char *>(p);
+    }
+    *out = g_noalloc_addr[dev];
+    return TC_OK;
+}
+
+}  // namespace
+
+extern "C" int tc_rank_all_noalloc(const uint64_t *d_edges, uint64_t w, uint32_t vertex_bits,
+                                   uint32_t *d_src, uint32_t *d_dst, uint32_t *d_pos,
+                                   uint32_t *d_rank, void *cuda_stream) {
+    if (vertex_bits < 1 || vertex_bits > 32) return TC_ERR_INVAL;
+    if (w > TC_NOALLOC_MAX_EDGES) return TC_ERR_RANGE;
+    if (w == 0) return TC_OK;
+    if (!d_edges || !d_src || !d_dst || !d_pos || !d_rank) return TC_ERR_INVAL;
+    int rc = configure_kernels();
+    if (rc) return rc;
+    unsigned char *z = nullptr;
+    rc = noalloc_scratch(&z);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const BatchShape s = make_shape(w, vertex_bits);
+    const u64 ta = tiles_of(2 * w);
+    const u64 la = pass_lookback_words(2 * w, s.bits_a);
+    if ((u64)s.npa * la > kNoAllocLookbackWords) return TC_ERR_RANGE;
+    const PassKernel ka = select_pass(s.bits_a, false, kRankBallot);
+    SortPlan *plans = reinterpret_cast<SortPlan *>(z);
+    u32 *lb = reinterpret_cast<u32 *>(z + kNoAllocOffLookback);
+    u32 *err = reinterpret_cast<u32 *>(z + kNoAllocOffErr);
+    u64 *a0 = reinterpret_cast<u64 *>(z + kNoAllocOffArcs0);
+    u64 *a1 = reinterpret_cast<u64 *>(z + kNoAllocOffArcs1);
+    // The array keeps the previous call's contents: clear the histograms,
+    // tile counters, this call's look-back words and the error word.
+    TC_CUDA(cudaMemsetAsync(z, 0, kNoAllocPlanBytes, st));
+    TC_CUDA(cudaMemsetAsync(lb, 0, (u64)s.npa * la * sizeof(u32), st));
+    TC_CUDA(cudaMemsetAsync(err, 0, sizeof(u32), st));
+    const u64 prep_blocks = std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
+    prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, prep_smem(s, false), st>>>(
+        d_edges, s, a0, nullptr, nullptr, plans, err, 0);
+    sort_plan_kernel<<<1, 256, 0, st>>>(plans, s.npa, (u32)(2 * w), s.bits_a, 0, 0, 8);
+    for (int p = 0; p < s.npa; ++p)
+        ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(a0, a1, nullptr, nullptr, (u32)(2 * w),
+                                                         s.sha + p * s.bits_a, p, &plans[0],
+                                                         lb + (u64)p * la, err, nullptr);
+    const u64 rb = (2 * w + kRankTile - 1) / kRankTile;
+    rank_out_kernel<<<(unsigned)rb, kRankThreads, 0, st>>>(d_edges, a0, a1, &plans[0], s, d_src,
+                                                           d_dst, d_pos, d_rank);
+    TC_CUDA(cudaGetLastError());
+    u32 h_err = 0;
+    TC_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(u32), cudaMemcpyDeviceToHost, st));
+    TC_CUDA(cudaStreamSynchronize(st));
+    return map_device_error(h_err & kErrTimeout);
+}
