@@ -105,16 +105,18 @@ int tc_process_batch_async(tc_ctx *c, const uint64_t *d_edges, uint64_t w,
  * device-side error recorded since the last tc_sync (then clear it). */
 int tc_sync(tc_ctx *c);
 
-/* The estimate of Lemma 3.1 averaged over the r estimators: one device
- * reduction of S in 128-bit integers, then N = m * S exactly.  Synchronises
- * (returns a pending device-side error first, as tc_sync). */
+/* The estimate of Lemma 3.1 averaged over the r estimators: S (128-bit) and
+ * the closed count are reduced on the device inside every accepted batch
+ * update, from the estimators' new state; N = m * S is formed exactly.
+ * Synchronises (returns a pending device-side error first, as tc_sync). */
 int tc_estimate(tc_ctx *c, tc_estimate_t *out);
 
-/* Enqueue the reduction of tc_estimate on `cuda_stream` without waiting:
- * writes four uint64 to the DEVICE array d_out -- S low word, S high word,
- * the closed count, and |E| -- once the stream reaches it (N = |E| * S and
- * tau_hat = N / r are then formed by the caller).  d_out is borrowed until
- * the stream passes this point.  Errors: TC_ERR_INVAL, TC_ERR_CUDA. */
+/* Enqueue, on `cuda_stream`, the copy of the current estimate to the DEVICE
+ * array d_out without waiting: four uint64 -- S low word, S high word, the
+ * closed count, and |E| -- as of the last batch enqueued before it on the
+ * same stream (N = |E| * S and tau_hat = N / r are then formed by the
+ * caller).  d_out is borrowed until the stream passes this point.  Errors:
+ * TC_ERR_INVAL, TC_ERR_CUDA. */
 int tc_estimate_async(tc_ctx *c, uint64_t *d_out, void *cuda_stream);
 
 /* Median-of-means aggregate (Sec. 3.1; the paper's implementation, Sec. 5):
@@ -166,10 +168,11 @@ int tc_profile_end(tc_ctx *c, tc_profile_t *out);
 /* Launch tuning of the two radix sorts (rankAll's arcs, Lemma 4.3; Step 3's
  * edges, Sec. 4.4).  arc_digit_bits / edge_digit_bits: 0 (automatic: the
  * fewest passes over the live key bits), 8, 10 or 11.  ranking (how a warp
- * finds the lanes holding equal digits): 1 = one match.any per key, 2 = one
- * ballot per digit bit, 0 or 3 = lanes OR their bit into a shared-memory
- * word per (warp, digit).  Results do not depend on the tuning.  Applies to
- * batches enqueued afterwards.
+ * finds the lanes holding equal digits): 0 or 2 = one ballot per digit bit
+ * (the default), 1 = one match.any per key, 3 = lanes OR their bit into a
+ * shared-memory word per (warp, digit; 8-bit digits only, else match.any).
+ * Results do not depend on the tuning.  Applies to batches enqueued
+ * afterwards.
  * Errors: TC_ERR_INVAL for other values. */
 int tc_tune(tc_ctx *c, uint32_t arc_digit_bits, uint32_t edge_digit_bits, uint32_t ranking);
 

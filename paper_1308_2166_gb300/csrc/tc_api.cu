@@ -56,17 +56,17 @@ void pass_variant(PassKernel &k) {
 // only fits shared memory for 8-bit digits; wider digits use match.any.
 PassKernel select_pass(u32 bits, bool values, int rank) {
     PassKernel k{};
-#define TC_PASS_RANK(B, V)                                                  \
-    if (rank == kRankBallot) pass_variant<B, V, kRankBallot>(k);            \
+#define TC_PASS_RANK(B, V)                                                   \
+    if (rank == kRankBallot) pass_variant<B, V, kRankBallot>(k);             \
     else if (rank == kRankMatch || B > 8) pass_variant<B, V, kRankMatch>(k); \
     else pass_variant<B, V, (B > 8 ? kRankMatch : kRankAtomicOr)>(k);
-#define TC_PASS_CASE(B)                                                     \
-    case B:                                                                 \
-        if (values) {                                                       \
-            TC_PASS_RANK(B, true)                                           \
-        } else {                                                            \
-            TC_PASS_RANK(B, false)                                          \
-        }                                                                   \
+#define TC_PASS_CASE(B)           \
+    case B:                       \
+        if (values) {             \
+            TC_PASS_RANK(B, true)  \
+        } else {                  \
+            TC_PASS_RANK(B, false) \
+        }                         \
         return k;
     switch (bits) {
         TC_PASS_CASE(8)
@@ -128,8 +128,7 @@ BatchShape make_shape(u64 w, u32 B, u32 force_a = 0, u32 force_e = 0) {
 
 u64 tiles_of(u64 n) { return (n + kSortTile - 1) / kSortTile; }
 
-// Look-back words of one digit pass over n keys with `bits`-bit digits
-// (digit-major rows of lookback_stride(tiles) words).
+// Look-back words of one digit pass over n keys with `bits`-bit digits.
 u64 pass_lookback_words(u64 n, u32 bits) {
     return (u64)lookback_stride((u32)tiles_of(n)) << bits;
 }
@@ -143,15 +142,21 @@ u64 lookback_words(const BatchShape &s, bool edges) {
 
 // Largest look-back need over every digit width a context may use.
 u64 lookback_words_max(u64 w, u32 B) {
-    u64 best = 0;
+    u64 best = lookback_words(make_shape(w, B), true);
     for (u32 ba : kDigitChoices)
-        for (u32 be : kDigitChoices) best = std::max(best, lookback_words(make_shape(w, B, ba, be), true));
-    return std::max(best, lookback_words(make_shape(w, B), true));
+        for (u32 be : kDigitChoices)
+            best = std::max(best, lookback_words(make_shape(w, B, ba, be), true));
+    return best;
 }
 
 size_t prep_smem(const BatchShape &s, bool edges) {
-    return (((size_t)s.npa << s.bits_a) + (edges ? ((size_t)s.npe << s.bits_e) : 0)) * sizeof(u32);
+    return (((size_t)s.npa << s.bits_a) + (edges ? ((size_t)s.npe << s.bits_e) : 0)) *
+           sizeof(u32);
 }
+
+// Per-batch zeroed scratch: BatchAcc, then SortPlan[2], then look-back words.
+constexpr u64 kOffPlans = sizeof(BatchAcc);
+constexpr u64 kOffLookback = kOffPlans + 2 * sizeof(SortPlan);
 
 }  // namespace
 
@@ -159,9 +164,9 @@ struct tc_ctx {
     int device = 0;
     u64 r = 0, seed = 0;
     u32 stream_id = 0, vertex_bits = 32;
-    u64 cap_w = 0;  // scratch capacity in edges
+    u64 cap_w = 0;                           // scratch capacity in edges
     u32 force_bits_a = 0, force_bits_e = 0;  // tc_tune digit widths (0 = automatic)
-    int rank_method = kRankAtomicOr;         // tc_tune warp ranking method
+    int rank_method = kRankBallot;           // tc_tune warp ranking method
     cudaStream_t own = nullptr;
     // estimator state (structure of arrays)
     u64 *f1 = nullptr, *f2 = nullptr, *chi = nullptr;
@@ -172,14 +177,10 @@ struct tc_ctx {
     u64 *ekeys[2] = {nullptr, nullptr};
     u32 *evals[2] = {nullptr, nullptr};
     u64 *staging = nullptr;
-    unsigned char *zeroed = nullptr;  // SortPlan[2] followed by look-back words
-    u64 *red = nullptr;               // reduction output (device, 4 words)
+    unsigned char *zeroed = nullptr;  // BatchAcc, SortPlan[2], look-back words
     DirEntry *adir = nullptr;         // per-vertex directories (ids < 2^kDirMaxBits)
     DirEntry *edir = nullptr;
-    // host side
-    Mailbox *mbox = nullptr;  // mapped pinned, written by finish_kernel
-    Mailbox *mbox_dev = nullptr;
-    u64 *h_red = nullptr;     // pinned
+    Control *h_ctl = nullptr;         // pinned host copy of the control block
     // launch accounting and stage timing
     u64 launches = 0;
     bool prof = false;
@@ -225,7 +226,7 @@ static int ensure_scratch(tc_ctx *c, u64 w) {
     if (w <= c->cap_w) return TC_OK;
     TC_CUDA(cudaDeviceSynchronize());
     free_scratch(c);
-    const u64 zb = 2 * sizeof(SortPlan) + lookback_words_max(w, c->vertex_bits) * sizeof(u32);
+    const u64 zb = kOffLookback + lookback_words_max(w, c->vertex_bits) * sizeof(u32);
     bool ok = true;
     for (int k = 0; k < 2 && ok; ++k) {
         ok &= cudaMalloc(&c->arcs[k], 2 * w * sizeof(u64)) == cudaSuccess;
@@ -252,17 +253,18 @@ static int map_device_error(u32 e) {
 // Enqueue one batch on `st`.  W is a device pointer; w in [1, cap_w].
 static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
     const BatchShape s = make_shape(w, c->vertex_bits, c->force_bits_a, c->force_bits_e);
-    SortPlan *plans = reinterpret_cast<SortPlan *>(c->zeroed);
-    u32 *lb = reinterpret_cast<u32 *>(c->zeroed + 2 * sizeof(SortPlan));
-    const u64 used = 2 * sizeof(SortPlan) + lookback_words(s, true) * sizeof(u32);
+    BatchAcc *acc = reinterpret_cast<BatchAcc *>(c->zeroed);
+    SortPlan *plans = reinterpret_cast<SortPlan *>(c->zeroed + kOffPlans);
+    u32 *lb = reinterpret_cast<u32 *>(c->zeroed + kOffLookback);
+    const u64 used = kOffLookback + lookback_words(s, true) * sizeof(u32);
     stamp(c, st, kStart);
     TC_CUDA(cudaMemsetAsync(c->zeroed, 0, used, st));
 
     const u64 prep_blocks = std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
     prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, prep_smem(s, true), st>>>(
         W, s, c->arcs[0], c->ekeys[0], c->evals[0], plans, &c->ctl->err, 1);
-    sort_plan_kernel<<<2, 256, 0, st>>>(plans, s.npa, (u32)(2 * w), s.bits_a, s.npe, (u32)w,
-                                        s.bits_e);
+    sort_plan_kernel<<<dim3((unsigned)std::max(s.npa, s.npe), 2), 256, 0, st>>>(
+        plans, s.npa, (u32)(2 * w), s.bits_a, s.npe, (u32)w, s.bits_e);
     stamp(c, st, kPrep);
     const u64 ta = tiles_of(2 * w), te = tiles_of(w);
     const u64 la = pass_lookback_words(2 * w, s.bits_a), le = pass_lookback_words(w, s.bits_e);
@@ -307,6 +309,7 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
     a.adir = c->adir;
     a.edir = c->edir;
     a.ctl = c->ctl;
+    a.acc = acc;
     a.s = s;
     a.key = make_uint2((u32)(c->seed & 0xFFFFFFFFu), (u32)(c->seed >> 32));
     a.stream = c->stream_id;
@@ -316,37 +319,33 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
     else
         sweep_kernel<false><<<(unsigned)sweep_blocks, kSweepThreads, 0, st>>>(a);
     stamp(c, st, kSweep);
-    finish_kernel<<<1, 1, 0, st>>>(c->ctl, c->mbox_dev, w);
+    finish_kernel<<<1, 1, 0, st>>>(c->ctl, acc, w);
     stamp(c, st, kFinish);
     TC_CUDA(cudaGetLastError());
     c->launches += 5 + (u64)s.npa + (u64)s.npe;
     if (c->prof) {
         c->prof_batches += 1;
         c->prof_sort_launches += (u64)s.npa + (u64)s.npe;
-        c->prof_sort_bytes += (u64)s.npa * 2 * w * 16 + (u64)s.npe * w * (s.ekeys_only ? 16 : 24);
+        c->prof_sort_bytes +=
+            (u64)s.npa * 2 * w * 16 + (u64)s.npe * w * (s.ekeys_only ? 16 : 24);
     }
     return TC_OK;
 }
 
-static int enqueue_estimate(tc_ctx *c, u64 *d_out, cudaStream_t st) {
-    stamp(c, st, kStart);
-    TC_CUDA(cudaMemsetAsync(d_out, 0, 3 * sizeof(u64), st));
-    const u64 blocks = std::min<u64>((c->r + kReduceThreads - 1) / kReduceThreads, 1216);
-    estimate_kernel<<<(unsigned)blocks, kReduceThreads, 0, st>>>(c->chi, c->flags, c->r, c->ctl,
-                                                                 d_out);
-    stamp(c, st, kEstimate);
-    TC_CUDA(cudaGetLastError());
-    c->launches += 1;
+// Wait for the device, copy the control block to the host.
+static int read_control(tc_ctx *c) {
+    TC_CUDA(cudaDeviceSynchronize());
+    TC_CUDA(cudaMemcpy(c->h_ctl, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost));
     return TC_OK;
 }
 
-// Read and clear the device-side error after the context's work is done.
+// After read_control: report and clear the first device-side error.
 static int collect_error(tc_ctx *c) {
-    const u32 e = c->mbox->err;
+    const u32 e = c->h_ctl->sticky;
     if (e) {
-        c->mbox->err = 0;
         TC_CUDA(cudaMemsetAsync(&c->ctl->sticky, 0, sizeof(u32), c->own));
         TC_CUDA(cudaStreamSynchronize(c->own));
+        c->h_ctl->sticky = 0;
     }
     return map_device_error(e);
 }
@@ -388,7 +387,7 @@ int tc_create_ex(uint64_t r, uint64_t seed, uint32_t stream_id, uint64_t w_max,
     ok &= ok && cudaMalloc(&c->chi, r * sizeof(u64)) == cudaSuccess;
     ok &= ok && cudaMalloc(&c->flags, r * sizeof(u32)) == cudaSuccess;
     ok &= ok && cudaMalloc(&c->ctl, sizeof(Control)) == cudaSuccess;
-    ok &= ok && cudaMalloc(&c->red, 4 * sizeof(u64)) == cudaSuccess;
+    ok &= ok && cudaHostAlloc(&c->h_ctl, sizeof(Control), cudaHostAllocDefault) == cudaSuccess;
     const u64 nverts = 1ull << vertex_bits;
     if (ok && vertex_bits <= kDirMaxBits) {
         ok &= cudaMalloc(&c->adir, nverts * sizeof(DirEntry)) == cudaSuccess;
@@ -396,11 +395,8 @@ int tc_create_ex(uint64_t r, uint64_t seed, uint32_t stream_id, uint64_t w_max,
         ok &= ok && cudaMemsetAsync(c->adir, 0, nverts * sizeof(DirEntry), c->own) == cudaSuccess;
         ok &= ok && cudaMemsetAsync(c->edir, 0, nverts * sizeof(DirEntry), c->own) == cudaSuccess;
     }
-    ok &= ok && cudaHostAlloc(&c->mbox, sizeof(Mailbox), cudaHostAllocMapped) == cudaSuccess;
-    ok &= ok && cudaHostGetDevicePointer((void **)&c->mbox_dev, c->mbox, 0) == cudaSuccess;
-    ok &= ok && cudaHostAlloc(&c->h_red, 4 * sizeof(u64), cudaHostAllocDefault) == cudaSuccess;
     if (ok) {
-        std::memset(c->mbox, 0, sizeof(Mailbox));
+        std::memset(c->h_ctl, 0, sizeof(Control));
         ok &= cudaMemsetAsync(c->f1, 0xFF, r * sizeof(u64), c->own) == cudaSuccess;
         ok &= cudaMemsetAsync(c->f2, 0xFF, r * sizeof(u64), c->own) == cudaSuccess;
         ok &= cudaMemsetAsync(c->chi, 0, r * sizeof(u64), c->own) == cudaSuccess;
@@ -437,11 +433,9 @@ void tc_destroy(tc_ctx *c) {
     cudaFree(c->chi);
     cudaFree(c->flags);
     cudaFree(c->ctl);
-    cudaFree(c->red);
     cudaFree(c->adir);
     cudaFree(c->edir);
-    if (c->mbox) cudaFreeHost(c->mbox);
-    if (c->h_red) cudaFreeHost(c->h_red);
+    if (c->h_ctl) cudaFreeHost(c->h_ctl);
     for (cudaEvent_t ev : c->pool) cudaEventDestroy(ev);
     if (c->own) cudaStreamDestroy(c->own);
     delete c;
@@ -470,40 +464,46 @@ int tc_process_batch(tc_ctx *c, const uint64_t *edges, uint64_t w) {
     rc = enqueue_batch(c, W, w, c->own);
     if (rc) return rc;
     TC_CUDA(cudaStreamSynchronize(c->own));
+    TC_CUDA(cudaMemcpy(c->h_ctl, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost));
     return collect_error(c);
 }
 
 int tc_sync(tc_ctx *c) {
     if (!c) return TC_ERR_INVAL;
-    TC_CUDA(cudaDeviceSynchronize());
+    int rc = read_control(c);
+    if (rc) return rc;
     return collect_error(c);
 }
 
 int tc_get_counters(tc_ctx *c, uint64_t *r, uint64_t *m, uint64_t *batches) {
     if (!c) return TC_ERR_INVAL;
-    TC_CUDA(cudaDeviceSynchronize());
+    int rc = read_control(c);
+    if (rc) return rc;
     if (r) *r = c->r;
-    if (m) *m = c->mbox->m;
-    if (batches) *batches = c->mbox->batches;
+    if (m) *m = c->h_ctl->m;
+    if (batches) *batches = c->h_ctl->batches;
     return TC_OK;
 }
 
 int tc_estimate_async(tc_ctx *c, uint64_t *d_out, void *cuda_stream) {
     if (!c || !d_out) return TC_ERR_INVAL;
-    return enqueue_estimate(c, d_out, (cudaStream_t)cuda_stream);
+    // The sweep reduced S and the closed count of the new state, and the
+    // batch's finish step committed them with |E|: copy the four words.
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    stamp(c, st, kStart);
+    TC_CUDA(cudaMemcpyAsync(d_out, c->ctl->est, 4 * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+    stamp(c, st, kEstimate);
+    return TC_OK;
 }
 
 int tc_estimate(tc_ctx *c, tc_estimate_t *out) {
     if (!c || !out) return TC_ERR_INVAL;
     int rc = tc_sync(c);
     if (rc) return rc;
-    rc = enqueue_estimate(c, c->red, c->own);
-    if (rc) return rc;
-    TC_CUDA(cudaMemcpyAsync(c->h_red, c->red, 4 * sizeof(u64), cudaMemcpyDeviceToHost, c->own));
-    TC_CUDA(cudaStreamSynchronize(c->own));
     using u128 = unsigned __int128;
-    const u128 S = ((u128)c->h_red[1] << 64) | c->h_red[0];
-    const u64 m = c->h_red[3];
+    const Control &h = *c->h_ctl;
+    const u128 S = ((u128)h.est[1] << 64) | h.est[0];
+    const u64 m = h.m;
     const u128 N = S * (u128)m;
     out->sum_lo = (u64)S;
     out->sum_hi = (u64)(S >> 64);
@@ -511,8 +511,8 @@ int tc_estimate(tc_ctx *c, tc_estimate_t *out) {
     out->num_hi = (u64)(N >> 64);
     out->r = c->r;
     out->m = m;
-    out->n_closed = c->h_red[2];
-    out->batches = c->mbox->batches;
+    out->n_closed = h.est[2];
+    out->batches = h.batches;
     const u128 q = N / c->r, rem = N % c->r;
     out->tau_hat = (double)q + (double)rem / (double)c->r;
     return TC_OK;
@@ -549,7 +549,7 @@ int tc_estimate_mom(tc_ctx *c, uint32_t g, uint64_t *num_lo, uint64_t *num_hi, u
     std::sort(gs.begin(), gs.end(),
               [](const G &a, const G &b) { return a.s * (u128)b.size < b.s * (u128)a.size; });
     const G &med = gs[(g - 1) / 2];
-    const u128 num = med.s * (u128)c->mbox->m;
+    const u128 num = med.s * (u128)c->h_ctl->m;
     if (num_lo) *num_lo = (u64)num;
     if (num_hi) *num_hi = (u64)(num >> 64);
     if (den) *den = med.size;
@@ -573,22 +573,21 @@ int tc_tune(tc_ctx *c, uint32_t arc_digit_bits, uint32_t edge_digit_bits, uint32
         return TC_ERR_INVAL;
     c->force_bits_a = arc_digit_bits;
     c->force_bits_e = edge_digit_bits;
-    c->rank_method = ranking == 1 ? kRankMatch : ranking == 2 ? kRankBallot : kRankAtomicOr;
+    c->rank_method = ranking == 1 ? kRankMatch : ranking == 3 ? kRankAtomicOr : kRankBallot;
     return TC_OK;
 }
 
 int tc_profile_begin(tc_ctx *c) {
     if (!c) return TC_ERR_INVAL;
-    TC_CUDA(cudaDeviceSynchronize());
     while (c->pool.size() < kEventPool) {
         cudaEvent_t ev;
         TC_CUDA(cudaEventCreate(&ev));
         c->pool.push_back(ev);
     }
-    Control h{};
-    TC_CUDA(cudaMemcpy(&h, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost));
-    c->prof_skip0 = h.skipped_passes;
-    c->prof_skipbytes0 = h.skipped_bytes;
+    int rc = read_control(c);
+    if (rc) return rc;
+    c->prof_skip0 = c->h_ctl->skipped_passes;
+    c->prof_skipbytes0 = c->h_ctl->skipped_bytes;
     c->pool_used = 0;
     c->stamps.clear();
     c->prof = true;
@@ -600,7 +599,8 @@ int tc_profile_begin(tc_ctx *c) {
 
 int tc_profile_end(tc_ctx *c, tc_profile_t *out) {
     if (!c || !out) return TC_ERR_INVAL;
-    TC_CUDA(cudaDeviceSynchronize());
+    int rc = read_control(c);
+    if (rc) return rc;
     std::memset(out, 0, sizeof(*out));
     double ms[kStages] = {0};
     for (size_t k = 1; k < c->stamps.size(); ++k) {
@@ -610,13 +610,12 @@ int tc_profile_end(tc_ctx *c, tc_profile_t *out) {
         TC_CUDA(cudaEventElapsedTime(&t, c->stamps[k - 1].ev, c->stamps[k].ev));
         ms[stg] += t;
     }
-    Control h{};
-    TC_CUDA(cudaMemcpy(&h, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost));
     out->batches = c->prof_batches;
     out->launches = c->launches - c->prof_launch0;
     out->sort_pass_launches = c->prof_sort_launches;
-    out->sort_pass_skipped = h.skipped_passes - c->prof_skip0;
-    out->sort_pass_bytes = c->prof_sort_bytes - (h.skipped_bytes - c->prof_skipbytes0);
+    out->sort_pass_skipped = c->h_ctl->skipped_passes - c->prof_skip0;
+    out->sort_pass_bytes =
+        c->prof_sort_bytes - (c->h_ctl->skipped_bytes - c->prof_skipbytes0);
     out->overflow = c->prof_overflow ? 1 : 0;
     out->ms_prep = ms[kPrep];
     out->ms_arc_sort = ms[kArcSort];
@@ -662,7 +661,8 @@ int tc_rank_all(const uint64_t *d_edges, uint64_t w, uint32_t vertex_bits, uint3
     const u64 prep_blocks = std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
     prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, prep_smem(s, false), st>>>(
         d_edges, s, a0, nullptr, nullptr, plans, err, 0);
-    sort_plan_kernel<<<1, 256, 0, st>>>(plans, s.npa, (u32)(2 * w), s.bits_a, 0, 0, 8);
+    sort_plan_kernel<<<dim3((unsigned)s.npa, 1), 256, 0, st>>>(plans, s.npa, (u32)(2 * w),
+                                                               s.bits_a, 0, 0, 8);
     for (int p = 0; p < s.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(a0, a1, nullptr, nullptr, (u32)(2 * w),
                                                          s.sha + p * s.bits_a, p, &plans[0],
@@ -770,7 +770,8 @@ extern "C" int tc_rank_all_noalloc(const uint64_t *d_edges, uint64_t w, uint32_t
     const u64 prep_blocks = std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
     prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, prep_smem(s, false), st>>>(
         d_edges, s, a0, nullptr, nullptr, plans, err, 0);
-    sort_plan_kernel<<<1, 256, 0, st>>>(plans, s.npa, (u32)(2 * w), s.bits_a, 0, 0, 8);
+    sort_plan_kernel<<<dim3((unsigned)s.npa, 1), 256, 0, st>>>(plans, s.npa, (u32)(2 * w),
+                                                               s.bits_a, 0, 0, 8);
     for (int p = 0; p < s.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(a0, a1, nullptr, nullptr, (u32)(2 * w),
                                                          s.sha + p * s.bits_a, p, &plans[0],

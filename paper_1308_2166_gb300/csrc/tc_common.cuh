@@ -33,6 +33,17 @@ struct Control {
     u64 skipped_bytes;   // their algorithmic bytes (not moved)
     u32 epoch;           // batches enqueued (accepted or not); tags directory entries
     u32 pad;
+    // Lemma 3.1 aggregate of the state after the last accepted batch:
+    // S (128-bit), closed count, |E|.
+    u64 est[4];
+};
+
+// Per-batch accumulator at the head of the zeroed scratch: the sweep adds
+// each estimator's final chi (if closed) into it; the batch's finish step
+// commits it to Control::est when the batch is accepted.
+struct BatchAcc {
+    u64 s_lo, s_hi, closed;
+    u64 pad[29];  // keeps what follows 256-byte aligned
 };
 
 // Per-vertex segment directory entry: the run [start, end) of vertex x in a

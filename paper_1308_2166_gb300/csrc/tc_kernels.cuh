@@ -15,6 +15,8 @@
 //     ekeys[2][w]   uint64 Step-3 keys, sorted on (src, dst):
 //                   keys-only form  u << (B+bw) | v << bw | pos  when
 //                   2B + bw <= 64, else  u << B | v  with evals[2][w] = pos.
+//     adir, edir    per-vertex directories over the sorted arcs / keys
+//                   (vertex ids < 2^kDirMaxBits), epoch-tagged.
 //   bw = bits of w-1, B = vertex id bits.
 #pragma once
 
@@ -96,10 +98,11 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(
     }
 }
 
-// In-batch repeats are adjacent after the Step-3 sort.
+// In-batch repeats are adjacent after the Step-3 sort (used when vertex ids
+// are too wide for directories; index_kernel does this check otherwise).
 __global__ void dups_kernel(const u64 *ekeys0, const u64 *ekeys1, const SortPlan *plans,
                             BatchShape s, u32 *err) {
-    const u64 *E = plans[1].sel[kMaxPasses] ? ekeys1 : ekeys0;
+    const u64 *E = plan_final_sel(&plans[1]) ? ekeys1 : ekeys0;
     const u32 drop = s.ekeys_only ? s.bw : 0;
     for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x + 1; k < s.w;
          k += (u64)gridDim.x * blockDim.x) {
@@ -109,25 +112,6 @@ __global__ void dups_kernel(const u64 *ekeys0, const u64 *ekeys1, const SortPlan
         }
     }
 }
-
-// ---------------------------------------------------------------------------
-// Fused Steps 1-3 per estimator.
-// ---------------------------------------------------------------------------
-struct SweepArgs {
-    const u64 *W;
-    u64 *f1, *f2, *chi;
-    u32 *flags;
-    u64 r;
-    const u64 *arcs0, *arcs1;
-    const u64 *ekeys0, *ekeys1;
-    const u32 *evals0, *evals1;
-    const SortPlan *plans;
-    const DirEntry *adir, *edir;  // null unless vertex ids < 2^kDirMaxBits
-    Control *ctl;
-    BatchShape s;
-    uint2 key;
-    u32 stream;
-};
 
 constexpr u32 kDirMaxBits = 26;
 
@@ -150,14 +134,14 @@ __device__ __forceinline__ void dir_segment(const DirEntry *dir, u32 epoch, u64 
 
 // ---------------------------------------------------------------------------
 // Directories over the two sorted arrays, plus the in-batch repeat check.
-// For the arcs, x = src; for the Step-3 keys, x = the smaller endpoint.
+// For the arcs, x = src; for the Step-3 keys, x = the smaller endpoint.  The
+// first element of a run writes (epoch, start), the last one writes end.
 // ---------------------------------------------------------------------------
-// The first element of a run writes (epoch, start), the last one writes end.
 __global__ void index_kernel(const u64 *arcs0, const u64 *arcs1, const u64 *ekeys0,
                              const u64 *ekeys1, const SortPlan *plans, BatchShape s,
                              DirEntry *adir, DirEntry *edir, const Control *ctl, u32 *err) {
-    const u64 *__restrict__ arcs = plans[0].sel[kMaxPasses] ? arcs1 : arcs0;
-    const u64 *__restrict__ E = plans[1].sel[kMaxPasses] ? ekeys1 : ekeys0;
+    const u64 *__restrict__ arcs = plan_final_sel(&plans[0]) ? arcs1 : arcs0;
+    const u64 *__restrict__ E = plan_final_sel(&plans[1]) ? ekeys1 : ekeys0;
     const u32 epoch = ctl->epoch + 1;
     const u64 n_a = 2ull * s.w, n_e = s.w;
     const u64 nverts = 1ull << s.B;
@@ -191,30 +175,81 @@ __global__ void index_kernel(const u64 *arcs0, const u64 *arcs1, const u64 *ekey
     if (dup) set_error(err, kErrInput);
 }
 
+// ---------------------------------------------------------------------------
+// 128-bit sums (Lemma 3.1's S can exceed 64 bits).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void add_u128(u64 *dst_lo_hi, u64 lo, u64 hi) {
+    const u64 old = atomicAdd((unsigned long long *)dst_lo_hi, (unsigned long long)lo);
+    const u64 carry = (old + lo < old) ? 1ull : 0ull;
+    if (hi + carry)
+        atomicAdd((unsigned long long *)(dst_lo_hi + 1), (unsigned long long)(hi + carry));
+}
+
+// Sum a per-thread (lo, hi) pair and a count over the CTA; result valid in
+// thread 0.  s_* hold blockDim.x / 32 words each.
+__device__ __forceinline__ void block_sum_u128(u64 &lo, u64 &hi, u64 &cnt, u64 *s_lo, u64 *s_hi,
+                                               u64 *s_cnt) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const u64 l2 = __shfl_down_sync(0xFFFFFFFFu, lo, o);
+        const u64 h2 = __shfl_down_sync(0xFFFFFFFFu, hi, o);
+        cnt += __shfl_down_sync(0xFFFFFFFFu, cnt, o);
+        const u64 s = lo + l2;
+        hi += h2 + (s < lo ? 1 : 0);
+        lo = s;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_lo[warp] = lo;
+        s_hi[warp] = hi;
+        s_cnt[warp] = cnt;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        lo = 0;
+        hi = 0;
+        cnt = 0;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+            const u64 s = lo + s_lo[k];
+            hi += s_hi[k] + (s < lo ? 1 : 0);
+            lo = s;
+            cnt += s_cnt[k];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Fused Steps 1-3 per estimator, with the Lemma 3.1 reduction of the
+// resulting state folded in.
+// ---------------------------------------------------------------------------
+struct SweepArgs {
+    const u64 *W;
+    u64 *f1, *f2, *chi;
+    u32 *flags;
+    u64 r;
+    const u64 *arcs0, *arcs1;
+    const u64 *ekeys0, *ekeys1;
+    const u32 *evals0, *evals1;
+    const SortPlan *plans;
+    const DirEntry *adir, *edir;  // null unless vertex ids < 2^kDirMaxBits
+    Control *ctl;
+    BatchAcc *acc;                // per-batch S / closed accumulator (zeroed)
+    BatchShape s;
+    uint2 key;
+    u32 stream;
+};
+
 constexpr int kSweepThreads = 256;
 
-// Fused Steps 1-3 for one estimator per thread.  kDir: segment lookups from
-// the directories (vertex ids < 2^26), else binary search on the sorted
-// arrays.
+// One estimator: Steps 1-3 of Sec. 4 applied to its state in place.
 template <bool kDir>
-__global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArgs a) {
-    if (ld_relaxed(&a.ctl->err)) return;  // rejected batch: state stays as it was
-    const u64 i = (u64)blockIdx.x * kSweepThreads + threadIdx.x;
-    if (i >= a.r) return;
-    const BatchShape s = a.s;
-    const u64 m = a.ctl->m;
-    const u32 epoch = a.ctl->epoch + 1;
-    const DrawKey dk{a.key, (u32)a.ctl->batches, a.stream};
-    const u64 *__restrict__ arcs = a.plans[0].sel[kMaxPasses] ? a.arcs1 : a.arcs0;
-    const bool e_sel = a.plans[1].sel[kMaxPasses] != 0;
-    const u64 *__restrict__ E = e_sel ? a.ekeys1 : a.ekeys0;
-    const u32 *__restrict__ EV = e_sel ? a.evals1 : a.evals0;
+__device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 epoch,
+                                          const DrawKey &dk, const u64 *__restrict__ arcs,
+                                          const u64 *__restrict__ E, const u32 *__restrict__ EV,
+                                          u64 &f1, u64 &f2, u64 &chi, u32 &fl) {
+    const BatchShape &s = a.s;
     const u64 n_arcs = 2ull * s.w;
     const u32 wm1 = s.w - 1;
     const u64 wmask = (1ull << s.bw) - 1;
-
-    u64 f1 = a.f1[i], f2 = a.f2[i], chi = a.chi[i];
-    u32 fl = a.flags[i];
 
     // ---- Step 1 (Sec. 4.2): level-1 reservoir over E u W
     const u64 x = draw_bounded(dk, (u32)i, kStep1, m + s.w);
@@ -289,112 +324,76 @@ __global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArgs a) {
         }
         if (found && (!new2 || q > p2)) fl |= TC_FLAG_CLOSED;
     }
-
-    a.f1[i] = f1;
-    a.f2[i] = f2;
-    a.chi[i] = chi;
-    a.flags[i] = fl;
 }
 
-// Close the batch: count it if accepted, record the error otherwise.
-struct Mailbox {
-    u32 err;      // first device-side error since the host last cleared it
-    u32 pad;
-    u64 m;
-    u64 batches;
-};
+// One estimator per thread.  kDir: segment lookups from the directories,
+// else binary search on the sorted arrays.  Adds sum(chi over closed) and
+// the closed count of the new state into a.acc.
+template <bool kDir>
+__global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArgs a) {
+    __shared__ u64 s_lo[kSweepThreads / 32], s_hi[kSweepThreads / 32], s_cnt[kSweepThreads / 32];
+    if (ld_relaxed(&a.ctl->err)) return;  // rejected batch: state stays as it was
+    const u64 i = (u64)blockIdx.x * kSweepThreads + threadIdx.x;
+    u64 add = 0, closed = 0;
+    if (i < a.r) {
+        const u64 m = a.ctl->m;
+        const u32 epoch = a.ctl->epoch + 1;
+        const DrawKey dk{a.key, (u32)a.ctl->batches, a.stream};
+        const u64 *arcs = plan_final_sel(&a.plans[0]) ? a.arcs1 : a.arcs0;
+        const bool e_sel = plan_final_sel(&a.plans[1]) != 0;
+        const u64 *E = e_sel ? a.ekeys1 : a.ekeys0;
+        const u32 *EV = e_sel ? a.evals1 : a.evals0;
+        u64 f1 = a.f1[i], f2 = a.f2[i], chi = a.chi[i];
+        u32 fl = a.flags[i];
+        sweep_one<kDir>(a, i, m, epoch, dk, arcs, E, EV, f1, f2, chi, fl);
+        a.f1[i] = f1;
+        a.f2[i] = f2;
+        a.chi[i] = chi;
+        a.flags[i] = fl;
+        if (fl & TC_FLAG_CLOSED) {
+            add = chi;
+            closed = 1;
+        }
+    }
+    u64 hi = 0;
+    block_sum_u128(add, hi, closed, s_lo, s_hi, s_cnt);
+    if (threadIdx.x == 0) {
+        if (add | hi) add_u128(&a.acc->s_lo, add, hi);
+        if (closed) atomicAdd((unsigned long long *)&a.acc->closed, (unsigned long long)closed);
+    }
+}
 
-__global__ void finish_kernel(Control *ctl, Mailbox *mbox, u64 w) {
+// Close the batch: if accepted, count it and commit the estimate of the new
+// state; otherwise record the error (state, |E|, batch counter and the
+// committed estimate stay as they were).
+__global__ void finish_kernel(Control *ctl, const BatchAcc *acc, u64 w) {
     const u32 e = ctl->err;
     if (e) {
         if (!ctl->sticky) ctl->sticky = e;
     } else {
         ctl->m += w;
         ctl->batches += 1;
+        ctl->est[0] = acc->s_lo;
+        ctl->est[1] = acc->s_hi;
+        ctl->est[2] = acc->closed;
+        ctl->est[3] = ctl->m;
     }
     ctl->epoch += 1;
     ctl->err = 0;
-    mbox->err = ctl->sticky;
-    mbox->m = ctl->m;
-    mbox->batches = ctl->batches;
-}
-
-// ---------------------------------------------------------------------------
-// Estimate (Lemma 3.1): S = sum of chi over closed estimators, in 128 bits.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void add_u128(u64 *dst_lo_hi, u64 lo, u64 hi) {
-    const u64 old = atomicAdd((unsigned long long *)dst_lo_hi, (unsigned long long)lo);
-    const u64 carry = (old + lo < old) ? 1ull : 0ull;
-    if (hi + carry) atomicAdd((unsigned long long *)(dst_lo_hi + 1), (unsigned long long)(hi + carry));
-}
-
-// Sum a per-thread (lo, hi) pair over the CTA; result valid in thread 0.
-__device__ __forceinline__ void block_sum_u128(u64 &lo, u64 &hi, u64 *s_lo, u64 *s_hi) {
-    for (int o = 16; o > 0; o >>= 1) {
-        const u64 l2 = __shfl_down_sync(0xFFFFFFFFu, lo, o);
-        const u64 h2 = __shfl_down_sync(0xFFFFFFFFu, hi, o);
-        const u64 s = lo + l2;
-        hi += h2 + (s < lo ? 1 : 0);
-        lo = s;
-    }
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        s_lo[warp] = lo;
-        s_hi[warp] = hi;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        lo = 0;
-        hi = 0;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
-            const u64 s = lo + s_lo[k];
-            hi += s_hi[k] + (s < lo ? 1 : 0);
-            lo = s;
-        }
-    }
-}
-
-constexpr int kReduceThreads = 256;
-
-// out[0..1] = S (lo, hi), out[2] = closed count (out[0..2] zeroed before).
-// out[3] = |E| (read from the control block).
-__global__ void __launch_bounds__(kReduceThreads) estimate_kernel(const u64 *chi, const u32 *flags,
-                                                                  u64 r, const Control *ctl,
-                                                                  u64 *out) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) out[3] = ctl->m;
-    __shared__ u64 s_lo[kReduceThreads / 32], s_hi[kReduceThreads / 32];
-    u64 lo = 0, hi = 0, nc = 0;
-    for (u64 i = (u64)blockIdx.x * kReduceThreads + threadIdx.x; i < r;
-         i += (u64)gridDim.x * kReduceThreads) {
-        if (flags[i] & TC_FLAG_CLOSED) {
-            const u64 c = chi[i];
-            const u64 s = lo + c;
-            hi += (s < lo) ? 1 : 0;
-            lo = s;
-            ++nc;
-        }
-    }
-    for (int o = 16; o > 0; o >>= 1) nc += __shfl_down_sync(0xFFFFFFFFu, nc, o);
-    __shared__ u64 s_nc[kReduceThreads / 32];
-    if ((threadIdx.x & 31) == 0) s_nc[threadIdx.x >> 5] = nc;
-    block_sum_u128(lo, hi, s_lo, s_hi);
-    if (threadIdx.x == 0) {
-        u64 t = 0;
-        for (int k = 0; k < kReduceThreads / 32; ++k) t += s_nc[k];
-        add_u128(out, lo, hi);
-        if (t) atomicAdd((unsigned long long *)(out + 2), (unsigned long long)t);
-    }
 }
 
 // Median-of-means groups: CTA k sums group k = [k*r/g, (k+1)*r/g) into
 // out[2k], out[2k+1] (128-bit).
+constexpr int kReduceThreads = 256;
+
 __global__ void __launch_bounds__(kReduceThreads) group_sum_kernel(const u64 *chi, const u32 *flags,
                                                                    u64 r, u32 g, u64 *out) {
-    __shared__ u64 s_lo[kReduceThreads / 32], s_hi[kReduceThreads / 32];
+    __shared__ u64 s_lo[kReduceThreads / 32], s_hi[kReduceThreads / 32],
+        s_cnt[kReduceThreads / 32];
     const u64 k = blockIdx.x;
     const u64 lo_i = (u64)(((unsigned __int128)k * r) / g);
     const u64 hi_i = (u64)(((unsigned __int128)(k + 1) * r) / g);
-    u64 lo = 0, hi = 0;
+    u64 lo = 0, hi = 0, cnt = 0;
     for (u64 i = lo_i + threadIdx.x; i < hi_i; i += kReduceThreads) {
         if (flags[i] & TC_FLAG_CLOSED) {
             const u64 s = lo + chi[i];
@@ -402,7 +401,7 @@ __global__ void __launch_bounds__(kReduceThreads) group_sum_kernel(const u64 *ch
             lo = s;
         }
     }
-    block_sum_u128(lo, hi, s_lo, s_hi);
+    block_sum_u128(lo, hi, cnt, s_lo, s_hi, s_cnt);
     if (threadIdx.x == 0) {
         out[2 * k] = lo;
         out[2 * k + 1] = hi;
@@ -424,7 +423,7 @@ __global__ void __launch_bounds__(kRankThreads) rank_out_kernel(
     u32 *src_out, u32 *dst_out, u32 *pos_out, u32 *rank_out) {
     __shared__ u64 s_seed;
     __shared__ u64 s_wmax[kRankThreads / 32];
-    const u64 *arcs = plan->sel[kMaxPasses] ? arcs1 : arcs0;
+    const u64 *arcs = plan_final_sel(plan) ? arcs1 : arcs0;
     const u64 n = 2ull * s.w;
     const u64 t0 = (u64)blockIdx.x * kRankTile;
     const u32 wm1 = s.w - 1;

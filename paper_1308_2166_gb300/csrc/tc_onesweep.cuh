@@ -54,9 +54,9 @@ struct SortPlan {
     u32 counts[kMaxPasses][kMaxRadix];   // digit histograms (filled by the key build)
     u32 offsets[kMaxPasses][kMaxRadix];  // exclusive bucket offsets
     u32 skip[kMaxPasses];                // 1 if every key has the same digit
-    u32 sel[kMaxPasses + 1];             // ping-pong buffer holding keys before pass p
+    u32 npass;                           // passes of this sort
     u32 tile_counter[kMaxPasses];
-    u32 pad[7];
+    u32 pad[15];
 };
 
 // Tiles whose look-back statuses one pass keeps (rounded up to whole
@@ -92,44 +92,49 @@ __device__ __forceinline__ u32 block_exclusive_sum(u32 x, u32 *s_tmp) {
     return before + inc - x;
 }
 
-// Turn the histograms of `npass` passes over `n` keys (digit width `bits`)
-// into bucket offsets, skip flags and buffer selections.  One CTA of 256
-// threads per plan; blockIdx.x selects the plan.
+// Turn the histogram of one pass over `n` keys (digit width `bits`) into
+// bucket offsets and its skip flag.  Grid (passes, 2): blockIdx.x is the
+// pass, blockIdx.y the plan; 256 threads per block.
 __global__ void __launch_bounds__(256) sort_plan_kernel(SortPlan *plans, int npass0, u32 n0,
                                                          u32 bits0, int npass1, u32 n1,
                                                          u32 bits1) {
     __shared__ u32 s_tmp[8];
-    SortPlan *plan = plans + blockIdx.x;
-    const int npass = blockIdx.x == 0 ? npass0 : npass1;
-    const u32 n = blockIdx.x == 0 ? n0 : n1;
-    const u32 radix = 1u << (blockIdx.x == 0 ? bits0 : bits1);
+    const int j = blockIdx.y;
+    SortPlan *plan = plans + j;
+    const int npass = j == 0 ? npass0 : npass1;
+    const int p = blockIdx.x;
+    if (p == 0 && threadIdx.x == 0) plan->npass = (u32)npass;
+    if (p >= npass) return;
+    const u32 n = j == 0 ? n0 : n1;
+    const u32 radix = 1u << (j == 0 ? bits0 : bits1);
     const u32 per = (radix + 255) / 256;  // digits per thread
     const u32 d0 = threadIdx.x * per;
-    for (int p = 0; p < npass; ++p) {
-        u32 local = 0;
-        bool single = false;
-        for (u32 k = 0; k < per; ++k) {
-            const u32 c = d0 + k < radix ? plan->counts[p][d0 + k] : 0u;
-            local += c;
-            single |= (c == n);
-        }
-        u32 run = block_exclusive_sum<256>(local, s_tmp);
-        for (u32 k = 0; k < per && d0 + k < radix; ++k) {
-            plan->offsets[p][d0 + k] = run;
-            run += plan->counts[p][d0 + k];
-        }
-        const int any_single = __syncthreads_or(single);
-        if (threadIdx.x == 0) plan->skip[p] = any_single ? 1u : 0u;
+    u32 local = 0;
+    bool single = false;
+    for (u32 k = 0; k < per; ++k) {
+        const u32 c = d0 + k < radix ? plan->counts[p][d0 + k] : 0u;
+        local += c;
+        single |= (c == n);
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        u32 sel = 0;
-        for (int p = 0; p < kMaxPasses; ++p) {
-            plan->sel[p] = sel;
-            if (p < npass && !plan->skip[p]) sel ^= 1u;
-        }
-        plan->sel[kMaxPasses] = sel;  // where the sorted keys end up
+    u32 run = block_exclusive_sum<256>(local, s_tmp);
+    for (u32 k = 0; k < per && d0 + k < radix; ++k) {
+        plan->offsets[p][d0 + k] = run;
+        run += plan->counts[p][d0 + k];
     }
+    const int any_single = __syncthreads_or(single);
+    if (threadIdx.x == 0) plan->skip[p] = any_single ? 1u : 0u;
+}
+
+// Ping-pong buffer holding the keys before pass `upto` (0 or 1): one flip
+// per pass that was not skipped.  upto = plan->npass gives the sorted keys.
+__device__ __forceinline__ u32 plan_sel(const SortPlan *plan, int upto) {
+    u32 sel = 0;
+    for (int q = 0; q < upto; ++q) sel ^= plan->skip[q] ? 0u : 1u;
+    return sel;
+}
+
+__device__ __forceinline__ u32 plan_final_sel(const SortPlan *plan) {
+    return plan_sel(plan, (int)plan->npass);
 }
 
 // Warp ranking methods: how a warp finds the lanes holding the same digit.
@@ -164,7 +169,7 @@ struct OnesweepSmem {
 };
 
 // One digit pass.  keys/vals ping-pong between buffers 0 and 1 as selected
-// by plan->sel[pass]; `lookback` holds this pass's status words, tile-major
+// by plan_sel(plan, pass); `lookback` holds this pass's status words, tile-major
 // ([tiles][2^kBits]), zeroed before the pass.
 template <int kBits, bool kHasValues, int kRank>
 __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits <= 8 ? 4 : 3))
@@ -187,7 +192,7 @@ __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits <= 8 ? 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     auto &S = *reinterpret_cast<OnesweepSmem<kBits, kHasValues, kRank> *>(smem_raw);
 
-    const u32 sel = plan->sel[pass];
+    const u32 sel = plan_sel(plan, pass);
     const u64 *__restrict__ kin = sel ? keys1 : keys0;
     u64 *__restrict__ kout = sel ? keys0 : keys1;
     const u32 *__restrict__ vin = sel ? vals1 : vals0;
