@@ -35,7 +35,7 @@ constexpr size_t kEventPool = 8192;
 enum Stage { kStart = -1, kPrep = 0, kArcSort, kEdgeSort, kDups, kSweep, kFinish, kEstimate,
              kStages };
 
-using PassFn = void (*)(u64 *, u64 *, u32 *, u32 *, u32, u32, int, SortPlan *, u32 *, u32 *,
+using PassFn = void (*)(u64 *, u64 *, u32 *, u32 *, u32, u32, u32, int, SortPlan *, u32 *, u32 *,
                         Control *);
 
 struct PassKernel {
@@ -147,6 +147,13 @@ u64 lookback_words_max(u64 w, u32 B) {
         for (u32 be : kDigitChoices)
             best = std::max(best, lookback_words(make_shape(w, B, ba, be), true));
     return best;
+}
+
+// Digit bits of pass p that can be nonzero when the sort's live key bits
+// are `total` and digits are `bits` wide.
+u32 live_bits(u32 total, u32 bits, int p) {
+    const u32 lo = (u32)p * bits;
+    return lo >= total ? 0u : std::min(bits, total - lo);
 }
 
 size_t prep_smem(const BatchShape &s, bool edges) {
@@ -272,13 +279,13 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
     const PassKernel ke = select_pass(s.bits_e, !s.ekeys_only, c->rank_method);
     for (int p = 0; p < s.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(
-            c->arcs[0], c->arcs[1], nullptr, nullptr, (u32)(2 * w), s.sha + p * s.bits_a, p,
+            c->arcs[0], c->arcs[1], nullptr, nullptr, (u32)(2 * w), s.sha + p * s.bits_a, live_bits(s.B, s.bits_a, p), p,
             &plans[0], lb + (u64)p * la, &c->ctl->err, c->ctl);
     stamp(c, st, kArcSort);
     u32 *lbe = lb + (u64)s.npa * la;
     for (int p = 0; p < s.npe; ++p)
         ke.fn<<<(unsigned)te, ke.threads, ke.smem, st>>>(
-            c->ekeys[0], c->ekeys[1], c->evals[0], c->evals[1], (u32)w, s.she + p * s.bits_e, p,
+            c->ekeys[0], c->ekeys[1], c->evals[0], c->evals[1], (u32)w, s.she + p * s.bits_e, live_bits(2 * s.B, s.bits_e, p), p,
             &plans[1], lbe + (u64)p * le, &c->ctl->err, c->ctl);
     stamp(c, st, kEdgeSort);
     if (c->adir) {
@@ -665,7 +672,7 @@ int tc_rank_all(const uint64_t *d_edges, uint64_t w, uint32_t vertex_bits, uint3
                                                                s.bits_a, 0, 0, 8);
     for (int p = 0; p < s.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(a0, a1, nullptr, nullptr, (u32)(2 * w),
-                                                         s.sha + p * s.bits_a, p, &plans[0],
+                                                         s.sha + p * s.bits_a, live_bits(s.B, s.bits_a, p), p, &plans[0],
                                                          lb + (u64)p * la, err, nullptr);
     const u64 rb = (2 * w + kRankTile - 1) / kRankTile;
     rank_out_kernel<<<(unsigned)rb, kRankThreads, 0, st>>>(d_edges, a0, a1, &plans[0], s, d_src,
@@ -774,7 +781,7 @@ extern "C" int tc_rank_all_noalloc(const uint64_t *d_edges, uint64_t w, uint32_t
                                                                s.bits_a, 0, 0, 8);
     for (int p = 0; p < s.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(a0, a1, nullptr, nullptr, (u32)(2 * w),
-                                                         s.sha + p * s.bits_a, p, &plans[0],
+                                                         s.sha + p * s.bits_a, live_bits(s.B, s.bits_a, p), p, &plans[0],
                                                          lb + (u64)p * la, err, nullptr);
     const u64 rb = (2 * w + kRankTile - 1) / kRankTile;
     rank_out_kernel<<<(unsigned)rb, kRankThreads, 0, st>>>(d_edges, a0, a1, &plans[0], s, d_src,

@@ -73,7 +73,7 @@ __device__ __forceinline__ u32 digit_bits(u64 key, u32 shift, u32 mask) {
 // `s_tmp` holds kThreads/32 words.  Must be reached by every thread of the
 // CTA; threads at or beyond kThreads contribute nothing.
 template <int kThreads>
-__device__ __forceinline__ u32 block_exclusive_sum(u32 x, u32 *s_tmp) {
+__device__ __forceinline__ u32 block_exclusive_sum(u32 x, u32 *s_tmp, u32 *total = nullptr) {
     constexpr int kWarps = kThreads / 32;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     u32 inc = x;
@@ -84,11 +84,15 @@ __device__ __forceinline__ u32 block_exclusive_sum(u32 x, u32 *s_tmp) {
     }
     if (lane == 31 && warp < kWarps) s_tmp[warp] = inc;
     __syncthreads();
-    u32 before = 0;
+    u32 before = 0, all = 0;
 #pragma unroll
-    for (int w2 = 0; w2 < kWarps; ++w2)
-        if (w2 < warp) before += s_tmp[w2];
+    for (int w2 = 0; w2 < kWarps; ++w2) {
+        const u32 v = s_tmp[w2];
+        if (w2 < warp) before += v;
+        all += v;
+    }
     __syncthreads();
+    if (total) *total = all;
     return before + inc - x;
 }
 
@@ -174,7 +178,10 @@ struct OnesweepSmem {
 template <int kBits, bool kHasValues, int kRank>
 __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits <= 8 ? 4 : 3))
     onesweep_pass_kernel(u64 *keys0, u64 *keys1, u32 *vals0, u32 *vals1, u32 n, u32 shift,
-                         int pass, SortPlan *plan, u32 *lookback, u32 *err, Control *ctl) {
+                         u32 live, int pass, SortPlan *plan, u32 *lookback, u32 *err,
+                         Control *ctl) {
+    // live: digit bits that can be nonzero in this pass (higher key bits are
+    // zero for every key), so ballot ranking votes only on those.
     using Shape = OnesweepShape<kBits>;
     constexpr int kRadix = Shape::kRadix;
     constexpr u32 kMask = kRadix - 1;
@@ -230,34 +237,28 @@ __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits <= 8 ? 
             atomicAdd(&S.cursor[warp][digit_bits(keys[j], shift, kMask)], 1u);
     __syncthreads();
 
-    // -- per digit: tile count, publish it, turn warp counts into slots
-    u32 local = 0;
-    if (ranker) {
+    // -- per digit (thread tid owns digits q*256 + tid, so a warp's status
+    //    words are consecutive): tile count, publish it, turn warp counts
+    //    into staging slots
+    u32 carry = 0;  // keys of this tile in earlier digit slices
 #pragma unroll
-        for (int q = 0; q < kDPT; ++q) {
-            const int d = tid * kDPT + q;
-            u32 c = 0;
+    for (int q = 0; q < kDPT; ++q) {
+        const int d = q * kRankThreads8 + tid;
+        u32 c = 0;
 #pragma unroll
-            for (int w2 = 0; w2 < kSortWarps; ++w2) c += S.cursor[w2][d];
-            st_relaxed(lookback + (u64)tile * kRadix + d, (tile == 0 ? kFlagPre : kFlagAgg) | c);
-            S.count[d] = c;
-            local += c;
-        }
-    }
-    u32 run = block_exclusive_sum<kRankThreads8>(local, S.scan_tmp);
-    if (ranker) {
+        for (int w2 = 0; w2 < kSortWarps; ++w2) c += S.cursor[w2][d];
+        st_relaxed(lookback + (u64)tile * kRadix + d, (tile == 0 ? kFlagPre : kFlagAgg) | c);
+        S.count[d] = c;
+        u32 total = 0;
+        const u32 excl = carry + block_exclusive_sum<kRankThreads8>(c, S.scan_tmp, &total);
+        carry += total;
+        S.tile_excl[d] = excl;
+        u32 slot = excl;
 #pragma unroll
-        for (int q = 0; q < kDPT; ++q) {
-            const int d = tid * kDPT + q;
-            S.tile_excl[d] = run;
-            u32 slot = run;
-#pragma unroll
-            for (int w2 = 0; w2 < kSortWarps; ++w2) {
-                const u32 t = S.cursor[w2][d];
-                S.cursor[w2][d] = slot;
-                slot += t;
-            }
-            run += S.count[d];
+        for (int w2 = 0; w2 < kSortWarps; ++w2) {
+            const u32 t = S.cursor[w2][d];
+            S.cursor[w2][d] = slot;
+            slot += t;
         }
     }
     __syncthreads();
@@ -276,6 +277,7 @@ __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits <= 8 ? 
                 peers = __ballot_sync(0xFFFFFFFFu, valid);
 #pragma unroll
                 for (int b = 0; b < kBits; ++b) {
+                    if ((u32)b >= live) break;
                     const bool bit = (d >> b) & 1u;
                     const u32 vote = __ballot_sync(0xFFFFFFFFu, bit);
                     peers &= bit ? vote : ~vote;
@@ -326,7 +328,7 @@ __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits <= 8 ? 
 #pragma unroll
             for (int q = 0; q < kDPT; ++q) {
                 if (!(pending & (1u << q))) continue;
-                const int d = tid * kDPT + q;
+                const int d = q * kRankThreads8 + tid;
                 // statuses of tiles next, next-1, ...: independent loads, each
                 // coalesced across the warp's consecutive digits
                 u32 st[kLookWin];
@@ -358,7 +360,7 @@ __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits <= 8 ? 
         }
 #pragma unroll
         for (int q = 0; q < kDPT; ++q) {
-            const int d = tid * kDPT + q;
+            const int d = q * kRankThreads8 + tid;
             if (tile > 0)
                 st_relaxed(lookback + (u64)tile * kRadix + d,
                            kFlagPre | ((sum[q] + S.count[d]) & kValMask));
