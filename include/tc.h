@@ -197,6 +197,66 @@ int tc_rank_all(const uint64_t *d_edges, uint64_t w, uint32_t vertex_bits,
                 uint32_t *d_src, uint32_t *d_dst, uint32_t *d_pos,
                 uint32_t *d_rank, void *cuda_stream);
 
+/* ---- Many streams at once -------------------------------------------------
+ * A tc_multi holds S independent streams (Sec. 4's bulkUpdateAll applied to
+ * each stream's own edges with its own r_s estimators) whose state stays
+ * resident in HBM.  One round folds one batch per stream into all of them
+ * with a single segmented launch sequence (one key build, one pair of radix
+ * sorts over every stream's keys, one repeat check, one estimator sweep,
+ * one bookkeeping launch).  Every stream's state is bit-identical to running
+ * it alone through tc_create_ex / tc_process_batch with the same seed,
+ * stream id and batch boundaries. */
+typedef struct tc_multi tc_multi;
+
+/* S = n_streams >= 1 streams; HOST arrays r[S] (estimators, 1..2^32-1),
+ * seeds[S], stream_ids[S]; w_max_round = most edges one round may carry in
+ * total; vertex_bits as in tc_create_ex.  Requires
+ * bits(S-1) + 2*vertex_bits <= 64 and bits(S-1) + vertex_bits +
+ * bits(w_max_round-1) + 1 <= 64 (sort keys carry the stream index).
+ * Errors: TC_ERR_INVAL, TC_ERR_NOMEM, TC_ERR_CUDA. */
+int tc_multi_create(uint32_t n_streams, const uint64_t *r, const uint64_t *seeds,
+                    const uint32_t *stream_ids, uint64_t w_max_round, uint32_t vertex_bits,
+                    tc_multi **out);
+
+/* Enqueue one round on `cuda_stream`: d_edges (DEVICE) holds the streams'
+ * batches concatenated in stream order; offsets (HOST, S+1 entries,
+ * offsets[0] = 0, non-decreasing) delimit stream s's batch as
+ * [offsets[s], offsets[s+1]); an empty range leaves the stream untouched.
+ * A batch that breaks the stream model (see TC_ERR_INPUT) is rejected for
+ * its stream only; that stream's state stays as it was and tc_multi_sync
+ * reports it.  d_edges is borrowed until the stream passes this round. */
+int tc_multi_process_async(tc_multi *M, const uint64_t *d_edges, const uint64_t *offsets,
+                           void *cuda_stream);
+
+/* Wait for all rounds; write each stream's first error since the last sync
+ * (TC_OK or a TC_ERR_* code) to the HOST array stream_errors[S] (may be
+ * NULL), clear them, and return the first nonzero one. */
+int tc_multi_sync(tc_multi *M, int32_t *stream_errors);
+
+/* Lemma 3.1's estimate of stream s, as tc_estimate.  Synchronises. */
+int tc_multi_estimate(tc_multi *M, uint32_t s, tc_estimate_t *out);
+
+/* Enqueue the copy of every stream's estimate words (S low, S high, closed
+ * count, |E|; four uint64 per stream, stream-major) to the DEVICE array
+ * d_out[4*S] on `cuda_stream`. */
+int tc_multi_estimates_async(tc_multi *M, uint64_t *d_out, void *cuda_stream);
+
+/* Stream s's estimator state into HOST arrays of r[s] entries (as
+ * tc_get_state), and its counters.  Synchronise. */
+int tc_multi_get_state(tc_multi *M, uint32_t s, uint64_t *f1, uint64_t *f2, uint64_t *chi,
+                       uint32_t *flags);
+int tc_multi_get_counters(tc_multi *M, uint32_t s, uint64_t *r, uint64_t *m,
+                          uint64_t *batches);
+
+/* Sort tuning for later rounds, as tc_tune (ranking 3 is treated as 2). */
+int tc_multi_tune(tc_multi *M, uint32_t arc_digit_bits, uint32_t edge_digit_bits,
+                  uint32_t ranking);
+
+/* Library kernels launched by this object so far. */
+int tc_multi_launches(tc_multi *M, uint64_t *launches);
+
+void tc_multi_destroy(tc_multi *M);
+
 /* Largest batch tc_rank_all_noalloc accepts. */
 #define TC_NOALLOC_MAX_EDGES (1u << 18)
 

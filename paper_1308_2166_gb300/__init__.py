@@ -31,6 +31,9 @@ EXPORTS = (
     "tc_sync", "tc_estimate", "tc_estimate_async", "tc_estimate_mom", "tc_get_state",
     "tc_get_counters", "tc_profile_begin", "tc_profile_end", "tc_tune", "tc_destroy",
     "tc_strerror", "tc_rank_all", "tc_rank_all_noalloc",
+    "tc_multi_create", "tc_multi_process_async", "tc_multi_sync", "tc_multi_estimate",
+    "tc_multi_estimates_async", "tc_multi_get_state", "tc_multi_get_counters",
+    "tc_multi_tune", "tc_multi_launches", "tc_multi_destroy",
 )
 
 
@@ -90,6 +93,17 @@ def load(path: str | None = None):
         "tc_strerror": (ctypes.c_char_p, [I]),
         "tc_rank_all": (I, [P, U64, U32, P, P, P, P, P]),
         "tc_rank_all_noalloc": (I, [P, U64, U32, P, P, P, P, P]),
+        "tc_multi_create": (I, [U32, P, P, P, U64, U32, ctypes.POINTER(P)]),
+        "tc_multi_process_async": (I, [P, P, P, P]),
+        "tc_multi_sync": (I, [P, P]),
+        "tc_multi_estimate": (I, [P, U32, ctypes.POINTER(tc_estimate_t)]),
+        "tc_multi_estimates_async": (I, [P, P, P]),
+        "tc_multi_get_state": (I, [P, U32, P, P, P, P]),
+        "tc_multi_get_counters": (I, [P, U32, ctypes.POINTER(U64), ctypes.POINTER(U64),
+                                      ctypes.POINTER(U64)]),
+        "tc_multi_tune": (I, [P, U32, U32, U32]),
+        "tc_multi_launches": (I, [P, ctypes.POINTER(U64)]),
+        "tc_multi_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -282,3 +296,84 @@ def tc_rank_all_noalloc(d_edges, w: int, vertex_bits: int, d_src, d_dst, d_pos, 
     _check(load().tc_rank_all_noalloc(_ptr(d_edges), w, vertex_bits, _ptr(d_src), _ptr(d_dst),
                                       _ptr(d_pos), _ptr(d_rank), stream or None),
            "tc_rank_all_noalloc")
+
+
+class MultiStream:
+    """Owning wrapper around a tc_multi: S independent streams, one round at a
+    time (one batch per stream, concatenated on the device)."""
+
+    def __init__(self, r, seeds, stream_ids, w_max_round: int, vertex_bits: int = 32):
+        import numpy as np
+        self.S = len(r)
+        self.r = np.ascontiguousarray(r, dtype=np.uint64)
+        sd = np.ascontiguousarray(seeds, dtype=np.uint64)
+        si = np.ascontiguousarray(stream_ids, dtype=np.uint32)
+        h = ctypes.c_void_p()
+        _check(load().tc_multi_create(self.S, self.r.ctypes.data, sd.ctypes.data, si.ctypes.data,
+                                      w_max_round, vertex_bits, ctypes.byref(h)),
+               "tc_multi_create")
+        self.h = h.value
+
+    def process_async(self, d_edges, offsets, stream: int = 0):
+        import numpy as np
+        off = np.ascontiguousarray(offsets, dtype=np.uint64)
+        if off.size != self.S + 1:
+            raise ValueError("offsets needs S+1 entries")
+        ptr = _ptr(d_edges) if int(off[-1]) else None
+        _check(load().tc_multi_process_async(self.h, ptr, off.ctypes.data, stream or None),
+               "tc_multi_process_async")
+
+    def sync(self):
+        """Per-stream error codes since the last sync (raises on none)."""
+        import numpy as np
+        errs = np.zeros(self.S, dtype=np.int32)
+        load().tc_multi_sync(self.h, errs.ctypes.data)
+        return errs
+
+    def estimate(self, s: int) -> dict:
+        out = tc_estimate_t()
+        _check(load().tc_multi_estimate(self.h, s, ctypes.byref(out)), "tc_multi_estimate")
+        return {"S": out.sum_lo | (out.sum_hi << 64), "N": out.num_lo | (out.num_hi << 64),
+                "r": out.r, "m": out.m, "n_closed": out.n_closed, "batches": out.batches,
+                "tau_hat": out.tau_hat}
+
+    def estimates_async(self, d_out, stream: int = 0):
+        _check(load().tc_multi_estimates_async(self.h, _ptr(d_out), stream or None),
+               "tc_multi_estimates_async")
+
+    def state(self, s: int):
+        import numpy as np
+        n = int(self.r[s])
+        f1 = np.empty(n, dtype=np.uint64)
+        f2 = np.empty(n, dtype=np.uint64)
+        chi = np.empty(n, dtype=np.uint64)
+        fl = np.empty(n, dtype=np.uint32)
+        _check(load().tc_multi_get_state(self.h, s, f1.ctypes.data, f2.ctypes.data,
+                                         chi.ctypes.data, fl.ctypes.data), "tc_multi_get_state")
+        return f1, f2, chi, fl
+
+    def counters(self, s: int):
+        r, m, b = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().tc_multi_get_counters(self.h, s, ctypes.byref(r), ctypes.byref(m),
+                                            ctypes.byref(b)), "tc_multi_get_counters")
+        return r.value, m.value, b.value
+
+    def tune(self, arc_digit_bits=0, edge_digit_bits=0, ranking=0):
+        _check(load().tc_multi_tune(self.h, arc_digit_bits, edge_digit_bits, ranking),
+               "tc_multi_tune")
+
+    def launches(self) -> int:
+        v = ctypes.c_uint64()
+        _check(load().tc_multi_launches(self.h, ctypes.byref(v)), "tc_multi_launches")
+        return v.value
+
+    def close(self):
+        if self.h:
+            load().tc_multi_destroy(self.h)
+            self.h = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

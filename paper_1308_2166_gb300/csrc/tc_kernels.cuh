@@ -48,7 +48,7 @@ struct BatchShape {
 // ---------------------------------------------------------------------------
 constexpr int kPrepThreads = 256;
 
-__global__ void __launch_bounds__(kPrepThreads) prep_kernel(
+static __global__ void __launch_bounds__(kPrepThreads) prep_kernel(
     const u64 *__restrict__ W, BatchShape s, u64 *__restrict__ arcs0, u64 *__restrict__ ekeys0,
     u32 *__restrict__ evals0, SortPlan *plans, u32 *err, int build_edges) {
     extern __shared__ u32 h[];
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kPrepThreads) prep_kernel(
 
 // In-batch repeats are adjacent after the Step-3 sort (used when vertex ids
 // are too wide for directories; index_kernel does this check otherwise).
-__global__ void dups_kernel(const u64 *ekeys0, const u64 *ekeys1, const SortPlan *plans,
+static __global__ void dups_kernel(const u64 *ekeys0, const u64 *ekeys1, const SortPlan *plans,
                             BatchShape s, u32 *err) {
     const u64 *E = plan_final_sel(&plans[1]) ? ekeys1 : ekeys0;
     const u32 drop = s.ekeys_only ? s.bw : 0;
@@ -137,7 +137,7 @@ __device__ __forceinline__ void dir_segment(const DirEntry *dir, u32 epoch, u64 
 // For the arcs, x = src; for the Step-3 keys, x = the smaller endpoint.  The
 // first element of a run writes (epoch, start), the last one writes end.
 // ---------------------------------------------------------------------------
-__global__ void index_kernel(const u64 *arcs0, const u64 *arcs1, const u64 *ekeys0,
+static __global__ void index_kernel(const u64 *arcs0, const u64 *arcs1, const u64 *ekeys0,
                              const u64 *ekeys1, const SortPlan *plans, BatchShape s,
                              DirEntry *adir, DirEntry *edir, const Control *ctl, u32 *err) {
     const u64 *__restrict__ arcs = plan_final_sel(&plans[0]) ? arcs1 : arcs0;
@@ -330,7 +330,7 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
 // else binary search on the sorted arrays.  Adds sum(chi over closed) and
 // the closed count of the new state into a.acc.
 template <bool kDir>
-__global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArgs a) {
+static __global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArgs a) {
     __shared__ u64 s_lo[kSweepThreads / 32], s_hi[kSweepThreads / 32], s_cnt[kSweepThreads / 32];
     if (ld_relaxed(&a.ctl->err)) return;  // rejected batch: state stays as it was
     const u64 i = (u64)blockIdx.x * kSweepThreads + threadIdx.x;
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArgs a) {
 // Close the batch: if accepted, count it and commit the estimate of the new
 // state; otherwise record the error (state, |E|, batch counter and the
 // committed estimate stay as they were).
-__global__ void finish_kernel(Control *ctl, const BatchAcc *acc, u64 w) {
+static __global__ void finish_kernel(Control *ctl, const BatchAcc *acc, u64 w) {
     const u32 e = ctl->err;
     if (e) {
         if (!ctl->sticky) ctl->sticky = e;
@@ -386,7 +386,7 @@ __global__ void finish_kernel(Control *ctl, const BatchAcc *acc, u64 w) {
 // out[2k], out[2k+1] (128-bit).
 constexpr int kReduceThreads = 256;
 
-__global__ void __launch_bounds__(kReduceThreads) group_sum_kernel(const u64 *chi, const u32 *flags,
+static __global__ void __launch_bounds__(kReduceThreads) group_sum_kernel(const u64 *chi, const u32 *flags,
                                                                    u64 r, u32 g, u64 *out) {
     __shared__ u64 s_lo[kReduceThreads / 32], s_hi[kReduceThreads / 32],
         s_cnt[kReduceThreads / 32];
@@ -418,7 +418,7 @@ constexpr int kRankThreads = 256;
 constexpr int kRankItems = 4;
 constexpr int kRankTile = kRankThreads * kRankItems;
 
-__global__ void __launch_bounds__(kRankThreads) rank_out_kernel(
+static __global__ void __launch_bounds__(kRankThreads) rank_out_kernel(
     const u64 *W, const u64 *arcs0, const u64 *arcs1, const SortPlan *plan, BatchShape s,
     u32 *src_out, u32 *dst_out, u32 *pos_out, u32 *rank_out) {
     __shared__ u64 s_seed;

@@ -99,7 +99,7 @@ __device__ __forceinline__ u32 block_exclusive_sum(u32 x, u32 *s_tmp, u32 *total
 // Turn the histogram of one pass over `n` keys (digit width `bits`) into
 // bucket offsets and its skip flag.  Grid (passes, 2): blockIdx.x is the
 // pass, blockIdx.y the plan; 256 threads per block.
-__global__ void __launch_bounds__(256) sort_plan_kernel(SortPlan *plans, int npass0, u32 n0,
+static __global__ void __launch_bounds__(256) sort_plan_kernel(SortPlan *plans, int npass0, u32 n0,
                                                          u32 bits0, int npass1, u32 n1,
                                                          u32 bits1) {
     __shared__ u32 s_tmp[8];
@@ -176,7 +176,7 @@ struct OnesweepSmem {
 // by plan_sel(plan, pass); `lookback` holds this pass's status words, tile-major
 // ([tiles][2^kBits]), zeroed before the pass.
 template <int kBits, bool kHasValues, int kRank>
-__global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits <= 8 ? 4 : 3))
+static __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits <= 8 ? 4 : 3))
     onesweep_pass_kernel(u64 *keys0, u64 *keys1, u32 *vals0, u32 *vals1, u32 n, u32 shift,
                          u32 live, int pass, SortPlan *plan, u32 *lookback, u32 *err,
                          Control *ctl) {
