@@ -64,7 +64,7 @@ def _args():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    p.add_argument("--workload", choices=["rmat20", "tiny"], default="rmat20")
+    p.add_argument("--workload", choices=["rmat20", "tiny", "multi512"], default="rmat20")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=None)
     return p.parse_args()
@@ -382,6 +382,146 @@ def run_gpu(args, rank, world, local_rank):
     return 0
 
 
+def run_multi(args, rank, world, local_rank):
+    """512 independent Chung-Lu streams advanced round by round.
+
+    Per-stream batch w_s = min(w_cap, len_s // rounds) so that every stream
+    takes part in every round (streams of uneven length advance at uneven
+    rates); w_cap is picked by timing a few rounds of each candidate.  Three
+    ways to run the same rounds, on fresh state each, timed on the device:
+      back_to_back  one tc_process_batch_async per stream per round
+                    (a native loop over 512 single-stream contexts);
+      batched       one tc_multi_process_async per round;
+      graph         the round captured once as a CUDA graph, replayed per
+                    round after a device copy of that round's edges into the
+                    captured buffer (the copy is inside the timed region).
+    Outputs of the three are compared estimator by estimator at the end.
+    """
+    import torch
+    import paper_1308_2166_gb300 as tc
+    import synth
+    from paper_1308_2166_gb300 import build
+
+    torch.cuda.set_device(local_rank)
+    build.build()
+    tc.load()
+    S, T = 512, max(2, min(args.steps, 16))
+    caps = (1024, 2048, 4096)
+    streams, r, n = synth.multi_streams(S, per_stream_edges=T * max(caps), seed=1)
+    B = int(max(1, int(n.max() - 1).bit_length()))
+    seeds = np.arange(1, S + 1, dtype=np.uint64)
+    sids = np.arange(S, dtype=np.uint32)
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+
+    def rounds_for(cap):
+        ws = [min(cap, x.size // T) for x in streams]
+        offs = np.concatenate([[0], np.cumsum(ws)]).astype(np.uint64)
+        rounds, parts_all = [], []
+        for k in range(T):
+            parts = [streams[s][k * ws[s]:(k + 1) * ws[s]] for s in range(S)]
+            rounds.append(torch.from_numpy(np.concatenate(parts).view(np.int64)).cuda())
+            parts_all.append(parts)
+        return ws, offs, rounds, parts_all
+
+    def time_batched(cap, nrounds, graph=False):
+        ws, offs, rounds, _ = rounds_for(cap)
+        M = tc.MultiStream(r, seeds, sids, w_max_round=int(offs[-1]), vertex_bits=B)
+        buf = torch.empty_like(rounds[0])
+        if graph:
+            M.capture(buf, offs, sh)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for k in range(nrounds):
+                if graph:
+                    buf.copy_(rounds[k], non_blocking=True)
+                    M.replay(sh)
+                else:
+                    M.process_async(rounds[k], offs, sh)
+            ev1.record(stream)
+        stream.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        errs = M.sync()
+        assert not errs.any(), "batched round rejected a stream"
+        return M, ms, int(offs[-1]) * nrounds, M.launches()
+
+    # autotune the per-stream batch cap on a few rounds (untimed for the result)
+    tune = {}
+    for cap in caps:
+        M, ms, edges, _ = time_batched(cap, 3)
+        tune[cap] = edges / (ms / 1e3)
+        M.close()
+    cap = max(tune, key=tune.get)
+    ws, offs, rounds, parts_all = rounds_for(cap)
+    edges_total = int(offs[-1]) * T
+
+    sampler = ClockSampler(local_rank)
+    Mg, ms_graph, _, launches_graph = time_batched(cap, T, graph=True)
+    clocks = sampler.stop()
+    Mb, ms_batched, _, launches_b = time_batched(cap, T, graph=False)
+
+    # back to back: one single-stream context per stream
+    ctxs = [tc.tc_create_ex(int(r[s]), int(seeds[s]), int(sids[s]), max(1, ws[s]), B)
+            for s in range(S)]
+    dev_parts = []
+    for k in range(T):
+        base = rounds[k]
+        views, o = [], 0
+        for s in range(S):
+            views.append(base[o:o + ws[s]])
+            o += ws[s]
+        dev_parts.append(views)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+        for k in range(T):
+            tc.tc_process_batches_async(ctxs, dev_parts[k], sh)
+        ev1.record(stream)
+    stream.synchronize()
+    ms_b2b = ev0.elapsed_time(ev1)
+
+    identical = True
+    for s in range(S):
+        a = Mg.state(s)
+        b = Mb.state(s)
+        c = tc.tc_get_state(ctxs[s])
+        for x, y, z in zip(a, b, c):
+            if not (np.array_equal(x, y) and np.array_equal(x, z)):
+                identical = False
+    for cx in ctxs:
+        tc.tc_destroy(cx)
+    Mg.close()
+    Mb.close()
+    val = edges_total / (ms_graph / 1e3)
+    line = {
+        "metric": "aggregate edges/s, 512 streams advanced together (round = one CUDA graph)",
+        "value": val, "unit": UNIT, "n_gpus": 1, "steps": T, "warmup": 0,
+        "ms_per_step": ms_graph / T, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"multi512: {S} Chung-Lu streams, gamma U[2.1,2.5], m log-uniform "
+                               f"[1e4,1e7], r log-uniform [2^10,2^16]; per-stream batch "
+                               f"min(w_cap, len/rounds)",
+                   "streams": S, "rounds": T, "w_cap": cap, "round_edges": int(offs[-1]),
+                   "estimators": int(r.sum()), "vertex_bits": B,
+                   "w_cap_table": {str(k): v for k, v in tune.items()}},
+        "updates_per_s": val * float(r.sum()) / float(offs[-1]) if offs[-1] else 0.0,
+        "batched_plain": {"value": edges_total / (ms_batched / 1e3), "ms_per_round": ms_batched / T,
+                          "launches_per_round": launches_b / T},
+        "back_to_back": {"value": edges_total / (ms_b2b / 1e3), "ms_per_round": ms_b2b / T,
+                         "launches_per_round": sum(1 for w in ws if w) * (5 + -(-B // 8) + -(-2 * B // 8))},
+        "speedup_vs_back_to_back": ms_b2b / ms_graph,
+        "identical_outputs": identical,
+        "gpu_launches": launches_graph,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     rank = int(os.environ.get("RANK", "0"))
@@ -389,6 +529,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "multi512":
+        return run_multi(args, rank, world, local_rank)
     return run_gpu(args, rank, world, local_rank)
 
 

@@ -101,6 +101,14 @@ int tc_process_batch(tc_ctx *c, const uint64_t *edges, uint64_t w);
 int tc_process_batch_async(tc_ctx *c, const uint64_t *d_edges, uint64_t w,
                            void *cuda_stream);
 
+/* tc_process_batch_async for n contexts in turn (a native loop, so that
+ * many independent streams can be advanced back to back without per-call
+ * host overhead): batch k = d_edges[k][0..w[k]) goes to ctxs[k]; w[k] == 0
+ * skips it.  Stops at the first error and returns it.  HOST arrays of n
+ * entries; the edge arrays are DEVICE pointers. */
+int tc_process_batches_async(tc_ctx *const *ctxs, const uint64_t *const *d_edges,
+                             const uint64_t *w, uint32_t n, void *cuda_stream);
+
 /* Wait for all work enqueued on the context and return the first
  * device-side error recorded since the last tc_sync (then clear it). */
 int tc_sync(tc_ctx *c);
@@ -227,6 +235,18 @@ int tc_multi_create(uint32_t n_streams, const uint64_t *r, const uint64_t *seeds
  * reports it.  d_edges is borrowed until the stream passes this round. */
 int tc_multi_process_async(tc_multi *M, const uint64_t *d_edges, const uint64_t *offsets,
                            void *cuda_stream);
+
+/* Capture one round as a CUDA graph on `cuda_stream` (which must not be
+ * capturing already) for the DEVICE buffer d_edges and the HOST offsets
+ * given here, without running it; tc_multi_replay then launches the whole
+ * round -- every kernel of it -- with one graph launch.  Each replay folds
+ * whatever d_edges holds at that moment into the streams (the caller
+ * refills the buffer between replays; the offsets stay fixed).  A new
+ * capture replaces the old one.  Errors: TC_ERR_INVAL (empty round, bad
+ * offsets), TC_ERR_CUDA. */
+int tc_multi_capture(tc_multi *M, const uint64_t *d_edges, const uint64_t *offsets,
+                     void *cuda_stream);
+int tc_multi_replay(tc_multi *M, void *cuda_stream);
 
 /* Wait for all rounds; write each stream's first error since the last sync
  * (TC_OK or a TC_ERR_* code) to the HOST array stream_errors[S] (may be

@@ -33,7 +33,8 @@ EXPORTS = (
     "tc_strerror", "tc_rank_all", "tc_rank_all_noalloc",
     "tc_multi_create", "tc_multi_process_async", "tc_multi_sync", "tc_multi_estimate",
     "tc_multi_estimates_async", "tc_multi_get_state", "tc_multi_get_counters",
-    "tc_multi_tune", "tc_multi_launches", "tc_multi_destroy",
+    "tc_multi_tune", "tc_multi_launches", "tc_multi_destroy", "tc_multi_capture",
+    "tc_multi_replay", "tc_process_batches_async",
 )
 
 
@@ -104,6 +105,9 @@ def load(path: str | None = None):
         "tc_multi_tune": (I, [P, U32, U32, U32]),
         "tc_multi_launches": (I, [P, ctypes.POINTER(U64)]),
         "tc_multi_destroy": (None, [P]),
+        "tc_multi_capture": (I, [P, P, P, P]),
+        "tc_multi_replay": (I, [P, P]),
+        "tc_process_batches_async": (I, [P, P, P, U32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -162,6 +166,16 @@ def tc_process_batch_async(ctx: int, d_edges, w: int | None = None, stream: int 
     w = _len(d_edges) if w is None else w
     _check(load().tc_process_batch_async(ctx, _ptr(d_edges) if w else None, w, stream or None),
            "tc_process_batch_async")
+
+
+def tc_process_batches_async(ctxs, d_edges, stream: int = 0) -> None:
+    """One batch per context, enqueued back to back by the library."""
+    n = len(ctxs)
+    cp = (ctypes.c_void_p * n)(*ctxs)
+    ep = (ctypes.c_void_p * n)(*[_ptr(d) if _len(d) else None for d in d_edges])
+    wv = (ctypes.c_uint64 * n)(*[_len(d) for d in d_edges])
+    _check(load().tc_process_batches_async(cp, ep, wv, n, stream or None),
+           "tc_process_batches_async")
 
 
 def tc_sync(ctx: int) -> None:
@@ -323,8 +337,18 @@ class MultiStream:
         _check(load().tc_multi_process_async(self.h, ptr, off.ctypes.data, stream or None),
                "tc_multi_process_async")
 
+    def capture(self, d_edges, offsets, stream: int):
+        """Capture one round (fixed buffer and offsets) as a CUDA graph."""
+        import numpy as np
+        off = np.ascontiguousarray(offsets, dtype=np.uint64)
+        _check(load().tc_multi_capture(self.h, _ptr(d_edges), off.ctypes.data, stream or None),
+               "tc_multi_capture")
+
+    def replay(self, stream: int = 0):
+        _check(load().tc_multi_replay(self.h, stream or None), "tc_multi_replay")
+
     def sync(self):
-        """Per-stream error codes since the last sync (raises on none)."""
+        """Per-stream error codes since the last sync."""
         import numpy as np
         errs = np.zeros(self.S, dtype=np.int32)
         load().tc_multi_sync(self.h, errs.ctypes.data)

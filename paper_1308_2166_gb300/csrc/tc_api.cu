@@ -98,19 +98,14 @@ int configure_kernels() {
     return TC_OK;
 }
 
-// Digit width and pass count for `live` key bits: fewest passes with digits
-// of at most 11 bits, then the narrowest compiled width giving that count
-// (or the width forced by tc_tune).
+// Digit width and pass count for `live` key bits: 8-bit digits unless
+// tc_tune forced another width (8-bit passes measured fastest on GB300: a
+// wider digit saves passes but each pass costs more than it saves).
 u32 pick_digits(u32 live, u32 forced, int &passes) {
-    if (forced) {
-        passes = (int)((live + forced - 1) / forced);
-        return forced;
-    }
-    passes = (int)((live + 10) / 11);
+    const u32 bits = forced ? forced : 8;
+    passes = (int)((live + bits - 1) / bits);
     if (passes < 1) passes = 1;
-    for (u32 b : kDigitChoices)
-        if (b * (u32)passes >= live) return b;
-    return 11;
+    return bits;
 }
 
 BatchShape make_shape(u64 w, u32 B, u32 force_a = 0, u32 force_e = 0) {
@@ -453,6 +448,16 @@ int tc_process_batch_async(tc_ctx *c, const uint64_t *d_edges, uint64_t w, void 
     if (w == 0) return TC_OK;
     if (w > c->cap_w) return TC_ERR_INVAL;
     return enqueue_batch(c, d_edges, w, (cudaStream_t)cuda_stream);
+}
+
+int tc_process_batches_async(tc_ctx *const *ctxs, const uint64_t *const *d_edges,
+                             const uint64_t *w, uint32_t n, void *cuda_stream) {
+    if (n && (!ctxs || !d_edges || !w)) return TC_ERR_INVAL;
+    for (uint32_t k = 0; k < n; ++k) {
+        const int rc = tc_process_batch_async(ctxs[k], d_edges[k], w[k], cuda_stream);
+        if (rc) return rc;
+    }
+    return TC_OK;
 }
 
 int tc_process_batch(tc_ctx *c, const uint64_t *edges, uint64_t w) {

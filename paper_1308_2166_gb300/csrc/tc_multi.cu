@@ -393,6 +393,9 @@ struct tc_multi {
     int ring = 0;
     u64 launches = 0;
     MStream *h_ms = nullptr;          // pinned host copy for reads
+    cudaGraphExec_t gexec = nullptr;  // captured round (tc_multi_capture)
+    u64 *g_eoff = nullptr;            // its fixed device offsets
+    u64 graph_launches = 0;           // kernels in the captured round
 };
 
 static void multi_free(tc_multi *M) {
@@ -415,6 +418,8 @@ static void multi_free(tc_multi *M) {
         if (M->ring_ev[k]) cudaEventDestroy(M->ring_ev[k]);
     }
     if (M->h_ms) cudaFreeHost(M->h_ms);
+    if (M->gexec) cudaGraphExecDestroy(M->gexec);
+    cudaFree(M->g_eoff);
     delete M;
 }
 
@@ -521,17 +526,29 @@ int tc_multi_tune(tc_multi *M, uint32_t arc_digit_bits, uint32_t edge_digit_bits
     return TC_OK;
 }
 
-int tc_multi_process_async(tc_multi *M, const uint64_t *d_edges, const uint64_t *offsets,
-                           void *cuda_stream) {
-    if (!M || !offsets || offsets[0] != 0) return TC_ERR_INVAL;
-    u64 wmax = 0;
+// Check a round's offsets; returns the largest batch through *wmax.
+static int check_round(const tc_multi *M, const uint64_t *offsets, u64 *wmax) {
+    if (!offsets || offsets[0] != 0) return TC_ERR_INVAL;
+    u64 w = 0;
     for (u32 s = 0; s < M->S; ++s) {
         if (offsets[s + 1] < offsets[s]) return TC_ERR_INVAL;
-        wmax = std::max<u64>(wmax, offsets[s + 1] - offsets[s]);
+        w = std::max<u64>(w, offsets[s + 1] - offsets[s]);
     }
-    const u64 Wt = offsets[M->S];
-    if (Wt > M->w_max) return TC_ERR_INVAL;
-    if (Wt == 0) return TC_OK;
+    if (offsets[M->S] > M->w_max) return TC_ERR_INVAL;
+    *wmax = w;
+    return TC_OK;
+}
+
+static int enqueue_round(tc_multi *M, const u64 *d_edges, const u64 *offsets, u64 wmax,
+                         const u64 *eoff, cudaStream_t st);
+
+int tc_multi_process_async(tc_multi *M, const uint64_t *d_edges, const uint64_t *offsets,
+                           void *cuda_stream) {
+    if (!M) return TC_ERR_INVAL;
+    u64 wmax = 0;
+    int rc = check_round(M, offsets, &wmax);
+    if (rc) return rc;
+    if (offsets[M->S] == 0) return TC_OK;
     if (!d_edges) return TC_ERR_INVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     // round offsets through a ring of pinned buffers
@@ -542,7 +559,51 @@ int tc_multi_process_async(tc_multi *M, const uint64_t *d_edges, const uint64_t 
     TCM_CUDA(cudaMemcpyAsync(M->eoff[slot], M->h_eoff[slot], (M->S + 1) * sizeof(u64),
                              cudaMemcpyHostToDevice, st));
     TCM_CUDA(cudaEventRecord(M->ring_ev[slot], st));
-    const u64 *eoff = M->eoff[slot];
+    return enqueue_round(M, d_edges, offsets, wmax, M->eoff[slot], st);
+}
+
+int tc_multi_capture(tc_multi *M, const uint64_t *d_edges, const uint64_t *offsets,
+                     void *cuda_stream) {
+    if (!M || !d_edges) return TC_ERR_INVAL;
+    u64 wmax = 0;
+    int rc = check_round(M, offsets, &wmax);
+    if (rc) return rc;
+    if (offsets[M->S] == 0) return TC_ERR_INVAL;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    if (M->gexec) {
+        cudaGraphExecDestroy(M->gexec);
+        M->gexec = nullptr;
+    }
+    if (!M->g_eoff) TCM_CUDA(cudaMalloc(&M->g_eoff, (M->S + 1) * sizeof(u64)));
+    TCM_CUDA(cudaMemcpy(M->g_eoff, offsets, (M->S + 1) * sizeof(u64), cudaMemcpyHostToDevice));
+    TCM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const u64 before = M->launches;
+    rc = enqueue_round(M, d_edges, offsets, wmax, M->g_eoff, st);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(st, &graph);
+    if (rc || ec != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return rc ? rc : TC_ERR_CUDA;
+    }
+    M->graph_launches = M->launches - before;
+    M->launches = before;
+    const cudaError_t ei = cudaGraphInstantiate(&M->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    return ei == cudaSuccess ? TC_OK : TC_ERR_CUDA;
+}
+
+int tc_multi_replay(tc_multi *M, void *cuda_stream) {
+    if (!M || !M->gexec) return TC_ERR_INVAL;
+    TCM_CUDA(cudaGraphLaunch(M->gexec, (cudaStream_t)cuda_stream));
+    M->launches += M->graph_launches;
+    return TC_OK;
+}
+
+}  // extern "C"
+
+static int enqueue_round(tc_multi *M, const u64 *d_edges, const u64 *offsets, u64 wmax,
+                         const u64 *eoff, cudaStream_t st) {
+    const u64 Wt = offsets[M->S];
 
     RoundShape rs{};
     rs.S = M->S;
@@ -607,6 +668,8 @@ int tc_multi_process_async(tc_multi *M, const uint64_t *d_edges, const uint64_t 
     M->launches += 5 + (u64)rs.npa + (u64)rs.npe;
     return TC_OK;
 }
+
+extern "C" {
 
 int tc_multi_sync(tc_multi *M, int32_t *stream_errors) {
     if (!M) return TC_ERR_INVAL;

@@ -38,3 +38,31 @@ def rmat20_single(gen_seed: int = 1, scale: int = 20) -> np.ndarray:
 def batches(keys: np.ndarray, w: int):
     """Split a stream into consecutive batches of w edges (last may be short)."""
     return [keys[i:i + w] for i in range(0, keys.size, w)]
+
+
+def multi_streams(S: int = 512, per_stream_edges: int = 32768, seed: int = 1,
+                  m_range=(1e4, 1e7), r_range=(2 ** 10, 2 ** 16), gamma_range=(2.1, 2.5),
+                  mean_degree: float = 16.0):
+    """S independent Chung-Lu streams for the batched multi-stream workload.
+
+    Stream s draws m_s log-uniform in m_range (its full length), r_s
+    log-uniform in r_range, exponent uniform in gamma_range, n_s = 2 m_s /
+    mean_degree vertices; only the first min(m_s, per_stream_edges) edges of
+    each stream are generated (the first distinct samples of its endpoint-
+    sampling process, relabelled and put in random order), which is all a
+    bounded number of rounds consumes.  Returns (streams, r, n).
+    """
+    rng = np.random.default_rng(seed)
+    lm = rng.uniform(np.log(m_range[0]), np.log(m_range[1]), size=S)
+    lr = rng.uniform(np.log(r_range[0]), np.log(r_range[1]), size=S)
+    gam = rng.uniform(gamma_range[0], gamma_range[1], size=S)
+    streams, rs, ns = [], [], []
+    for s in range(S):
+        m = int(np.exp(lm[s]))
+        n = max(64, int(2 * m / mean_degree))
+        k = min(m, per_stream_edges)
+        keys = chung_lu(n, float(gam[s]), 2.0 * m / n, k, seed=seed * 100_003 + s)
+        streams.append(finish(keys, n, seed=seed * 100_003 + s + 50_000))
+        rs.append(int(np.exp(lr[s])))
+        ns.append(n)
+    return streams, np.array(rs, dtype=np.uint64), np.array(ns, dtype=np.int64)

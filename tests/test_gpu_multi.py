@@ -110,3 +110,36 @@ def test_rejected_batch_affects_only_its_stream():
         assert M.counters(2)[2] == 1 and M.counters(0)[2] == 2
     finally:
         M.close()
+
+
+def test_captured_round_replays_match_oracle():
+    """One round captured as a CUDA graph, replayed with fresh batches."""
+    import torch
+    streams = _streams(5, seed=41)
+    r = [300, 10, 1000, 77, 512]
+    M = tc.MultiStream(r, [5, 6, 7, 8, 9], [9, 8, 7, 6, 5], w_max_round=5000, vertex_bits=12)
+    refs = [nbsi_bulk.BulkStream(r[s], seed=5 + s, stream=9 - s, vertex_bits=12)
+            for s in range(5)]
+    sizes = [200, 50, 0, 120, 300]
+    s_torch = torch.cuda.Stream()
+    try:
+        cur = [0] * 5
+        cat, offs, parts = _round(streams, cur, sizes)
+        buf = to_device(cat)
+        M.capture(buf, offs, s_torch.cuda_stream)
+        for rep in range(3):
+            if rep:
+                cat, offs2, parts = _round(streams, cur, sizes)
+                assert list(offs2) == list(offs)
+                with torch.cuda.stream(s_torch):
+                    buf.copy_(to_device(cat))
+            M.replay(s_torch.cuda_stream)
+            s_torch.synchronize()
+            for s in range(5):
+                if parts[s].size:
+                    refs[s].process_batch(parts[s])
+            assert not M.sync().any()
+            for s in range(5):
+                assert_state_equal(M.state(s), refs[s].state_arrays(), f"replay {rep} stream {s}")
+    finally:
+        M.close()
