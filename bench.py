@@ -508,7 +508,7 @@ def run_multi(args, rank, world, local_rank):
                    "streams": S, "rounds": T, "w_cap": cap, "round_edges": int(offs[-1]),
                    "estimators": int(r.sum()), "vertex_bits": B,
                    "w_cap_table": {str(k): v for k, v in tune.items()}},
-        "updates_per_s": val * float(r.sum()) / float(offs[-1]) if offs[-1] else 0.0,
+        "updates_per_s": float(sum(int(r[s2]) * ws[s2] for s2 in range(S))) * T / (ms_graph / 1e3),
         "batched_plain": {"value": edges_total / (ms_batched / 1e3), "ms_per_round": ms_batched / T,
                           "launches_per_round": launches_b / T},
         "back_to_back": {"value": edges_total / (ms_b2b / 1e3), "ms_per_round": ms_b2b / T,
