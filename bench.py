@@ -43,18 +43,22 @@ UNIT = "edges/s"
 
 # ncu DRAM traffic of the dominant kernel, per algorithmic byte, with the
 # hash of the source it was taken on (profiles/ holds the capture summary).
+# Taken from profiles/onesweep_pass_rmat20.md: DRAM read + write of one arc
+# and one edge pass over their algorithmic bytes (writes largely stay in L2).
 TRAFFIC = {
-    "onesweep_pass_kernel": None,
-    "sweep_kernel": None,
+    "onesweep_pass_kernel": {"src_hash": "a0d1e3856b242de9",
+                             "bytes_per_algorithmic_byte": 118.114048 / 201.326592},
 }
+
+# Sources the single-stream sort pass is built from.
+_SORT_SOURCES = ("tc_api.cu", "tc_common.cuh", "tc_onesweep.cuh")
 
 
 def _src_hash() -> str:
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_1308_2166_gb300", "csrc")
-    for f in sorted(os.listdir(cs)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(cs, f), "rb").read())
+    for f in _SORT_SOURCES:
+        h.update(open(os.path.join(cs, f), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -64,9 +68,11 @@ def _args():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    p.add_argument("--workload", choices=["rmat20", "tiny", "multi512"], default="rmat20")
+    p.add_argument("--workload", choices=["rmat20", "tiny", "multi512", "serve4096"], default="rmat20")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=None)
+    p.add_argument("--no-autotune", action="store_true",
+                   help="keep the library's default sort tuning (8-bit digits, ballot ranking)")
     return p.parse_args()
 
 
@@ -223,8 +229,11 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
     from paper_1308_2166_gb300 import autotune
-    tuning, tune_table = autotune.tune(dev_batches, r, cfg["vertex_bits"], seed=cfg["seed"] + 99,
-                                       reps=1, stream=sh)
+    if args.no_autotune:
+        tuning, tune_table = (8, 8, 2), {}
+    else:
+        tuning, tune_table = autotune.tune(dev_batches, r, cfg["vertex_bits"],
+                                           seed=cfg["seed"] + 99, reps=1, stream=sh)
     ctx = tc.tc_create_ex(r, cfg["seed"], rank, w, cfg["vertex_bits"])
     tc.tc_tune(ctx, *tuning)
     est_words = torch.zeros(4, dtype=torch.int64, device="cuda")
@@ -522,6 +531,200 @@ def run_multi(args, rank, world, local_rank):
     return 0
 
 
+class _ServeClient:
+    """Request generator for the serving workload: S concurrent streams, each
+    a rotation of one of the R-MAT base graphs (scale 14..22) read in batches
+    of log-uniform [1e3, 1e6] edges; a stream that has delivered its whole
+    graph closes and a fresh stream (new scale, r, seed) takes its place.
+    10% of requests are estimate queries."""
+
+    def __init__(self, srv, graphs, S, seed):
+        self.srv, self.graphs, self.S = srv, graphs, S
+        self.rng = np.random.default_rng(seed)
+        self.streams = [None] * S
+        self.sid = 0
+        self.out_edges = 0            # submitted, not yet completed batch edges
+        self.w_of = {}                # ticket -> (edges, r) of a batch
+        self.kind_of = {}
+        self.done = []                # completion arrays
+        for i in range(S):
+            self._open(i)
+
+    def _open(self, i):
+        sc = int(self.rng.integers(14, 23))
+        g = self.graphs[sc]
+        r = int(round(2 ** self.rng.uniform(10, 16)))
+        h, t = self.srv.open(r, int(self.rng.integers(1, 2**63)), self.sid)
+        self.sid += 1
+        m = g.numel()
+        self.streams[i] = {"h": h, "g": g, "m": m, "pos": int(self.rng.integers(0, m)),
+                           "left": m, "r": r}
+
+    def one(self):
+        """Submit one request (query or batch; close + reopen when spent)."""
+        i = int(self.rng.integers(0, self.S))
+        st = self.streams[i]
+        if self.rng.random() < 0.1:
+            t = self.srv.query(st["h"])
+            self.kind_of[t] = 3
+            return
+        if st["left"] == 0:
+            self.srv.close(st["h"])
+            self._open(i)
+            st = self.streams[i]
+        w = int(round(10 ** self.rng.uniform(3, 6)))
+        w = min(w, st["left"], st["m"] - st["pos"])
+        t = self.srv.submit(st["h"], st["g"][st["pos"]:st["pos"] + w])
+        st["pos"] = (st["pos"] + w) % st["m"]
+        st["left"] -= w
+        self.w_of[t] = (w, st["r"])
+        self.out_edges += w
+
+    def poll(self, wait_us=0):
+        c = self.srv.poll(wait_us)
+        if c.size:
+            for t in c["ticket"][c["kind"] == 2]:
+                w, _ = self.w_of.get(int(t), (0, 0))
+                self.out_edges -= w
+            self.done.append(c)
+        return c.size
+
+
+def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_round_streams=0,
+                 seed=7):
+    """Run one serving phase on a fresh server; returns measured figures.
+    rate: Poisson request rate (open loop); else closed loop keeping at most
+    cap_edges batch edges outstanding."""
+    srv = tc.Server(max_streams=S, vertex_bits=cfg["vertex_bits"],
+                    budget_bytes=cfg["budget_bytes"], w_max_round=cfg["w_max_round"],
+                    depth=cfg["depth"], max_round_streams=max_round_streams)
+    cl = _ServeClient(srv, graphs, S, seed)
+    srv.drain(600000)
+    cl.poll()
+    rng = np.random.default_rng(seed + 1)
+    t0 = time.perf_counter()
+    t_end = t0 + seconds
+    st0 = srv.stats()
+    if rate:
+        nxt = t0
+        while True:
+            now = time.perf_counter()
+            if now >= t_end:
+                break
+            while nxt <= now:
+                cl.one()
+                nxt += rng.exponential(1.0 / rate)
+            cl.poll(wait_us=int(max(0, min(nxt - time.perf_counter(), 5e-4)) * 1e6))
+    else:
+        while time.perf_counter() < t_end:
+            sub = 0
+            while cl.out_edges < cap_edges and sub < 64:
+                cl.one()
+                sub += 1
+            cl.poll(wait_us=0 if sub else 200)
+    srv.drain(600000)
+    cl.poll()
+    st1 = srv.stats()
+    srv.destroy()
+    comp = np.concatenate(cl.done) if cl.done else np.zeros(0)
+    # window: completions of requests submitted inside the phase
+    sub_ns = comp["t_submit_ns"]
+    first = int(np.min(sub_ns[comp["kind"] != 1])) if comp.size else 0
+    phase = comp[(comp["kind"] != 1) & (sub_ns >= first)]
+    batches = phase[phase["kind"] == 2]
+    queries = phase[phase["kind"] == 3]
+    ws = np.array([cl.w_of.get(int(t), (0, 0))[0] for t in batches["ticket"]], dtype=np.float64)
+    rs = np.array([cl.w_of.get(int(t), (0, 0))[1] for t in batches["ticket"]], dtype=np.float64)
+    span = (int(phase["t_done_ns"].max()) - first) / 1e9 if phase.size else 1.0
+    lat_b = (batches["t_done_ns"] - batches["t_submit_ns"]) / 1e6
+    lat_q = (queries["t_done_ns"] - queries["t_submit_ns"]) / 1e6
+    pct = (lambda a, q: float(np.percentile(a, q)) if a.size else None)
+    return {
+        "edges_per_s": float(ws.sum()) / span,
+        "updates_per_s": float((ws * rs).sum()) / span,
+        "seconds": span, "batches": int(batches.size), "queries": int(queries.size),
+        "rejected": int((batches["status"] != 0).sum()),
+        "edges": int(ws.sum()), "mean_batch": float(ws.mean()) if ws.size else 0.0,
+        "p50_batch_ms": pct(lat_b, 50), "p99_batch_ms": pct(lat_b, 99),
+        "p50_query_ms": pct(lat_q, 50), "p99_query_ms": pct(lat_q, 99),
+        "rounds": int(st1["rounds"] - st0["rounds"]),
+        "kernel_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
+        "max_round_edges": int(st1["max_round_edges"]),
+        "max_round_streams": int(st1["max_round_streams"]),
+        "admission_waits": int(st1["admission_waits"]),
+        "bytes_peak": int(st1["bytes_peak"]), "bytes_fixed": int(st1["bytes_fixed"]),
+        "opens": int(st1["opens"]), "closes": int(st1["closes"]),
+    }
+
+
+def run_serve(args, rank, world, local_rank):
+    """Serving: 4096 concurrent R-MAT streams (scale 14-22, edge factor 16),
+    batches of log-uniform [1e3, 1e6] edges, 10% estimate queries, state
+    resident in HBM, admission by a 120 GB budget, through tc_server
+    (continuous batching).  Phases, each on a fresh server and fresh streams:
+      saturation     closed loop (at most 3 rounds of edges outstanding):
+                     the served throughput -- the headline value;
+      back_to_back   the same closed loop with one stream per round (every
+                     batch folded by its own launch sequence, no batching);
+      poisson        open loop, Poisson arrivals at 70% of the saturation
+                     request rate: p50/p99 batch and query latency.
+    All times are host clock (submit to completion record), so the value is
+    end to end: host batch buffers (pinned) copied to HBM by the server."""
+    import torch
+    import paper_1308_2166_gb300 as tc
+    from paper_1308_2166_gb300 import build
+    from synth.device import rmat_device
+
+    torch.cuda.set_device(local_rank)
+    build.build()
+    tc.load()
+    S = 4096
+    graphs = {}
+    t = time.perf_counter()
+    for sc in range(14, 23):
+        keys = rmat_device(sc, 16, 0.57, 0.19, 0.19, seed=1000 + sc)
+        graphs[sc] = keys.cpu().pin_memory()
+        del keys
+        torch.cuda.empty_cache()
+    gen_s = time.perf_counter() - t
+    cfg = {"vertex_bits": 22, "budget_bytes": 120 << 30, "w_max_round": 1 << 23, "depth": 2}
+    secs = max(3.0, min(20.0, args.steps / 10.0))
+    sampler = ClockSampler(local_rank)
+    sat = _serve_phase(tc, graphs, cfg, S, secs, cap_edges=3 * cfg["w_max_round"])
+    clocks = sampler.stop()
+    b2b = _serve_phase(tc, graphs, cfg, S, max(3.0, secs / 2), cap_edges=3 * cfg["w_max_round"],
+                       max_round_streams=1)
+    req_rate = 0.7 * sat["edges_per_s"] / max(1.0, sat["mean_batch"]) / 0.9
+    poi = _serve_phase(tc, graphs, cfg, S, secs, rate=req_rate)
+    line = {
+        "metric": "aggregate edges/s served: 4096 concurrent streams, continuous batching",
+        "value": sat["edges_per_s"], "unit": UNIT, "n_gpus": 1, "steps": sat["rounds"],
+        "warmup": 0, "ms_per_step": 1e3 * sat["seconds"] / max(1, sat["rounds"]),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": "serve4096: 4096 concurrent R-MAT streams, scale U{14..22}, "
+                               "ef 16 (0.57,0.19,0.19,0.05), batches log-uniform [1e3,1e6] "
+                               "edges, 10% queries, r log-uniform [2^10,2^16], 120 GB budget",
+                   "streams": S, "w_max_round": cfg["w_max_round"], "depth": cfg["depth"],
+                   "vertex_bits": cfg["vertex_bits"], "budget_bytes": cfg["budget_bytes"],
+                   "phase_seconds": secs, "graph_gen_s": round(gen_s, 1),
+                   "base_graph_edges": {str(k): int(v.numel()) for k, v in graphs.items()}},
+        "updates_per_s": sat["updates_per_s"],
+        "saturation": sat,
+        "back_to_back": b2b,
+        "speedup_vs_back_to_back": sat["edges_per_s"] / max(1.0, b2b["edges_per_s"]),
+        "poisson": dict(poi, offered_requests_per_s=req_rate),
+        "p50_ms": poi["p50_batch_ms"], "p99_ms": poi["p99_batch_ms"],
+        "e2e": {"value": sat["edges_per_s"], "unit": UNIT, "h2d_bytes_per_step":
+                8 * sat["edges"] // max(1, sat["rounds"]),
+                "d2h_bytes_per_step": 48 * (sat["batches"] + sat["queries"]) // max(1, sat["rounds"])},
+        "gpu_launches": sat["kernel_launches"],
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     rank = int(os.environ.get("RANK", "0"))
@@ -531,6 +734,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload == "multi512":
         return run_multi(args, rank, world, local_rank)
+    if args.workload == "serve4096":
+        return run_serve(args, rank, world, local_rank)
     return run_gpu(args, rank, world, local_rank)
 
 
