@@ -43,7 +43,8 @@ extern "C" {
                                repeated inside the batch */
 #define TC_ERR_CUDA (-4)    /* a CUDA runtime call failed */
 #define TC_ERR_TIMEOUT (-5) /* a bounded device-side wait gave up */
-#define TC_ERR_RANGE (-6)   /* size beyond the fixed maximum of tc_rank_all_noalloc */
+#define TC_ERR_RANGE (-6)   /* size beyond a fixed maximum: tc_rank_all_noalloc's
+                               scratch, a tc_server's round or memory budget */
 
 /* Empty level-1 / level-2 edge in tc_get_state output. */
 #define TC_EMPTY_EDGE 0xFFFFFFFFFFFFFFFFull
@@ -236,6 +237,15 @@ int tc_multi_create(uint32_t n_streams, const uint64_t *r, const uint64_t *seeds
 int tc_multi_process_async(tc_multi *M, const uint64_t *d_edges, const uint64_t *offsets,
                            void *cuda_stream);
 
+/* As tc_multi_process_async, with each stream's batch in its own DEVICE
+ * buffer: d_batches (HOST array of S device pointers) and w (HOST array of
+ * S batch lengths; w[s] = 0 sits stream s out and d_batches[s] may then be
+ * NULL).  Lets a caller fold batches where they already lie without
+ * gathering them into one buffer.  Buffers are borrowed until the stream
+ * passes this round.  Errors as tc_multi_process_async. */
+int tc_multi_process_ptrs_async(tc_multi *M, const uint64_t *const *d_batches,
+                                const uint64_t *w, void *cuda_stream);
+
 /* Capture one round as a CUDA graph on `cuda_stream` (which must not be
  * capturing already) for the DEVICE buffer d_edges and the HOST offsets
  * given here, without running it; tc_multi_replay then launches the whole
@@ -276,6 +286,110 @@ int tc_multi_tune(tc_multi *M, uint32_t arc_digit_bits, uint32_t edge_digit_bits
 int tc_multi_launches(tc_multi *M, uint64_t *launches);
 
 void tc_multi_destroy(tc_multi *M);
+
+/* ---- Serving ---------------------------------------------------------------
+ * A tc_server takes requests from many concurrent streams as they arrive --
+ * open a stream, fold an edge batch, query the estimate, close -- and serves
+ * them with continuous batching: a native scheduler thread admits requests
+ * in arrival order as stream slots and device memory (within budget_bytes)
+ * free up, copies admitted batches to HBM on a copy stream while earlier
+ * rounds run, and, whenever fewer than `depth` rounds are in flight, forms
+ * the next round from every stream with admitted work (its queued queries,
+ * then at most one batch; round robin, up to w_max_round edges) and folds it
+ * with the multi-stream engine.  Estimator state stays in HBM from open to
+ * close.  A query is answered with the stream's Lemma 3.1 sums after exactly
+ * the batches submitted before it, so every result equals that of running
+ * the stream alone (tc_create_ex / tc_process_batch, same seed, stream id
+ * and batch boundaries), whatever else is in the mix.
+ *
+ * All calls are thread-safe.  Requests return a ticket at once; each request
+ * later yields one tc_completion_t through tc_server_poll. */
+typedef struct tc_server tc_server;
+
+#define TC_REQ_OPEN 1
+#define TC_REQ_BATCH 2
+#define TC_REQ_QUERY 3
+#define TC_REQ_CLOSE 4
+
+typedef struct {
+    uint32_t max_streams;  /* stream slots open at once, >= 1 */
+    uint32_t vertex_bits;  /* every stream's vertex ids < 2^vertex_bits (1..32) */
+    uint64_t budget_bytes; /* device memory the server may hold: engine scratch,
+                              round buffers, open streams' state (28 B per
+                              estimator) and admitted batches (8 B per edge) */
+    uint64_t w_max_round;  /* most edges one round folds (and the largest batch) */
+    uint32_t depth;        /* rounds in flight, 1..8; 0 means 2 */
+    uint32_t max_round_streams; /* most streams one round folds; 0 = max_streams
+                                   (1 serves one batch per round, back to back) */
+} tc_server_config_t;
+
+typedef struct {
+    uint64_t ticket;
+    uint32_t handle;
+    int32_t kind;          /* TC_REQ_* */
+    int32_t status;        /* TC_OK, TC_ERR_INPUT (batch rejected, stream
+                              unchanged), or the error that stopped the server */
+    uint32_t pad;
+    /* batch and query: the stream's state after this request, as
+     * tc_estimate: batch count, S = sum of closed chi (128-bit), closed
+     * count, |E|; zero for open and close */
+    uint64_t batches, sum_lo, sum_hi, n_closed, m;
+    /* host steady-clock nanoseconds since tc_server_create: submitted,
+     * admitted (slot/memory granted), completion recorded */
+    uint64_t t_submit_ns, t_admit_ns, t_done_ns;
+} tc_completion_t;
+
+typedef struct {
+    uint64_t rounds, kernel_launches;
+    uint64_t batches, rejected, edges, queries, opens, closes;
+    uint64_t streams_open;      /* now */
+    uint64_t requests_waiting;  /* not yet admitted, now */
+    uint64_t admission_waits;   /* head requests that had to wait for memory or a slot */
+    uint64_t max_round_edges, max_round_streams;
+    uint64_t bytes_budget, bytes_fixed, bytes_reserved, bytes_peak;
+} tc_server_stats_t;
+
+/* Errors: TC_ERR_INVAL (bad config; key bits as tc_multi_create with
+ * S = max_streams), TC_ERR_RANGE (budget below the fixed scratch),
+ * TC_ERR_NOMEM, TC_ERR_CUDA.  Uses the current CUDA device. */
+int tc_server_create(const tc_server_config_t *cfg, tc_server **out);
+
+/* Request a new stream with r estimators (1..2^32-1), Philox seed and stream
+ * id; *handle names it in later calls at once (requests may follow before
+ * the open is admitted).  TC_ERR_RANGE if its state can never fit. */
+int tc_server_open(tc_server *S, uint64_t r, uint64_t seed, uint32_t stream_id,
+                   uint32_t *handle, uint64_t *ticket);
+
+/* Submit a batch of w edges (HOST memory, (min << 32) | max, arrival order;
+ * pinned memory lets the copy overlap).  The buffer is borrowed until the
+ * batch's completion.  w = 0 completes as a no-op.  TC_ERR_INVAL for an
+ * unknown or closed handle, TC_ERR_RANGE for w > w_max_round or a batch that
+ * can never fit the budget.  A batch that breaks the stream model completes
+ * with TC_ERR_INPUT and leaves its stream as it was. */
+int tc_server_submit(tc_server *S, uint32_t handle, const uint64_t *h_edges, uint64_t w,
+                     uint64_t *ticket);
+
+/* Ask for the stream's estimate after every batch submitted before this call. */
+int tc_server_query(tc_server *S, uint32_t handle, uint64_t *ticket);
+
+/* Close the stream after its earlier requests; its slot and state memory
+ * return to the server.  The handle is invalid from this call on. */
+int tc_server_close(tc_server *S, uint32_t handle, uint64_t *ticket);
+
+/* Copy up to max_n completions, in completion order, to the HOST array out;
+ * wait up to wait_us microseconds if none is ready.  *n_out = count. */
+int tc_server_poll(tc_server *S, tc_completion_t *out, uint32_t max_n, uint32_t wait_us,
+                   uint32_t *n_out);
+
+/* Wait until every request submitted so far has completed (TC_ERR_TIMEOUT
+ * after timeout_ms milliseconds).  Returns the server's failure code, if any. */
+int tc_server_drain(tc_server *S, uint32_t timeout_ms);
+
+int tc_server_stats(tc_server *S, tc_server_stats_t *out);
+
+/* Stop the scheduler, wait for the rounds in flight and free everything;
+ * requests not yet in a round are dropped without completion. */
+void tc_server_destroy(tc_server *S);
 
 /* Largest batch tc_rank_all_noalloc accepts. */
 #define TC_NOALLOC_MAX_EDGES (1u << 18)

@@ -34,8 +34,13 @@ EXPORTS = (
     "tc_multi_create", "tc_multi_process_async", "tc_multi_sync", "tc_multi_estimate",
     "tc_multi_estimates_async", "tc_multi_get_state", "tc_multi_get_counters",
     "tc_multi_tune", "tc_multi_launches", "tc_multi_destroy", "tc_multi_capture",
-    "tc_multi_replay", "tc_process_batches_async",
+    "tc_multi_replay", "tc_process_batches_async", "tc_multi_process_ptrs_async",
+    "tc_server_create", "tc_server_open", "tc_server_submit", "tc_server_query",
+    "tc_server_close", "tc_server_poll", "tc_server_drain", "tc_server_stats",
+    "tc_server_destroy",
 )
+
+TC_REQ_OPEN, TC_REQ_BATCH, TC_REQ_QUERY, TC_REQ_CLOSE = 1, 2, 3, 4
 
 
 class TcError(RuntimeError):
@@ -60,6 +65,31 @@ class tc_profile_t(ctypes.Structure):
                 ("ms_edge_sort", ctypes.c_double), ("ms_dups", ctypes.c_double),
                 ("ms_sweep", ctypes.c_double), ("ms_finish", ctypes.c_double),
                 ("ms_estimate", ctypes.c_double)]
+
+
+class tc_server_config_t(ctypes.Structure):
+    _fields_ = [("max_streams", ctypes.c_uint32), ("vertex_bits", ctypes.c_uint32),
+                ("budget_bytes", ctypes.c_uint64), ("w_max_round", ctypes.c_uint64),
+                ("depth", ctypes.c_uint32), ("max_round_streams", ctypes.c_uint32)]
+
+
+class tc_completion_t(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("handle", ctypes.c_uint32),
+                ("kind", ctypes.c_int32), ("status", ctypes.c_int32), ("pad", ctypes.c_uint32),
+                ("batches", ctypes.c_uint64), ("sum_lo", ctypes.c_uint64),
+                ("sum_hi", ctypes.c_uint64), ("n_closed", ctypes.c_uint64),
+                ("m", ctypes.c_uint64), ("t_submit_ns", ctypes.c_uint64),
+                ("t_admit_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64)]
+
+
+_STATS_FIELDS = ("rounds", "kernel_launches", "batches", "rejected", "edges", "queries", "opens",
+                 "closes", "streams_open", "requests_waiting", "admission_waits",
+                 "max_round_edges", "max_round_streams", "bytes_budget", "bytes_fixed",
+                 "bytes_reserved", "bytes_peak")
+
+
+class tc_server_stats_t(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_uint64) for f in _STATS_FIELDS]
 
 
 _lib = None
@@ -108,6 +138,16 @@ def load(path: str | None = None):
         "tc_multi_capture": (I, [P, P, P, P]),
         "tc_multi_replay": (I, [P, P]),
         "tc_process_batches_async": (I, [P, P, P, U32, P]),
+        "tc_multi_process_ptrs_async": (I, [P, P, P, P]),
+        "tc_server_create": (I, [ctypes.POINTER(tc_server_config_t), ctypes.POINTER(P)]),
+        "tc_server_open": (I, [P, U64, U64, U32, ctypes.POINTER(U32), ctypes.POINTER(U64)]),
+        "tc_server_submit": (I, [P, U32, P, U64, ctypes.POINTER(U64)]),
+        "tc_server_query": (I, [P, U32, ctypes.POINTER(U64)]),
+        "tc_server_close": (I, [P, U32, ctypes.POINTER(U64)]),
+        "tc_server_poll": (I, [P, P, U32, U32, ctypes.POINTER(U32)]),
+        "tc_server_drain": (I, [P, U32]),
+        "tc_server_stats": (I, [P, ctypes.POINTER(tc_server_stats_t)]),
+        "tc_server_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -337,6 +377,22 @@ class MultiStream:
         _check(load().tc_multi_process_async(self.h, ptr, off.ctypes.data, stream or None),
                "tc_multi_process_async")
 
+    def process_ptrs_async(self, d_batches, stream: int = 0):
+        """One round with each stream's batch in its own device tensor
+        (None or an empty tensor sits the stream out)."""
+        import numpy as np
+        if len(d_batches) != self.S:
+            raise ValueError("need one batch (or None) per stream")
+        ptrs = np.zeros(self.S, dtype=np.uint64)
+        w = np.zeros(self.S, dtype=np.uint64)
+        for s, b in enumerate(d_batches):
+            if b is not None and b.numel():
+                ptrs[s] = _ptr(b)
+                w[s] = b.numel()
+        _check(load().tc_multi_process_ptrs_async(self.h, ptrs.ctypes.data, w.ctypes.data,
+                                                  stream or None),
+               "tc_multi_process_ptrs_async")
+
     def capture(self, d_edges, offsets, stream: int):
         """Capture one round (fixed buffer and offsets) as a CUDA graph."""
         import numpy as np
@@ -399,5 +455,99 @@ class MultiStream:
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+# numpy view of tc_completion_t
+COMPLETION_DTYPE = None
+
+
+def _completion_dtype():
+    global COMPLETION_DTYPE
+    if COMPLETION_DTYPE is None:
+        import numpy as np
+        COMPLETION_DTYPE = np.dtype([
+            ("ticket", "<u8"), ("handle", "<u4"), ("kind", "<i4"), ("status", "<i4"),
+            ("pad", "<u4"), ("batches", "<u8"), ("sum_lo", "<u8"), ("sum_hi", "<u8"),
+            ("n_closed", "<u8"), ("m", "<u8"), ("t_submit_ns", "<u8"), ("t_admit_ns", "<u8"),
+            ("t_done_ns", "<u8")])
+        assert COMPLETION_DTYPE.itemsize == ctypes.sizeof(tc_completion_t)
+    return COMPLETION_DTYPE
+
+
+class Server:
+    """Owning wrapper around a tc_server (continuous-batching request server).
+
+    Host batch buffers are kept alive here until their completion is polled.
+    """
+
+    def __init__(self, max_streams: int, vertex_bits: int, budget_bytes: int,
+                 w_max_round: int, depth: int = 2, max_round_streams: int = 0):
+        import numpy as np
+        cfg = tc_server_config_t(max_streams, vertex_bits, budget_bytes, w_max_round, depth,
+                                 max_round_streams)
+        h = ctypes.c_void_p()
+        _check(load().tc_server_create(ctypes.byref(cfg), ctypes.byref(h)), "tc_server_create")
+        self.h = h.value
+        self._keep = {}
+        self._buf = np.zeros(4096, dtype=_completion_dtype())
+
+    def open(self, r: int, seed: int, stream_id: int):
+        """Returns (handle, ticket)."""
+        hd, t = ctypes.c_uint32(), ctypes.c_uint64()
+        _check(load().tc_server_open(self.h, r, seed, stream_id, ctypes.byref(hd),
+                                     ctypes.byref(t)), "tc_server_open")
+        return hd.value, t.value
+
+    def submit(self, handle: int, edges) -> int:
+        """Submit a host batch (numpy uint64 array or CPU torch tensor,
+        ideally pinned); returns the ticket."""
+        t = ctypes.c_uint64()
+        w = int(edges.numel() if hasattr(edges, "numel") else edges.size)
+        ptr = _ptr(edges) if w else None
+        _check(load().tc_server_submit(self.h, handle, ptr, w, ctypes.byref(t)),
+               "tc_server_submit")
+        if w:
+            self._keep[t.value] = edges
+        return t.value
+
+    def query(self, handle: int) -> int:
+        t = ctypes.c_uint64()
+        _check(load().tc_server_query(self.h, handle, ctypes.byref(t)), "tc_server_query")
+        return t.value
+
+    def close(self, handle: int) -> int:
+        t = ctypes.c_uint64()
+        _check(load().tc_server_close(self.h, handle, ctypes.byref(t)), "tc_server_close")
+        return t.value
+
+    def poll(self, wait_us: int = 0):
+        """Completions ready now (numpy structured array, COMPLETION_DTYPE)."""
+        n = ctypes.c_uint32()
+        _check(load().tc_server_poll(self.h, self._buf.ctypes.data, self._buf.size, wait_us,
+                                     ctypes.byref(n)), "tc_server_poll")
+        out = self._buf[:n.value].copy()
+        for t in out["ticket"]:
+            self._keep.pop(int(t), None)
+        return out
+
+    def drain(self, timeout_ms: int = 600000):
+        _check(load().tc_server_drain(self.h, timeout_ms), "tc_server_drain")
+
+    def stats(self) -> dict:
+        st = tc_server_stats_t()
+        _check(load().tc_server_stats(self.h, ctypes.byref(st)), "tc_server_stats")
+        return {f: getattr(st, f) for f in _STATS_FIELDS}
+
+    def destroy(self):
+        if self.h:
+            load().tc_server_destroy(self.h)
+            self.h = 0
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.destroy()
         except Exception:
             pass

@@ -1,21 +1,23 @@
-// Many independent streams advanced together: one round folds one batch per
-// stream (any stream may sit a round out) into every stream's estimators
-// with a single segmented launch sequence -- one key build, one pair of
-// radix sorts over all streams' keys, one repeat check, one estimator sweep
-// and one bookkeeping launch -- instead of a full launch sequence per
-// stream.  Each stream is the bulkUpdateAll of Sec. 4 on its own stream of
-// edges; results are bit-identical to processing each stream alone with the
-// same seed, stream id and batch boundaries.
+// Many independent streams advanced together: one round folds one batch into
+// each of K participating streams with a single segmented launch sequence --
+// one key build, one pair of radix sorts over all participants' keys, one
+// repeat check, one estimator sweep and one bookkeeping launch -- instead of
+// a full launch sequence per stream.  Each stream is the bulkUpdateAll of
+// Sec. 4 on its own stream of edges; results are bit-identical to processing
+// each stream alone with the same seed, stream id and batch boundaries.
 //
-// Layout per round (S streams, round edges D[0..Wt) = the streams' batches
-// concatenated in stream order, stream s at [eoff_s, eoff_s + w_s)):
-//   arc keys   s << (B+bw+1) | src << (bw+1) | (w_s-1-j) << 1 | side, written
-//              stream-major in decreasing local position j and sorted on the
-//              (s, src) bits: every stream's arcs end up in its own range
-//              [2 eoff_s, 2 eoff_s + 2 w_s), in Lemma 4.3's order;
-//   edge keys  s << 2B | u << B | v with value j: stream s's keys end up in
-//              [eoff_s, eoff_s + w_s) sorted by (u, v).
-//   bw = bits of (max_s w_s) - 1, sb = bits of S-1, B = vertex id bits.
+// Layout per round (K participants k = 0..K-1, participant k folds batch
+// D_k[0..w_k) into slot slot_k; eoff = exclusive prefix sums of w_k, roff =
+// exclusive prefix sums of the participants' estimator counts r_k):
+//   descriptor  u64 words: eoff[K+1], D_k pointers[K], roff[K+1], slot_k[K]
+//   arc keys    k << (B+bw+1) | src << (bw+1) | (w_k-1-j) << 1 | side, written
+//               participant-major in decreasing local position j and sorted
+//               on the (k, src) bits: every participant's arcs end up in its
+//               own range [2 eoff_k, 2 eoff_k + 2 w_k), in Lemma 4.3's order;
+//   edge keys   k << 2B | u << B | v with value j: participant k's keys end up
+//               in [eoff_k, eoff_k + w_k) sorted by (u, v);
+//   sweep       one thread per estimator of the participants only (roff).
+//   bw = bits of (max_k w_k) - 1, kb = bits of K-1, B = vertex id bits.
 #include <algorithm>
 #include <cstddef>
 #include <cstring>
@@ -23,6 +25,7 @@
 #include <vector>
 
 #include "tc_kernels.cuh"
+#include "tc_multi_impl.cuh"
 
 using namespace tc;
 
@@ -33,36 +36,37 @@ namespace {
         if ((call) != cudaSuccess) return TC_ERR_CUDA; \
     } while (0)
 
-// Per-stream device record.
-struct MStream {
-    u64 est_off;  // first global estimator index
-    u64 r;        // estimators
-    u64 m;        // |E| of this stream
-    u64 batches;
-    uint2 key;    // Philox key (seed lo, seed hi)
-    u32 stream_id;
-    u32 err;      // error of the round in flight
-    u32 sticky;   // first error since the host last looked
-    u32 pad;
-    u64 est[4];   // committed estimate: S lo, S hi, closed, m
-    u64 acc[3];   // this round's S lo, S hi, closed
-    u64 pad2;
-};
-
 struct RoundShape {
-    u32 S;      // streams
-    u32 sb;     // stream id bits
+    u32 K;      // participants
+    u32 kb;     // participant index bits
     u32 B;      // vertex id bits
-    u32 bw;     // bits of max w_s - 1
+    u32 bw;     // bits of max w_k - 1
     u32 sha;    // arc key: src shift = bw + 1
     u64 Wt;     // edges this round
     int npa, npe;
     u32 bits_a, bits_e;
 };
 
-__device__ __forceinline__ u32 stream_of(const u64 *__restrict__ off, u32 S, u64 x) {
-    // last s with off[s] <= x (off has S+1 entries, off[0] = 0)
-    u32 lo = 0, hi = S;
+// Views of a round descriptor.
+struct Desc {
+    const u64 *eoff;              // K+1
+    const u64 *const *ebase;      // K
+    const u64 *roff;              // K+1
+    const u64 *slot;              // K
+};
+
+__device__ __forceinline__ Desc desc_view(const u64 *d, u32 K) {
+    Desc v;
+    v.eoff = d;
+    v.ebase = reinterpret_cast<const u64 *const *>(d + K + 1);
+    v.roff = d + 2 * K + 1;
+    v.slot = d + 3 * K + 2;
+    return v;
+}
+
+__device__ __forceinline__ u32 segment_of(const u64 *__restrict__ off, u32 K, u64 x) {
+    // last k with off[k] <= x (off has K+1 entries, off[0] = 0)
+    u32 lo = 0, hi = K;
     while (hi - lo > 1) {
         const u32 mid = (lo + hi) >> 1;
         if (__ldg(off + mid) <= x) lo = mid;
@@ -73,14 +77,14 @@ __device__ __forceinline__ u32 stream_of(const u64 *__restrict__ off, u32 S, u64
 
 constexpr int kMThreads = 256;
 
-__global__ void __launch_bounds__(kMThreads) mprep_kernel(const u64 *__restrict__ D,
-                                                           const u64 *__restrict__ eoff,
+__global__ void __launch_bounds__(kMThreads) mprep_kernel(const u64 *__restrict__ desc,
                                                            RoundShape rs, MStream *ms,
                                                            u64 *__restrict__ arcs0,
                                                            u64 *__restrict__ ekeys0,
                                                            u32 *__restrict__ evals0,
                                                            SortPlan *plans) {
     extern __shared__ u32 h[];
+    const Desc d = desc_view(desc, rs.K);
     const u32 ra = 1u << rs.bits_a, re = 1u << rs.bits_e;
     const u32 na = (u32)rs.npa * ra, nh = na + (u32)rs.npe * re;
     u32 *he = h + na;
@@ -89,13 +93,13 @@ __global__ void __launch_bounds__(kMThreads) mprep_kernel(const u64 *__restrict_
     const u64 id_lim = (rs.B >= 32) ? (1ull << 32) : (1ull << rs.B);
     for (u64 j = (u64)blockIdx.x * kMThreads + threadIdx.x; j < rs.Wt;
          j += (u64)gridDim.x * kMThreads) {
-        const u32 s = stream_of(eoff, rs.S, j);
-        const u64 e0 = __ldg(eoff + s), ws = __ldg(eoff + s + 1) - e0;
+        const u32 k = segment_of(d.eoff, rs.K, j);
+        const u64 e0 = __ldg(d.eoff + k), ws = __ldg(d.eoff + k + 1) - e0;
         const u64 jl = j - e0;
-        const u64 e = D[j];
+        const u64 e = d.ebase[k][jl];
         const u64 u = e >> 32, v = e & kMask32;
-        if (!(u < v) || v >= id_lim) atomicOr(&ms[s].err, kErrInput);
-        const u64 sp = (u64)s << (rs.B + rs.sha);
+        if (!(u < v) || v >= id_lim) atomicOr(&ms[__ldg(d.slot + k)].err, kErrInput);
+        const u64 sp = (u64)k << (rs.B + rs.sha);
         const u64 rpos = (ws - 1 - jl) << 1;
         const u64 au = sp | (u << rs.sha) | rpos;
         const u64 av = sp | (v << rs.sha) | rpos | 1ull;
@@ -104,7 +108,7 @@ __global__ void __launch_bounds__(kMThreads) mprep_kernel(const u64 *__restrict_
             atomicAdd(&h[p * ra + digit_bits(au, rs.sha + p * rs.bits_a, ra - 1)], 1u);
             atomicAdd(&h[p * ra + digit_bits(av, rs.sha + p * rs.bits_a, ra - 1)], 1u);
         }
-        const u64 ek = ((u64)s << (2 * rs.B)) | (u << rs.B) | v;
+        const u64 ek = ((u64)k << (2 * rs.B)) | (u << rs.B) | v;
         ekeys0[j] = ek;
         evals0[j] = (u32)jl;
         for (int p = 0; p < rs.npe; ++p)
@@ -119,24 +123,21 @@ __global__ void __launch_bounds__(kMThreads) mprep_kernel(const u64 *__restrict_
     }
 }
 
-// Repeats inside one stream's batch are adjacent after the edge sort.
+// Repeats inside one participant's batch are adjacent after the edge sort.
 __global__ void mdups_kernel(const u64 *ekeys0, const u64 *ekeys1, const SortPlan *plans,
-                             RoundShape rs, MStream *ms) {
+                             const u64 *__restrict__ desc, RoundShape rs, MStream *ms) {
+    const Desc d = desc_view(desc, rs.K);
     const u64 *E = plan_final_sel(&plans[1]) ? ekeys1 : ekeys0;
     for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x + 1; k < rs.Wt;
          k += (u64)gridDim.x * blockDim.x) {
         const u64 a = E[k];
-        if (a == E[k - 1]) atomicOr(&ms[a >> (2 * rs.B)].err, kErrInput);
+        if (a == E[k - 1]) atomicOr(&ms[__ldg(d.slot + (a >> (2 * rs.B)))].err, kErrInput);
     }
 }
 
 struct MSweepArgs {
-    const u64 *D;
-    const u64 *eoff;     // round edge offsets, S+1
-    const u64 *est_off;  // estimator offsets, S+1
-    u64 *f1, *f2, *chi;
-    u32 *flags;
-    u64 R;
+    const u64 *desc;
+    u64 R;               // estimators of the participants
     const u64 *arcs0, *arcs1, *ekeys0, *ekeys1;
     const u32 *evals0, *evals1;
     const SortPlan *plans;
@@ -166,43 +167,47 @@ __device__ __forceinline__ bool warp_segment_sum(u32 key, u64 &lo, u64 &hi, u64 
     return lane == __ffs(grp) - 1;
 }
 
-__global__ void __launch_bounds__(kMThreads) msweep_kernel(MSweepArgs a) {
+__global__ void __launch_bounds__(kMThreads, 3) msweep_kernel(MSweepArgs a) {
     if (ld_relaxed(a.gerr)) return;
     const u64 g = (u64)blockIdx.x * kMThreads + threadIdx.x;
     const RoundShape &rs = a.rs;
-    u32 s = 0xFFFFFFFFu;
+    const Desc d = desc_view(a.desc, rs.K);
+    u32 k = 0xFFFFFFFFu;
     u64 add = 0, closed = 0;
     if (g < a.R) {
-        s = stream_of(a.est_off, rs.S, g);
-        const u64 e0 = __ldg(a.eoff + s), ws = __ldg(a.eoff + s + 1) - e0;
-        MStream &st = a.ms[s];
+        k = segment_of(d.roff, rs.K, g);
+        const u64 e0 = __ldg(d.eoff + k), ws = __ldg(d.eoff + k + 1) - e0;
+        MStream &st = a.ms[__ldg(d.slot + k)];
         if (ws > 0 && !ld_relaxed(&st.err)) {
-            const u64 i = g - __ldg(a.est_off + s);
+            const u64 i = g - __ldg(d.roff + k);
             const u64 m = st.m;
             const DrawKey dk{st.key, (u32)st.batches, st.stream_id};
+            const u64 *D = d.ebase[k];
+            u64 *const F1 = st.f1, *const F2 = st.f2, *const CHI = st.chi;
+            u32 *const FL = st.flags;
             const u64 *arcs = plan_final_sel(&a.plans[0]) ? a.arcs1 : a.arcs0;
             const bool es = plan_final_sel(&a.plans[1]) != 0;
             const u64 *E = es ? a.ekeys1 : a.ekeys0;
             const u32 *EV = es ? a.evals1 : a.evals0;
             const u64 a_lo = 2 * e0, a_hi = 2 * (e0 + ws);
-            const u64 sp = (u64)s << (rs.B + rs.sha);
+            const u64 sp = (u64)k << (rs.B + rs.sha);
             const u64 wmask = (1ull << rs.bw) - 1;
-            u64 f1 = a.f1[g], f2 = a.f2[g], chi = a.chi[g];
-            u32 fl = a.flags[g];
+            u64 f1 = F1[i], f2 = F2[i], chi = CHI[i];
+            u32 fl = FL[i];
             // ---- Step 1 (Sec. 4.2)
             const u64 x = draw_bounded(dk, (u32)i, kStep1, m + ws);
             const bool new1 = x >= m;
             u64 p1 = 0;
             if (new1) {
                 p1 = x - m;
-                f1 = __ldg(a.D + e0 + p1);
+                f1 = __ldg(D + p1);
                 chi = 0;
                 f2 = kEmpty;
                 fl = 0;
             }
             // ---- Step 2 (Sec. 4.3)
             const u64 u = f1 >> 32, v = f1 & kMask32;
-            // (x + 1) << sha may carry into the stream bits: add, do not OR
+            // (x + 1) << sha may carry into the participant bits: add, do not OR
             const u64 su = lower_bound_range(arcs, a_lo, a_hi, sp + (u << rs.sha));
             const u64 eu = lower_bound_range(arcs, su, a_hi, sp + ((u + 1) << rs.sha));
             const u64 sv = lower_bound_range(arcs, a_lo, a_hi, sp + (v << rs.sha));
@@ -223,9 +228,9 @@ __global__ void __launch_bounds__(kMThreads) msweep_kernel(MSweepArgs a) {
                 const u64 y = draw_bounded(dk, (u32)i, kStep2, chi + chi_plus);
                 if (y >= chi) {
                     const u64 phi = y - chi;
-                    const u64 k = (phi < ld) ? su + phi : sv + (phi - ld);
-                    p2 = ws - 1 - ((__ldg(arcs + k) >> 1) & wmask);
-                    f2 = __ldg(a.D + e0 + p2);
+                    const u64 q = (phi < ld) ? su + phi : sv + (phi - ld);
+                    p2 = ws - 1 - ((__ldg(arcs + q) >> 1) & wmask);
+                    f2 = __ldg(D + p2);
                     fl &= ~TC_FLAG_CLOSED;
                     new2 = true;
                 }
@@ -237,54 +242,81 @@ __global__ void __launch_bounds__(kMThreads) msweep_kernel(MSweepArgs a) {
                 const u64 x1 = (a1 == a2 || a1 == b2) ? b1 : a1;
                 const u64 x2 = (a2 == a1 || a2 == b1) ? b2 : a2;
                 const u64 gu = x1 < x2 ? x1 : x2, gv = x1 < x2 ? x2 : x1;
-                const u64 probe = ((u64)s << (2 * rs.B)) | (gu << rs.B) | gv;
-                const u64 k = lower_bound_range(E, e0, e0 + ws, probe);
-                if (k < e0 + ws && __ldg(E + k) == probe) {
-                    const u64 q = __ldg(EV + k);
-                    if (!new2 || q > p2) fl |= TC_FLAG_CLOSED;
+                const u64 probe = ((u64)k << (2 * rs.B)) | (gu << rs.B) | gv;
+                const u64 q = lower_bound_range(E, e0, e0 + ws, probe);
+                if (q < e0 + ws && __ldg(E + q) == probe) {
+                    const u64 pq = __ldg(EV + q);
+                    if (!new2 || pq > p2) fl |= TC_FLAG_CLOSED;
                 }
             }
-            a.f1[g] = f1;
-            a.f2[g] = f2;
-            a.chi[g] = chi;
-            a.flags[g] = fl;
+            F1[i] = f1;
+            F2[i] = f2;
+            CHI[i] = chi;
+            FL[i] = fl;
             if (fl & TC_FLAG_CLOSED) {
                 add = chi;
                 closed = 1;
             }
         } else {
-            s = 0xFFFFFFFFu;  // untouched stream: contributes nothing
+            k = 0xFFFFFFFFu;  // rejected batch: contributes nothing
         }
     }
     u64 hi = 0;
-    if (warp_segment_sum(s, add, hi, closed) && s != 0xFFFFFFFFu) {
-        MStream &st = a.ms[s];
+    if (warp_segment_sum(k, add, hi, closed) && k != 0xFFFFFFFFu) {
+        MStream &st = a.ms[__ldg(d.slot + k)];
         if (add | hi) add_u128(st.acc, add, hi);
         if (closed) atomicAdd((unsigned long long *)&st.acc[2], (unsigned long long)closed);
     }
 }
 
-// Close the round for every stream that had a batch.
-__global__ void mfinish_kernel(MStream *ms, const u64 *eoff, u32 S, u32 *gerr) {
-    const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= S) return;
-    MStream &st = ms[s];
-    const u64 ws = eoff[s + 1] - eoff[s];
-    if (ws > 0) {
-        const u32 e = st.err ? st.err : *gerr;
-        if (e) {
-            if (!st.sticky) st.sticky = e;
-        } else {
-            st.m += ws;
-            st.batches += 1;
-            st.est[0] = st.acc[0];
-            st.est[1] = st.acc[1];
-            st.est[2] = st.acc[2];
-            st.est[3] = st.m;
-        }
+__device__ __forceinline__ void write_record(u64 *o, u32 status, const MStream &st) {
+    o[0] = status;
+    o[1] = st.batches;
+    o[2] = st.est[0];
+    o[3] = st.est[1];
+    o[4] = st.est[2];
+    o[5] = st.est[3];
+}
+
+// Close the round for every participant.
+__global__ void mfinish_kernel(MStream *ms, const u64 *__restrict__ desc, u32 K, u32 *gerr,
+                               u64 *out) {
+    const u32 k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= K) return;
+    const Desc d = desc_view(desc, K);
+    MStream &st = ms[d.slot[k]];
+    const u64 ws = d.eoff[k + 1] - d.eoff[k];
+    const u32 e = st.err ? st.err : *gerr;
+    if (e) {
+        if (!st.sticky) st.sticky = e;
+    } else if (ws > 0) {
+        st.m += ws;
+        st.batches += 1;
+        st.est[0] = st.acc[0];
+        st.est[1] = st.acc[1];
+        st.est[2] = st.acc[2];
+        st.est[3] = st.m;
     }
+    if (out) write_record(out + (u64)k * kRecordWords, e, st);
     st.err = 0;
     st.acc[0] = st.acc[1] = st.acc[2] = 0;
+}
+
+__global__ void mgather_kernel(const MStream *ms, const u32 *slots, u32 Q, u64 *out) {
+    const u32 q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < Q) write_record(out + (u64)q * kRecordWords, 0, ms[slots[q]]);
+}
+
+// Reset one slot: its record, and its r estimators to the empty state.
+__global__ void mopen_kernel(MStream *ms, u32 slot, MStream rec) {
+    const u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) ms[slot] = rec;
+    if (i < rec.r) {
+        rec.f1[i] = kEmpty;
+        rec.f2[i] = kEmpty;
+        rec.chi[i] = 0;
+        rec.flags[i] = 0;
+    }
 }
 
 using PassFn = void (*)(u64 *, u64 *, u32 *, u32 *, u32, u32, u32, int, SortPlan *, u32 *, u32 *,
@@ -367,99 +399,9 @@ u32 mlive(u32 total, u32 bits, int p) {
     return lo >= total ? 0u : std::min(bits, total - lo);
 }
 
-constexpr int kRing = 8;
-
-}  // namespace
-
-struct tc_multi {
-    u32 S = 0, B = 32, sb = 1;
-    u64 R = 0, w_max = 0;
-    u32 force_a = 0, force_e = 0;
-    int rank = kRankBallot;
-    u64 *f1 = nullptr, *f2 = nullptr, *chi = nullptr;
-    u32 *flags = nullptr;
-    MStream *ms = nullptr;
-    u64 *est_off = nullptr;
-    std::vector<u64> h_est_off;
-    // round scratch
-    u64 *arcs[2] = {nullptr, nullptr};
-    u64 *ekeys[2] = {nullptr, nullptr};
-    u32 *evals[2] = {nullptr, nullptr};
-    unsigned char *zeroed = nullptr;  // SortPlan[2], look-back, global error
-    u64 zeroed_bytes = 0;
-    u64 *eoff[kRing] = {};            // device copies of round offsets
-    u64 *h_eoff[kRing] = {};          // pinned staging
-    cudaEvent_t ring_ev[kRing] = {};
-    int ring = 0;
-    u64 launches = 0;
-    MStream *h_ms = nullptr;          // pinned host copy for reads
-    cudaGraphExec_t gexec = nullptr;  // captured round (tc_multi_capture)
-    u64 *g_eoff = nullptr;            // its fixed device offsets
-    u64 graph_launches = 0;           // kernels in the captured round
-};
-
-static void multi_free(tc_multi *M) {
-    cudaDeviceSynchronize();
-    cudaFree(M->f1);
-    cudaFree(M->f2);
-    cudaFree(M->chi);
-    cudaFree(M->flags);
-    cudaFree(M->ms);
-    cudaFree(M->est_off);
-    for (int k = 0; k < 2; ++k) {
-        cudaFree(M->arcs[k]);
-        cudaFree(M->ekeys[k]);
-        cudaFree(M->evals[k]);
-    }
-    cudaFree(M->zeroed);
-    for (int k = 0; k < kRing; ++k) {
-        cudaFree(M->eoff[k]);
-        if (M->h_eoff[k]) cudaFreeHost(M->h_eoff[k]);
-        if (M->ring_ev[k]) cudaEventDestroy(M->ring_ev[k]);
-    }
-    if (M->h_ms) cudaFreeHost(M->h_ms);
-    if (M->gexec) cudaGraphExecDestroy(M->gexec);
-    cudaFree(M->g_eoff);
-    delete M;
-}
-
-extern "C" {
-
-int tc_multi_create(uint32_t n_streams, const uint64_t *r, const uint64_t *seeds,
-                    const uint32_t *stream_ids, uint64_t w_max_round, uint32_t vertex_bits,
-                    tc_multi **out) {
-    if (!out || n_streams == 0 || !r || !seeds || !stream_ids || w_max_round == 0 ||
-        w_max_round > (1ull << 28) || vertex_bits < 1 || vertex_bits > 32)
-        return TC_ERR_INVAL;
-    *out = nullptr;
-    const u32 sb = mbits_for(n_streams - 1);
-    const u32 bwmax = mbits_for(w_max_round - 1);
-    if (sb + vertex_bits + bwmax + 1 > 64 || sb + 2 * vertex_bits > 64) return TC_ERR_INVAL;
-    u64 R = 0;
-    for (u32 s = 0; s < n_streams; ++s) {
-        if (r[s] == 0 || r[s] > 0xFFFFFFFFull) return TC_ERR_INVAL;
-        R += r[s];
-    }
-    int rc = mconfigure();
-    if (rc) return rc;
-    tc_multi *M = new (std::nothrow) tc_multi();
-    if (!M) return TC_ERR_NOMEM;
-    M->S = n_streams;
-    M->B = vertex_bits;
-    M->sb = sb;
-    M->R = R;
-    M->w_max = w_max_round;
-    std::vector<MStream> h(n_streams);
-    M->h_est_off.assign(n_streams + 1, 0);
-    for (u32 s = 0; s < n_streams; ++s) {
-        std::memset(&h[s], 0, sizeof(MStream));
-        h[s].est_off = M->h_est_off[s];
-        h[s].r = r[s];
-        h[s].key = make_uint2((u32)(seeds[s] & 0xFFFFFFFFu), (u32)(seeds[s] >> 32));
-        h[s].stream_id = stream_ids[s];
-        M->h_est_off[s + 1] = M->h_est_off[s] + r[s];
-    }
-    // worst-case look-back: any digit width for both sorts
+// Bytes of the zero-initialised scratch block: SortPlan[2], the worst-case
+// look-back of both sorts for any digit width, 256 bytes for the error word.
+u64 zeroed_bytes_for(u32 sb, u64 w_max_round, u32 vertex_bits) {
     u64 lb = 0;
     for (u32 ba : {8u, 10u, 11u})
         for (u32 be : {8u, 10u, 11u}) {
@@ -469,13 +411,63 @@ int tc_multi_create(uint32_t n_streams, const uint64_t *r, const uint64_t *seeds
             lb = std::max(lb, (u64)pa * mlookback(2 * w_max_round, ba) +
                                   (u64)pe * mlookback(w_max_round, be));
         }
-    M->zeroed_bytes = 2 * sizeof(SortPlan) + lb * sizeof(u32) + 256;
-    bool ok = cudaMalloc(&M->f1, R * sizeof(u64)) == cudaSuccess;
-    ok &= ok && cudaMalloc(&M->f2, R * sizeof(u64)) == cudaSuccess;
-    ok &= ok && cudaMalloc(&M->chi, R * sizeof(u64)) == cudaSuccess;
-    ok &= ok && cudaMalloc(&M->flags, R * sizeof(u32)) == cudaSuccess;
-    ok &= ok && cudaMalloc(&M->ms, n_streams * sizeof(MStream)) == cudaSuccess;
-    ok &= ok && cudaMalloc(&M->est_off, (n_streams + 1) * sizeof(u64)) == cudaSuccess;
+    return 2 * sizeof(SortPlan) + lb * sizeof(u32) + 256;
+}
+
+// Per-stream state block bytes (f1, f2, chi, flags), padded to 256 bytes.
+u64 state_bytes(u64 r) { return (28 * r + 255) & ~255ull; }
+
+}  // namespace
+
+namespace tc {
+
+u64 multi_scratch_bytes(u32 S, u64 w_max_round, u32 vertex_bits) {
+    const u32 sb = mbits_for(S - 1);
+    return (u64)S * sizeof(MStream) + 2 * (2 * w_max_round * 8 + w_max_round * 8 + w_max_round * 4) +
+           zeroed_bytes_for(sb, w_max_round, vertex_bits) + kRing * desc_words(S) * 8;
+}
+
+void multi_free(tc_multi *M) {
+    cudaDeviceSynchronize();
+    cudaFree(M->state);
+    cudaFree(M->ms);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(M->arcs[k]);
+        cudaFree(M->ekeys[k]);
+        cudaFree(M->evals[k]);
+    }
+    cudaFree(M->zeroed);
+    for (int k = 0; k < kRing; ++k) {
+        cudaFree(M->desc[k]);
+        if (M->h_desc[k]) cudaFreeHost(M->h_desc[k]);
+        if (M->ring_ev[k]) cudaEventDestroy(M->ring_ev[k]);
+    }
+    if (M->h_ms) cudaFreeHost(M->h_ms);
+    if (M->gexec) cudaGraphExecDestroy(M->gexec);
+    cudaFree(M->g_desc);
+    delete M;
+}
+
+int multi_alloc(u32 S, u64 w_max_round, u32 vertex_bits, tc_multi **out) {
+    *out = nullptr;
+    if (S == 0 || w_max_round == 0 || w_max_round > (1ull << 28) || vertex_bits < 1 ||
+        vertex_bits > 32)
+        return TC_ERR_INVAL;
+    const u32 sb = mbits_for(S - 1);
+    const u32 bwmax = mbits_for(w_max_round - 1);
+    if (sb + vertex_bits + bwmax + 1 > 64 || sb + 2 * vertex_bits > 64) return TC_ERR_INVAL;
+    int rc = mconfigure();
+    if (rc) return rc;
+    tc_multi *M = new (std::nothrow) tc_multi();
+    if (!M) return TC_ERR_NOMEM;
+    M->S = S;
+    M->B = vertex_bits;
+    M->sb = sb;
+    M->w_max = w_max_round;
+    M->rank = kRankBallot;
+    M->h_rec.assign(S, MStream{});
+    M->zeroed_bytes = zeroed_bytes_for(sb, w_max_round, vertex_bits);
+    bool ok = cudaMalloc(&M->ms, S * sizeof(MStream)) == cudaSuccess;
     for (int k = 0; k < 2 && ok; ++k) {
         ok &= cudaMalloc(&M->arcs[k], 2 * w_max_round * sizeof(u64)) == cudaSuccess;
         ok &= ok && cudaMalloc(&M->ekeys[k], w_max_round * sizeof(u64)) == cudaSuccess;
@@ -483,23 +475,15 @@ int tc_multi_create(uint32_t n_streams, const uint64_t *r, const uint64_t *seeds
     }
     ok &= ok && cudaMalloc(&M->zeroed, M->zeroed_bytes) == cudaSuccess;
     for (int k = 0; k < kRing && ok; ++k) {
-        ok &= cudaMalloc(&M->eoff[k], (n_streams + 1) * sizeof(u64)) == cudaSuccess;
-        ok &= ok && cudaHostAlloc(&M->h_eoff[k], (n_streams + 1) * sizeof(u64),
+        ok &= cudaMalloc(&M->desc[k], desc_words(S) * sizeof(u64)) == cudaSuccess;
+        ok &= ok && cudaHostAlloc(&M->h_desc[k], desc_words(S) * sizeof(u64),
                                   cudaHostAllocDefault) == cudaSuccess;
         ok &= ok && cudaEventCreateWithFlags(&M->ring_ev[k], cudaEventDisableTiming) == cudaSuccess;
     }
-    ok &= ok && cudaHostAlloc(&M->h_ms, n_streams * sizeof(MStream), cudaHostAllocDefault) ==
-                    cudaSuccess;
+    ok &= ok && cudaHostAlloc(&M->h_ms, S * sizeof(MStream), cudaHostAllocDefault) == cudaSuccess;
     if (ok) {
-        ok &= cudaMemset(M->f1, 0xFF, R * sizeof(u64)) == cudaSuccess;
-        ok &= cudaMemset(M->f2, 0xFF, R * sizeof(u64)) == cudaSuccess;
-        ok &= cudaMemset(M->chi, 0, R * sizeof(u64)) == cudaSuccess;
-        ok &= cudaMemset(M->flags, 0, R * sizeof(u32)) == cudaSuccess;
+        ok &= cudaMemset(M->ms, 0, S * sizeof(MStream)) == cudaSuccess;
         ok &= cudaMemset(M->zeroed, 0, M->zeroed_bytes) == cudaSuccess;
-        ok &= cudaMemcpy(M->ms, h.data(), n_streams * sizeof(MStream), cudaMemcpyHostToDevice) ==
-              cudaSuccess;
-        ok &= cudaMemcpy(M->est_off, M->h_est_off.data(), (n_streams + 1) * sizeof(u64),
-                         cudaMemcpyHostToDevice) == cudaSuccess;
         ok &= cudaDeviceSynchronize() == cudaSuccess;
     }
     if (!ok) {
@@ -507,6 +491,183 @@ int tc_multi_create(uint32_t n_streams, const uint64_t *r, const uint64_t *seeds
         multi_free(M);
         return e == cudaErrorMemoryAllocation ? TC_ERR_NOMEM : TC_ERR_CUDA;
     }
+    *out = M;
+    return TC_OK;
+}
+
+int multi_open_slot(tc_multi *M, u32 slot, u64 r, u64 seed, u32 stream_id, void *state,
+                    cudaStream_t st) {
+    if (slot >= M->S || r == 0 || r > 0xFFFFFFFFull || !state) return TC_ERR_INVAL;
+    MStream rec{};
+    u64 *base = static_cast<u64 *>(state);
+    rec.f1 = base;
+    rec.f2 = base + r;
+    rec.chi = base + 2 * r;
+    rec.flags = reinterpret_cast<u32 *>(base + 3 * r);
+    rec.r = r;
+    rec.key = make_uint2((u32)(seed & 0xFFFFFFFFu), (u32)(seed >> 32));
+    rec.stream_id = stream_id;
+    const u64 blocks = (r + 255) / 256;
+    mopen_kernel<<<(unsigned)blocks, 256, 0, st>>>(M->ms, slot, rec);
+    TCM_CUDA(cudaGetLastError());
+    M->h_rec[slot] = rec;
+    M->launches += 1;
+    return TC_OK;
+}
+
+u64 write_descriptor(const tc_multi *M, const RoundItem *items, u32 K, u64 *h) {
+    u64 *eoff = h, *ebase = h + K + 1, *roff = h + 2 * K + 1, *slot = h + 3 * K + 2;
+    u64 wmax = 0;
+    eoff[0] = 0;
+    roff[0] = 0;
+    for (u32 k = 0; k < K; ++k) {
+        eoff[k + 1] = eoff[k] + items[k].w;
+        ebase[k] = (u64)items[k].edges;
+        roff[k + 1] = roff[k] + M->h_rec[items[k].slot].r;
+        slot[k] = items[k].slot;
+        wmax = std::max(wmax, items[k].w);
+    }
+    return wmax;
+}
+
+int multi_gather(tc_multi *M, const u32 *d_slots, u32 Q, u64 *out, cudaStream_t st) {
+    if (Q == 0) return TC_OK;
+    mgather_kernel<<<(Q + 255) / 256, 256, 0, st>>>(M->ms, d_slots, Q, out);
+    TCM_CUDA(cudaGetLastError());
+    M->launches += 1;
+    return TC_OK;
+}
+
+int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, const u64 *desc, u64 *out,
+                  cudaStream_t st) {
+    u64 Wt = 0, wmax = 0, R = 0;
+    for (u32 k = 0; k < K; ++k) {
+        Wt += items[k].w;
+        wmax = std::max(wmax, items[k].w);
+        R += M->h_rec[items[k].slot].r;
+    }
+    if (K == 0 || Wt == 0 || Wt > M->w_max) return TC_ERR_INVAL;
+    RoundShape rs{};
+    rs.K = K;
+    rs.kb = mbits_for(K - 1);
+    rs.B = M->B;
+    rs.bw = mbits_for(wmax - 1);
+    rs.sha = rs.bw + 1;
+    rs.Wt = Wt;
+    rs.bits_a = mpick(M->B + rs.kb, M->force_a, rs.npa);
+    rs.bits_e = mpick(2 * M->B + rs.kb, M->force_e, rs.npe);
+    SortPlan *plans = reinterpret_cast<SortPlan *>(M->zeroed);
+    u32 *lb = reinterpret_cast<u32 *>(M->zeroed + 2 * sizeof(SortPlan));
+    const u64 la = mlookback(2 * Wt, rs.bits_a), le = mlookback(Wt, rs.bits_e);
+    const u64 lwords = (u64)rs.npa * la + (u64)rs.npe * le;
+    u32 *gerr = reinterpret_cast<u32 *>(M->zeroed + M->zeroed_bytes - 256);
+    TCM_CUDA(cudaMemsetAsync(M->zeroed, 0, 2 * sizeof(SortPlan) + lwords * sizeof(u32), st));
+    TCM_CUDA(cudaMemsetAsync(gerr, 0, sizeof(u32), st));
+
+    const size_t hsm = (((size_t)rs.npa << rs.bits_a) + ((size_t)rs.npe << rs.bits_e)) * 4;
+    const u64 pb = std::min<u64>((Wt + kMThreads * 8 - 1) / (kMThreads * 8), 1216);
+    mprep_kernel<<<(unsigned)pb, kMThreads, hsm, st>>>(desc, rs, M->ms, M->arcs[0], M->ekeys[0],
+                                                       M->evals[0], plans);
+    sort_plan_kernel<<<dim3((unsigned)std::max(rs.npa, rs.npe), 2), 256, 0, st>>>(
+        plans, rs.npa, (u32)(2 * Wt), rs.bits_a, rs.npe, (u32)Wt, rs.bits_e);
+    const PassK ka = mselect(rs.bits_a, false, M->rank);
+    const PassK ke = mselect(rs.bits_e, true, M->rank);
+    const u64 ta = mtiles(2 * Wt), te = mtiles(Wt);
+    for (int p = 0; p < rs.npa; ++p)
+        ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(
+            M->arcs[0], M->arcs[1], nullptr, nullptr, (u32)(2 * Wt), rs.sha + p * rs.bits_a,
+            mlive(M->B + rs.kb, rs.bits_a, p), p, &plans[0], lb + (u64)p * la, gerr, nullptr);
+    u32 *lbe = lb + (u64)rs.npa * la;
+    for (int p = 0; p < rs.npe; ++p)
+        ke.fn<<<(unsigned)te, ke.threads, ke.smem, st>>>(
+            M->ekeys[0], M->ekeys[1], M->evals[0], M->evals[1], (u32)Wt, p * rs.bits_e,
+            mlive(2 * M->B + rs.kb, rs.bits_e, p), p, &plans[1], lbe + (u64)p * le, gerr,
+            nullptr);
+    const u64 db = std::min<u64>((Wt + 255) / 256, 1216);
+    mdups_kernel<<<(unsigned)db, 256, 0, st>>>(M->ekeys[0], M->ekeys[1], plans, desc, rs, M->ms);
+    MSweepArgs a{};
+    a.desc = desc;
+    a.R = R;
+    a.arcs0 = M->arcs[0];
+    a.arcs1 = M->arcs[1];
+    a.ekeys0 = M->ekeys[0];
+    a.ekeys1 = M->ekeys[1];
+    a.evals0 = M->evals[0];
+    a.evals1 = M->evals[1];
+    a.plans = plans;
+    a.ms = M->ms;
+    a.gerr = gerr;
+    a.rs = rs;
+    msweep_kernel<<<(unsigned)((R + kMThreads - 1) / kMThreads), kMThreads, 0, st>>>(a);
+    mfinish_kernel<<<(K + 255) / 256, 256, 0, st>>>(M->ms, desc, K, gerr, out);
+    TCM_CUDA(cudaGetLastError());
+    M->launches += 5 + (u64)rs.npa + (u64)rs.npe;
+    return TC_OK;
+}
+
+}  // namespace tc
+
+// ---- tc_multi_* entry points ----------------------------------------------
+
+// Participants of a round given as offsets into one buffer (w_s > 0 only).
+static int items_from_offsets(const tc_multi *M, const u64 *d_edges, const uint64_t *offsets,
+                              std::vector<RoundItem> &items) {
+    if (!offsets || offsets[0] != 0) return TC_ERR_INVAL;
+    for (u32 s = 0; s < M->S; ++s) {
+        if (offsets[s + 1] < offsets[s]) return TC_ERR_INVAL;
+        const u64 w = offsets[s + 1] - offsets[s];
+        if (w) items.push_back(RoundItem{s, d_edges + offsets[s], w});
+    }
+    if (offsets[M->S] > M->w_max) return TC_ERR_INVAL;
+    if (offsets[M->S] && !d_edges) return TC_ERR_INVAL;
+    return TC_OK;
+}
+
+// Write the descriptor through the ring of pinned buffers and enqueue.
+static int upload_and_enqueue(tc_multi *M, const std::vector<RoundItem> &items,
+                              cudaStream_t st) {
+    const u32 K = (u32)items.size();
+    const int slot = M->ring;
+    M->ring = (M->ring + 1) % kRing;
+    TCM_CUDA(cudaEventSynchronize(M->ring_ev[slot]));
+    write_descriptor(M, items.data(), K, M->h_desc[slot]);
+    TCM_CUDA(cudaMemcpyAsync(M->desc[slot], M->h_desc[slot], desc_words(K) * sizeof(u64),
+                             cudaMemcpyHostToDevice, st));
+    TCM_CUDA(cudaEventRecord(M->ring_ev[slot], st));
+    return multi_enqueue(M, items.data(), K, M->desc[slot], nullptr, st);
+}
+
+extern "C" {
+
+int tc_multi_create(uint32_t n_streams, const uint64_t *r, const uint64_t *seeds,
+                    const uint32_t *stream_ids, uint64_t w_max_round, uint32_t vertex_bits,
+                    tc_multi **out) {
+    if (!out || n_streams == 0 || !r || !seeds || !stream_ids) return TC_ERR_INVAL;
+    *out = nullptr;
+    u64 total = 0;
+    for (u32 s = 0; s < n_streams; ++s) {
+        if (r[s] == 0 || r[s] > 0xFFFFFFFFull) return TC_ERR_INVAL;
+        total += state_bytes(r[s]);
+    }
+    tc_multi *M = nullptr;
+    int rc = multi_alloc(n_streams, w_max_round, vertex_bits, &M);
+    if (rc) return rc;
+    if (cudaMalloc(&M->state, total) != cudaSuccess) {
+        const cudaError_t e = cudaGetLastError();
+        multi_free(M);
+        return e == cudaErrorMemoryAllocation ? TC_ERR_NOMEM : TC_ERR_CUDA;
+    }
+    unsigned char *p = reinterpret_cast<unsigned char *>(M->state);
+    for (u32 s = 0; s < n_streams && rc == TC_OK; ++s) {
+        rc = multi_open_slot(M, s, r[s], seeds[s], stream_ids[s], p, 0);
+        p += state_bytes(r[s]);
+    }
+    if (rc == TC_OK && cudaDeviceSynchronize() != cudaSuccess) rc = TC_ERR_CUDA;
+    if (rc) {
+        multi_free(M);
+        return rc;
+    }
+    M->launches = 0;
     *out = M;
     return TC_OK;
 }
@@ -526,59 +687,50 @@ int tc_multi_tune(tc_multi *M, uint32_t arc_digit_bits, uint32_t edge_digit_bits
     return TC_OK;
 }
 
-// Check a round's offsets; returns the largest batch through *wmax.
-static int check_round(const tc_multi *M, const uint64_t *offsets, u64 *wmax) {
-    if (!offsets || offsets[0] != 0) return TC_ERR_INVAL;
-    u64 w = 0;
-    for (u32 s = 0; s < M->S; ++s) {
-        if (offsets[s + 1] < offsets[s]) return TC_ERR_INVAL;
-        w = std::max<u64>(w, offsets[s + 1] - offsets[s]);
-    }
-    if (offsets[M->S] > M->w_max) return TC_ERR_INVAL;
-    *wmax = w;
-    return TC_OK;
-}
-
-static int enqueue_round(tc_multi *M, const u64 *d_edges, const u64 *offsets, u64 wmax,
-                         const u64 *eoff, cudaStream_t st);
-
 int tc_multi_process_async(tc_multi *M, const uint64_t *d_edges, const uint64_t *offsets,
                            void *cuda_stream) {
     if (!M) return TC_ERR_INVAL;
-    u64 wmax = 0;
-    int rc = check_round(M, offsets, &wmax);
-    if (rc) return rc;
-    if (offsets[M->S] == 0) return TC_OK;
-    if (!d_edges) return TC_ERR_INVAL;
-    cudaStream_t st = (cudaStream_t)cuda_stream;
-    // round offsets through a ring of pinned buffers
-    const int slot = M->ring;
-    M->ring = (M->ring + 1) % kRing;
-    TCM_CUDA(cudaEventSynchronize(M->ring_ev[slot]));
-    std::memcpy(M->h_eoff[slot], offsets, (M->S + 1) * sizeof(u64));
-    TCM_CUDA(cudaMemcpyAsync(M->eoff[slot], M->h_eoff[slot], (M->S + 1) * sizeof(u64),
-                             cudaMemcpyHostToDevice, st));
-    TCM_CUDA(cudaEventRecord(M->ring_ev[slot], st));
-    return enqueue_round(M, d_edges, offsets, wmax, M->eoff[slot], st);
+    std::vector<RoundItem> items;
+    int rc = items_from_offsets(M, d_edges, offsets, items);
+    if (rc || items.empty()) return rc;
+    return upload_and_enqueue(M, items, (cudaStream_t)cuda_stream);
+}
+
+int tc_multi_process_ptrs_async(tc_multi *M, const uint64_t *const *d_batches,
+                                const uint64_t *w, void *cuda_stream) {
+    if (!M || !d_batches || !w) return TC_ERR_INVAL;
+    std::vector<RoundItem> items;
+    u64 total = 0;
+    for (u32 s = 0; s < M->S; ++s) {
+        if (!w[s]) continue;
+        if (!d_batches[s]) return TC_ERR_INVAL;
+        total += w[s];
+        items.push_back(RoundItem{s, d_batches[s], w[s]});
+    }
+    if (total > M->w_max) return TC_ERR_INVAL;
+    if (items.empty()) return TC_OK;
+    return upload_and_enqueue(M, items, (cudaStream_t)cuda_stream);
 }
 
 int tc_multi_capture(tc_multi *M, const uint64_t *d_edges, const uint64_t *offsets,
                      void *cuda_stream) {
     if (!M || !d_edges) return TC_ERR_INVAL;
-    u64 wmax = 0;
-    int rc = check_round(M, offsets, &wmax);
+    std::vector<RoundItem> items;
+    int rc = items_from_offsets(M, d_edges, offsets, items);
     if (rc) return rc;
-    if (offsets[M->S] == 0) return TC_ERR_INVAL;
+    if (items.empty()) return TC_ERR_INVAL;
     cudaStream_t st = (cudaStream_t)cuda_stream;
     if (M->gexec) {
         cudaGraphExecDestroy(M->gexec);
         M->gexec = nullptr;
     }
-    if (!M->g_eoff) TCM_CUDA(cudaMalloc(&M->g_eoff, (M->S + 1) * sizeof(u64)));
-    TCM_CUDA(cudaMemcpy(M->g_eoff, offsets, (M->S + 1) * sizeof(u64), cudaMemcpyHostToDevice));
+    if (!M->g_desc) TCM_CUDA(cudaMalloc(&M->g_desc, desc_words(M->S) * sizeof(u64)));
+    std::vector<u64> h(desc_words((u32)items.size()));
+    write_descriptor(M, items.data(), (u32)items.size(), h.data());
+    TCM_CUDA(cudaMemcpy(M->g_desc, h.data(), h.size() * sizeof(u64), cudaMemcpyHostToDevice));
     TCM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const u64 before = M->launches;
-    rc = enqueue_round(M, d_edges, offsets, wmax, M->g_eoff, st);
+    rc = multi_enqueue(M, items.data(), (u32)items.size(), M->g_desc, nullptr, st);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(st, &graph);
     if (rc || ec != cudaSuccess) {
@@ -598,78 +750,6 @@ int tc_multi_replay(tc_multi *M, void *cuda_stream) {
     M->launches += M->graph_launches;
     return TC_OK;
 }
-
-}  // extern "C"
-
-static int enqueue_round(tc_multi *M, const u64 *d_edges, const u64 *offsets, u64 wmax,
-                         const u64 *eoff, cudaStream_t st) {
-    const u64 Wt = offsets[M->S];
-
-    RoundShape rs{};
-    rs.S = M->S;
-    rs.sb = M->sb;
-    rs.B = M->B;
-    rs.bw = mbits_for(wmax - 1);
-    rs.sha = rs.bw + 1;
-    rs.Wt = Wt;
-    rs.bits_a = mpick(M->B + M->sb, M->force_a, rs.npa);
-    rs.bits_e = mpick(2 * M->B + M->sb, M->force_e, rs.npe);
-    SortPlan *plans = reinterpret_cast<SortPlan *>(M->zeroed);
-    u32 *lb = reinterpret_cast<u32 *>(M->zeroed + 2 * sizeof(SortPlan));
-    const u64 la = mlookback(2 * Wt, rs.bits_a), le = mlookback(Wt, rs.bits_e);
-    const u64 lwords = (u64)rs.npa * la + (u64)rs.npe * le;
-    u32 *gerr = reinterpret_cast<u32 *>(M->zeroed + M->zeroed_bytes - 256);
-    TCM_CUDA(cudaMemsetAsync(M->zeroed, 0, 2 * sizeof(SortPlan) + lwords * sizeof(u32), st));
-    TCM_CUDA(cudaMemsetAsync(gerr, 0, sizeof(u32), st));
-
-    const size_t hsm = (((size_t)rs.npa << rs.bits_a) + ((size_t)rs.npe << rs.bits_e)) * 4;
-    const u64 pb = std::min<u64>((Wt + kMThreads * 8 - 1) / (kMThreads * 8), 1216);
-    mprep_kernel<<<(unsigned)pb, kMThreads, hsm, st>>>(d_edges, eoff, rs, M->ms, M->arcs[0],
-                                                       M->ekeys[0], M->evals[0], plans);
-    sort_plan_kernel<<<dim3((unsigned)std::max(rs.npa, rs.npe), 2), 256, 0, st>>>(
-        plans, rs.npa, (u32)(2 * Wt), rs.bits_a, rs.npe, (u32)Wt, rs.bits_e);
-    const PassK ka = mselect(rs.bits_a, false, M->rank);
-    const PassK ke = mselect(rs.bits_e, true, M->rank);
-    const u64 ta = mtiles(2 * Wt), te = mtiles(Wt);
-    for (int p = 0; p < rs.npa; ++p)
-        ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(
-            M->arcs[0], M->arcs[1], nullptr, nullptr, (u32)(2 * Wt), rs.sha + p * rs.bits_a,
-            mlive(M->B + M->sb, rs.bits_a, p), p, &plans[0], lb + (u64)p * la, gerr, nullptr);
-    u32 *lbe = lb + (u64)rs.npa * la;
-    for (int p = 0; p < rs.npe; ++p)
-        ke.fn<<<(unsigned)te, ke.threads, ke.smem, st>>>(
-            M->ekeys[0], M->ekeys[1], M->evals[0], M->evals[1], (u32)Wt, p * rs.bits_e,
-            mlive(2 * M->B + M->sb, rs.bits_e, p), p, &plans[1], lbe + (u64)p * le, gerr,
-            nullptr);
-    const u64 db = std::min<u64>((Wt + 255) / 256, 1216);
-    mdups_kernel<<<(unsigned)db, 256, 0, st>>>(M->ekeys[0], M->ekeys[1], plans, rs, M->ms);
-    MSweepArgs a{};
-    a.D = d_edges;
-    a.eoff = eoff;
-    a.est_off = M->est_off;
-    a.f1 = M->f1;
-    a.f2 = M->f2;
-    a.chi = M->chi;
-    a.flags = M->flags;
-    a.R = M->R;
-    a.arcs0 = M->arcs[0];
-    a.arcs1 = M->arcs[1];
-    a.ekeys0 = M->ekeys[0];
-    a.ekeys1 = M->ekeys[1];
-    a.evals0 = M->evals[0];
-    a.evals1 = M->evals[1];
-    a.plans = plans;
-    a.ms = M->ms;
-    a.gerr = gerr;
-    a.rs = rs;
-    msweep_kernel<<<(unsigned)((M->R + kMThreads - 1) / kMThreads), kMThreads, 0, st>>>(a);
-    mfinish_kernel<<<(M->S + 255) / 256, 256, 0, st>>>(M->ms, eoff, M->S, gerr);
-    TCM_CUDA(cudaGetLastError());
-    M->launches += 5 + (u64)rs.npa + (u64)rs.npe;
-    return TC_OK;
-}
-
-extern "C" {
 
 int tc_multi_sync(tc_multi *M, int32_t *stream_errors) {
     if (!M) return TC_ERR_INVAL;
@@ -695,7 +775,7 @@ int tc_multi_sync(tc_multi *M, int32_t *stream_errors) {
 }
 
 int tc_multi_estimate(tc_multi *M, uint32_t s, tc_estimate_t *out) {
-    if (!M || !out || s >= M->S) return TC_ERR_INVAL;
+    if (!M || !out || s >= M->S || M->h_rec[s].r == 0) return TC_ERR_INVAL;
     TCM_CUDA(cudaDeviceSynchronize());
     MStream h{};
     TCM_CUDA(cudaMemcpy(&h, M->ms + s, sizeof(MStream), cudaMemcpyDeviceToHost));
@@ -727,13 +807,14 @@ int tc_multi_estimates_async(tc_multi *M, uint64_t *d_out, void *cuda_stream) {
 
 int tc_multi_get_state(tc_multi *M, uint32_t s, uint64_t *f1, uint64_t *f2, uint64_t *chi,
                        uint32_t *flags) {
-    if (!M || s >= M->S) return TC_ERR_INVAL;
+    if (!M || s >= M->S || M->h_rec[s].r == 0) return TC_ERR_INVAL;
     TCM_CUDA(cudaDeviceSynchronize());
-    const u64 o = M->h_est_off[s], n = M->h_est_off[s + 1] - o;
-    if (f1) TCM_CUDA(cudaMemcpy(f1, M->f1 + o, n * sizeof(u64), cudaMemcpyDeviceToHost));
-    if (f2) TCM_CUDA(cudaMemcpy(f2, M->f2 + o, n * sizeof(u64), cudaMemcpyDeviceToHost));
-    if (chi) TCM_CUDA(cudaMemcpy(chi, M->chi + o, n * sizeof(u64), cudaMemcpyDeviceToHost));
-    if (flags) TCM_CUDA(cudaMemcpy(flags, M->flags + o, n * sizeof(u32), cudaMemcpyDeviceToHost));
+    const MStream &h = M->h_rec[s];
+    const u64 n = h.r;
+    if (f1) TCM_CUDA(cudaMemcpy(f1, h.f1, n * sizeof(u64), cudaMemcpyDeviceToHost));
+    if (f2) TCM_CUDA(cudaMemcpy(f2, h.f2, n * sizeof(u64), cudaMemcpyDeviceToHost));
+    if (chi) TCM_CUDA(cudaMemcpy(chi, h.chi, n * sizeof(u64), cudaMemcpyDeviceToHost));
+    if (flags) TCM_CUDA(cudaMemcpy(flags, h.flags, n * sizeof(u32), cudaMemcpyDeviceToHost));
     return TC_OK;
 }
 

@@ -1,0 +1,742 @@
+// Request server: many concurrent streams send edge batches and estimate
+// queries as they arrive; a native scheduler thread keeps every open stream's
+// estimator state resident in HBM and folds the batches in with continuous
+// batching over the multi-stream round engine.
+//
+// Pipeline (one scheduler thread, two CUDA streams):
+//   admission   requests leave the submission queue in arrival order.  An
+//               open needs a free stream slot and its state bytes, a batch
+//               its own bytes, within the device-memory budget; the head
+//               request waits until earlier work completes and frees them.
+//               An admitted batch is copied host -> device on the copy
+//               stream at once, overlapping the rounds in flight.
+//   rounds      whenever fewer than `depth` rounds are in flight, the next
+//               round takes, from each stream with admitted work (round
+//               robin), the queries at the head of its queue and then at
+//               most one batch, up to w_max_round edges.  The queries are
+//               answered from the stream records at the start of the round,
+//               i.e. after exactly the batches submitted before them; the
+//               batches are folded by one segmented launch sequence on the
+//               compute stream, which waits only for their own copies.
+//   completion  when a round's event has fired, every request in it gets a
+//               completion record (status, the stream's batch count and
+//               Lemma 3.1 sums, host timestamps) and its batch memory goes
+//               back to the budget.
+// Each stream's results are those of running it alone with the same seed,
+// stream id and batch boundaries: rounds keep every stream's batches in
+// submission order and a stream's arithmetic never depends on the others.
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <thread>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "tc_multi_impl.cuh"
+
+using namespace tc;
+
+namespace {
+
+struct Req {
+    u64 ticket = 0;
+    int kind = 0;
+    u32 handle = 0;
+    const u64 *h_edges = nullptr;
+    u64 w = 0;
+    u64 r = 0, seed = 0;
+    u32 stream_id = 0;
+    u64 t_submit = 0, t_admit = 0;
+    u64 *d_edges = nullptr;  // device copy of an admitted batch
+    u64 bytes = 0;           // budget bytes it holds until completion
+    int ev = -1;             // copy event
+    u64 seq = 0;             // copy order
+    bool waited = false;     // had to wait for admission
+};
+
+struct Slot {
+    u32 handle = 0;
+    void *state = nullptr;
+    u64 state_bytes = 0;
+    bool used = false;
+    bool in_ready = false;
+    std::deque<Req> q;
+};
+
+struct Round {
+    int buf = 0;
+    std::vector<Req> queries;
+    std::vector<Req> batches;
+    std::vector<Req> closes;
+};
+
+u64 round_up(u64 x) { return (x + 255) & ~255ull; }
+u64 state_bytes_for(u64 r) { return round_up(28 * r); }
+
+int status_of(u64 e) {
+    return e == 0 ? TC_OK : e == kErrInput ? TC_ERR_INPUT : e == kErrTimeout ? TC_ERR_TIMEOUT
+                                                                               : TC_ERR_CUDA;
+}
+
+}  // namespace
+
+struct tc_server {
+    tc_server_config_t cfg{};
+    int dev = 0;
+    int depth = 2;
+    tc_multi *M = nullptr;
+    cudaStream_t cs = nullptr;  // rounds
+    cudaStream_t xs = nullptr;  // host -> device batch copies
+    cudaMemPool_t pool = nullptr;
+    std::chrono::steady_clock::time_point t0;
+    u64 fixed = 0;
+
+    // ---- shared with client threads (mu)
+    std::mutex mu;
+    std::condition_variable cv_in, cv_out;
+    std::deque<Req> inbox;
+    std::deque<tc_completion_t> done;
+    std::unordered_map<u32, bool> handles;  // open handles
+    u64 next_ticket = 1;
+    u32 next_handle = 1;
+    u64 submitted = 0, completed = 0;
+    int fatal = TC_OK;
+    bool stop = false;
+    tc_server_stats_t stats{};
+
+    // ---- scheduler thread only
+    std::thread th;
+    std::deque<Req> pending;
+    std::vector<Slot> slots;
+    std::vector<u32> free_slots;
+    std::unordered_map<u32, u32> slot_of;  // handle -> slot
+    std::deque<u32> ready;                 // slots with queued work, round-robin
+    std::deque<Round> inflight;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_free;
+    u64 copy_seq = 0;
+    int nbuf = 0;
+    std::vector<u64 *> d_out, h_out, d_desc, h_desc;
+    std::vector<u32 *> d_qs, h_qs;
+    std::vector<cudaEvent_t> round_ev;
+    u64 round_no = 0;
+    u64 reserved = 0, peak = 0;
+    int err = TC_OK;          // first CUDA failure seen by the scheduler
+    bool dirty = false;       // arrivals or freed slots/memory since the last admission pass
+    tc_server_stats_t local{};
+    std::vector<tc_completion_t> outbox;
+
+    u64 now() const {
+        return (u64)std::chrono::duration_cast<std::chrono::nanoseconds>(
+                   std::chrono::steady_clock::now() - t0)
+            .count();
+    }
+    void run();
+    bool admit();
+    bool form_round();
+    bool retire();
+    void publish();
+    void fail_all(int code);
+    int get_event();
+    void complete(const Req &q, int status, const u64 *rec);
+};
+
+void tc_server::complete(const Req &q, int status, const u64 *rec) {
+    tc_completion_t c{};
+    c.ticket = q.ticket;
+    c.handle = q.handle;
+    c.kind = q.kind;
+    c.status = status;
+    if (rec) {
+        c.batches = rec[1];
+        c.sum_lo = rec[2];
+        c.sum_hi = rec[3];
+        c.n_closed = rec[4];
+        c.m = rec[5];
+    }
+    c.t_submit_ns = q.t_submit;
+    c.t_admit_ns = q.t_admit;
+    c.t_done_ns = now();
+    outbox.push_back(c);
+}
+
+int tc_server::get_event() {
+    if (ev_free.empty()) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return -1;
+        ev_pool.push_back(e);
+        return (int)ev_pool.size() - 1;
+    }
+    const int k = ev_free.back();
+    ev_free.pop_back();
+    return k;
+}
+
+// Admit what can be admitted, in arrival order.  An open needs a free slot
+// and its state bytes, a batch its own bytes; once an open (a batch) has to
+// wait, no later open (batch) overtakes it.  Queries, closes and empty
+// batches of admitted streams need nothing and pass waiting requests of
+// other streams -- a close may be what frees the slot an open waits for --
+// but no request overtakes an earlier one of its own stream.  Returns
+// whether anything was admitted; a CUDA failure is left in `err`.
+bool tc_server::admit() {
+    if (pending.empty() || !dirty) return false;
+    dirty = false;
+    bool moved = false, open_blocked = false, mem_blocked = false;
+    std::unordered_set<u32> held;  // handles with an earlier request still waiting
+    std::deque<Req> keep;
+    while (!pending.empty()) {
+        Req q = std::move(pending.front());
+        pending.pop_front();
+        bool wait = held.count(q.handle) != 0;
+        if (!wait && q.kind == TC_REQ_OPEN) {
+            const u64 b = state_bytes_for(q.r);
+            wait = open_blocked || free_slots.empty() || reserved + b > cfg.budget_bytes;
+            if (wait) {
+                open_blocked = true;
+            } else {
+                void *p = nullptr;
+                if (cudaMallocFromPoolAsync(&p, b, pool, cs) != cudaSuccess) {
+                    err = TC_ERR_NOMEM;
+                    pending.push_front(std::move(q));
+                    break;
+                }
+                const u32 s = free_slots.back();
+                free_slots.pop_back();
+                if (multi_open_slot(M, s, q.r, q.seed, q.stream_id, p, cs) != TC_OK) {
+                    err = TC_ERR_CUDA;
+                    pending.push_front(std::move(q));
+                    break;
+                }
+                Slot &sl = slots[s];
+                sl.handle = q.handle;
+                sl.state = p;
+                sl.state_bytes = b;
+                sl.used = true;
+                slot_of[q.handle] = s;
+                reserved += b;
+                q.t_admit = now();
+                local.opens++;
+                local.streams_open++;
+                complete(q, TC_OK, nullptr);
+            }
+        } else if (!wait) {
+            if (q.kind == TC_REQ_BATCH && q.w > 0) {
+                const u64 b = round_up(8 * q.w);
+                wait = mem_blocked || reserved + b > cfg.budget_bytes;
+                if (wait) {
+                    mem_blocked = true;
+                } else {
+                    if (cudaMallocFromPoolAsync((void **)&q.d_edges, 8 * q.w, pool, xs) !=
+                        cudaSuccess) {
+                        err = TC_ERR_NOMEM;
+                        pending.push_front(std::move(q));
+                        break;
+                    }
+                    q.ev = get_event();
+                    if (q.ev < 0 ||
+                        cudaMemcpyAsync(q.d_edges, q.h_edges, 8 * q.w, cudaMemcpyHostToDevice,
+                                        xs) != cudaSuccess ||
+                        cudaEventRecord(ev_pool[q.ev], xs) != cudaSuccess) {
+                        err = TC_ERR_CUDA;
+                        pending.push_front(std::move(q));
+                        break;
+                    }
+                    q.bytes = b;
+                    q.seq = ++copy_seq;
+                    reserved += b;
+                }
+            }
+            if (!wait) {
+                q.t_admit = now();
+                const u32 s = slot_of.at(q.handle);
+                Slot &sl = slots[s];
+                sl.q.push_back(std::move(q));
+                if (!sl.in_ready) {
+                    sl.in_ready = true;
+                    ready.push_back(s);
+                }
+            }
+        }
+        if (wait) {
+            if (!q.waited) local.admission_waits++;
+            q.waited = true;
+            held.insert(q.handle);
+            keep.push_back(std::move(q));
+        } else {
+            moved = true;
+            if (reserved > peak) peak = reserved;
+        }
+    }
+    while (!keep.empty()) {  // waiting requests go back in arrival order
+        pending.push_front(std::move(keep.back()));
+        keep.pop_back();
+    }
+    return moved;
+}
+
+bool tc_server::form_round() {
+    if (ready.empty()) return false;
+    const u32 S = M->S;
+    Round R;
+    std::vector<RoundItem> items;
+    std::vector<u32> qslots;
+    std::vector<u32> closed_slots;
+    u64 edges = 0, wait_seq = 0;
+    int wait_ev = -1;
+    std::deque<u32> again;
+    size_t n = ready.size();
+    bool full = false;
+    while (n-- > 0 && !full) {
+        const u32 s = ready.front();
+        ready.pop_front();
+        Slot &sl = slots[s];
+        sl.in_ready = false;
+        bool closing = false;
+        while (!sl.q.empty()) {
+            Req &h = sl.q.front();
+            if (h.kind == TC_REQ_QUERY || (h.kind == TC_REQ_BATCH && h.w == 0)) {
+                if (qslots.size() >= S) {
+                    full = true;
+                    break;
+                }
+                qslots.push_back(s);
+                R.queries.push_back(std::move(h));
+                sl.q.pop_front();
+                continue;
+            }
+            if (h.kind == TC_REQ_CLOSE) {
+                R.closes.push_back(std::move(h));
+                sl.q.pop_front();
+                closing = true;
+                break;
+            }
+            // a batch: at most one per stream per round; queries behind it
+            // wait for the next round (they must see this batch)
+            if (edges + h.w > cfg.w_max_round || items.size() >= cfg.max_round_streams) {
+                full = true;
+                break;
+            }
+            items.push_back(RoundItem{s, h.d_edges, h.w});
+            edges += h.w;
+            if (h.seq > wait_seq) {
+                wait_seq = h.seq;
+                wait_ev = h.ev;
+            }
+            R.batches.push_back(std::move(h));
+            sl.q.pop_front();
+            break;
+        }
+        if (closing) {
+            closed_slots.push_back(s);
+        } else if (!sl.q.empty()) {
+            sl.in_ready = true;
+            if (full) ready.push_front(s);
+            else again.push_back(s);
+        }
+    }
+    for (u32 s : again) ready.push_back(s);
+    if (items.empty() && qslots.empty() && R.closes.empty()) return false;
+
+    const int b = (int)(round_no % (u64)nbuf);
+    const u32 Q = (u32)qslots.size(), K = (u32)items.size();
+    bool ok = true;
+    if (Q) {
+        std::memcpy(h_qs[b], qslots.data(), Q * sizeof(u32));
+        ok &= cudaMemcpyAsync(d_qs[b], h_qs[b], Q * sizeof(u32), cudaMemcpyHostToDevice, cs) ==
+              cudaSuccess;
+        ok &= ok && multi_gather(M, d_qs[b], Q, d_out[b], cs) == TC_OK;
+    }
+    if (K && ok) {
+        if (wait_ev >= 0) ok &= cudaStreamWaitEvent(cs, ev_pool[wait_ev], 0) == cudaSuccess;
+        write_descriptor(M, items.data(), K, h_desc[b]);
+        ok &= ok && cudaMemcpyAsync(d_desc[b], h_desc[b], desc_words(K) * sizeof(u64),
+                                    cudaMemcpyHostToDevice, cs) == cudaSuccess;
+        ok &= ok && multi_enqueue(M, items.data(), K, d_desc[b],
+                                  d_out[b] + (u64)Q * kRecordWords, cs) == TC_OK;
+        for (Req &q : R.batches) {
+            ok &= ok && cudaFreeAsync(q.d_edges, cs) == cudaSuccess;
+            q.d_edges = nullptr;
+            ev_free.push_back(q.ev);
+            q.ev = -1;
+        }
+    }
+    const u64 words = (u64)(Q + K) * kRecordWords;
+    if (words && ok)
+        ok &= cudaMemcpyAsync(h_out[b], d_out[b], words * sizeof(u64), cudaMemcpyDeviceToHost,
+                              cs) == cudaSuccess;
+    for (u32 s : closed_slots) {
+        Slot &sl = slots[s];
+        ok &= ok && cudaFreeAsync(sl.state, cs) == cudaSuccess;
+        reserved -= sl.state_bytes;
+        slot_of.erase(sl.handle);
+        sl.state = nullptr;
+        sl.state_bytes = 0;
+        sl.used = false;
+        free_slots.push_back(s);
+        dirty = true;
+        local.closes++;
+        local.streams_open--;
+    }
+    ok &= ok && cudaEventRecord(round_ev[b], cs) == cudaSuccess;
+    if (!ok) {
+        err = TC_ERR_CUDA;
+        return false;
+    }
+    R.buf = b;
+    inflight.push_back(std::move(R));
+    round_no++;
+    local.rounds++;
+    local.edges += edges;
+    if (edges > local.max_round_edges) local.max_round_edges = edges;
+    if (K > local.max_round_streams) local.max_round_streams = K;
+    return true;
+}
+
+bool tc_server::retire() {
+    bool any = false;
+    while (!inflight.empty()) {
+        Round &R = inflight.front();
+        const cudaError_t e = cudaEventQuery(round_ev[R.buf]);
+        if (e == cudaErrorNotReady) break;
+        if (e != cudaSuccess) {
+            err = TC_ERR_CUDA;
+            return any;
+        }
+        const u64 *o = h_out[R.buf];
+        const size_t Q = R.queries.size();
+        for (size_t i = 0; i < Q; ++i) {
+            complete(R.queries[i], TC_OK, o + i * kRecordWords);
+            local.queries++;
+        }
+        for (size_t k = 0; k < R.batches.size(); ++k) {
+            const u64 *rec = o + (Q + k) * kRecordWords;
+            const int st = status_of(rec[0]);
+            complete(R.batches[k], st, rec);
+            reserved -= R.batches[k].bytes;
+            dirty = true;
+            if (st) local.rejected++;
+            else local.batches++;
+        }
+        for (const Req &q : R.closes) complete(q, TC_OK, nullptr);
+        inflight.pop_front();
+        any = true;
+    }
+    return any;
+}
+
+// Hand the completions gathered by this pass to the clients.
+void tc_server::publish() {
+    std::lock_guard<std::mutex> lk(mu);
+    local.kernel_launches = M->launches;
+    local.bytes_reserved = reserved;
+    local.bytes_peak = peak;
+    local.requests_waiting = pending.size() + inbox.size();
+    stats = local;
+    stats.bytes_budget = cfg.budget_bytes;
+    stats.bytes_fixed = fixed;
+    if (!outbox.empty()) {
+        for (const tc_completion_t &c : outbox) done.push_back(c);
+        completed += outbox.size();
+        outbox.clear();
+        cv_out.notify_all();
+    }
+}
+
+// After a CUDA error: every request not yet completed fails with `code`.
+void tc_server::fail_all(int code) {
+    cudaStreamSynchronize(cs);
+    cudaStreamSynchronize(xs);
+    for (Round &R : inflight) {
+        for (const Req &q : R.queries) complete(q, code, nullptr);
+        for (const Req &q : R.batches) complete(q, code, nullptr);
+        for (const Req &q : R.closes) complete(q, code, nullptr);
+    }
+    inflight.clear();
+    for (Slot &sl : slots) {
+        for (const Req &q : sl.q) complete(q, code, nullptr);
+        sl.q.clear();
+    }
+    ready.clear();
+    for (const Req &q : pending) complete(q, code, nullptr);
+    pending.clear();
+}
+
+void tc_server::run() {
+    cudaSetDevice(dev);
+    for (;;) {
+        bool stopping;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            stopping = stop;
+            if (!inbox.empty()) dirty = true;
+            while (!inbox.empty()) {
+                pending.push_back(std::move(inbox.front()));
+                inbox.pop_front();
+            }
+        }
+        if (stopping) break;
+        if (err == TC_OK) {
+            bool progress = retire();
+            if (err == TC_OK) progress |= admit();
+            while (err == TC_OK && (int)inflight.size() < depth && form_round()) progress = true;
+            if (err != TC_OK) {
+                {
+                    std::lock_guard<std::mutex> lk(mu);
+                    fatal = err;
+                }
+                fail_all(err);
+            }
+            publish();
+            if (!progress && err == TC_OK) {
+                std::unique_lock<std::mutex> lk(mu);
+                cv_in.wait_for(lk, std::chrono::microseconds(inflight.empty() ? 500 : 10),
+                               [&] { return stop || !inbox.empty(); });
+            }
+            continue;
+        }
+        // after a failure every request still arriving completes with it
+        for (const Req &q : pending) complete(q, err, nullptr);
+        pending.clear();
+        publish();
+        std::unique_lock<std::mutex> lk(mu);
+        cv_in.wait(lk, [&] { return stop || !inbox.empty(); });
+    }
+    // leaving: let the rounds in flight finish before their memory goes
+    cudaStreamSynchronize(xs);
+    cudaStreamSynchronize(cs);
+}
+
+static void server_free(tc_server *S) {
+    if (S->cs) cudaStreamSynchronize(S->cs);
+    if (S->xs) cudaStreamSynchronize(S->xs);
+    for (Slot &sl : S->slots) {
+        for (Req &q : sl.q)
+            if (q.d_edges) cudaFreeAsync(q.d_edges, S->cs);
+        if (sl.state) cudaFreeAsync(sl.state, S->cs);
+    }
+    for (Req &q : S->pending)
+        if (q.d_edges) cudaFreeAsync(q.d_edges, S->cs);
+    if (S->cs) cudaStreamSynchronize(S->cs);
+    for (int k = 0; k < S->nbuf; ++k) {
+        cudaFree(S->d_out[k]);
+        cudaFree(S->d_desc[k]);
+        cudaFree(S->d_qs[k]);
+        if (S->h_out[k]) cudaFreeHost(S->h_out[k]);
+        if (S->h_desc[k]) cudaFreeHost(S->h_desc[k]);
+        if (S->h_qs[k]) cudaFreeHost(S->h_qs[k]);
+        if (S->round_ev[k]) cudaEventDestroy(S->round_ev[k]);
+    }
+    for (cudaEvent_t e : S->ev_pool) cudaEventDestroy(e);
+    if (S->M) multi_free(S->M);
+    if (S->pool) cudaMemPoolDestroy(S->pool);
+    if (S->cs) cudaStreamDestroy(S->cs);
+    if (S->xs) cudaStreamDestroy(S->xs);
+    delete S;
+}
+
+extern "C" {
+
+int tc_server_create(const tc_server_config_t *cfg, tc_server **out) {
+    if (!cfg || !out) return TC_ERR_INVAL;
+    *out = nullptr;
+    if (cfg->max_streams == 0 || cfg->depth > 8 || cfg->w_max_round == 0) return TC_ERR_INVAL;
+    const u32 S = cfg->max_streams;
+    const int depth = cfg->depth ? (int)cfg->depth : 2;
+    const int nbuf = depth + 1;
+    const u64 ring_bytes = (u64)nbuf * (2ull * S * kRecordWords * 8 + desc_words(S) * 8 + S * 4);
+    const u64 fixed = multi_scratch_bytes(S, cfg->w_max_round, cfg->vertex_bits) + ring_bytes;
+    if (fixed >= cfg->budget_bytes) return TC_ERR_RANGE;
+
+    tc_server *Sv = new (std::nothrow) tc_server();
+    if (!Sv) return TC_ERR_NOMEM;
+    Sv->cfg = *cfg;
+    if (Sv->cfg.max_round_streams == 0 || Sv->cfg.max_round_streams > S)
+        Sv->cfg.max_round_streams = S;
+    Sv->depth = depth;
+    Sv->nbuf = nbuf;
+    Sv->fixed = fixed;
+    Sv->reserved = fixed;
+    Sv->peak = fixed;
+    Sv->t0 = std::chrono::steady_clock::now();
+    int rc = TC_OK;
+    if (cudaGetDevice(&Sv->dev) != cudaSuccess) rc = TC_ERR_CUDA;
+    if (!rc) rc = multi_alloc(S, cfg->w_max_round, cfg->vertex_bits, &Sv->M);
+    bool ok = rc == TC_OK;
+    ok &= ok && cudaStreamCreateWithFlags(&Sv->cs, cudaStreamNonBlocking) == cudaSuccess;
+    ok &= ok && cudaStreamCreateWithFlags(&Sv->xs, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = Sv->dev;
+        ok &= cudaMemPoolCreate(&Sv->pool, &props) == cudaSuccess;
+        u64 keep = ~0ull;
+        int no = 0;
+        ok &= ok && cudaMemPoolSetAttribute(Sv->pool, cudaMemPoolAttrReleaseThreshold, &keep) ==
+                        cudaSuccess;
+        // never make the copy stream wait for the compute stream to reuse memory
+        ok &= ok && cudaMemPoolSetAttribute(Sv->pool, cudaMemPoolReuseAllowInternalDependencies,
+                                            &no) == cudaSuccess;
+    }
+    Sv->d_out.assign(nbuf, nullptr);
+    Sv->h_out.assign(nbuf, nullptr);
+    Sv->d_desc.assign(nbuf, nullptr);
+    Sv->h_desc.assign(nbuf, nullptr);
+    Sv->d_qs.assign(nbuf, nullptr);
+    Sv->h_qs.assign(nbuf, nullptr);
+    Sv->round_ev.assign(nbuf, nullptr);
+    for (int k = 0; k < nbuf && ok; ++k) {
+        const u64 ob = 2ull * S * kRecordWords * 8;
+        ok &= cudaMalloc(&Sv->d_out[k], ob) == cudaSuccess;
+        ok &= ok && cudaHostAlloc(&Sv->h_out[k], ob, cudaHostAllocDefault) == cudaSuccess;
+        ok &= ok && cudaMalloc(&Sv->d_desc[k], desc_words(S) * 8) == cudaSuccess;
+        ok &= ok && cudaHostAlloc(&Sv->h_desc[k], desc_words(S) * 8, cudaHostAllocDefault) ==
+                        cudaSuccess;
+        ok &= ok && cudaMalloc(&Sv->d_qs[k], S * 4) == cudaSuccess;
+        ok &= ok && cudaHostAlloc(&Sv->h_qs[k], S * 4, cudaHostAllocDefault) == cudaSuccess;
+        ok &= ok && cudaEventCreateWithFlags(&Sv->round_ev[k], cudaEventDisableTiming) ==
+                        cudaSuccess;
+    }
+    if (!ok) {
+        if (rc == TC_OK) rc = cudaGetLastError() == cudaErrorMemoryAllocation ? TC_ERR_NOMEM
+                                                                              : TC_ERR_CUDA;
+        server_free(Sv);
+        return rc;
+    }
+    Sv->slots.resize(S);
+    Sv->free_slots.reserve(S);
+    for (u32 s = S; s-- > 0;) Sv->free_slots.push_back(s);
+    try {
+        Sv->th = std::thread([Sv] { Sv->run(); });
+    } catch (...) {
+        server_free(Sv);
+        return TC_ERR_NOMEM;
+    }
+    *out = Sv;
+    return TC_OK;
+}
+
+static int submit(tc_server *S, Req &&q, uint64_t *ticket) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->fatal) return S->fatal;
+    q.ticket = S->next_ticket++;
+    q.t_submit = S->now();
+    if (ticket) *ticket = q.ticket;
+    S->inbox.push_back(std::move(q));
+    S->submitted++;
+    S->cv_in.notify_one();
+    return TC_OK;
+}
+
+int tc_server_open(tc_server *S, uint64_t r, uint64_t seed, uint32_t stream_id,
+                   uint32_t *handle, uint64_t *ticket) {
+    if (!S || !handle || r == 0 || r > 0xFFFFFFFFull) return TC_ERR_INVAL;
+    if (S->fixed + state_bytes_for(r) > S->cfg.budget_bytes) return TC_ERR_RANGE;
+    Req q;
+    q.kind = TC_REQ_OPEN;
+    q.r = r;
+    q.seed = seed;
+    q.stream_id = stream_id;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        if (S->fatal) return S->fatal;
+        q.handle = S->next_handle++;
+        S->handles[q.handle] = true;
+    }
+    *handle = q.handle;
+    return submit(S, std::move(q), ticket);
+}
+
+static bool handle_open(tc_server *S, uint32_t handle, bool closing) {
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->handles.find(handle);
+    if (it == S->handles.end()) return false;
+    if (closing) S->handles.erase(it);
+    return true;
+}
+
+int tc_server_submit(tc_server *S, uint32_t handle, const uint64_t *h_edges, uint64_t w,
+                     uint64_t *ticket) {
+    if (!S || (w && !h_edges)) return TC_ERR_INVAL;
+    if (w > S->cfg.w_max_round || w > (1ull << 28) ||
+        S->fixed + round_up(8 * w) > S->cfg.budget_bytes)
+        return TC_ERR_RANGE;
+    if (!handle_open(S, handle, false)) return TC_ERR_INVAL;
+    Req q;
+    q.kind = TC_REQ_BATCH;
+    q.handle = handle;
+    q.h_edges = h_edges;
+    q.w = w;
+    return submit(S, std::move(q), ticket);
+}
+
+int tc_server_query(tc_server *S, uint32_t handle, uint64_t *ticket) {
+    if (!S) return TC_ERR_INVAL;
+    if (!handle_open(S, handle, false)) return TC_ERR_INVAL;
+    Req q;
+    q.kind = TC_REQ_QUERY;
+    q.handle = handle;
+    return submit(S, std::move(q), ticket);
+}
+
+int tc_server_close(tc_server *S, uint32_t handle, uint64_t *ticket) {
+    if (!S) return TC_ERR_INVAL;
+    if (!handle_open(S, handle, true)) return TC_ERR_INVAL;
+    Req q;
+    q.kind = TC_REQ_CLOSE;
+    q.handle = handle;
+    return submit(S, std::move(q), ticket);
+}
+
+int tc_server_poll(tc_server *S, tc_completion_t *out, uint32_t max_n, uint32_t wait_us,
+                   uint32_t *n_out) {
+    if (!S || !n_out || (max_n && !out)) return TC_ERR_INVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    if (S->done.empty() && wait_us)
+        S->cv_out.wait_for(lk, std::chrono::microseconds(wait_us),
+                           [&] { return !S->done.empty(); });
+    u32 n = 0;
+    while (n < max_n && !S->done.empty()) {
+        out[n++] = S->done.front();
+        S->done.pop_front();
+    }
+    *n_out = n;
+    return TC_OK;
+}
+
+int tc_server_drain(tc_server *S, uint32_t timeout_ms) {
+    if (!S) return TC_ERR_INVAL;
+    std::unique_lock<std::mutex> lk(S->mu);
+    const bool ok = S->cv_out.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] {
+        return S->completed == S->submitted;
+    });
+    if (!ok) return TC_ERR_TIMEOUT;
+    return S->fatal;
+}
+
+int tc_server_stats(tc_server *S, tc_server_stats_t *out) {
+    if (!S || !out) return TC_ERR_INVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    *out = S->stats;
+    out->bytes_budget = S->cfg.budget_bytes;
+    out->bytes_fixed = S->fixed;
+    return TC_OK;
+}
+
+void tc_server_destroy(tc_server *S) {
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+        S->cv_in.notify_all();
+    }
+    if (S->th.joinable()) S->th.join();
+    server_free(S);
+}
+
+}  // extern "C"

@@ -65,7 +65,10 @@ def test_rounds_match_oracle_and_single_stream(S, vertex_bits):
             cat, offs, parts = _round(streams, cur, sizes)
             if offs[-1] == 0:
                 continue
-            M.process_async(to_device(cat), offs)
+            if rnd % 2:
+                M.process_ptrs_async([to_device(b) if b.size else None for b in parts])
+            else:
+                M.process_async(to_device(cat), offs)
             for s in range(S):
                 if parts[s].size:
                     refs[s].process_batch(parts[s])
