@@ -172,6 +172,60 @@ struct OnesweepSmem {
     u32 vals[kHasValues ? kSortTile : 1];
 };
 
+// Stable ranking of one warp's kSortItems rows of 32 keys: every key goes to
+// its tile staging slot S.cursor[warp][digit] + (earlier equal digits of the
+// warp).  kLive > 0: the digit has exactly kLive live bits (ballot votes on
+// those only); kLive == 0: `live` bits, decided at run time.  kFull: every
+// key of the warp is valid (no tail predicates).
+template <int kBits, int kLive, bool kFull, bool kHasValues, int kRank, typename Smem>
+__device__ __forceinline__ void rank_warp(Smem &S, const u64 (&keys)[kSortItems],
+                                          const u32 (&vals)[kHasValues ? kSortItems : 1],
+                                          u32 nvalid, u32 shift, u32 live, int lane, int warp) {
+    constexpr u32 kMask = (1u << kBits) - 1;
+    const u32 lt_mask = (1u << lane) - 1u;
+#pragma unroll
+    for (int j = 0; j < kSortItems; ++j) {
+        const bool valid = kFull || (u32)(j * 32 + lane) < nvalid;
+        const u32 d = digit_bits(keys[j], shift, kMask);
+        u32 peers;
+        if constexpr (kRank == kRankMatch) {
+            peers = __match_any_sync(0xFFFFFFFFu, valid ? d : (u32)(1u << kBits) + lane);
+        } else if constexpr (kRank == kRankBallot) {
+            peers = kFull ? 0xFFFFFFFFu : __ballot_sync(0xFFFFFFFFu, valid);
+#pragma unroll
+            for (int b = 0; b < kBits; ++b) {
+                if (kLive == 0 ? (u32)b >= live : b >= kLive) break;
+                const bool bit = (d >> b) & 1u;
+                const u32 vote = __ballot_sync(0xFFFFFFFFu, bit);
+                peers &= bit ? vote : ~vote;
+            }
+        } else {
+            u32 *word = &S.peers[j & 1][warp][d];
+            if (valid) atomicOr(word, 1u << lane);
+            __syncwarp();
+            peers = valid ? *word : (1u << lane);
+        }
+        const int leader = 31 - __clz(peers);
+        u32 slot = 0;
+        if (valid && lane == leader) {
+            slot = S.cursor[warp][d];
+            S.cursor[warp][d] = slot + __popc(peers);
+        }
+        if constexpr (kRank == kRankAtomicOr) {
+            // every lane has read this iteration's mask before its leader
+            // clears it; the buffer is next OR-ed two iterations later
+            __syncwarp();
+            if (valid && lane == leader) S.peers[j & 1][warp][d] = 0;
+        }
+        slot = __shfl_sync(0xFFFFFFFFu, slot, leader) + __popc(peers & lt_mask);
+        if (valid) {
+            S.keys[slot] = keys[j];
+            if constexpr (kHasValues) S.vals[slot] = vals[j];
+        }
+        __syncwarp();
+    }
+}
+
 // One digit pass.  keys/vals ping-pong between buffers 0 and 1 as selected
 // by plan_sel(plan, pass); `lookback` holds this pass's status words, tile-major
 // ([tiles][2^kBits]), zeroed before the pass.
@@ -206,7 +260,6 @@ static __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits 
     u32 *__restrict__ vout = sel ? vals0 : vals1;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const bool ranker = true;  // every warp ranks keys
     if (tid == 0) S.tile = atomicAdd(&plan->tile_counter[pass], 1u);
     for (int k = tid; k < kSortWarps * kRadix; k += Shape::kThreads) (&S.cursor[0][0])[k] = 0;
     if constexpr (kRank == kRankAtomicOr)
@@ -217,24 +270,39 @@ static __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits 
     const u64 tile_base = (u64)tile * kSortTile;
     const u64 warp_base = tile_base + (u64)warp * 32 * kSortItems;
     // items of a ranking thread: warp_base + j*32 + lane, valid while < n
-    const u32 nvalid = (!ranker || warp_base >= n)
+    const u32 nvalid = (warp_base >= n)
                            ? 0u
                            : (u32)min((u64)kSortItems * 32, (u64)n - warp_base);
 
+    const bool full = nvalid == (u32)(kSortItems * 32);  // no tail in this warp
     u64 keys[kSortItems];
     u32 vals[kHasValues ? kSortItems : 1];
+    if (full) {
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j) {
-        const bool valid = (u32)(j * 32 + lane) < nvalid;
-        keys[j] = valid ? kin[warp_base + j * 32 + lane] : ~0ull;
-        if constexpr (kHasValues) vals[j] = valid ? vin[warp_base + j * 32 + lane] : 0u;
+        for (int j = 0; j < kSortItems; ++j) {
+            keys[j] = kin[warp_base + j * 32 + lane];
+            if constexpr (kHasValues) vals[j] = vin[warp_base + j * 32 + lane];
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j) {
+            const bool valid = (u32)(j * 32 + lane) < nvalid;
+            keys[j] = valid ? kin[warp_base + j * 32 + lane] : ~0ull;
+            if constexpr (kHasValues) vals[j] = valid ? vin[warp_base + j * 32 + lane] : 0u;
+        }
     }
 
     // -- early digit counts per warp (order-free)
+    if (full) {
 #pragma unroll
-    for (int j = 0; j < kSortItems; ++j)
-        if ((u32)(j * 32 + lane) < nvalid)
+        for (int j = 0; j < kSortItems; ++j)
             atomicAdd(&S.cursor[warp][digit_bits(keys[j], shift, kMask)], 1u);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kSortItems; ++j)
+            if ((u32)(j * 32 + lane) < nvalid)
+                atomicAdd(&S.cursor[warp][digit_bits(keys[j], shift, kMask)], 1u);
+    }
     __syncthreads();
 
     // -- per digit (thread tid owns digits q*256 + tid, so a warp's status
@@ -263,50 +331,17 @@ static __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits 
     }
     __syncthreads();
 
-    if (ranker) {
-        // -- stable ranking inside each warp, written straight to the staging area
-        const u32 lt_mask = (1u << lane) - 1u;
-#pragma unroll
-        for (int j = 0; j < kSortItems; ++j) {
-            const bool valid = (u32)(j * 32 + lane) < nvalid;
-            const u32 d = digit_bits(keys[j], shift, kMask);
-            u32 peers;
-            if constexpr (kRank == kRankMatch) {
-                peers = __match_any_sync(0xFFFFFFFFu, valid ? d : (u32)kRadix + lane);
-            } else if constexpr (kRank == kRankBallot) {
-                peers = __ballot_sync(0xFFFFFFFFu, valid);
-#pragma unroll
-                for (int b = 0; b < kBits; ++b) {
-                    if ((u32)b >= live) break;
-                    const bool bit = (d >> b) & 1u;
-                    const u32 vote = __ballot_sync(0xFFFFFFFFu, bit);
-                    peers &= bit ? vote : ~vote;
-                }
-            } else {
-                u32 *word = &S.peers[j & 1][warp][d];
-                if (valid) atomicOr(word, 1u << lane);
-                __syncwarp();
-                peers = valid ? *word : (1u << lane);
-            }
-            const int leader = 31 - __clz(peers);
-            u32 slot = 0;
-            if (valid && lane == leader) {
-                slot = S.cursor[warp][d];
-                S.cursor[warp][d] = slot + __popc(peers);
-            }
-            if constexpr (kRank == kRankAtomicOr) {
-                // every lane has read this iteration's mask before its leader
-                // clears it; the buffer is next OR-ed two iterations later
-                __syncwarp();
-                if (valid && lane == leader) S.peers[j & 1][warp][d] = 0;
-            }
-            slot = __shfl_sync(0xFFFFFFFFu, slot, leader) + __popc(peers & lt_mask);
-            if (valid) {
-                S.keys[slot] = keys[j];
-                if constexpr (kHasValues) S.vals[slot] = vals[j];
-            }
-            __syncwarp();
-        }
+    // -- stable ranking inside each warp, written straight to the staging area
+    if (full) {
+        if (kRank != kRankBallot || live >= (u32)kBits)
+            rank_warp<kBits, kBits, true, kHasValues, kRank>(S, keys, vals, nvalid, shift, live,
+                                                             lane, warp);
+        else
+            rank_warp<kBits, 0, true, kHasValues, kRank>(S, keys, vals, nvalid, shift, live, lane,
+                                                         warp);
+    } else {
+        rank_warp<kBits, 0, false, kHasValues, kRank>(S, keys, vals, nvalid, shift, live, lane,
+                                                      warp);
     }
     {
         // -- look-back: each thread walks back for its kDPT digits, in aligned
