@@ -68,7 +68,7 @@ def _args():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    p.add_argument("--workload", choices=["rmat20", "tiny", "multi512", "serve4096"], default="rmat20")
+    p.add_argument("--workload", choices=["rmat20", "tiny", "large", "multi512", "serve4096"], default="rmat20")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--no-autotune", action="store_true",
@@ -78,8 +78,13 @@ def _args():
 
 def _workload(name):
     import synth
-    cfg = dict(synth.WORKLOADS[name])
-    keys = synth.rmat20_single() if name == "rmat20" else synth.tiny_chung_lu()
+    cfg = dict(synth.WORKLOADS[name], name=name)
+    if name == "rmat20":
+        keys = synth.rmat20_single()
+    elif name == "large":
+        keys = synth.large_prefix(2)     # the first two batches of the 1.2e9-edge stream
+    else:
+        keys = synth.tiny_chung_lu()
     cfg["m"] = int(keys.size)
     return cfg, keys
 
@@ -161,6 +166,57 @@ def _cpu_baseline(keys, cfg, budget_s=20.0):
             "kind": "oracle",
             "sample": f"first {nb} batch(es) ({done} edges) of the stream at r={cfg['r']}, "
                       f"w={cfg['w']}, single process, {t_all:.1f} s"}
+
+
+def reduce_over_ranks(dist, t, units, device):
+    """Whole-job timing of replicas: the slowest rank's time and the units
+    (edges) of all ranks; (t, units) unchanged without a process group."""
+    if dist is None:
+        return t, float(units)
+    import torch
+    tt = torch.tensor([float(t)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    uu = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(uu)
+    return float(tt.item()), float(uu.item())
+
+
+def _l2_note(cfg, n_batches):
+    w, r = cfg["w"], cfg["r"]
+    ws = 8 * w + 2 * 16 * w + 2 * 8 * w + 28 * r
+    return (f"working set per step {ws / 2**20:.0f} MB (batch, arcs x2, edge keys x2, state) vs "
+            f"the 126 MB L2; each step reads a batch untouched for the previous "
+            f"{n_batches - 1} steps" if ws > 126 * 2**20 else
+            f"working set per step {ws / 2**20:.1f} MB fits in L2 (launch-bound case)")
+
+
+def _accuracy(tc, cfg, keys, dev_batches, rank):
+    """One pass over the whole stream on a fresh context (untimed): tau_hat
+    against the exact count stored in tests/golden/exact_tau.json (by a
+    script that calls only the CPU exact counter) when the generated stream
+    hashes the same, and the epsilon that Theorem 3.2's sample bound gives
+    for this r at delta = 0.05."""
+    import hashlib
+    import math
+    ctx = tc.tc_create_ex(cfg["r"], cfg["seed"], rank, cfg["w"], cfg["vertex_bits"])
+    try:
+        for b in dev_batches:
+            tc.tc_process_batch(ctx, b)
+        est = tc.tc_estimate(ctx)
+    finally:
+        tc.tc_destroy(ctx)
+    out = {"tau_hat": est["tau_hat"], "m": est["m"], "n_closed": est["n_closed"],
+           "r": cfg["r"], "batches": est["batches"]}
+    path = os.path.join(ROOT, "tests", "golden", "exact_tau.json")
+    name = cfg.get("name")
+    gold = json.load(open(path)).get(name) if os.path.exists(path) and name else None
+    if gold and gold["keys_sha256"] == hashlib.sha256(keys.astype("<u8").tobytes()).hexdigest():
+        tau = gold["tau"]
+        out["tau_exact"] = tau
+        out["rel_error"] = abs(est["tau_hat"] - tau) / tau
+        out["thm32_eps_delta_0.05"] = math.sqrt(96.0 * gold["m"] * gold["max_degree"] / tau *
+                                                math.log(1 / 0.05) / cfg["r"])
+    return out
 
 
 def run_reference(args, rank, world):
@@ -275,18 +331,8 @@ def run_gpu(args, rank, world, local_rank):
     clocks = sampler.stop() if sampler else None
     tc.tc_sync(ctx)
     per_step = [evs[j].elapsed_time(evs[j + 1]) for j in range(args.steps)]
-    t_ms = evs[0].elapsed_time(evs[-1])
-    if dist:
-        t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-        e = torch.tensor([edges], dtype=torch.float64, device="cuda")
-        dist.all_reduce(e)
-        edges_all = float(e.item())
-    else:
-        edges_all = float(edges)
+    t_ms, edges_all = reduce_over_ranks(dist, evs[0].elapsed_time(evs[-1]), edges, "cuda")
     value = edges_all / (t_ms / 1e3)
-    est = tc.estimate_from_words(est_words.cpu().numpy().view(np.uint64), r)
 
     # ---- end to end: pinned host batches through the synchronous C-ABI call
     e2e_steps = args.e2e_steps or min(args.steps, 40)
@@ -306,12 +352,8 @@ def run_gpu(args, rank, world, local_rank):
         tc.tc_process_batch(ctx, hb)
         tc.tc_estimate(ctx)          # D2H of the step's result
         e2e_edges += hb.numel()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = e2e_edges * world / e2e_s
+    e2e_s, e2e_all = reduce_over_ranks(dist, time.perf_counter() - t0, e2e_edges, "cuda")
+    e2e_value = e2e_all / e2e_s
 
     if rank != 0:
         tc.tc_destroy(ctx)
@@ -360,9 +402,7 @@ def run_gpu(args, rank, world, local_rank):
                             "ranking": autotune.RANKINGS[tuning[2]],
                             "table_ms": {f"{a}/{b}/{autotune.RANKINGS[c]}": round(v, 4)
                                          for (a, b, c), v in sorted(tune_table.items())}},
-            "l2": "working set per step (batch 32 MB, arcs 2x64 MB, edge keys 2x32 MB, state "
-                  "28 MB) exceeds the 126 MB L2; each step reads a batch untouched for the "
-                  "previous 3 steps",
+            "l2": _l2_note(cfg, len(dev_batches)),
         },
         "updates_per_s": value * r,
         "p50_ms": statistics.median(per_step),
@@ -379,7 +419,7 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": w * 8,
                 "d2h_bytes_per_step": 32, "steps": e2e_steps},
-        "estimate": {"tau_hat": est["tau_hat"], "m": est["m"]},
+        "estimate": _accuracy(tc, cfg, keys, dev_batches, rank),
         "src_hash": _src_hash(),
     }
     tc.tc_destroy(ctx)

@@ -35,6 +35,21 @@ def rmat20_single(gen_seed: int = 1, scale: int = 20) -> np.ndarray:
     return finish(keys, 1 << scale, seed=gen_seed + 1000)
 
 
+def large_prefix(n_batches: int = 2, gen_seed: int = 1) -> np.ndarray:
+    """The first n_batches * 2^24 edges of the ``large`` stream.
+
+    Chung-Lu, exponent 2.1, n = 2^25, expected degrees scaled to the full
+    stream's mean (2 * 1.2e9 / 2^25, about 71.5) and capped at 3e5.  Endpoint
+    sampling draws every edge independently, so the first k distinct samples
+    (relabelled, in random order) are a prefix of a random-order stream of
+    the full graph; only that prefix is generated.
+    """
+    n = 1 << 25
+    mean_degree = 2 * 1.2e9 / n
+    keys = chung_lu(n, 2.1, mean_degree, n_batches << 24, seed=gen_seed, max_degree=3e5)
+    return finish(keys, n, seed=gen_seed + 1000)
+
+
 def batches(keys: np.ndarray, w: int):
     """Split a stream into consecutive batches of w edges (last may be short)."""
     return [keys[i:i + w] for i in range(0, keys.size, w)]
