@@ -163,9 +163,13 @@ typedef struct {
     uint64_t sort_pass_skipped;   /* passes that found one digit value and did no work */
     uint64_t overflow;            /* 1 if events ran out and some stages went unrecorded */
     double ms_prep;               /* key build, histograms, validation, sort plans */
-    double ms_arc_sort;           /* rankAll digit passes (Lemma 4.3) */
-    double ms_edge_sort;          /* Step-3 `edges` digit passes (Sec. 4.4) */
-    double ms_dups;               /* in-batch repeat check */
+    double ms_arc_sort;           /* rankAll digit passes (Lemma 4.3), with the
+                                     Step-3 `edges` passes (Sec. 4.4) running
+                                     beside them on a second CUDA stream */
+    double ms_edge_sort;          /* the rest of the `edges` passes after the
+                                     arc passes end (the two sum to the wall
+                                     time of both sorts) */
+    double ms_dups;               /* directories and in-batch repeat check */
     double ms_sweep;              /* fused Steps 1-3 per estimator (searches) */
     double ms_finish;             /* batch bookkeeping */
     double ms_estimate;           /* tc_estimate / tc_estimate_async reductions */

@@ -170,6 +170,9 @@ struct tc_ctx {
     u32 force_bits_a = 0, force_bits_e = 0;  // tc_tune digit widths (0 = automatic)
     int rank_method = kRankBallot;           // tc_tune warp ranking method
     cudaStream_t own = nullptr;
+    // the edge sort runs on `side`, concurrently with the arc sort
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // estimator state (structure of arrays)
     u64 *f1 = nullptr, *f2 = nullptr, *chi = nullptr;
     u32 *flags = nullptr;
@@ -272,17 +275,25 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
     const u64 la = pass_lookback_words(2 * w, s.bits_a), le = pass_lookback_words(w, s.bits_e);
     const PassKernel ka = select_pass(s.bits_a, false, c->rank_method);
     const PassKernel ke = select_pass(s.bits_e, !s.ekeys_only, c->rank_method);
-    for (int p = 0; p < s.npa; ++p)
-        ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(
-            c->arcs[0], c->arcs[1], nullptr, nullptr, (u32)(2 * w), s.sha + p * s.bits_a, live_bits(s.B, s.bits_a, p), p,
-            &plans[0], lb + (u64)p * la, &c->ctl->err, c->ctl);
-    stamp(c, st, kArcSort);
+    // The two sorts are independent: the edge sort forks onto the side
+    // stream and joins before the index build, so the passes of one fill the
+    // SMs the other leaves idle (tails of its waves, look-back waits).
+    TC_CUDA(cudaEventRecord(c->ev_fork, st));
+    TC_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     u32 *lbe = lb + (u64)s.npa * la;
     for (int p = 0; p < s.npe; ++p)
-        ke.fn<<<(unsigned)te, ke.threads, ke.smem, st>>>(
-            c->ekeys[0], c->ekeys[1], c->evals[0], c->evals[1], (u32)w, s.she + p * s.bits_e, live_bits(2 * s.B, s.bits_e, p), p,
-            &plans[1], lbe + (u64)p * le, &c->ctl->err, c->ctl);
-    stamp(c, st, kEdgeSort);
+        ke.fn<<<(unsigned)te, ke.threads, ke.smem, c->side>>>(
+            c->ekeys[0], c->ekeys[1], c->evals[0], c->evals[1], (u32)w, s.she + p * s.bits_e,
+            live_bits(2 * s.B, s.bits_e, p), p, &plans[1], lbe + (u64)p * le, &c->ctl->err,
+            c->ctl);
+    TC_CUDA(cudaEventRecord(c->ev_join, c->side));
+    for (int p = 0; p < s.npa; ++p)
+        ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(
+            c->arcs[0], c->arcs[1], nullptr, nullptr, (u32)(2 * w), s.sha + p * s.bits_a,
+            live_bits(s.B, s.bits_a, p), p, &plans[0], lb + (u64)p * la, &c->ctl->err, c->ctl);
+    stamp(c, st, kArcSort);  // arc sort, with the edge sort running beside it
+    TC_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
+    stamp(c, st, kEdgeSort);  // what is left of the edge sort after the arcs
     if (c->adir) {
         const u64 idx_blocks = std::min<u64>((3 * w + 255) / 256, 152 * 16);
         index_kernel<<<(unsigned)idx_blocks, 256, 0, st>>>(c->arcs[0], c->arcs[1], c->ekeys[0],
@@ -384,6 +395,9 @@ int tc_create_ex(uint64_t r, uint64_t seed, uint32_t stream_id, uint64_t w_max,
     c->vertex_bits = vertex_bits;
     bool ok = cudaGetDevice(&c->device) == cudaSuccess;
     ok &= ok && cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) == cudaSuccess;
+    ok &= ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
+    ok &= ok && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    ok &= ok && cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
     ok &= ok && cudaMalloc(&c->f1, r * sizeof(u64)) == cudaSuccess;
     ok &= ok && cudaMalloc(&c->f2, r * sizeof(u64)) == cudaSuccess;
     ok &= ok && cudaMalloc(&c->chi, r * sizeof(u64)) == cudaSuccess;
@@ -440,6 +454,9 @@ void tc_destroy(tc_ctx *c) {
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     for (cudaEvent_t ev : c->pool) cudaEventDestroy(ev);
     if (c->own) cudaStreamDestroy(c->own);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 

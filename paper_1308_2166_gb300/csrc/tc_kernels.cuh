@@ -240,6 +240,16 @@ struct SweepArgs {
 
 constexpr int kSweepThreads = 256;
 
+// The two non-shared endpoints of the wedge (f1, f2): the closing edge
+// (gu < gv) that Step 3 looks up.
+__device__ __forceinline__ void closing_pair(u64 f1, u64 f2, u64 &gu, u64 &gv) {
+    const u64 a1 = f1 >> 32, b1 = f1 & kMask32, a2 = f2 >> 32, b2 = f2 & kMask32;
+    const u64 x1 = (a1 == a2 || a1 == b2) ? b1 : a1;
+    const u64 x2 = (a2 == a1 || a2 == b1) ? b2 : a2;
+    gu = x1 < x2 ? x1 : x2;
+    gv = x1 < x2 ? x2 : x1;
+}
+
 // One estimator: Steps 1-3 of Sec. 4 applied to its state in place.
 template <bool kDir>
 __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 epoch,
@@ -302,11 +312,8 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
 
     // ---- Step 3 (Sec. 4.4): closing edge after f2
     if (f2 != kEmpty && !(fl & TC_FLAG_CLOSED)) {
-        const u64 a1 = f1 >> 32, b1 = f1 & kMask32, a2 = f2 >> 32, b2 = f2 & kMask32;
-        const u64 x1 = (a1 == a2 || a1 == b2) ? b1 : a1;
-        const u64 x2 = (a2 == a1 || a2 == b1) ? b2 : a2;
-        const u64 gu = x1 < x2 ? x1 : x2, gv = x1 < x2 ? x2 : x1;
-        u64 lo = 0, hi = s.w;
+        u64 gu, gv, lo = 0, hi = s.w;
+        closing_pair(f1, f2, gu, gv);
         if constexpr (kDir) dir_segment(a.edir, epoch, gu, lo, hi);
         bool found;
         u32 q;
@@ -343,13 +350,15 @@ static __global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArg
         const bool e_sel = plan_final_sel(&a.plans[1]) != 0;
         const u64 *E = e_sel ? a.ekeys1 : a.ekeys0;
         const u32 *EV = e_sel ? a.evals1 : a.evals0;
-        u64 f1 = a.f1[i], f2 = a.f2[i], chi = a.chi[i];
-        u32 fl = a.flags[i];
+        // the state streams through once: evict-first, so that L2 keeps the
+        // directories and sorted arrays the searches hit at random
+        u64 f1 = __ldcs(a.f1 + i), f2 = __ldcs(a.f2 + i), chi = __ldcs(a.chi + i);
+        u32 fl = __ldcs(a.flags + i);
         sweep_one<kDir>(a, i, m, epoch, dk, arcs, E, EV, f1, f2, chi, fl);
-        a.f1[i] = f1;
-        a.f2[i] = f2;
-        a.chi[i] = chi;
-        a.flags[i] = fl;
+        __stcs(a.f1 + i, f1);
+        __stcs(a.f2 + i, f2);
+        __stcs(a.chi + i, chi);
+        __stcs(a.flags + i, fl);
         if (fl & TC_FLAG_CLOSED) {
             add = chi;
             closed = 1;

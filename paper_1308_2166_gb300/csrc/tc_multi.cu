@@ -445,6 +445,9 @@ void multi_free(tc_multi *M) {
     if (M->h_ms) cudaFreeHost(M->h_ms);
     if (M->gexec) cudaGraphExecDestroy(M->gexec);
     cudaFree(M->g_desc);
+    if (M->side) cudaStreamDestroy(M->side);
+    if (M->ev_fork) cudaEventDestroy(M->ev_fork);
+    if (M->ev_join) cudaEventDestroy(M->ev_join);
     delete M;
 }
 
@@ -481,6 +484,9 @@ int multi_alloc(u32 S, u64 w_max_round, u32 vertex_bits, tc_multi **out) {
         ok &= ok && cudaEventCreateWithFlags(&M->ring_ev[k], cudaEventDisableTiming) == cudaSuccess;
     }
     ok &= ok && cudaHostAlloc(&M->h_ms, S * sizeof(MStream), cudaHostAllocDefault) == cudaSuccess;
+    ok &= ok && cudaStreamCreateWithFlags(&M->side, cudaStreamNonBlocking) == cudaSuccess;
+    ok &= ok && cudaEventCreateWithFlags(&M->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+    ok &= ok && cudaEventCreateWithFlags(&M->ev_join, cudaEventDisableTiming) == cudaSuccess;
     if (ok) {
         ok &= cudaMemset(M->ms, 0, S * sizeof(MStream)) == cudaSuccess;
         ok &= cudaMemset(M->zeroed, 0, M->zeroed_bytes) == cudaSuccess;
@@ -573,16 +579,21 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, const u64 *desc, u
     const PassK ka = mselect(rs.bits_a, false, M->rank);
     const PassK ke = mselect(rs.bits_e, true, M->rank);
     const u64 ta = mtiles(2 * Wt), te = mtiles(Wt);
+    // the two sorts are independent: the edge sort forks onto the side stream
+    TCM_CUDA(cudaEventRecord(M->ev_fork, st));
+    TCM_CUDA(cudaStreamWaitEvent(M->side, M->ev_fork, 0));
+    u32 *lbe = lb + (u64)rs.npa * la;
+    for (int p = 0; p < rs.npe; ++p)
+        ke.fn<<<(unsigned)te, ke.threads, ke.smem, M->side>>>(
+            M->ekeys[0], M->ekeys[1], M->evals[0], M->evals[1], (u32)Wt, p * rs.bits_e,
+            mlive(2 * M->B + rs.kb, rs.bits_e, p), p, &plans[1], lbe + (u64)p * le, gerr,
+            nullptr);
+    TCM_CUDA(cudaEventRecord(M->ev_join, M->side));
     for (int p = 0; p < rs.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(
             M->arcs[0], M->arcs[1], nullptr, nullptr, (u32)(2 * Wt), rs.sha + p * rs.bits_a,
             mlive(M->B + rs.kb, rs.bits_a, p), p, &plans[0], lb + (u64)p * la, gerr, nullptr);
-    u32 *lbe = lb + (u64)rs.npa * la;
-    for (int p = 0; p < rs.npe; ++p)
-        ke.fn<<<(unsigned)te, ke.threads, ke.smem, st>>>(
-            M->ekeys[0], M->ekeys[1], M->evals[0], M->evals[1], (u32)Wt, p * rs.bits_e,
-            mlive(2 * M->B + rs.kb, rs.bits_e, p), p, &plans[1], lbe + (u64)p * le, gerr,
-            nullptr);
+    TCM_CUDA(cudaStreamWaitEvent(st, M->ev_join, 0));
     const u64 db = std::min<u64>((Wt + 255) / 256, 1216);
     mdups_kernel<<<(unsigned)db, 256, 0, st>>>(M->ekeys[0], M->ekeys[1], plans, desc, rs, M->ms);
     MSweepArgs a{};

@@ -68,6 +68,8 @@ struct tc_multi {
     cudaEvent_t ring_ev[tc::kRing] = {};
     int ring = 0;
     tc::u64 launches = 0;
+    cudaStream_t side = nullptr;         // the edge sort runs here, beside the arc sort
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     tc::MStream *h_ms = nullptr;         // pinned host copy for reads
     cudaGraphExec_t gexec = nullptr;     // captured round (tc_multi_capture)
     tc::u64 *g_desc = nullptr;           // its fixed descriptor
