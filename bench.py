@@ -68,7 +68,7 @@ def _args():
     p.add_argument("--steps", type=int, default=200)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    p.add_argument("--workload", choices=["rmat20", "tiny", "large", "multi512", "serve4096"], default="rmat20")
+    p.add_argument("--workload", choices=["rmat20", "tiny", "large", "multi512", "serve4096", "wsweep"], default="rmat20")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--no-autotune", action="store_true",
@@ -765,6 +765,76 @@ def run_serve(args, rank, world, local_rank):
     return 0
 
 
+def run_wsweep(args, rank, world, local_rank):
+    """Throughput against batch size and the time split by stage (the
+    analogues of the paper's Figs. 7 and 6) on the rmat20 stream at
+    r = 2^20: for each w from 2^16 to 2^23 the stream is cut into batches of
+    w edges, 3 batches warm up, then enough batches for at least 2^25 edges
+    (and at least 8) are timed on the device; each row gives edges/s,
+    edge-estimator updates/s, ms per batch and the stage times per batch."""
+    import torch
+    import paper_1308_2166_gb300 as tc
+    import synth
+    from paper_1308_2166_gb300 import build
+
+    torch.cuda.set_device(local_rank)
+    build.build()
+    tc.load()
+    cfg, keys = _workload("rmat20")
+    r, vb = cfg["r"], cfg["vertex_bits"]
+    dev = torch.from_numpy(keys.view(np.int64)).cuda()
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    rows = []
+    sampler = ClockSampler(local_rank)
+    for lw in range(16, 24):
+        w = 1 << lw
+        nb = keys.size // w
+        views = [dev[j * w:(j + 1) * w] for j in range(nb)]
+        ctx = tc.tc_create_ex(r, cfg["seed"], 0, w, vb)
+        steps = max(8, (1 << 25) // w)
+        with torch.cuda.stream(stream):
+            for j in range(3):
+                tc.tc_process_batch_async(ctx, views[j % nb], stream=sh)
+        tc.tc_sync(ctx)
+        torch.cuda.synchronize()
+        tc.tc_profile_begin(ctx)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            for j in range(steps):
+                tc.tc_process_batch_async(ctx, views[(3 + j) % nb], stream=sh)
+            ev1.record(stream)
+        stream.synchronize()
+        prof = tc.tc_profile_end(ctx)
+        tc.tc_sync(ctx)
+        tc.tc_destroy(ctx)
+        ms = ev0.elapsed_time(ev1)
+        st = {k[3:]: round(1e3 * prof[k] / steps, 2) for k in
+              ("ms_prep", "ms_arc_sort", "ms_edge_sort", "ms_dups", "ms_sweep", "ms_finish")}
+        tot = sum(st.values())
+        rows.append({"w": w, "edges_per_s": steps * w / (ms / 1e3),
+                     "updates_per_s": steps * w * r / (ms / 1e3), "ms_per_batch": ms / steps,
+                     "batches_timed": steps, "stage_us_per_batch": st,
+                     "share": {"sort": round((st["arc_sort"] + st["edge_sort"]) / tot, 3),
+                               "search_sweep": round(st["sweep"] / tot, 3),
+                               "other": round((st["prep"] + st["dups"] + st["finish"]) / tot, 3)}})
+    clocks = sampler.stop()
+    head = next(x for x in rows if x["w"] == cfg["w"])
+    line = {
+        "metric": "edges/s against batch size w (rmat20 stream, r = 2^20)",
+        "value": head["edges_per_s"], "unit": UNIT, "n_gpus": 1,
+        "steps": sum(x["batches_timed"] for x in rows), "warmup": 3,
+        "ms_per_step": head["ms_per_batch"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": f"wsweep: rmat20 ({cfg['graph']}, m={keys.size}), r={r}, "
+                               f"w = 2^16 .. 2^23; value at w = {cfg['w']}"},
+        "table": rows, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     rank = int(os.environ.get("RANK", "0"))
@@ -776,6 +846,8 @@ def main():
         return run_multi(args, rank, world, local_rank)
     if args.workload == "serve4096":
         return run_serve(args, rank, world, local_rank)
+    if args.workload == "wsweep":
+        return run_wsweep(args, rank, world, local_rank)
     return run_gpu(args, rank, world, local_rank)
 
 

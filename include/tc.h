@@ -395,6 +395,16 @@ int tc_server_stats(tc_server *S, tc_server_stats_t *out);
  * requests not yet in a round are dropped without completion. */
 void tc_server_destroy(tc_server *S);
 
+/* Self-test of the bounded device-side waits (no counterpart in the paper;
+ * the radix sort's look-back is the library's only spin-wait).  Runs one
+ * digit pass over two tiles of keys with a single CTA that is handed tile 1,
+ * so the predecessor its look-back waits for never publishes; the wait gives
+ * up after its iteration limit (about a second), records the timeout and the
+ * CTA finishes.  Returns TC_ERR_TIMEOUT when that happened (the expected
+ * result), TC_OK if the wait somehow completed, TC_ERR_CUDA on a CUDA error.
+ * The device stays usable afterwards.  Synchronises the device. */
+int tc_selftest_wait_timeout(void);
+
 /* Largest batch tc_rank_all_noalloc accepts. */
 #define TC_NOALLOC_MAX_EDGES (1u << 18)
 

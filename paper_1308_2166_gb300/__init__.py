@@ -37,7 +37,7 @@ EXPORTS = (
     "tc_multi_replay", "tc_process_batches_async", "tc_multi_process_ptrs_async",
     "tc_server_create", "tc_server_open", "tc_server_submit", "tc_server_query",
     "tc_server_close", "tc_server_poll", "tc_server_drain", "tc_server_stats",
-    "tc_server_destroy",
+    "tc_server_destroy", "tc_selftest_wait_timeout",
 )
 
 TC_REQ_OPEN, TC_REQ_BATCH, TC_REQ_QUERY, TC_REQ_CLOSE = 1, 2, 3, 4
@@ -148,6 +148,7 @@ def load(path: str | None = None):
         "tc_server_drain": (I, [P, U32]),
         "tc_server_stats": (I, [P, ctypes.POINTER(tc_server_stats_t)]),
         "tc_server_destroy": (None, [P]),
+        "tc_selftest_wait_timeout": (I, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -336,6 +337,12 @@ class TriangleStream:
             self.close()
         except Exception:
             pass
+
+
+def tc_selftest_wait_timeout() -> int:
+    """Run the bounded-wait self-test; returns its TC_* code (TC_ERR_TIMEOUT
+    is the expected result)."""
+    return load().tc_selftest_wait_timeout()
 
 
 def tc_rank_all_noalloc(d_edges, w: int, vertex_bits: int, d_src, d_dst, d_pos, d_rank,

@@ -814,3 +814,49 @@ extern "C" int tc_rank_all_noalloc(const uint64_t *d_edges, uint64_t w, uint32_t
     TC_CUDA(cudaStreamSynchronize(st));
     return map_device_error(h_err & kErrTimeout);
 }
+
+// ---- self-test of the bounded device-side waits -----------------------------
+// One keys-only 8-bit digit pass over two tiles with a single CTA whose tile
+// counter starts at 1: it takes tile 1, and tile 0 -- the predecessor its
+// look-back waits for -- is never processed, so the wait must give up after
+// kSpinLimit idle rounds and record kErrTimeout.  Every key has digit 0, so
+// the scatter after the timeout stays inside the output buffer.
+extern "C" int tc_selftest_wait_timeout(void) {
+    int rc = configure_kernels();
+    if (rc) return rc;
+    constexpr u32 n = 2 * kSortTile;
+    const u64 lb_words = (u64)lookback_stride(2) << 8;
+    u64 *k0 = nullptr, *k1 = nullptr;
+    SortPlan *plan = nullptr;
+    u32 *lb = nullptr, *err = nullptr;
+    bool ok = cudaMalloc(&k0, n * sizeof(u64)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&k1, n * sizeof(u64)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&plan, sizeof(SortPlan)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&lb, lb_words * sizeof(u32)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&err, sizeof(u32)) == cudaSuccess;
+    u32 h_err = 0;
+    if (ok) {
+        const u32 one = 1;
+        ok &= cudaMemset(k0, 0, n * sizeof(u64)) == cudaSuccess;
+        ok &= cudaMemset(plan, 0, sizeof(SortPlan)) == cudaSuccess;
+        ok &= cudaMemcpy(&plan->tile_counter[0], &one, sizeof(u32), cudaMemcpyHostToDevice) ==
+              cudaSuccess;
+        ok &= cudaMemset(lb, 0, lb_words * sizeof(u32)) == cudaSuccess;
+        ok &= cudaMemset(err, 0, sizeof(u32)) == cudaSuccess;
+        const PassKernel k = select_pass(8, false, kRankBallot);
+        if (ok) {
+            k.fn<<<1, k.threads, k.smem>>>(k0, k1, nullptr, nullptr, n, 0, 8, 0, plan, lb, err,
+                                           nullptr);
+            ok &= cudaGetLastError() == cudaSuccess;
+            ok &= cudaDeviceSynchronize() == cudaSuccess;
+            ok &= ok && cudaMemcpy(&h_err, err, sizeof(u32), cudaMemcpyDeviceToHost) == cudaSuccess;
+        }
+    }
+    cudaFree(k0);
+    cudaFree(k1);
+    cudaFree(plan);
+    cudaFree(lb);
+    cudaFree(err);
+    if (!ok) return TC_ERR_CUDA;
+    return h_err == kErrTimeout ? TC_ERR_TIMEOUT : h_err ? TC_ERR_CUDA : TC_OK;
+}

@@ -107,6 +107,25 @@ def test_empty_batch_is_noop():
         tc.tc_destroy(ctx)
 
 
+def test_bounded_wait_gives_up_and_device_stays_usable():
+    """A look-back wait whose predecessor never publishes runs out (about a
+    second) and reports TC_ERR_TIMEOUT; afterwards a batch still matches the
+    oracle."""
+    import time
+    t0 = time.perf_counter()
+    assert tc.tc_selftest_wait_timeout() == tc.TC_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 60.0
+    keys = synth.tiny_chung_lu()[:3000]
+    ctx = tc.tc_create_ex(64, 5, 0, 4096, 12)
+    ref = nbsi_bulk.BulkStream(64, seed=5, stream=0, vertex_bits=12)
+    try:
+        tc.tc_process_batch(ctx, to_device(keys))
+        ref.process_batch(keys)
+        assert_state_equal(tc.tc_get_state(ctx), ref.state_arrays(), "after the timeout")
+    finally:
+        tc.tc_destroy(ctx)
+
+
 def _rank_all_gpu(W, vertex_bits):
     import torch
     n = 2 * W.size
