@@ -163,16 +163,19 @@ typedef struct {
     uint64_t sort_pass_skipped;   /* passes that found one digit value and did no work */
     uint64_t overflow;            /* 1 if events ran out and some stages went unrecorded */
     double ms_prep;               /* key build, histograms, validation, sort plans */
+    /* The two sorts run side by side (the Step-3 `edges` sort and its index
+     * on a second CUDA stream); the next four stages partition the main
+     * stream's time between the sort plans and the sweep: */
     double ms_arc_sort;           /* rankAll digit passes (Lemma 4.3), with the
-                                     Step-3 `edges` passes (Sec. 4.4) running
-                                     beside them on a second CUDA stream */
-    double ms_edge_sort;          /* the rest of the `edges` passes after the
-                                     arc passes end (the two sum to the wall
-                                     time of both sorts) */
-    double ms_dups;               /* directories and in-batch repeat check */
+                                     `edges` passes (Sec. 4.4) beside them */
+    double ms_edge_sort;          /* what is left of the `edges` passes and
+                                     their directory after the arc index */
+    double ms_dups;               /* arc directory, beside the `edges` branch */
     double ms_sweep;              /* fused Steps 1-3 per estimator (searches) */
     double ms_finish;             /* batch bookkeeping */
     double ms_estimate;           /* tc_estimate / tc_estimate_async reductions */
+    double ms_sort_wall;          /* wall time of both sorts' digit passes:
+                                     from their start to the later end */
 } tc_profile_t;
 
 int tc_profile_begin(tc_ctx *c);

@@ -64,7 +64,7 @@ class tc_profile_t(ctypes.Structure):
                 ("ms_prep", ctypes.c_double), ("ms_arc_sort", ctypes.c_double),
                 ("ms_edge_sort", ctypes.c_double), ("ms_dups", ctypes.c_double),
                 ("ms_sweep", ctypes.c_double), ("ms_finish", ctypes.c_double),
-                ("ms_estimate", ctypes.c_double)]
+                ("ms_estimate", ctypes.c_double), ("ms_sort_wall", ctypes.c_double)]
 
 
 class tc_server_config_t(ctypes.Structure):

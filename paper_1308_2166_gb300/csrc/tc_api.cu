@@ -196,10 +196,27 @@ struct tc_ctx {
         int stage;  // stage that ends here; kStart opens a sequence
     };
     std::vector<Stamp> stamps;
+    // per batch: sorts begin (main), arc passes end (main), edge passes end (side)
+    struct SortSpan {
+        cudaEvent_t begin, arc_end, edge_end;
+    };
+    std::vector<SortSpan> spans;
     u64 prof_launch0 = 0, prof_batches = 0, prof_sort_launches = 0, prof_sort_bytes = 0;
     u64 prof_skip0 = 0, prof_skipbytes0 = 0;
     bool prof_overflow = false;
 };
+
+// A profiling event recorded on `st` (nullptr when not profiling or out of events).
+static cudaEvent_t mark(tc_ctx *c, cudaStream_t st) {
+    if (!c->prof) return nullptr;
+    if (c->pool_used >= c->pool.size()) {
+        c->prof_overflow = true;
+        return nullptr;
+    }
+    cudaEvent_t ev = c->pool[c->pool_used++];
+    cudaEventRecord(ev, st);
+    return ev;
+}
 
 static void stamp(tc_ctx *c, cudaStream_t st, int stage) {
     if (!c->prof) return;
@@ -275,36 +292,44 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
     const u64 la = pass_lookback_words(2 * w, s.bits_a), le = pass_lookback_words(w, s.bits_e);
     const PassKernel ka = select_pass(s.bits_a, false, c->rank_method);
     const PassKernel ke = select_pass(s.bits_e, !s.ekeys_only, c->rank_method);
-    // The two sorts are independent: the edge sort forks onto the side
-    // stream and joins before the index build, so the passes of one fill the
-    // SMs the other leaves idle (tails of its waves, look-back waits).
+    // The two sorts are independent: the edge sort (and, with directories,
+    // its index) forks onto the side stream and joins before the sweep, so
+    // the kernels of one fill the SMs the other leaves idle (tails of its
+    // waves, look-back waits).
     TC_CUDA(cudaEventRecord(c->ev_fork, st));
     TC_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    const cudaEvent_t sort_begin = mark(c, st);
     u32 *lbe = lb + (u64)s.npa * la;
     for (int p = 0; p < s.npe; ++p)
         ke.fn<<<(unsigned)te, ke.threads, ke.smem, c->side>>>(
             c->ekeys[0], c->ekeys[1], c->evals[0], c->evals[1], (u32)w, s.she + p * s.bits_e,
             live_bits(2 * s.B, s.bits_e, p), p, &plans[1], lbe + (u64)p * le, &c->ctl->err,
             c->ctl);
+    const cudaEvent_t edge_end = mark(c, c->side);
+    const u64 idx_blocks = std::min<u64>((w + 255) / 256, 152 * 16);
+    if (c->adir) {
+        index_kernel<false><<<(unsigned)idx_blocks, 256, 0, c->side>>>(
+            c->ekeys[0], c->ekeys[1], &plans[1], s, c->edir, c->ctl, &c->ctl->err);
+    } else {
+        const u64 dup_blocks = std::min<u64>((w + 255) / 256, 1216);
+        dups_kernel<<<(unsigned)dup_blocks, 256, 0, c->side>>>(c->ekeys[0], c->ekeys[1], plans,
+                                                               s, &c->ctl->err);
+    }
     TC_CUDA(cudaEventRecord(c->ev_join, c->side));
     for (int p = 0; p < s.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(
             c->arcs[0], c->arcs[1], nullptr, nullptr, (u32)(2 * w), s.sha + p * s.bits_a,
             live_bits(s.B, s.bits_a, p), p, &plans[0], lb + (u64)p * la, &c->ctl->err, c->ctl);
-    stamp(c, st, kArcSort);  // arc sort, with the edge sort running beside it
+    const cudaEvent_t arc_end = mark(c, st);
+    if (sort_begin && edge_end && arc_end) c->spans.push_back({sort_begin, arc_end, edge_end});
+    stamp(c, st, kArcSort);  // arc passes, with the edge passes beside them
+    if (c->adir)
+        index_kernel<true><<<(unsigned)std::min<u64>((2 * w + 255) / 256, 152 * 16), 256, 0,
+                             st>>>(c->arcs[0], c->arcs[1], &plans[0], s, c->adir, c->ctl,
+                                   &c->ctl->err);
+    stamp(c, st, kDups);  // the arc index, beside the rest of the edge branch
     TC_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
-    stamp(c, st, kEdgeSort);  // what is left of the edge sort after the arcs
-    if (c->adir) {
-        const u64 idx_blocks = std::min<u64>((3 * w + 255) / 256, 152 * 16);
-        index_kernel<<<(unsigned)idx_blocks, 256, 0, st>>>(c->arcs[0], c->arcs[1], c->ekeys[0],
-                                                           c->ekeys[1], plans, s, c->adir,
-                                                           c->edir, c->ctl, &c->ctl->err);
-    } else {
-        const u64 dup_blocks = std::min<u64>((w + 255) / 256, 1216);
-        dups_kernel<<<(unsigned)dup_blocks, 256, 0, st>>>(c->ekeys[0], c->ekeys[1], plans, s,
-                                                          &c->ctl->err);
-    }
-    stamp(c, st, kDups);
+    stamp(c, st, kEdgeSort);  // what is left of the edge passes and their index
     SweepArgs a{};
     a.W = W;
     a.f1 = c->f1;
@@ -335,7 +360,7 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
     finish_kernel<<<1, 1, 0, st>>>(c->ctl, acc, w);
     stamp(c, st, kFinish);
     TC_CUDA(cudaGetLastError());
-    c->launches += 5 + (u64)s.npa + (u64)s.npe;
+    c->launches += (c->adir ? 6 : 5) + (u64)s.npa + (u64)s.npe;
     if (c->prof) {
         c->prof_batches += 1;
         c->prof_sort_launches += (u64)s.npa + (u64)s.npe;
@@ -619,6 +644,7 @@ int tc_profile_begin(tc_ctx *c) {
     c->prof_skipbytes0 = c->h_ctl->skipped_bytes;
     c->pool_used = 0;
     c->stamps.clear();
+    c->spans.clear();
     c->prof = true;
     c->prof_overflow = false;
     c->prof_launch0 = c->launches;
@@ -639,6 +665,14 @@ int tc_profile_end(tc_ctx *c, tc_profile_t *out) {
         TC_CUDA(cudaEventElapsedTime(&t, c->stamps[k - 1].ev, c->stamps[k].ev));
         ms[stg] += t;
     }
+    double wall = 0;
+    for (const tc_ctx::SortSpan &sp : c->spans) {
+        float ta = 0.f, te = 0.f;
+        TC_CUDA(cudaEventElapsedTime(&ta, sp.begin, sp.arc_end));
+        TC_CUDA(cudaEventElapsedTime(&te, sp.begin, sp.edge_end));
+        wall += ta > te ? ta : te;
+    }
+    out->ms_sort_wall = wall;
     out->batches = c->prof_batches;
     out->launches = c->launches - c->prof_launch0;
     out->sort_pass_launches = c->prof_sort_launches;
@@ -655,6 +689,7 @@ int tc_profile_end(tc_ctx *c, tc_profile_t *out) {
     out->ms_estimate = ms[kEstimate];
     c->prof = false;
     c->stamps.clear();
+    c->spans.clear();
     c->pool_used = 0;
     return TC_OK;
 }

@@ -137,40 +137,31 @@ __device__ __forceinline__ void dir_segment(const DirEntry *dir, u32 epoch, u64 
 // For the arcs, x = src; for the Step-3 keys, x = the smaller endpoint.  The
 // first element of a run writes (epoch, start), the last one writes end.
 // ---------------------------------------------------------------------------
-static __global__ void index_kernel(const u64 *arcs0, const u64 *arcs1, const u64 *ekeys0,
-                             const u64 *ekeys1, const SortPlan *plans, BatchShape s,
-                             DirEntry *adir, DirEntry *edir, const Control *ctl, u32 *err) {
-    const u64 *__restrict__ arcs = plan_final_sel(&plans[0]) ? arcs1 : arcs0;
-    const u64 *__restrict__ E = plan_final_sel(&plans[1]) ? ekeys1 : ekeys0;
+// kArcs: the arc directory (after the arc sort); else the Step-3 key
+// directory and the repeat check (after the edge sort).  The two run on the
+// streams of their sorts.
+template <bool kArcs>
+static __global__ void index_kernel(const u64 *keys0, const u64 *keys1, const SortPlan *plan,
+                                    BatchShape s, DirEntry *dir, const Control *ctl, u32 *err) {
+    const u64 *__restrict__ K = plan_final_sel(plan) ? keys1 : keys0;
     const u32 epoch = ctl->epoch + 1;
-    const u64 n_a = 2ull * s.w, n_e = s.w;
+    const u64 n = kArcs ? 2ull * s.w : (u64)s.w;
     const u64 nverts = 1ull << s.B;
-    const u32 esh = s.ekeys_only ? s.B + s.bw : s.B;  // edge key -> smaller endpoint
-    const u32 drop = s.ekeys_only ? s.bw : 0;          // edge key -> (u, v)
+    // key -> vertex x: arcs by src; Step-3 keys by the smaller endpoint
+    const u32 sh = kArcs ? s.sha : (s.ekeys_only ? s.B + s.bw : s.B);
+    const u32 drop = s.ekeys_only ? s.bw : 0;  // Step-3 key -> (u, v)
     bool dup = false;
-    for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x; k < n_a + n_e;
+    for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (u64)gridDim.x * blockDim.x) {
-        if (k < n_a) {
-            const u64 x = __ldg(arcs + k) >> s.sha;
-            const u64 prev = k ? __ldg(arcs + k - 1) >> s.sha : ~0ull;
-            const u64 next = k + 1 < n_a ? __ldg(arcs + k + 1) >> s.sha : ~0ull;
-            if (x >= nverts) continue;  // invalid batch (already flagged by the key build)
-            if (x != prev)
-                *reinterpret_cast<u64 *>(&adir[x].epoch) = ((u64)k << 32) | epoch;
-            if (x != next) adir[x].end = (u32)(k + 1);
-        } else {
-            const u64 j = k - n_a;
-            const u64 ek = __ldg(E + j);
-            const u64 x = ek >> esh;
-            const u64 pk = j ? __ldg(E + j - 1) : ~0ull;
-            const u64 prev = j ? pk >> esh : ~0ull;
-            const u64 next = j + 1 < n_e ? __ldg(E + j + 1) >> esh : ~0ull;
-            dup |= j && (ek >> drop) == (pk >> drop);
-            if (x >= nverts) continue;
-            if (x != prev)
-                *reinterpret_cast<u64 *>(&edir[x].epoch) = ((u64)j << 32) | epoch;
-            if (x != next) edir[x].end = (u32)(j + 1);
-        }
+        const u64 key = __ldg(K + k);
+        const u64 x = key >> sh;
+        const u64 pk = k ? __ldg(K + k - 1) : ~0ull;
+        const u64 prev = k ? pk >> sh : ~0ull;
+        const u64 next = k + 1 < n ? __ldg(K + k + 1) >> sh : ~0ull;
+        if constexpr (!kArcs) dup |= k && (key >> drop) == (pk >> drop);
+        if (x >= nverts) continue;  // invalid batch (already flagged by the key build)
+        if (x != prev) *reinterpret_cast<u64 *>(&dir[x].epoch) = ((u64)k << 32) | epoch;
+        if (x != next) dir[x].end = (u32)(k + 1);
     }
     if (dup) set_error(err, kErrInput);
 }

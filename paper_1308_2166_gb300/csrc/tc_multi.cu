@@ -588,14 +588,15 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, const u64 *desc, u
             M->ekeys[0], M->ekeys[1], M->evals[0], M->evals[1], (u32)Wt, p * rs.bits_e,
             mlive(2 * M->B + rs.kb, rs.bits_e, p), p, &plans[1], lbe + (u64)p * le, gerr,
             nullptr);
+    const u64 db = std::min<u64>((Wt + 255) / 256, 1216);
+    mdups_kernel<<<(unsigned)db, 256, 0, M->side>>>(M->ekeys[0], M->ekeys[1], plans, desc, rs,
+                                                    M->ms);
     TCM_CUDA(cudaEventRecord(M->ev_join, M->side));
     for (int p = 0; p < rs.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(
             M->arcs[0], M->arcs[1], nullptr, nullptr, (u32)(2 * Wt), rs.sha + p * rs.bits_a,
             mlive(M->B + rs.kb, rs.bits_a, p), p, &plans[0], lb + (u64)p * la, gerr, nullptr);
     TCM_CUDA(cudaStreamWaitEvent(st, M->ev_join, 0));
-    const u64 db = std::min<u64>((Wt + 255) / 256, 1216);
-    mdups_kernel<<<(unsigned)db, 256, 0, st>>>(M->ekeys[0], M->ekeys[1], plans, desc, rs, M->ms);
     MSweepArgs a{};
     a.desc = desc;
     a.R = R;
