@@ -44,14 +44,15 @@ UNIT = "edges/s"
 # ncu DRAM traffic of the dominant kernel, per algorithmic byte, with the
 # hash of the source it was taken on (profiles/ holds the capture summary).
 # Taken from profiles/onesweep_pass_rmat20.md: DRAM read + write of one arc
-# and one edge pass over their algorithmic bytes (writes largely stay in L2).
+# and one edge pass over their algorithmic bytes (writes largely stay in L2),
+# valid while the pass kernel's sources hash the same.
 TRAFFIC = {
-    "onesweep_pass_kernel": {"src_hash": "a0d1e3856b242de9",
-                             "bytes_per_algorithmic_byte": 118.114048 / 201.326592},
+    "onesweep_pass_kernel": {"src_hash": "ec67c4990354bfbd",
+                             "bytes_per_algorithmic_byte": 117.673472 / 201.326592},
 }
 
-# Sources the single-stream sort pass is built from.
-_SORT_SOURCES = ("tc_api.cu", "tc_common.cuh", "tc_onesweep.cuh")
+# Sources the sort pass kernel is built from.
+_SORT_SOURCES = ("tc_common.cuh", "tc_onesweep.cuh")
 
 
 def _src_hash() -> str:

@@ -398,6 +398,31 @@ int tc_server_stats(tc_server *S, tc_server_stats_t *out);
  * requests not yet in a round are dropped without completion. */
 void tc_server_destroy(tc_server *S);
 
+/* ---- Checkpoint / resume ----------------------------------------------------
+ * A stream's whole state -- the estimator tuples (f1, f2, f3 as the closed
+ * bit, chi), |E|, the batch counter, seed, stream id and vertex bits -- as
+ * one host blob: a 128-byte header (magic "TCSTATE1", version 1, then r,
+ * seed, stream id, vertex bits, |E|, batches, S low, S high, closed count,
+ * as little-endian uint64) followed by f1[r], f2[r], chi[r] (uint64) and
+ * flags[r] (uint32).  Because every draw is a function of (seed, stream id,
+ * estimator, batch, slot), a stream loaded from a blob continues bit for bit
+ * as if it had never stopped.  (The paper keeps its state in memory only;
+ * this is the library's own.) */
+
+/* Bytes tc_save writes for this context: 128 + 28 r. */
+uint64_t tc_save_size(tc_ctx *c);
+
+/* Write the blob to the HOST buffer buf of `size` bytes (>= tc_save_size).
+ * Synchronises.  Errors: TC_ERR_INVAL, TC_ERR_CUDA. */
+int tc_save(tc_ctx *c, void *buf, uint64_t size);
+
+/* Create a context from a blob (scratch for batches of up to w_max edges,
+ * as tc_create_ex).  TC_ERR_INVAL if the header is not a version-1 blob,
+ * `size` is short, a flag word has bits other than TC_FLAG_CLOSED, or the
+ * stored S and closed count disagree with the state; TC_ERR_NOMEM,
+ * TC_ERR_CUDA as tc_create_ex. */
+int tc_load(const void *buf, uint64_t size, uint64_t w_max, tc_ctx **out);
+
 /* Self-test of the bounded device-side waits (no counterpart in the paper;
  * the radix sort's look-back is the library's only spin-wait).  Runs one
  * digit pass over two tiles of keys with a single CTA that is handed tile 1,

@@ -37,7 +37,7 @@ EXPORTS = (
     "tc_multi_replay", "tc_process_batches_async", "tc_multi_process_ptrs_async",
     "tc_server_create", "tc_server_open", "tc_server_submit", "tc_server_query",
     "tc_server_close", "tc_server_poll", "tc_server_drain", "tc_server_stats",
-    "tc_server_destroy", "tc_selftest_wait_timeout",
+    "tc_server_destroy", "tc_selftest_wait_timeout", "tc_save_size", "tc_save", "tc_load",
 )
 
 TC_REQ_OPEN, TC_REQ_BATCH, TC_REQ_QUERY, TC_REQ_CLOSE = 1, 2, 3, 4
@@ -149,6 +149,9 @@ def load(path: str | None = None):
         "tc_server_stats": (I, [P, ctypes.POINTER(tc_server_stats_t)]),
         "tc_server_destroy": (None, [P]),
         "tc_selftest_wait_timeout": (I, []),
+        "tc_save_size": (U64, [P]),
+        "tc_save": (I, [P, P, U64]),
+        "tc_load": (I, [P, U64, U64, ctypes.POINTER(P)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -337,6 +340,21 @@ class TriangleStream:
             self.close()
         except Exception:
             pass
+
+
+def tc_save(ctx: int) -> bytes:
+    """The context's whole state as a checkpoint blob (see tc.h)."""
+    n = load().tc_save_size(ctx)
+    buf = ctypes.create_string_buffer(n)
+    _check(load().tc_save(ctx, buf, n), "tc_save")
+    return buf.raw
+
+
+def tc_load(blob: bytes, w_max: int) -> int:
+    """A new context resumed from a tc_save blob."""
+    h = ctypes.c_void_p()
+    _check(load().tc_load(blob, len(blob), w_max, ctypes.byref(h)), "tc_load")
+    return h.value
 
 
 def tc_selftest_wait_timeout() -> int:

@@ -895,3 +895,106 @@ extern "C" int tc_selftest_wait_timeout(void) {
     if (!ok) return TC_ERR_CUDA;
     return h_err == kErrTimeout ? TC_ERR_TIMEOUT : h_err ? TC_ERR_CUDA : TC_OK;
 }
+
+// ---- checkpoint / resume -------------------------------------------------------
+// Blob: a 128-byte header of little-endian uint64 words, then f1[r], f2[r],
+// chi[r] (uint64) and flags[r] (uint32).  Restoring the estimator tuples,
+// |E| and the batch counter (with seed and stream id, the whole Philox
+// counter context) resumes a stream bit for bit.
+namespace {
+
+constexpr u64 kSaveMagic = 0x3145544154534354ull;  // "TCSTATE1"
+constexpr u64 kSaveVersion = 1;
+
+struct SaveHeader {
+    u64 magic, version, r, seed, stream_id, vertex_bits, m, batches;
+    u64 s_lo, s_hi, closed;
+    u64 pad[5];
+};
+static_assert(sizeof(SaveHeader) == 128, "header is 16 words");
+
+u64 save_bytes(u64 r) { return sizeof(SaveHeader) + 28 * r; }
+
+}  // namespace
+
+extern "C" uint64_t tc_save_size(tc_ctx *c) { return c ? save_bytes(c->r) : 0; }
+
+extern "C" int tc_save(tc_ctx *c, void *buf, uint64_t size) {
+    if (!c || !buf || size < save_bytes(c->r)) return TC_ERR_INVAL;
+    int rc = read_control(c);
+    if (rc) return rc;
+    SaveHeader h{};
+    h.magic = kSaveMagic;
+    h.version = kSaveVersion;
+    h.r = c->r;
+    h.seed = c->seed;
+    h.stream_id = c->stream_id;
+    h.vertex_bits = c->vertex_bits;
+    h.m = c->h_ctl->m;
+    h.batches = c->h_ctl->batches;
+    h.s_lo = c->h_ctl->est[0];
+    h.s_hi = c->h_ctl->est[1];
+    h.closed = c->h_ctl->est[2];
+    unsigned char *p = static_cast<unsigned char *>(buf);
+    std::memcpy(p, &h, sizeof(h));
+    p += sizeof(h);
+    const u64 r = c->r;
+    TC_CUDA(cudaMemcpy(p, c->f1, r * 8, cudaMemcpyDeviceToHost));
+    TC_CUDA(cudaMemcpy(p + 8 * r, c->f2, r * 8, cudaMemcpyDeviceToHost));
+    TC_CUDA(cudaMemcpy(p + 16 * r, c->chi, r * 8, cudaMemcpyDeviceToHost));
+    TC_CUDA(cudaMemcpy(p + 24 * r, c->flags, r * 4, cudaMemcpyDeviceToHost));
+    return TC_OK;
+}
+
+extern "C" int tc_load(const void *buf, uint64_t size, uint64_t w_max, tc_ctx **out) {
+    if (!buf || !out || size < sizeof(SaveHeader)) return TC_ERR_INVAL;
+    *out = nullptr;
+    SaveHeader h;
+    std::memcpy(&h, buf, sizeof(h));
+    if (h.magic != kSaveMagic || h.version != kSaveVersion || h.r == 0 ||
+        h.r > 0xFFFFFFFFull || h.vertex_bits < 1 || h.vertex_bits > 32 ||
+        h.stream_id > 0xFFFFFFFFull || size < save_bytes(h.r))
+        return TC_ERR_INVAL;
+    const u64 r = h.r;
+    const unsigned char *p = static_cast<const unsigned char *>(buf) + sizeof(h);
+    // the committed estimate must be the one the state gives (Lemma 3.1's
+    // S over the closed estimators): a cheap check against a damaged blob
+    using u128 = unsigned __int128;
+    u128 S = 0;
+    u64 closed = 0;
+    for (u64 i = 0; i < r; ++i) {
+        u32 fl;
+        std::memcpy(&fl, p + 24 * r + 4 * i, 4);
+        if (fl & ~TC_FLAG_CLOSED) return TC_ERR_INVAL;
+        if (fl & TC_FLAG_CLOSED) {
+            u64 x;
+            std::memcpy(&x, p + 16 * r + 8 * i, 8);
+            S += x;
+            ++closed;
+        }
+    }
+    if ((u64)S != h.s_lo || (u64)(S >> 64) != h.s_hi || closed != h.closed) return TC_ERR_INVAL;
+    tc_ctx *c = nullptr;
+    int rc = tc_create_ex(r, h.seed, (u32)h.stream_id, w_max, (u32)h.vertex_bits, &c);
+    if (rc) return rc;
+    bool ok = cudaMemcpy(c->f1, p, r * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaMemcpy(c->f2, p + 8 * r, r * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaMemcpy(c->chi, p + 16 * r, r * 8, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= cudaMemcpy(c->flags, p + 24 * r, r * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok &= read_control(c) == TC_OK;
+    if (ok) {
+        c->h_ctl->m = h.m;
+        c->h_ctl->batches = h.batches;
+        c->h_ctl->est[0] = h.s_lo;
+        c->h_ctl->est[1] = h.s_hi;
+        c->h_ctl->est[2] = h.closed;
+        c->h_ctl->est[3] = h.m;
+        ok &= cudaMemcpy(c->ctl, c->h_ctl, sizeof(Control), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    if (!ok) {
+        tc_destroy(c);
+        return TC_ERR_CUDA;
+    }
+    *out = c;
+    return TC_OK;
+}
