@@ -34,6 +34,7 @@ def _stale() -> bool:
         return True
     t = os.path.getmtime(LIB)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + \
+        glob.glob(os.path.join(CSRC, "*.h")) + \
         glob.glob(os.path.join(ROOT, "include", "*.h"))
     return any(os.path.getmtime(d) > t for d in deps)
 
@@ -58,7 +59,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         raise subprocess.CalledProcessError(1, failed[0])
     tmp = LIB + tag + ".tmp"
-    link = [_nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs]
+    link = [_nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs,
+            "-ldl"]
     if verbose:
         print(" ".join(link))
     subprocess.check_call(link)

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "tc_kernels.cuh"
+#include "tc_nvtx.h"
 
 using namespace tc;
 
@@ -274,6 +275,7 @@ static int map_device_error(u32 e) {
 
 // Enqueue one batch on `st`.  W is a device pointer; w in [1, cap_w].
 static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
+    const NvtxRange range("tc batch");
     const BatchShape s = make_shape(w, c->vertex_bits, c->force_bits_a, c->force_bits_e);
     BatchAcc *acc = reinterpret_cast<BatchAcc *>(c->zeroed);
     SortPlan *plans = reinterpret_cast<SortPlan *>(c->zeroed + kOffPlans);

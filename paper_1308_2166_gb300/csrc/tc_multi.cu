@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "tc_kernels.cuh"
+#include "tc_nvtx.h"
 #include "tc_multi_impl.cuh"
 
 using namespace tc;
@@ -546,6 +547,7 @@ int multi_gather(tc_multi *M, const u32 *d_slots, u32 Q, u64 *out, cudaStream_t 
 
 int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, const u64 *desc, u64 *out,
                   cudaStream_t st) {
+    const NvtxRange range("tc round");
     u64 Wt = 0, wmax = 0, R = 0;
     for (u32 k = 0; k < K; ++k) {
         Wt += items[k].w;

@@ -37,6 +37,7 @@
 #include <vector>
 
 #include "tc_multi_impl.cuh"
+#include "tc_nvtx.h"
 
 using namespace tc;
 
@@ -184,6 +185,7 @@ int tc_server::get_event() {
 // but no request overtakes an earlier one of its own stream.  Returns
 // whether anything was admitted; a CUDA failure is left in `err`.
 bool tc_server::admit() {
+    const NvtxRange range("tc server admit");
     if (pending.empty() || !dirty) return false;
     dirty = false;
     bool moved = false, open_blocked = false, mem_blocked = false;
@@ -280,6 +282,7 @@ bool tc_server::admit() {
 }
 
 bool tc_server::form_round() {
+    const NvtxRange range("tc server round");
     if (ready.empty()) return false;
     const u32 S = M->S;
     Round R;
