@@ -168,7 +168,7 @@ __device__ __forceinline__ bool warp_segment_sum(u32 key, u64 &lo, u64 &hi, u64 
     return lane == __ffs(grp) - 1;
 }
 
-__global__ void __launch_bounds__(kMThreads, 3) msweep_kernel(MSweepArgs a) {
+__global__ void __launch_bounds__(kMThreads, 5) msweep_kernel(MSweepArgs a) {
     if (ld_relaxed(a.gerr)) return;
     const u64 g = (u64)blockIdx.x * kMThreads + threadIdx.x;
     const RoundShape &rs = a.rs;
