@@ -124,12 +124,16 @@ __device__ __forceinline__ void arc_segment(const u64 *arcs, u64 n, u32 sha, u64
 }
 
 // Segment [start, end) of vertex x from a directory (empty if x is absent).
-__device__ __forceinline__ void dir_segment(const DirEntry *dir, u32 epoch, u64 x, u64 &start,
-                                            u64 &end) {
+// The entry is clamped to start <= end <= n, so that a directory built over
+// an array that is not sorted (only possible after a rejected batch, whose
+// sweep does not run) could never send a search outside the array.
+__device__ __forceinline__ void dir_segment(const DirEntry *dir, u32 epoch, u64 x, u64 n,
+                                            u64 &start, u64 &end) {
     const uint4 e = __ldg(reinterpret_cast<const uint4 *>(dir + x));
     const bool hit = e.x == epoch;
-    start = hit ? e.y : 0;
-    end = hit ? e.z : 0;
+    const u64 s0 = hit ? e.y : 0, e0 = hit ? e.z : 0;
+    end = e0 < n ? e0 : n;
+    start = s0 < end ? s0 : end;
 }
 
 // ---------------------------------------------------------------------------
@@ -268,8 +272,8 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
     const u64 u = f1 >> 32, v = f1 & kMask32;
     u64 su, eu, sv, ev;
     if constexpr (kDir) {
-        dir_segment(a.adir, epoch, u, su, eu);
-        dir_segment(a.adir, epoch, v, sv, ev);
+        dir_segment(a.adir, epoch, u, n_arcs, su, eu);
+        dir_segment(a.adir, epoch, v, n_arcs, sv, ev);
     } else {
         arc_segment(arcs, n_arcs, s.sha, u, su, eu);
         arc_segment(arcs, n_arcs, s.sha, v, sv, ev);
@@ -305,7 +309,7 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
     if (f2 != kEmpty && !(fl & TC_FLAG_CLOSED)) {
         u64 gu, gv, lo = 0, hi = s.w;
         closing_pair(f1, f2, gu, gv);
-        if constexpr (kDir) dir_segment(a.edir, epoch, gu, lo, hi);
+        if constexpr (kDir) dir_segment(a.edir, epoch, gu, s.w, lo, hi);
         bool found;
         u32 q;
         if (s.ekeys_only) {
