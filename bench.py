@@ -458,8 +458,8 @@ def run_multi(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     build.build()
     tc.load()
-    S, T = 512, max(2, min(args.steps, 16))
-    caps = (1024, 2048, 4096)
+    S, T = 512, max(2, min(args.steps, 8))
+    caps = (2048, 4096, 8192, 16384)
     streams, r, n = synth.multi_streams(S, per_stream_edges=T * max(caps), seed=1)
     B = int(max(1, int(n.max() - 1).bit_length()))
     seeds = np.arange(1, S + 1, dtype=np.uint64)
@@ -477,9 +477,11 @@ def run_multi(args, rank, world, local_rank):
             parts_all.append(parts)
         return ws, offs, rounds, parts_all
 
-    def time_batched(cap, nrounds, graph=False):
+    def time_batched(cap, nrounds, graph=False, tuning=None):
         ws, offs, rounds, _ = rounds_for(cap)
         M = tc.MultiStream(r, seeds, sids, w_max_round=int(offs[-1]), vertex_bits=B)
+        if tuning:
+            M.tune(*tuning)
         buf = torch.empty_like(rounds[0])
         if graph:
             M.capture(buf, offs, sh)
@@ -507,17 +509,26 @@ def run_multi(args, rank, world, local_rank):
         tune[cap] = edges / (ms / 1e3)
         M.close()
     cap = max(tune, key=tune.get)
+    # then the sort tuning (digit widths, warp ranking) at that cap
+    dtune = {}
+    for cand in ((8, 8, 2), (8, 8, 1), (8, 10, 2), (10, 8, 2), (10, 10, 2)):
+        M, ms, edges, _ = time_batched(cap, 3, tuning=cand)
+        dtune[cand] = edges / (ms / 1e3)
+        M.close()
+    tuning = max(dtune, key=dtune.get)
     ws, offs, rounds, parts_all = rounds_for(cap)
     edges_total = int(offs[-1]) * T
 
     sampler = ClockSampler(local_rank)
-    Mg, ms_graph, _, launches_graph = time_batched(cap, T, graph=True)
+    Mg, ms_graph, _, launches_graph = time_batched(cap, T, graph=True, tuning=tuning)
     clocks = sampler.stop()
-    Mb, ms_batched, _, launches_b = time_batched(cap, T, graph=False)
+    Mb, ms_batched, _, launches_b = time_batched(cap, T, graph=False, tuning=tuning)
 
     # back to back: one single-stream context per stream
     ctxs = [tc.tc_create_ex(int(r[s]), int(seeds[s]), int(sids[s]), max(1, ws[s]), B)
             for s in range(S)]
+    for cx in ctxs:                      # the same sort tuning as the rounds
+        tc.tc_tune(cx, *tuning)
     dev_parts = []
     for k in range(T):
         base = rounds[k]
@@ -560,7 +571,11 @@ def run_multi(args, rank, world, local_rank):
                                f"min(w_cap, len/rounds)",
                    "streams": S, "rounds": T, "w_cap": cap, "round_edges": int(offs[-1]),
                    "estimators": int(r.sum()), "vertex_bits": B,
-                   "w_cap_table": {str(k): v for k, v in tune.items()}},
+                   "w_cap_table": {str(k): v for k, v in tune.items()},
+                   "sort_tuning": {"arc_digit_bits": tuning[0], "edge_digit_bits": tuning[1],
+                                   "ranking": "match" if tuning[2] == 1 else "ballot",
+                                   "table": {f"{a}/{b}/{'match' if c == 1 else 'ballot'}": v
+                                             for (a, b, c), v in dtune.items()}}},
         "updates_per_s": float(sum(int(r[s2]) * ws[s2] for s2 in range(S))) * T / (ms_graph / 1e3),
         "batched_plain": {"value": edges_total / (ms_batched / 1e3), "ms_per_round": ms_batched / T,
                           "launches_per_round": launches_b / T},
