@@ -69,6 +69,20 @@ __device__ __forceinline__ u32 digit_bits(u64 key, u32 shift, u32 mask) {
     return (u32)(key >> shift) & mask;
 }
 
+// The digit at bit `shift` of a 64-bit key, on 32-bit halves: a pass's
+// shift is uniform, so the word choice is a uniform predicate and the
+// extraction one funnel or plain shift plus a mask.
+struct DigitAt {
+    bool hi;  // digit lies in the high word
+    u32 sh;   // shift inside the word pair
+    __device__ __forceinline__ explicit DigitAt(u32 shift)
+        : hi(shift >= 32), sh(shift >= 32 ? shift - 32 : shift) {}
+    __device__ __forceinline__ u32 operator()(u64 key, u32 mask) const {
+        const u32 lo = (u32)key, hw = (u32)(key >> 32);
+        return (hi ? (hw >> sh) : __funnelshift_r(lo, hw, sh)) & mask;
+    }
+};
+
 // Exclusive prefix over the values `x` of threads [0, kThreads) of a CTA.
 // `s_tmp` holds kThreads/32 words.  Must be reached by every thread of the
 // CTA; threads at or beyond kThreads contribute nothing.
@@ -180,13 +194,14 @@ struct OnesweepSmem {
 template <int kBits, int kLive, bool kFull, bool kHasValues, int kRank, typename Smem>
 __device__ __forceinline__ void rank_warp(Smem &S, const u64 (&keys)[kSortItems],
                                           const u32 (&vals)[kHasValues ? kSortItems : 1],
-                                          u32 nvalid, u32 shift, u32 live, int lane, int warp) {
+                                          u32 nvalid, const DigitAt &dig, u32 live, int lane,
+                                          int warp) {
     constexpr u32 kMask = (1u << kBits) - 1;
     const u32 lt_mask = (1u << lane) - 1u;
 #pragma unroll
     for (int j = 0; j < kSortItems; ++j) {
         const bool valid = kFull || (u32)(j * 32 + lane) < nvalid;
-        const u32 d = digit_bits(keys[j], shift, kMask);
+        const u32 d = dig(keys[j], kMask);
         u32 peers;
         if constexpr (kRank == kRankMatch) {
             peers = __match_any_sync(0xFFFFFFFFu, valid ? d : (u32)(1u << kBits) + lane);
@@ -260,6 +275,7 @@ static __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits 
     u32 *__restrict__ vout = sel ? vals0 : vals1;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const DigitAt dig(shift);
     if (tid == 0) S.tile = atomicAdd(&plan->tile_counter[pass], 1u);
     for (int k = tid; k < kSortWarps * kRadix; k += Shape::kThreads) (&S.cursor[0][0])[k] = 0;
     if constexpr (kRank == kRankAtomicOr)
@@ -296,12 +312,12 @@ static __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits 
     if (full) {
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j)
-            atomicAdd(&S.cursor[warp][digit_bits(keys[j], shift, kMask)], 1u);
+            atomicAdd(&S.cursor[warp][dig(keys[j], kMask)], 1u);
     } else {
 #pragma unroll
         for (int j = 0; j < kSortItems; ++j)
             if ((u32)(j * 32 + lane) < nvalid)
-                atomicAdd(&S.cursor[warp][digit_bits(keys[j], shift, kMask)], 1u);
+                atomicAdd(&S.cursor[warp][dig(keys[j], kMask)], 1u);
     }
     __syncthreads();
 
@@ -334,13 +350,13 @@ static __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits 
     // -- stable ranking inside each warp, written straight to the staging area
     if (full) {
         if (kRank != kRankBallot || live >= (u32)kBits)
-            rank_warp<kBits, kBits, true, kHasValues, kRank>(S, keys, vals, nvalid, shift, live,
+            rank_warp<kBits, kBits, true, kHasValues, kRank>(S, keys, vals, nvalid, dig, live,
                                                              lane, warp);
         else
-            rank_warp<kBits, 0, true, kHasValues, kRank>(S, keys, vals, nvalid, shift, live, lane,
+            rank_warp<kBits, 0, true, kHasValues, kRank>(S, keys, vals, nvalid, dig, live, lane,
                                                          warp);
     } else {
-        rank_warp<kBits, 0, false, kHasValues, kRank>(S, keys, vals, nvalid, shift, live, lane,
+        rank_warp<kBits, 0, false, kHasValues, kRank>(S, keys, vals, nvalid, dig, live, lane,
                                                       warp);
     }
     {
@@ -348,12 +364,12 @@ static __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits 
         //    groups of kLookWin predecessors per round trip (earlier tiles
         //    have had the ranking time to publish)
         u32 sum[kDPT];
-        long next[kDPT];  // next predecessor tile to examine
+        int next[kDPT];  // next predecessor tile to examine
         u32 pending = 0;
 #pragma unroll
         for (int q = 0; q < kDPT; ++q) {
             sum[q] = 0;
-            next[q] = (long)tile - 1;
+            next[q] = (int)tile - 1;
             if (tile > 0) pending |= 1u << q;
         }
         u32 idle = 0;
@@ -363,25 +379,28 @@ static __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits 
 #pragma unroll
             for (int q = 0; q < kDPT; ++q) {
                 if (!(pending & (1u << q))) continue;
-                const int d = q * kRankThreads8 + tid;
-                // statuses of tiles next, next-1, ...: independent loads, each
-                // coalesced across the warp's consecutive digits
+                // statuses of tiles next, next-1, ...: independent loads at a
+                // fixed stride from one base, each coalesced across the warp's
+                // consecutive digits
+                const u32 *p = lookback + ((u32)next[q] * kRadix + q * kRankThreads8 + tid);
+                const int lim = min(window, next[q] + 1);  // tiles >= 0 only
                 u32 st[kLookWin];
 #pragma unroll
                 for (int t = 0; t < kLookWin; ++t)
-                    st[t] = (t < window && next[q] - t >= 0)
-                                ? ld_relaxed(lookback + (u64)(next[q] - t) * kRadix + d)
-                                : 0u;
+                    st[t] = t < lim ? ld_relaxed(p - t * kRadix) : 0u;
 #pragma unroll
                 for (int t = 0; t < kLookWin; ++t) {
-                    if (t >= window || !(pending & (1u << q))) break;
+                    if (t >= lim) break;
                     const u32 s = st[t];
                     const u32 flag = s & kFlagMask;
                     if (flag == 0) break;  // not published yet: retry this tile
                     sum[q] += s & kValMask;
                     progress = true;
-                    if (flag == kFlagPre) pending &= ~(1u << q);
-                    else --next[q];  // tile 0 always publishes a prefix
+                    if (flag == kFlagPre) {
+                        pending &= ~(1u << q);
+                        break;
+                    }
+                    --next[q];  // tile 0 always publishes a prefix
                 }
             }
             window = kLookWin;
@@ -410,7 +429,7 @@ static __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits 
     const u32 tile_n = left < (u64)kSortTile ? (u32)left : (u32)kSortTile;
     for (u32 i = tid; i < tile_n; i += Shape::kThreads) {
         const u64 key = S.keys[i];
-        const u32 pos = S.base[digit_bits(key, shift, kMask)] + i;
+        const u32 pos = S.base[dig(key, kMask)] + i;
         if (pos < n) {  // only a timed-out look-back can make it larger
             kout[pos] = key;
             if constexpr (kHasValues) vout[pos] = S.vals[i];
