@@ -335,7 +335,7 @@ def run_gpu(args, rank, world, local_rank):
     t_ms, edges_all = reduce_over_ranks(dist, evs[0].elapsed_time(evs[-1]), edges, "cuda")
     value = edges_all / (t_ms / 1e3)
 
-    # ---- end to end: pinned host batches through the synchronous C-ABI call
+    # ---- end to end: pinned host batches through the C-ABI host-input call
     e2e_steps = args.e2e_steps or min(args.steps, 40)
     pinned = []
     for b in host_batches:
@@ -344,15 +344,28 @@ def run_gpu(args, rank, world, local_rank):
         pinned.append(t)
     if dist:
         dist.barrier()
+    # each step: the pinned host batch goes in through the pipelined host-input
+    # call (its copy overlaps the previous batch's update) and the step's
+    # estimate words come back to pinned host memory
+    res_dev = torch.zeros(4, dtype=torch.int64, device="cuda")
+    res_host = [torch.zeros(4, dtype=torch.int64, pin_memory=True) for _ in range(4)]
+    for j in range(2):                   # untimed: both staging buffers in place
+        tc.tc_process_batch_host_async(ctx, pinned[k % nb], stream=sh)
+        k += 1
+    tc.tc_sync(ctx)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e2e_edges = 0
-    for j in range(e2e_steps):
-        hb = pinned[k % nb]
-        k += 1
-        tc.tc_process_batch(ctx, hb)
-        tc.tc_estimate(ctx)          # D2H of the step's result
-        e2e_edges += hb.numel()
+    with torch.cuda.stream(stream):
+        for j in range(e2e_steps):
+            hb = pinned[k % nb]
+            k += 1
+            tc.tc_process_batch_host_async(ctx, hb, stream=sh)
+            tc.tc_estimate_async(ctx, res_dev, stream=sh)
+            res_host[j % 4].copy_(res_dev, non_blocking=True)
+            e2e_edges += hb.numel()
+    stream.synchronize()
+    tc.tc_sync(ctx)
     e2e_s, e2e_all = reduce_over_ranks(dist, time.perf_counter() - t0, e2e_edges, "cuda")
     e2e_value = e2e_all / e2e_s
 
@@ -422,7 +435,11 @@ def run_gpu(args, rank, world, local_rank):
         "gpu_launches": prof["launches"],
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": w * 8,
-                "d2h_bytes_per_step": 32, "steps": e2e_steps},
+                "d2h_bytes_per_step": 32, "steps": e2e_steps,
+                "how": "tc_process_batch_host_async from pinned host batches (each batch's "
+                       "copy overlaps the previous batch's update) + tc_estimate_async and a "
+                       "copy of the 4 estimate words to pinned host memory every step; "
+                       "host wall clock"},
         "estimate": _accuracy(tc, cfg, keys, dev_batches, rank),
         "src_hash": _src_hash(),
     }

@@ -102,6 +102,18 @@ int tc_process_batch(tc_ctx *c, const uint64_t *edges, uint64_t w);
 int tc_process_batch_async(tc_ctx *c, const uint64_t *d_edges, uint64_t w,
                            void *cuda_stream);
 
+/* tc_process_batch_async for a HOST array (pinned memory for the copy to
+ * run asynchronously): the batch is copied to one of two device staging
+ * buffers on an internal copy stream, so the copy of each batch overlaps the
+ * update of the one before it, and the update is enqueued on `cuda_stream`
+ * behind its copy.  Returns without waiting.  h_edges is borrowed until the
+ * work on `cuda_stream` passes this batch.  w must not exceed the context's
+ * scratch capacity, else TC_ERR_INVAL; errors are reported as for
+ * tc_process_batch_async.  Do not interleave with tc_process_batch from
+ * another host thread. */
+int tc_process_batch_host_async(tc_ctx *c, const uint64_t *h_edges, uint64_t w,
+                                void *cuda_stream);
+
 /* tc_process_batch_async for n contexts in turn (a native loop, so that
  * many independent streams can be advanced back to back without per-call
  * host overhead): batch k = d_edges[k][0..w[k]) goes to ctxs[k]; w[k] == 0

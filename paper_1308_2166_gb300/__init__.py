@@ -38,6 +38,7 @@ EXPORTS = (
     "tc_server_create", "tc_server_open", "tc_server_submit", "tc_server_query",
     "tc_server_close", "tc_server_poll", "tc_server_drain", "tc_server_stats",
     "tc_server_destroy", "tc_selftest_wait_timeout", "tc_save_size", "tc_save", "tc_load",
+    "tc_process_batch_host_async",
 )
 
 TC_REQ_OPEN, TC_REQ_BATCH, TC_REQ_QUERY, TC_REQ_CLOSE = 1, 2, 3, 4
@@ -149,6 +150,7 @@ def load(path: str | None = None):
         "tc_server_stats": (I, [P, ctypes.POINTER(tc_server_stats_t)]),
         "tc_server_destroy": (None, [P]),
         "tc_selftest_wait_timeout": (I, []),
+        "tc_process_batch_host_async": (I, [P, P, U64, P]),
         "tc_save_size": (U64, [P]),
         "tc_save": (I, [P, P, U64]),
         "tc_load": (I, [P, U64, U64, ctypes.POINTER(P)]),
@@ -210,6 +212,17 @@ def tc_process_batch_async(ctx: int, d_edges, w: int | None = None, stream: int 
     w = _len(d_edges) if w is None else w
     _check(load().tc_process_batch_async(ctx, _ptr(d_edges) if w else None, w, stream or None),
            "tc_process_batch_async")
+
+
+def tc_process_batch_host_async(ctx: int, h_edges, w: int | None = None,
+                                stream: int = 0) -> None:
+    """Pipelined host-input update: the copy of this batch overlaps the
+    update of the previous one (h_edges: pinned CPU tensor or numpy array,
+    kept alive by the caller until the stream passes this batch)."""
+    w = _len(h_edges) if w is None else w
+    _check(load().tc_process_batch_host_async(ctx, _ptr(h_edges) if w else None, w,
+                                              stream or None),
+           "tc_process_batch_host_async")
 
 
 def tc_process_batches_async(ctxs, d_edges, stream: int = 0) -> None:

@@ -174,6 +174,11 @@ struct tc_ctx {
     // the edge sort runs on `side`, concurrently with the arc sort
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // pipelined host input: two device staging buffers filled on `copy`
+    cudaStream_t copy = nullptr;
+    cudaEvent_t ev_copied[2] = {}, ev_used[2] = {};
+    u64 *staging2 = nullptr;
+    int stage_next = 0;
     // estimator state (structure of arrays)
     u64 *f1 = nullptr, *f2 = nullptr, *chi = nullptr;
     u32 *flags = nullptr;
@@ -239,8 +244,10 @@ static void free_scratch(tc_ctx *c) {
         c->evals[k] = nullptr;
     }
     cudaFree(c->staging);
+    cudaFree(c->staging2);
     cudaFree(c->zeroed);
     c->staging = nullptr;
+    c->staging2 = nullptr;
     c->zeroed = nullptr;
     c->cap_w = 0;
 }
@@ -425,6 +432,11 @@ int tc_create_ex(uint64_t r, uint64_t seed, uint32_t stream_id, uint64_t w_max,
     ok &= ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
     ok &= ok && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;
     ok &= ok && cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) == cudaSuccess;
+    ok &= ok && cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k < 2; ++k) {
+        ok &= ok && cudaEventCreateWithFlags(&c->ev_copied[k], cudaEventDisableTiming) == cudaSuccess;
+        ok &= ok && cudaEventCreateWithFlags(&c->ev_used[k], cudaEventDisableTiming) == cudaSuccess;
+    }
     ok &= ok && cudaMalloc(&c->f1, r * sizeof(u64)) == cudaSuccess;
     ok &= ok && cudaMalloc(&c->f2, r * sizeof(u64)) == cudaSuccess;
     ok &= ok && cudaMalloc(&c->chi, r * sizeof(u64)) == cudaSuccess;
@@ -484,6 +496,11 @@ void tc_destroy(tc_ctx *c) {
     if (c->side) cudaStreamDestroy(c->side);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->copy) cudaStreamDestroy(c->copy);
+    for (int k = 0; k < 2; ++k) {
+        if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
+        if (c->ev_used[k]) cudaEventDestroy(c->ev_used[k]);
+    }
     delete c;
 }
 
@@ -513,6 +530,8 @@ int tc_process_batch(tc_ctx *c, const uint64_t *edges, uint64_t w) {
     TC_CUDA(cudaPointerGetAttributes(&attr, edges));
     const u64 *W = edges;
     if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged) {
+        // staging may still feed a pipelined batch (tc_process_batch_host_async)
+        TC_CUDA(cudaStreamWaitEvent(c->own, c->ev_used[0], 0));
         TC_CUDA(cudaMemcpyAsync(c->staging, edges, w * sizeof(u64), cudaMemcpyHostToDevice,
                                 c->own));
         W = c->staging;
@@ -522,6 +541,31 @@ int tc_process_batch(tc_ctx *c, const uint64_t *edges, uint64_t w) {
     TC_CUDA(cudaStreamSynchronize(c->own));
     TC_CUDA(cudaMemcpy(c->h_ctl, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost));
     return collect_error(c);
+}
+
+int tc_process_batch_host_async(tc_ctx *c, const uint64_t *h_edges, uint64_t w,
+                                void *cuda_stream) {
+    if (!c || (w && !h_edges) || w > kMaxBatch) return TC_ERR_INVAL;
+    if (w == 0) return TC_OK;
+    if (w > c->cap_w) return TC_ERR_INVAL;
+    if (!c->staging2 && cudaMalloc(&c->staging2, c->cap_w * sizeof(u64)) != cudaSuccess) {
+        cudaGetLastError();
+        return TC_ERR_NOMEM;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    const int b = c->stage_next;
+    c->stage_next ^= 1;
+    u64 *buf = b ? c->staging2 : c->staging;
+    // the copy of this batch overlaps the update of the previous one; it only
+    // waits for the batch before that to have finished reading this buffer
+    TC_CUDA(cudaStreamWaitEvent(c->copy, c->ev_used[b], 0));
+    TC_CUDA(cudaMemcpyAsync(buf, h_edges, w * sizeof(u64), cudaMemcpyHostToDevice, c->copy));
+    TC_CUDA(cudaEventRecord(c->ev_copied[b], c->copy));
+    TC_CUDA(cudaStreamWaitEvent(st, c->ev_copied[b], 0));
+    const int rc = enqueue_batch(c, buf, w, st);
+    if (rc) return rc;
+    TC_CUDA(cudaEventRecord(c->ev_used[b], st));
+    return TC_OK;
 }
 
 int tc_sync(tc_ctx *c) {

@@ -107,6 +107,34 @@ def test_empty_batch_is_noop():
         tc.tc_destroy(ctx)
 
 
+def test_pipelined_host_input_matches_oracle():
+    """tc_process_batch_host_async: pinned host batches, copies overlapping
+    the previous batch's update through two staging buffers."""
+    import torch
+    keys = synth.tiny_chung_lu()
+    parts = synth.batches(keys, 3000)
+    pinned = []
+    for b in parts:
+        t = torch.empty(b.size, dtype=torch.int64, pin_memory=True)
+        t.numpy()[:] = b.view(np.int64)
+        pinned.append(t)
+    ctx = tc.tc_create_ex(300, 9, 4, 3000, 12)
+    ref = nbsi_bulk.BulkStream(300, seed=9, stream=4, vertex_bits=12)
+    s = torch.cuda.Stream()
+    try:
+        for t in pinned:
+            tc.tc_process_batch_host_async(ctx, t, stream=s.cuda_stream)
+        s.synchronize()
+        tc.tc_sync(ctx)
+        for b in parts:
+            ref.process_batch(b)
+        assert_state_equal(tc.tc_get_state(ctx), ref.state_arrays(), "pipelined host input")
+        with pytest.raises(tc.TcError):          # above the scratch capacity
+            tc.tc_process_batch_host_async(ctx, np.zeros(3001, dtype=np.uint64))
+    finally:
+        tc.tc_destroy(ctx)
+
+
 def test_bounded_wait_gives_up_and_device_stays_usable():
     """A look-back wait whose predecessor never publishes runs out (about a
     second) and reports TC_ERR_TIMEOUT; afterwards a batch still matches the
