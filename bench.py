@@ -397,16 +397,18 @@ def run_gpu(args, rank, world, local_rank):
     tr = TRAFFIC.get("onesweep_pass_kernel")
     if tr and tr.get("src_hash") == _src_hash():
         roofline["traffic"] = tr["bytes_per_algorithmic_byte"] * roofline["bytes_per_launch"]
-    # algorithmic bytes of the whole step (minimal passes of this design) and
-    # of the survey's formula (full-key passes), per edge
+    # algorithmic bytes of the whole step: this design's minimal passes (arcs
+    # on the src bits, Step-3 keys on a 32-bit edge hash with the position
+    # packed below it) and the survey's formula (arcs on src + position,
+    # Step-3 keys on (u, v), a u32 position value once 2B + bw > 64)
     bw = max(1, (w - 1).bit_length())
     B = cfg["vertex_bits"]
     pa = -(-B // 8)
-    pe = -(-2 * B // 8)
-    e_bytes = 16 if 2 * B + bw <= 64 else 24
-    own_bytes = 32 * w + pa * 2 * w * 16 + pe * w * e_bytes + 8 * w + 2 * 28 * r
+    own_bytes = 32 * w + pa * 2 * w * 16 + 4 * w * 16 + 8 * w + 2 * 28 * r
+    pe_s = -(-2 * B // 8)
+    e_bytes_s = 16 if 2 * B + bw <= 64 else 24
     survey_bytes = 8 * w + (2 * w * 8 + (-(-(B + bw) // 8)) * 2 * w * 16) + \
-        (w * 8 + pe * w * e_bytes) + 64 * r
+        (w * 8 + pe_s * w * e_bytes_s) + 64 * r
     step_s = (t_ms / 1e3) / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

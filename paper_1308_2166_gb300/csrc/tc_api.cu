@@ -109,16 +109,22 @@ u32 pick_digits(u32 live, u32 forced, int &passes) {
     return bits;
 }
 
+// Bits of the Step-3 hash-bucket directory for batches of w edges: about
+// w/4 buckets, so a bucket holds a handful of keys.
+u32 hash_bucket_bits(u64 w) {
+    const u32 bw = bits_for(w - 1);
+    return bw > 3 ? bw - 2 : 1;
+}
+
 BatchShape make_shape(u64 w, u32 B, u32 force_a = 0, u32 force_e = 0) {
     BatchShape s{};
     s.w = (u32)w;
     s.bw = bits_for(w - 1);
     s.B = B;
     s.sha = s.bw + 1;
-    s.ekeys_only = (2 * B + s.bw <= 64) ? 1u : 0u;
-    s.she = s.ekeys_only ? s.bw : 0u;
+    s.hb = hash_bucket_bits(w);
     s.bits_a = pick_digits(B, force_a, s.npa);
-    s.bits_e = pick_digits(2 * B, force_e, s.npe);
+    s.bits_e = pick_digits(32, force_e, s.npe);  // the 32-bit edge hash
     return s;
 }
 
@@ -186,11 +192,10 @@ struct tc_ctx {
     // per-batch scratch
     u64 *arcs[2] = {nullptr, nullptr};
     u64 *ekeys[2] = {nullptr, nullptr};
-    u32 *evals[2] = {nullptr, nullptr};
     u64 *staging = nullptr;
     unsigned char *zeroed = nullptr;  // BatchAcc, SortPlan[2], look-back words
-    DirEntry *adir = nullptr;         // per-vertex directories (ids < 2^kDirMaxBits)
-    DirEntry *edir = nullptr;
+    DirEntry *adir = nullptr;         // per-vertex arc directory (ids < 2^kDirMaxBits)
+    DirEntry *edir = nullptr;         // Step-3 hash-bucket directory (sized with the scratch)
     Control *h_ctl = nullptr;         // pinned host copy of the control block
     // launch accounting and stage timing
     u64 launches = 0;
@@ -239,10 +244,10 @@ static void free_scratch(tc_ctx *c) {
     for (int k = 0; k < 2; ++k) {
         cudaFree(c->arcs[k]);
         cudaFree(c->ekeys[k]);
-        cudaFree(c->evals[k]);
         c->arcs[k] = c->ekeys[k] = nullptr;
-        c->evals[k] = nullptr;
     }
+    cudaFree(c->edir);
+    c->edir = nullptr;
     cudaFree(c->staging);
     cudaFree(c->staging2);
     cudaFree(c->zeroed);
@@ -261,8 +266,10 @@ static int ensure_scratch(tc_ctx *c, u64 w) {
     for (int k = 0; k < 2 && ok; ++k) {
         ok &= cudaMalloc(&c->arcs[k], 2 * w * sizeof(u64)) == cudaSuccess;
         ok &= ok && cudaMalloc(&c->ekeys[k], w * sizeof(u64)) == cudaSuccess;
-        ok &= ok && cudaMalloc(&c->evals[k], w * sizeof(u32)) == cudaSuccess;
     }
+    const u64 nb = 1ull << hash_bucket_bits(w);
+    ok &= ok && cudaMalloc(&c->edir, nb * sizeof(DirEntry)) == cudaSuccess;
+    ok &= ok && cudaMemset(c->edir, 0, nb * sizeof(DirEntry)) == cudaSuccess;
     ok &= ok && cudaMalloc(&c->staging, w * sizeof(u64)) == cudaSuccess;
     ok &= ok && cudaMalloc(&c->zeroed, zb) == cudaSuccess;
     if (!ok) {
@@ -293,16 +300,16 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
 
     const u64 prep_blocks = std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
     prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, prep_smem(s, true), st>>>(
-        W, s, c->arcs[0], c->ekeys[0], c->evals[0], plans, &c->ctl->err, 1);
+        W, s, c->arcs[0], c->ekeys[0], plans, &c->ctl->err, 1);
     sort_plan_kernel<<<dim3((unsigned)std::max(s.npa, s.npe), 2), 256, 0, st>>>(
         plans, s.npa, (u32)(2 * w), s.bits_a, s.npe, (u32)w, s.bits_e);
     stamp(c, st, kPrep);
     const u64 ta = tiles_of(2 * w), te = tiles_of(w);
     const u64 la = pass_lookback_words(2 * w, s.bits_a), le = pass_lookback_words(w, s.bits_e);
     const PassKernel ka = select_pass(s.bits_a, false, c->rank_method);
-    const PassKernel ke = select_pass(s.bits_e, !s.ekeys_only, c->rank_method);
-    // The two sorts are independent: the edge sort (and, with directories,
-    // its index) forks onto the side stream and joins before the sweep, so
+    const PassKernel ke = select_pass(s.bits_e, false, c->rank_method);
+    // The two sorts are independent: the edge sort and its index fork onto
+    // the side stream and join before the sweep, so
     // the kernels of one fill the SMs the other leaves idle (tails of its
     // waves, look-back waits).
     TC_CUDA(cudaEventRecord(c->ev_fork, st));
@@ -311,19 +318,12 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
     u32 *lbe = lb + (u64)s.npa * la;
     for (int p = 0; p < s.npe; ++p)
         ke.fn<<<(unsigned)te, ke.threads, ke.smem, c->side>>>(
-            c->ekeys[0], c->ekeys[1], c->evals[0], c->evals[1], (u32)w, s.she + p * s.bits_e,
-            live_bits(2 * s.B, s.bits_e, p), p, &plans[1], lbe + (u64)p * le, &c->ctl->err,
-            c->ctl);
+            c->ekeys[0], c->ekeys[1], nullptr, nullptr, (u32)w, s.bw + p * s.bits_e,
+            live_bits(32, s.bits_e, p), p, &plans[1], lbe + (u64)p * le, &c->ctl->err, c->ctl);
     const cudaEvent_t edge_end = mark(c, c->side);
     const u64 idx_blocks = std::min<u64>((w + 255) / 256, 152 * 16);
-    if (c->adir) {
-        index_kernel<false><<<(unsigned)idx_blocks, 256, 0, c->side>>>(
-            c->ekeys[0], c->ekeys[1], &plans[1], s, c->edir, c->ctl, &c->ctl->err);
-    } else {
-        const u64 dup_blocks = std::min<u64>((w + 255) / 256, 1216);
-        dups_kernel<<<(unsigned)dup_blocks, 256, 0, c->side>>>(c->ekeys[0], c->ekeys[1], plans,
-                                                               s, &c->ctl->err);
-    }
+    index_kernel<false><<<(unsigned)idx_blocks, 256, 0, c->side>>>(
+        c->ekeys[0], c->ekeys[1], &plans[1], s, c->edir, W, c->ctl, &c->ctl->err);
     TC_CUDA(cudaEventRecord(c->ev_join, c->side));
     for (int p = 0; p < s.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(
@@ -334,7 +334,7 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
     stamp(c, st, kArcSort);  // arc passes, with the edge passes beside them
     if (c->adir)
         index_kernel<true><<<(unsigned)std::min<u64>((2 * w + 255) / 256, 152 * 16), 256, 0,
-                             st>>>(c->arcs[0], c->arcs[1], &plans[0], s, c->adir, c->ctl,
+                             st>>>(c->arcs[0], c->arcs[1], &plans[0], s, c->adir, W, c->ctl,
                                    &c->ctl->err);
     stamp(c, st, kDups);  // the arc index, beside the rest of the edge branch
     TC_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
@@ -350,8 +350,6 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
     a.arcs1 = c->arcs[1];
     a.ekeys0 = c->ekeys[0];
     a.ekeys1 = c->ekeys[1];
-    a.evals0 = c->evals[0];
-    a.evals1 = c->evals[1];
     a.plans = plans;
     a.adir = c->adir;
     a.edir = c->edir;
@@ -374,7 +372,7 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
         c->prof_batches += 1;
         c->prof_sort_launches += (u64)s.npa + (u64)s.npe;
         c->prof_sort_bytes +=
-            (u64)s.npa * 2 * w * 16 + (u64)s.npe * w * (s.ekeys_only ? 16 : 24);
+            (u64)s.npa * 2 * w * 16 + (u64)s.npe * w * 16;
     }
     return TC_OK;
 }
@@ -446,9 +444,7 @@ int tc_create_ex(uint64_t r, uint64_t seed, uint32_t stream_id, uint64_t w_max,
     const u64 nverts = 1ull << vertex_bits;
     if (ok && vertex_bits <= kDirMaxBits) {
         ok &= cudaMalloc(&c->adir, nverts * sizeof(DirEntry)) == cudaSuccess;
-        ok &= ok && cudaMalloc(&c->edir, nverts * sizeof(DirEntry)) == cudaSuccess;
         ok &= ok && cudaMemsetAsync(c->adir, 0, nverts * sizeof(DirEntry), c->own) == cudaSuccess;
-        ok &= ok && cudaMemsetAsync(c->edir, 0, nverts * sizeof(DirEntry), c->own) == cudaSuccess;
     }
     if (ok) {
         std::memset(c->h_ctl, 0, sizeof(Control));
@@ -489,7 +485,6 @@ void tc_destroy(tc_ctx *c) {
     cudaFree(c->flags);
     cudaFree(c->ctl);
     cudaFree(c->adir);
-    cudaFree(c->edir);
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     for (cudaEvent_t ev : c->pool) cudaEventDestroy(ev);
     if (c->own) cudaStreamDestroy(c->own);
@@ -770,7 +765,7 @@ int tc_rank_all(const uint64_t *d_edges, uint64_t w, uint32_t vertex_bits, uint3
     cudaMemsetAsync(z, 0, zb, st);
     const u64 prep_blocks = std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
     prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, prep_smem(s, false), st>>>(
-        d_edges, s, a0, nullptr, nullptr, plans, err, 0);
+        d_edges, s, a0, nullptr, plans, err, 0);
     sort_plan_kernel<<<dim3((unsigned)s.npa, 1), 256, 0, st>>>(plans, s.npa, (u32)(2 * w),
                                                                s.bits_a, 0, 0, 8);
     for (int p = 0; p < s.npa; ++p)
@@ -879,7 +874,7 @@ extern "C" int tc_rank_all_noalloc(const uint64_t *d_edges, uint64_t w, uint32_t
     TC_CUDA(cudaMemsetAsync(err, 0, sizeof(u32), st));
     const u64 prep_blocks = std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
     prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, prep_smem(s, false), st>>>(
-        d_edges, s, a0, nullptr, nullptr, plans, err, 0);
+        d_edges, s, a0, nullptr, plans, err, 0);
     sort_plan_kernel<<<dim3((unsigned)s.npa, 1), 256, 0, st>>>(plans, s.npa, (u32)(2 * w),
                                                                s.bits_a, 0, 0, 8);
     for (int p = 0; p < s.npa; ++p)

@@ -12,12 +12,15 @@
 //                   decreasing pos order and sorted stably on the src bits
 //                   only, which yields Lemma 4.3's order (src asc, pos desc)
 //                   and makes the arc's rank its offset in the src segment.
-//     ekeys[2][w]   uint64 Step-3 keys, sorted on (src, dst):
-//                   keys-only form  u << (B+bw) | v << bw | pos  when
-//                   2B + bw <= 64, else  u << B | v  with evals[2][w] = pos.
-//     adir, edir    per-vertex directories over the sorted arcs / keys
-//                   (vertex ids < 2^kDirMaxBits), epoch-tagged.
-//   bw = bits of w-1, B = vertex id bits.
+//     ekeys[2][w]   uint64 Step-3 keys  h(u, v) << bw | pos, sorted on the
+//                   32-bit mix h of the packed edge (edge_hash): equal edges
+//                   are adjacent and every edge is found by its hash bucket.
+//     adir          per-vertex directory over the sorted arcs (vertex ids
+//                   < 2^kDirMaxBits), epoch-tagged;
+//     edir          directory of the 2^hb hash buckets (top hb bits of h)
+//                   over the sorted Step-3 keys, epoch-tagged.
+//   bw = bits of w-1, B = vertex id bits, hb = bucket bits (about w/4
+//   buckets).
 #pragma once
 
 #include "tc_common.cuh"
@@ -32,13 +35,26 @@ struct BatchShape {
     u32 bw;         // bits of w-1
     u32 B;          // vertex id bits
     u32 sha;        // arc key: src shift = bw + 1
-    u32 she;        // edge key: sort bits start (bw keys-only, 0 with values)
-    u32 ekeys_only; // 1: pos packed in the edge key
+    u32 hb;         // Step-3 hash bucket bits
     int npa;        // arc sort passes
     int npe;        // edge sort passes
     u32 bits_a;     // arc sort digit width
     u32 bits_e;     // edge sort digit width
 };
+
+// 32-bit mix of a packed edge (u << 32) | v for the Step-3 keys: the
+// finaliser of Steele, Lea and Flood's SplitMix64 (OOPSLA 2014, constants
+// as published by Vigna), high half.  Any fixed mix gives the same lookup
+// results -- a lookup verifies the edge itself -- a good one keeps the
+// buckets even whatever the degree distribution.
+__host__ __device__ __forceinline__ u32 edge_hash(u64 x) {
+    x ^= x >> 30;
+    x *= 0xbf58476d1ce4e5b9ull;
+    x ^= x >> 27;
+    x *= 0x94d049bb133111ebull;
+    x ^= x >> 31;
+    return (u32)(x >> 32);
+}
 
 // ---------------------------------------------------------------------------
 // Key build + all digit histograms (one pass over the batch).
@@ -50,7 +66,7 @@ constexpr int kPrepThreads = 256;
 
 static __global__ void __launch_bounds__(kPrepThreads) prep_kernel(
     const u64 *__restrict__ W, BatchShape s, u64 *__restrict__ arcs0, u64 *__restrict__ ekeys0,
-    u32 *__restrict__ evals0, SortPlan *plans, u32 *err, int build_edges) {
+    SortPlan *plans, u32 *err, int build_edges) {
     extern __shared__ u32 h[];
     const u32 ra = 1u << s.bits_a, re = 1u << s.bits_e;
     const u32 ma = ra - 1, me = re - 1;
@@ -76,16 +92,10 @@ static __global__ void __launch_bounds__(kPrepThreads) prep_kernel(
             atomicAdd(&h[p * ra + digit_bits(av, s.sha + p * s.bits_a, ma)], 1u);
         }
         if (build_edges) {
-            u64 ek;
-            if (s.ekeys_only) {
-                ek = (u << (s.B + s.bw)) | (v << s.bw) | j;
-            } else {
-                ek = (u << s.B) | v;
-                evals0[j] = (u32)j;
-            }
+            const u64 ek = ((u64)edge_hash(e) << s.bw) | j;
             ekeys0[j] = ek;
             for (int p = 0; p < s.npe; ++p)
-                atomicAdd(&he[p * re + digit_bits(ek, s.she + p * s.bits_e, me)], 1u);
+                atomicAdd(&he[p * re + digit_bits(ek, s.bw + p * s.bits_e, me)], 1u);
         }
     }
     if (bad) set_error(err, kErrInput);
@@ -95,21 +105,6 @@ static __global__ void __launch_bounds__(kPrepThreads) prep_kernel(
         if (!c) continue;
         if (k < na) atomicAdd(&plans[0].counts[k / ra][k % ra], c);
         else atomicAdd(&plans[1].counts[(k - na) / re][(k - na) % re], c);
-    }
-}
-
-// In-batch repeats are adjacent after the Step-3 sort (used when vertex ids
-// are too wide for directories; index_kernel does this check otherwise).
-static __global__ void dups_kernel(const u64 *ekeys0, const u64 *ekeys1, const SortPlan *plans,
-                            BatchShape s, u32 *err) {
-    const u64 *E = plan_final_sel(&plans[1]) ? ekeys1 : ekeys0;
-    const u32 drop = s.ekeys_only ? s.bw : 0;
-    for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x + 1; k < s.w;
-         k += (u64)gridDim.x * blockDim.x) {
-        if ((E[k] >> drop) == (E[k - 1] >> drop)) {
-            set_error(err, kErrInput);
-            return;
-        }
     }
 }
 
@@ -141,28 +136,38 @@ __device__ __forceinline__ void dir_segment(const DirEntry *dir, u32 epoch, u64 
 // For the arcs, x = src; for the Step-3 keys, x = the smaller endpoint.  The
 // first element of a run writes (epoch, start), the last one writes end.
 // ---------------------------------------------------------------------------
-// kArcs: the arc directory (after the arc sort); else the Step-3 key
-// directory and the repeat check (after the edge sort).  The two run on the
-// streams of their sorts.
+// kArcs: the arc directory (after the arc sort); else the Step-3 bucket
+// directory and the in-batch repeat check (after the edge sort).  The two
+// run on the streams of their sorts.
 template <bool kArcs>
 static __global__ void index_kernel(const u64 *keys0, const u64 *keys1, const SortPlan *plan,
-                                    BatchShape s, DirEntry *dir, const Control *ctl, u32 *err) {
+                                    BatchShape s, DirEntry *dir, const u64 *__restrict__ W,
+                                    const Control *ctl, u32 *err) {
     const u64 *__restrict__ K = plan_final_sel(plan) ? keys1 : keys0;
     const u32 epoch = ctl->epoch + 1;
     const u64 n = kArcs ? 2ull * s.w : (u64)s.w;
-    const u64 nverts = 1ull << s.B;
-    // key -> vertex x: arcs by src; Step-3 keys by the smaller endpoint
-    const u32 sh = kArcs ? s.sha : (s.ekeys_only ? s.B + s.bw : s.B);
-    const u32 drop = s.ekeys_only ? s.bw : 0;  // Step-3 key -> (u, v)
+    const u64 nverts = kArcs ? (1ull << s.B) : (1ull << s.hb);
+    // key -> directory slot: arcs by src; Step-3 keys by hash bucket
+    const u32 sh = kArcs ? s.sha : s.bw + 32 - s.hb;
+    const u64 pmask = (1ull << s.bw) - 1;
     bool dup = false;
     for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (u64)gridDim.x * blockDim.x) {
         const u64 key = __ldg(K + k);
         const u64 x = key >> sh;
-        const u64 pk = k ? __ldg(K + k - 1) : ~0ull;
-        const u64 prev = k ? pk >> sh : ~0ull;
+        const u64 prev = k ? __ldg(K + k - 1) >> sh : ~0ull;
         const u64 next = k + 1 < n ? __ldg(K + k + 1) >> sh : ~0ull;
-        if constexpr (!kArcs) dup |= k && (key >> drop) == (pk >> drop);
+        if constexpr (!kArcs) {
+            // a repeated edge has the repeated hash: compare the edges of the
+            // run of equal hashes that follows (almost always empty)
+            const u64 h = key >> s.bw;
+            const u64 e = __ldg(W + (key & pmask));
+            for (u64 j = k + 1; j < n; ++j) {
+                const u64 kj = __ldg(K + j);
+                if ((kj >> s.bw) != h) break;
+                dup |= __ldg(W + (kj & pmask)) == e;
+            }
+        }
         if (x >= nverts) continue;  // invalid batch (already flagged by the key build)
         if (x != prev) *reinterpret_cast<u64 *>(&dir[x].epoch) = ((u64)k << 32) | epoch;
         if (x != next) dir[x].end = (u32)(k + 1);
@@ -223,9 +228,9 @@ struct SweepArgs {
     u64 r;
     const u64 *arcs0, *arcs1;
     const u64 *ekeys0, *ekeys1;
-    const u32 *evals0, *evals1;
     const SortPlan *plans;
-    const DirEntry *adir, *edir;  // null unless vertex ids < 2^kDirMaxBits
+    const DirEntry *adir;         // null unless vertex ids < 2^kDirMaxBits
+    const DirEntry *edir;         // Step-3 hash buckets
     Control *ctl;
     BatchAcc *acc;                // per-batch S / closed accumulator (zeroed)
     BatchShape s;
@@ -249,8 +254,8 @@ __device__ __forceinline__ void closing_pair(u64 f1, u64 f2, u64 &gu, u64 &gv) {
 template <bool kDir>
 __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 epoch,
                                           const DrawKey &dk, const u64 *__restrict__ arcs,
-                                          const u64 *__restrict__ E, const u32 *__restrict__ EV,
-                                          u64 &f1, u64 &f2, u64 &chi, u32 &fl) {
+                                          const u64 *__restrict__ E, u64 &f1, u64 &f2, u64 &chi,
+                                          u32 &fl) {
     const BatchShape &s = a.s;
     const u64 n_arcs = 2ull * s.w;
     const u32 wm1 = s.w - 1;
@@ -305,31 +310,29 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
     }
     chi += chi_plus;
 
-    // ---- Step 3 (Sec. 4.4): closing edge after f2
+    // ---- Step 3 (Sec. 4.4): closing edge after f2, looked up by its hash
+    // bucket; the candidates with its hash are checked against W itself
     if (f2 != kEmpty && !(fl & TC_FLAG_CLOSED)) {
-        u64 gu, gv, lo = 0, hi = s.w;
+        u64 gu, gv, lo, hi;
         closing_pair(f1, f2, gu, gv);
-        if constexpr (kDir) dir_segment(a.edir, epoch, gu, s.w, lo, hi);
-        bool found;
-        u32 q;
-        if (s.ekeys_only) {
-            const u64 probe = (gu << (s.B + s.bw)) | (gv << s.bw);
-            const u64 k = lower_bound_range(E, lo, hi, probe);
-            const u64 ek = k < hi ? __ldg(E + k) : ~0ull;
-            found = k < hi && (ek >> s.bw) == (probe >> s.bw);
-            q = (u32)(ek & wmask);
-        } else {
-            const u64 probe = (gu << s.B) | gv;
-            const u64 k = lower_bound_range(E, lo, hi, probe);
-            found = k < hi && __ldg(E + k) == probe;
-            q = found ? __ldg(EV + k) : 0u;
+        const u64 g = (gu << 32) | gv;
+        const u64 h = edge_hash(g);
+        dir_segment(a.edir, epoch, h >> (32 - s.hb), s.w, lo, hi);
+        u64 k = lower_bound_range(E, lo, hi, h << s.bw);
+        for (; k < hi; ++k) {
+            const u64 ek = __ldg(E + k);
+            if ((ek >> s.bw) != h) break;
+            const u32 q = (u32)(ek & wmask);
+            if (__ldg(a.W + q) == g) {
+                if (!new2 || q > p2) fl |= TC_FLAG_CLOSED;
+                break;
+            }
         }
-        if (found && (!new2 || q > p2)) fl |= TC_FLAG_CLOSED;
     }
 }
 
-// One estimator per thread.  kDir: segment lookups from the directories,
-// else binary search on the sorted arrays.  Adds sum(chi over closed) and
+// One estimator per thread.  kDir: arc segments from the vertex directory,
+// else by binary search on the sorted arcs.  Adds sum(chi over closed) and
 // the closed count of the new state into a.acc.
 template <bool kDir>
 static __global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArgs a) {
@@ -344,12 +347,11 @@ static __global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArg
         const u64 *arcs = plan_final_sel(&a.plans[0]) ? a.arcs1 : a.arcs0;
         const bool e_sel = plan_final_sel(&a.plans[1]) != 0;
         const u64 *E = e_sel ? a.ekeys1 : a.ekeys0;
-        const u32 *EV = e_sel ? a.evals1 : a.evals0;
         // the state streams through once: evict-first, so that L2 keeps the
         // directories and sorted arrays the searches hit at random
         u64 f1 = __ldcs(a.f1 + i), f2 = __ldcs(a.f2 + i), chi = __ldcs(a.chi + i);
         u32 fl = __ldcs(a.flags + i);
-        sweep_one<kDir>(a, i, m, epoch, dk, arcs, E, EV, f1, f2, chi, fl);
+        sweep_one<kDir>(a, i, m, epoch, dk, arcs, E, f1, f2, chi, fl);
         __stcs(a.f1 + i, f1);
         __stcs(a.f2 + i, f2);
         __stcs(a.chi + i, chi);
