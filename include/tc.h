@@ -238,9 +238,9 @@ typedef struct tc_multi tc_multi;
 
 /* S = n_streams >= 1 streams; HOST arrays r[S] (estimators, 1..2^32-1),
  * seeds[S], stream_ids[S]; w_max_round = most edges one round may carry in
- * total; vertex_bits as in tc_create_ex.  Requires
- * bits(S-1) + 2*vertex_bits <= 64 and bits(S-1) + vertex_bits +
- * bits(w_max_round-1) + 1 <= 64 (sort keys carry the stream index).
+ * total; vertex_bits as in tc_create_ex.  Requires bits(S-1) + vertex_bits +
+ * bits(w_max_round-1) + 1 <= 64 (the rankAll sort keys carry the stream
+ * index; the Step-3 keys carry it beside a 32-bit hash of the edge).
  * Errors: TC_ERR_INVAL, TC_ERR_NOMEM, TC_ERR_CUDA. */
 int tc_multi_create(uint32_t n_streams, const uint64_t *r, const uint64_t *seeds,
                     const uint32_t *stream_ids, uint64_t w_max_round, uint32_t vertex_bits,

@@ -14,8 +14,10 @@
 //               participant-major in decreasing local position j and sorted
 //               on the (k, src) bits: every participant's arcs end up in its
 //               own range [2 eoff_k, 2 eoff_k + 2 w_k), in Lemma 4.3's order;
-//   edge keys   k << 2B | u << B | v with value j: participant k's keys end up
-//               in [eoff_k, eoff_k + w_k) sorted by (u, v);
+//   edge keys   k << (32+bw) | h << bw | j, h = edge_hash(u, v) (or k << 32 | h
+//               with value j when kb + 32 + bw > 64): participant k's keys
+//               end up in [eoff_k, eoff_k + w_k) sorted by hash; a lookup
+//               checks each candidate with the probe's hash against D_k;
 //   sweep       one thread per estimator of the participants only (roff).
 //   bw = bits of (max_k w_k) - 1, kb = bits of K-1, B = vertex id bits.
 #include <algorithm>
@@ -46,7 +48,19 @@ struct RoundShape {
     u64 Wt;     // edges this round
     int npa, npe;
     u32 bits_a, bits_e;
+    u32 eko;    // 1: Step-3 keys carry j in their low bw bits (else as a value)
+    u32 she;    // Step-3 key: sort bits start (bw or 0)
 };
+
+// Step-3 key of participant k's edge at local position j with hash h.
+__device__ __forceinline__ u64 mkey(const RoundShape &rs, u64 k, u64 h, u64 j) {
+    return rs.eko ? (k << (32 + rs.bw)) | (h << rs.bw) | j : (k << 32) | h;
+}
+
+// (participant, hash) part of a Step-3 key.
+__device__ __forceinline__ u64 mkey_prefix(const RoundShape &rs, u64 key) {
+    return rs.eko ? key >> rs.bw : key;
+}
 
 // Views of a round descriptor.
 struct Desc {
@@ -109,11 +123,11 @@ __global__ void __launch_bounds__(kMThreads) mprep_kernel(const u64 *__restrict_
             atomicAdd(&h[p * ra + digit_bits(au, rs.sha + p * rs.bits_a, ra - 1)], 1u);
             atomicAdd(&h[p * ra + digit_bits(av, rs.sha + p * rs.bits_a, ra - 1)], 1u);
         }
-        const u64 ek = ((u64)k << (2 * rs.B)) | (u << rs.B) | v;
+        const u64 ek = mkey(rs, k, edge_hash(e), jl);
         ekeys0[j] = ek;
-        evals0[j] = (u32)jl;
+        if (!rs.eko) evals0[j] = (u32)jl;
         for (int p = 0; p < rs.npe; ++p)
-            atomicAdd(&he[p * re + digit_bits(ek, p * rs.bits_e, re - 1)], 1u);
+            atomicAdd(&he[p * re + digit_bits(ek, rs.she + p * rs.bits_e, re - 1)], 1u);
     }
     __syncthreads();
     for (u32 k = threadIdx.x; k < nh; k += kMThreads) {
@@ -124,15 +138,34 @@ __global__ void __launch_bounds__(kMThreads) mprep_kernel(const u64 *__restrict_
     }
 }
 
-// Repeats inside one participant's batch are adjacent after the edge sort.
-__global__ void mdups_kernel(const u64 *ekeys0, const u64 *ekeys1, const SortPlan *plans,
+// Repeats inside one participant's batch share participant and hash, so
+// they lie in one run of equal (participant, hash) after the edge sort: each
+// key compares its edge with those of the rest of its run (almost always
+// empty).
+__global__ void mdups_kernel(const u64 *ekeys0, const u64 *ekeys1, const u32 *evals0,
+                             const u32 *evals1, const SortPlan *plans,
                              const u64 *__restrict__ desc, RoundShape rs, MStream *ms) {
     const Desc d = desc_view(desc, rs.K);
-    const u64 *E = plan_final_sel(&plans[1]) ? ekeys1 : ekeys0;
-    for (u64 k = (u64)blockIdx.x * blockDim.x + threadIdx.x + 1; k < rs.Wt;
-         k += (u64)gridDim.x * blockDim.x) {
-        const u64 a = E[k];
-        if (a == E[k - 1]) atomicOr(&ms[__ldg(d.slot + (a >> (2 * rs.B)))].err, kErrInput);
+    const bool sel = plan_final_sel(&plans[1]) != 0;
+    const u64 *E = sel ? ekeys1 : ekeys0;
+    const u32 *EV = sel ? evals1 : evals0;
+    const u64 jmask = (1ull << rs.bw) - 1;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < rs.Wt;
+         i += (u64)gridDim.x * blockDim.x) {
+        const u64 a = __ldg(E + i);
+        const u64 pa = mkey_prefix(rs, a);
+        if (i + 1 >= rs.Wt || mkey_prefix(rs, __ldg(E + i + 1)) != pa) continue;
+        const u64 k = rs.eko ? a >> (32 + rs.bw) : a >> 32;
+        const u64 *D = d.ebase[k];
+        const u64 ea = __ldg(D + (rs.eko ? (a & jmask) : __ldg(EV + i)));
+        for (u64 j = i + 1; j < rs.Wt; ++j) {
+            const u64 b = __ldg(E + j);
+            if (mkey_prefix(rs, b) != pa) break;
+            if (__ldg(D + (rs.eko ? (b & jmask) : __ldg(EV + j))) == ea) {
+                atomicOr(&ms[__ldg(d.slot + k)].err, kErrInput);
+                break;
+            }
+        }
     }
 }
 
@@ -237,17 +270,24 @@ __global__ void __launch_bounds__(kMThreads, 5) msweep_kernel(MSweepArgs a) {
                 }
             }
             chi += chi_plus;
-            // ---- Step 3 (Sec. 4.4)
+            // ---- Step 3 (Sec. 4.4): by the closing edge's hash, each
+            // candidate checked against the batch itself
             if (f2 != kEmpty && !(fl & TC_FLAG_CLOSED)) {
                 const u64 a1 = f1 >> 32, b1 = f1 & kMask32, a2 = f2 >> 32, b2 = f2 & kMask32;
                 const u64 x1 = (a1 == a2 || a1 == b2) ? b1 : a1;
                 const u64 x2 = (a2 == a1 || a2 == b1) ? b2 : a2;
                 const u64 gu = x1 < x2 ? x1 : x2, gv = x1 < x2 ? x2 : x1;
-                const u64 probe = ((u64)k << (2 * rs.B)) | (gu << rs.B) | gv;
-                const u64 q = lower_bound_range(E, e0, e0 + ws, probe);
-                if (q < e0 + ws && __ldg(E + q) == probe) {
-                    const u64 pq = __ldg(EV + q);
-                    if (!new2 || pq > p2) fl |= TC_FLAG_CLOSED;
+                const u64 gkey = (gu << 32) | gv;
+                const u64 probe = mkey(rs, k, edge_hash(gkey), 0);
+                const u64 pp = mkey_prefix(rs, probe);
+                for (u64 q = lower_bound_range(E, e0, e0 + ws, probe); q < e0 + ws; ++q) {
+                    const u64 ek = __ldg(E + q);
+                    if (mkey_prefix(rs, ek) != pp) break;
+                    const u64 pq = rs.eko ? (ek & wmask) : __ldg(EV + q);
+                    if (__ldg(D + pq) == gkey) {
+                        if (!new2 || pq > p2) fl |= TC_FLAG_CLOSED;
+                        break;
+                    }
                 }
             }
             F1[i] = f1;
@@ -408,7 +448,7 @@ u64 zeroed_bytes_for(u32 sb, u64 w_max_round, u32 vertex_bits) {
         for (u32 be : {8u, 10u, 11u}) {
             int pa, pe;
             mpick(vertex_bits + sb, ba, pa);
-            mpick(2 * vertex_bits + sb, be, pe);
+            mpick(32 + sb, be, pe);
             lb = std::max(lb, (u64)pa * mlookback(2 * w_max_round, ba) +
                                   (u64)pe * mlookback(w_max_round, be));
         }
@@ -459,7 +499,7 @@ int multi_alloc(u32 S, u64 w_max_round, u32 vertex_bits, tc_multi **out) {
         return TC_ERR_INVAL;
     const u32 sb = mbits_for(S - 1);
     const u32 bwmax = mbits_for(w_max_round - 1);
-    if (sb + vertex_bits + bwmax + 1 > 64 || sb + 2 * vertex_bits > 64) return TC_ERR_INVAL;
+    if (sb + vertex_bits + bwmax + 1 > 64) return TC_ERR_INVAL;
     int rc = mconfigure();
     if (rc) return rc;
     tc_multi *M = new (std::nothrow) tc_multi();
@@ -563,7 +603,9 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, const u64 *desc, u
     rs.sha = rs.bw + 1;
     rs.Wt = Wt;
     rs.bits_a = mpick(M->B + rs.kb, M->force_a, rs.npa);
-    rs.bits_e = mpick(2 * M->B + rs.kb, M->force_e, rs.npe);
+    rs.bits_e = mpick(32 + rs.kb, M->force_e, rs.npe);
+    rs.eko = rs.kb + 32 + rs.bw <= 64 ? 1u : 0u;
+    rs.she = rs.eko ? rs.bw : 0u;
     SortPlan *plans = reinterpret_cast<SortPlan *>(M->zeroed);
     u32 *lb = reinterpret_cast<u32 *>(M->zeroed + 2 * sizeof(SortPlan));
     const u64 la = mlookback(2 * Wt, rs.bits_a), le = mlookback(Wt, rs.bits_e);
@@ -579,7 +621,7 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, const u64 *desc, u
     sort_plan_kernel<<<dim3((unsigned)std::max(rs.npa, rs.npe), 2), 256, 0, st>>>(
         plans, rs.npa, (u32)(2 * Wt), rs.bits_a, rs.npe, (u32)Wt, rs.bits_e);
     const PassK ka = mselect(rs.bits_a, false, M->rank);
-    const PassK ke = mselect(rs.bits_e, true, M->rank);
+    const PassK ke = mselect(rs.bits_e, !rs.eko, M->rank);
     const u64 ta = mtiles(2 * Wt), te = mtiles(Wt);
     // the two sorts are independent: the edge sort forks onto the side stream
     TCM_CUDA(cudaEventRecord(M->ev_fork, st));
@@ -587,12 +629,13 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, const u64 *desc, u
     u32 *lbe = lb + (u64)rs.npa * la;
     for (int p = 0; p < rs.npe; ++p)
         ke.fn<<<(unsigned)te, ke.threads, ke.smem, M->side>>>(
-            M->ekeys[0], M->ekeys[1], M->evals[0], M->evals[1], (u32)Wt, p * rs.bits_e,
-            mlive(2 * M->B + rs.kb, rs.bits_e, p), p, &plans[1], lbe + (u64)p * le, gerr,
+            M->ekeys[0], M->ekeys[1], rs.eko ? nullptr : M->evals[0],
+            rs.eko ? nullptr : M->evals[1], (u32)Wt, rs.she + p * rs.bits_e,
+            mlive(32 + rs.kb, rs.bits_e, p), p, &plans[1], lbe + (u64)p * le, gerr,
             nullptr);
     const u64 db = std::min<u64>((Wt + 255) / 256, 1216);
-    mdups_kernel<<<(unsigned)db, 256, 0, M->side>>>(M->ekeys[0], M->ekeys[1], plans, desc, rs,
-                                                    M->ms);
+    mdups_kernel<<<(unsigned)db, 256, 0, M->side>>>(M->ekeys[0], M->ekeys[1], M->evals[0],
+                                                    M->evals[1], plans, desc, rs, M->ms);
     TCM_CUDA(cudaEventRecord(M->ev_join, M->side));
     for (int p = 0; p < rs.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(
