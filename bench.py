@@ -43,12 +43,12 @@ UNIT = "edges/s"
 
 # ncu DRAM traffic of the dominant kernel, per algorithmic byte, with the
 # hash of the source it was taken on (profiles/ holds the capture summary).
-# Taken from profiles/onesweep_pass_rmat20.md: DRAM read + write of one arc
-# and one edge pass over their algorithmic bytes (writes largely stay in L2),
-# valid while the pass kernel's sources hash the same.
+# Taken from profiles/onesweep_pass_rmat20.md: DRAM read + write of two arc
+# passes over their algorithmic bytes (writes largely stay in L2), valid
+# while the pass kernel's sources hash the same.
 TRAFFIC = {
-    "onesweep_pass_kernel": {"src_hash": "8744424ee280bd8f",
-                             "bytes_per_algorithmic_byte": 117.770496 / 201.326592},
+    "onesweep_pass_kernel": {"src_hash": "1f2e5f68f12875e3",
+                             "bytes_per_algorithmic_byte": 167.717888 / 268.435456},
 }
 
 # Sources the sort pass kernel is built from.

@@ -1,7 +1,7 @@
 // Onesweep LSD radix sort of packed uint64 keys (optionally carrying a
 // uint32 value), used for the two sorts of the estimator update: the arcs of
-// rankAll (Lemma 4.3: by src, ties by decreasing pos) and the `edges` array
-// of Step 3 (Sec. 4.4: by (src, dst)).
+// rankAll (Lemma 4.3: by src, ties by decreasing pos) and the Step-3 keys of
+// Sec. 4.4 (by a hash of the edge).
 //
 // Design (after Adinets and Merrill, "Onesweep: A Faster Least Significant
 // Digit Radix Sort for GPUs", 2022):
