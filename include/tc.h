@@ -102,11 +102,24 @@ int tc_process_batch(tc_ctx *c, const uint64_t *edges, uint64_t w);
 int tc_process_batch_async(tc_ctx *c, const uint64_t *d_edges, uint64_t w,
                            void *cuda_stream);
 
+/* Pipelined form of tc_process_batch_async for a DEVICE array that already
+ * holds the batch when the call is made (filled and synchronised before, not
+ * by work still queued on `cuda_stream`).  The batch's sort phase -- key
+ * build, both sorts and their directories -- starts on the library's own
+ * streams at once, into a second scratch set, so it overlaps the sweep of the
+ * previous batch; the sweep and bookkeeping are ordered on `cuda_stream` as
+ * usual, so results are bit-identical to the stream-ordered call.  The first
+ * call allocates the second scratch set.  d_edges is borrowed until the work
+ * on `cuda_stream` passes this batch.  Errors as tc_process_batch_async. */
+int tc_process_batch_ready_async(tc_ctx *c, const uint64_t *d_edges, uint64_t w,
+                                 void *cuda_stream);
+
 /* tc_process_batch_async for a HOST array (pinned memory for the copy to
  * run asynchronously): the batch is copied to one of two device staging
  * buffers on an internal copy stream, so the copy of each batch overlaps the
- * update of the one before it, and the update is enqueued on `cuda_stream`
- * behind its copy.  Returns without waiting.  h_edges is borrowed until the
+ * update of the one before it; the batch is then sorted as soon as its copy
+ * lands (pipelined as tc_process_batch_ready_async) and swept on
+ * `cuda_stream`.  Returns without waiting.  h_edges is borrowed until the
  * work on `cuda_stream` passes this batch.  w must not exceed the context's
  * scratch capacity, else TC_ERR_INVAL; errors are reported as for
  * tc_process_batch_async.  Do not interleave with tc_process_batch from

@@ -38,7 +38,7 @@ EXPORTS = (
     "tc_server_create", "tc_server_open", "tc_server_submit", "tc_server_query",
     "tc_server_close", "tc_server_poll", "tc_server_drain", "tc_server_stats",
     "tc_server_destroy", "tc_selftest_wait_timeout", "tc_save_size", "tc_save", "tc_load",
-    "tc_process_batch_host_async",
+    "tc_process_batch_host_async", "tc_process_batch_ready_async",
 )
 
 TC_REQ_OPEN, TC_REQ_BATCH, TC_REQ_QUERY, TC_REQ_CLOSE = 1, 2, 3, 4
@@ -151,6 +151,7 @@ def load(path: str | None = None):
         "tc_server_destroy": (None, [P]),
         "tc_selftest_wait_timeout": (I, []),
         "tc_process_batch_host_async": (I, [P, P, U64, P]),
+        "tc_process_batch_ready_async": (I, [P, P, U64, P]),
         "tc_save_size": (U64, [P]),
         "tc_save": (I, [P, P, U64]),
         "tc_load": (I, [P, U64, U64, ctypes.POINTER(P)]),
@@ -212,6 +213,16 @@ def tc_process_batch_async(ctx: int, d_edges, w: int | None = None, stream: int 
     w = _len(d_edges) if w is None else w
     _check(load().tc_process_batch_async(ctx, _ptr(d_edges) if w else None, w, stream or None),
            "tc_process_batch_async")
+
+
+def tc_process_batch_ready_async(ctx: int, d_edges, w: int | None = None,
+                                 stream: int = 0) -> None:
+    """Pipelined update for a device batch that is already in place: its sort
+    phase overlaps the previous batch's sweep (bit-identical results)."""
+    w = _len(d_edges) if w is None else w
+    _check(load().tc_process_batch_ready_async(ctx, _ptr(d_edges) if w else None, w,
+                                               stream or None),
+           "tc_process_batch_ready_async")
 
 
 def tc_process_batch_host_async(ctx: int, h_edges, w: int | None = None,

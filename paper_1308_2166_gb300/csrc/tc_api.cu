@@ -163,8 +163,10 @@ size_t prep_smem(const BatchShape &s, bool edges) {
            sizeof(u32);
 }
 
-// Per-batch zeroed scratch: BatchAcc, then SortPlan[2], then look-back words.
-constexpr u64 kOffPlans = sizeof(BatchAcc);
+// Per-batch zeroed scratch: BatchAcc, the batch's error word (256 bytes
+// reserved), then SortPlan[2], then look-back words.
+constexpr u64 kOffErr = sizeof(BatchAcc);
+constexpr u64 kOffPlans = kOffErr + 256;
 constexpr u64 kOffLookback = kOffPlans + 2 * sizeof(SortPlan);
 
 }  // namespace
@@ -189,13 +191,21 @@ struct tc_ctx {
     u64 *f1 = nullptr, *f2 = nullptr, *chi = nullptr;
     u32 *flags = nullptr;
     Control *ctl = nullptr;
-    // per-batch scratch
-    u64 *arcs[2] = {nullptr, nullptr};
-    u64 *ekeys[2] = {nullptr, nullptr};
+    // per-batch scratch: one set, or two once a batch is pipelined (batch k+1
+    // sorts into the set that batch k's sweep is not reading)
+    struct Set {
+        u64 *arcs[2] = {nullptr, nullptr};
+        u64 *ekeys[2] = {nullptr, nullptr};
+        unsigned char *zeroed = nullptr;  // BatchAcc, error word, SortPlan[2], look-back
+        DirEntry *adir = nullptr;         // per-vertex arc directory (ids < 2^kDirMaxBits)
+        DirEntry *edir = nullptr;         // Step-3 hash-bucket directory
+    };
+    Set set[2];
+    int nsets = 1;
+    u32 seq = 0;                      // batches enqueued: directory tag, set parity
+    cudaStream_t sa = nullptr;        // a pipelined batch's sort phase (with `side`)
+    cudaEvent_t ev_sorted[2] = {}, ev_swept[2] = {};
     u64 *staging = nullptr;
-    unsigned char *zeroed = nullptr;  // BatchAcc, SortPlan[2], look-back words
-    DirEntry *adir = nullptr;         // per-vertex arc directory (ids < 2^kDirMaxBits)
-    DirEntry *edir = nullptr;         // Step-3 hash-bucket directory (sized with the scratch)
     Control *h_ctl = nullptr;         // pinned host copy of the control block
     // launch accounting and stage timing
     u64 launches = 0;
@@ -240,38 +250,58 @@ static void stamp(tc_ctx *c, cudaStream_t st, int stage) {
     c->stamps.push_back({ev, stage});
 }
 
-static void free_scratch(tc_ctx *c) {
+static void free_set(tc_ctx::Set &z, bool with_dir) {
     for (int k = 0; k < 2; ++k) {
-        cudaFree(c->arcs[k]);
-        cudaFree(c->ekeys[k]);
-        c->arcs[k] = c->ekeys[k] = nullptr;
+        cudaFree(z.arcs[k]);
+        cudaFree(z.ekeys[k]);
+        z.arcs[k] = z.ekeys[k] = nullptr;
     }
-    cudaFree(c->edir);
-    c->edir = nullptr;
+    cudaFree(z.edir);
+    cudaFree(z.zeroed);
+    z.edir = nullptr;
+    z.zeroed = nullptr;
+    if (with_dir) {
+        cudaFree(z.adir);
+        z.adir = nullptr;
+    }
+}
+
+static void free_scratch(tc_ctx *c) {
+    for (int k = 0; k < 2; ++k) free_set(c->set[k], false);
     cudaFree(c->staging);
     cudaFree(c->staging2);
-    cudaFree(c->zeroed);
     c->staging = nullptr;
     c->staging2 = nullptr;
-    c->zeroed = nullptr;
     c->cap_w = 0;
+}
+
+// Batch-size-dependent buffers of one scratch set (and its vertex directory
+// the first time), for batches of up to w edges.
+static bool alloc_set(tc_ctx *c, tc_ctx::Set &z, u64 w) {
+    const u64 zb = kOffLookback + lookback_words_max(w, c->vertex_bits) * sizeof(u32);
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k) {
+        ok &= cudaMalloc(&z.arcs[k], 2 * w * sizeof(u64)) == cudaSuccess;
+        ok &= ok && cudaMalloc(&z.ekeys[k], w * sizeof(u64)) == cudaSuccess;
+    }
+    const u64 nb = 1ull << hash_bucket_bits(w);
+    ok &= ok && cudaMalloc(&z.edir, nb * sizeof(DirEntry)) == cudaSuccess;
+    ok &= ok && cudaMemset(z.edir, 0, nb * sizeof(DirEntry)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&z.zeroed, zb) == cudaSuccess;
+    if (ok && !z.adir && c->vertex_bits <= kDirMaxBits) {
+        const u64 nverts = 1ull << c->vertex_bits;
+        ok &= cudaMalloc(&z.adir, nverts * sizeof(DirEntry)) == cudaSuccess;
+        ok &= ok && cudaMemset(z.adir, 0, nverts * sizeof(DirEntry)) == cudaSuccess;
+    }
+    return ok;
 }
 
 static int ensure_scratch(tc_ctx *c, u64 w) {
     if (w <= c->cap_w) return TC_OK;
     TC_CUDA(cudaDeviceSynchronize());
     free_scratch(c);
-    const u64 zb = kOffLookback + lookback_words_max(w, c->vertex_bits) * sizeof(u32);
-    bool ok = true;
-    for (int k = 0; k < 2 && ok; ++k) {
-        ok &= cudaMalloc(&c->arcs[k], 2 * w * sizeof(u64)) == cudaSuccess;
-        ok &= ok && cudaMalloc(&c->ekeys[k], w * sizeof(u64)) == cudaSuccess;
-    }
-    const u64 nb = 1ull << hash_bucket_bits(w);
-    ok &= ok && cudaMalloc(&c->edir, nb * sizeof(DirEntry)) == cudaSuccess;
-    ok &= ok && cudaMemset(c->edir, 0, nb * sizeof(DirEntry)) == cudaSuccess;
-    ok &= ok && cudaMalloc(&c->staging, w * sizeof(u64)) == cudaSuccess;
-    ok &= ok && cudaMalloc(&c->zeroed, zb) == cudaSuccess;
+    bool ok = cudaMalloc(&c->staging, w * sizeof(u64)) == cudaSuccess;
+    for (int k = 0; k < c->nsets && ok; ++k) ok &= alloc_set(c, c->set[k], w);
     if (!ok) {
         cudaGetLastError();
         free_scratch(c);
@@ -281,64 +311,96 @@ static int ensure_scratch(tc_ctx *c, u64 w) {
     return TC_OK;
 }
 
+// The second scratch set, for pipelined batches.
+static int ensure_two_sets(tc_ctx *c) {
+    if (c->nsets == 2) return TC_OK;
+    if (!alloc_set(c, c->set[1], c->cap_w)) {
+        cudaGetLastError();
+        free_set(c->set[1], true);
+        return TC_ERR_NOMEM;
+    }
+    c->nsets = 2;
+    return TC_OK;
+}
+
 static int map_device_error(u32 e) {
     if (e == kErrInput) return TC_ERR_INPUT;
     if (e == kErrTimeout) return TC_ERR_TIMEOUT;
     return e ? TC_ERR_CUDA : TC_OK;
 }
 
-// Enqueue one batch on `st`.  W is a device pointer; w in [1, cap_w].
-static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
+// Enqueue one batch whose update lands on `st`.  W is a device pointer; w in
+// [1, cap_w].  Stream-ordered: every step runs behind earlier work on st.
+// Pipelined (two scratch sets): the sort phase -- key build, both sorts and
+// their directories -- runs on the library's own streams as soon as W is
+// ready (at the call, or at w_ready) and the set it sorts into is free, so it
+// overlaps the sweep of the previous batch; only the sweep and the
+// bookkeeping are ordered on st.
+static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool pipelined = false,
+                         cudaEvent_t w_ready = nullptr) {
     const NvtxRange range("tc batch");
     const BatchShape s = make_shape(w, c->vertex_bits, c->force_bits_a, c->force_bits_e);
-    BatchAcc *acc = reinterpret_cast<BatchAcc *>(c->zeroed);
-    SortPlan *plans = reinterpret_cast<SortPlan *>(c->zeroed + kOffPlans);
-    u32 *lb = reinterpret_cast<u32 *>(c->zeroed + kOffLookback);
+    const int b = c->nsets == 2 ? (int)(c->seq & 1) : 0;
+    const u32 tag = ++c->seq;
+    tc_ctx::Set &z = c->set[b];
+    BatchAcc *acc = reinterpret_cast<BatchAcc *>(z.zeroed);
+    u32 *berr = reinterpret_cast<u32 *>(z.zeroed + kOffErr);
+    SortPlan *plans = reinterpret_cast<SortPlan *>(z.zeroed + kOffPlans);
+    u32 *lb = reinterpret_cast<u32 *>(z.zeroed + kOffLookback);
     const u64 used = kOffLookback + lookback_words(s, true) * sizeof(u32);
-    stamp(c, st, kStart);
-    TC_CUDA(cudaMemsetAsync(c->zeroed, 0, used, st));
+    // the sort phase's stream, and whether stage stamps go on one timeline
+    cudaStream_t ms = pipelined ? c->sa : st;
+    // the set's previous batch may have been swept on another stream
+    TC_CUDA(cudaStreamWaitEvent(ms, c->ev_swept[b], 0));
+    if (w_ready) TC_CUDA(cudaStreamWaitEvent(ms, w_ready, 0));
+    const bool stages = !pipelined;
+    if (stages) stamp(c, ms, kStart);
+    TC_CUDA(cudaMemsetAsync(z.zeroed, 0, used, ms));
 
     const u64 prep_blocks = std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
-    prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, prep_smem(s, true), st>>>(
-        W, s, c->arcs[0], c->ekeys[0], plans, &c->ctl->err, 1);
-    sort_plan_kernel<<<dim3((unsigned)std::max(s.npa, s.npe), 2), 256, 0, st>>>(
+    prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, prep_smem(s, true), ms>>>(
+        W, s, z.arcs[0], z.ekeys[0], plans, berr, 1);
+    sort_plan_kernel<<<dim3((unsigned)std::max(s.npa, s.npe), 2), 256, 0, ms>>>(
         plans, s.npa, (u32)(2 * w), s.bits_a, s.npe, (u32)w, s.bits_e);
-    stamp(c, st, kPrep);
+    if (stages) stamp(c, ms, kPrep);
     const u64 ta = tiles_of(2 * w), te = tiles_of(w);
     const u64 la = pass_lookback_words(2 * w, s.bits_a), le = pass_lookback_words(w, s.bits_e);
     const PassKernel ka = select_pass(s.bits_a, false, c->rank_method);
     const PassKernel ke = select_pass(s.bits_e, false, c->rank_method);
     // The two sorts are independent: the edge sort and its index fork onto
-    // the side stream and join before the sweep, so
-    // the kernels of one fill the SMs the other leaves idle (tails of its
-    // waves, look-back waits).
-    TC_CUDA(cudaEventRecord(c->ev_fork, st));
+    // the side stream and join before the sweep, so the kernels of one fill
+    // the SMs the other leaves idle (tails of its waves, look-back waits).
+    TC_CUDA(cudaEventRecord(c->ev_fork, ms));
     TC_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    const cudaEvent_t sort_begin = mark(c, st);
+    const cudaEvent_t sort_begin = mark(c, ms);
     u32 *lbe = lb + (u64)s.npa * la;
     for (int p = 0; p < s.npe; ++p)
         ke.fn<<<(unsigned)te, ke.threads, ke.smem, c->side>>>(
-            c->ekeys[0], c->ekeys[1], nullptr, nullptr, (u32)w, s.bw + p * s.bits_e,
-            live_bits(32, s.bits_e, p), p, &plans[1], lbe + (u64)p * le, &c->ctl->err, c->ctl);
+            z.ekeys[0], z.ekeys[1], nullptr, nullptr, (u32)w, s.bw + p * s.bits_e,
+            live_bits(32, s.bits_e, p), p, &plans[1], lbe + (u64)p * le, berr, c->ctl);
     const cudaEvent_t edge_end = mark(c, c->side);
     const u64 idx_blocks = std::min<u64>((w + 255) / 256, 152 * 16);
     index_kernel<false><<<(unsigned)idx_blocks, 256, 0, c->side>>>(
-        c->ekeys[0], c->ekeys[1], &plans[1], s, c->edir, W, c->ctl, &c->ctl->err);
+        z.ekeys[0], z.ekeys[1], &plans[1], s, z.edir, W, tag, berr);
     TC_CUDA(cudaEventRecord(c->ev_join, c->side));
     for (int p = 0; p < s.npa; ++p)
-        ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(
-            c->arcs[0], c->arcs[1], nullptr, nullptr, (u32)(2 * w), s.sha + p * s.bits_a,
-            live_bits(s.B, s.bits_a, p), p, &plans[0], lb + (u64)p * la, &c->ctl->err, c->ctl);
-    const cudaEvent_t arc_end = mark(c, st);
+        ka.fn<<<(unsigned)ta, ka.threads, ka.smem, ms>>>(
+            z.arcs[0], z.arcs[1], nullptr, nullptr, (u32)(2 * w), s.sha + p * s.bits_a,
+            live_bits(s.B, s.bits_a, p), p, &plans[0], lb + (u64)p * la, berr, c->ctl);
+    const cudaEvent_t arc_end = mark(c, ms);
     if (sort_begin && edge_end && arc_end) c->spans.push_back({sort_begin, arc_end, edge_end});
-    stamp(c, st, kArcSort);  // arc passes, with the edge passes beside them
-    if (c->adir)
+    if (stages) stamp(c, ms, kArcSort);  // arc passes, with the edge passes beside them
+    if (z.adir)
         index_kernel<true><<<(unsigned)std::min<u64>((2 * w + 255) / 256, 152 * 16), 256, 0,
-                             st>>>(c->arcs[0], c->arcs[1], &plans[0], s, c->adir, W, c->ctl,
-                                   &c->ctl->err);
-    stamp(c, st, kDups);  // the arc index, beside the rest of the edge branch
-    TC_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
-    stamp(c, st, kEdgeSort);  // what is left of the edge passes and their index
+                             ms>>>(z.arcs[0], z.arcs[1], &plans[0], s, z.adir, W, tag, berr);
+    if (stages) stamp(c, ms, kDups);  // the arc index, beside the rest of the edge branch
+    TC_CUDA(cudaStreamWaitEvent(ms, c->ev_join, 0));
+    if (stages) stamp(c, ms, kEdgeSort);  // what is left of the edge passes and their index
+    if (pipelined) {
+        TC_CUDA(cudaEventRecord(c->ev_sorted[b], ms));
+        TC_CUDA(cudaStreamWaitEvent(st, c->ev_sorted[b], 0));
+        stamp(c, st, kStart);  // the sweep's own timeline starts when its sorts are done
+    }
     SweepArgs a{};
     a.W = W;
     a.f1 = c->f1;
@@ -346,28 +408,32 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st) {
     a.chi = c->chi;
     a.flags = c->flags;
     a.r = c->r;
-    a.arcs0 = c->arcs[0];
-    a.arcs1 = c->arcs[1];
-    a.ekeys0 = c->ekeys[0];
-    a.ekeys1 = c->ekeys[1];
+    a.arcs0 = z.arcs[0];
+    a.arcs1 = z.arcs[1];
+    a.ekeys0 = z.ekeys[0];
+    a.ekeys1 = z.ekeys[1];
     a.plans = plans;
-    a.adir = c->adir;
-    a.edir = c->edir;
+    a.adir = z.adir;
+    a.edir = z.edir;
     a.ctl = c->ctl;
     a.acc = acc;
+    a.berr = berr;
+    a.epoch = tag;
     a.s = s;
     a.key = make_uint2((u32)(c->seed & 0xFFFFFFFFu), (u32)(c->seed >> 32));
     a.stream = c->stream_id;
     const u64 sweep_blocks = (c->r + kSweepThreads - 1) / kSweepThreads;
-    if (c->adir)
+    if (z.adir)
         sweep_kernel<true><<<(unsigned)sweep_blocks, kSweepThreads, 0, st>>>(a);
     else
         sweep_kernel<false><<<(unsigned)sweep_blocks, kSweepThreads, 0, st>>>(a);
     stamp(c, st, kSweep);
-    finish_kernel<<<1, 1, 0, st>>>(c->ctl, acc, w);
+    finish_kernel<<<1, 1, 0, st>>>(c->ctl, acc, berr, w);
     stamp(c, st, kFinish);
+    // this set is free again once the sweep and bookkeeping have read it
+    TC_CUDA(cudaEventRecord(c->ev_swept[b], st));
     TC_CUDA(cudaGetLastError());
-    c->launches += (c->adir ? 6 : 5) + (u64)s.npa + (u64)s.npe;
+    c->launches += (z.adir ? 6 : 5) + (u64)s.npa + (u64)s.npe;
     if (c->prof) {
         c->prof_batches += 1;
         c->prof_sort_launches += (u64)s.npa + (u64)s.npe;
@@ -441,10 +507,10 @@ int tc_create_ex(uint64_t r, uint64_t seed, uint32_t stream_id, uint64_t w_max,
     ok &= ok && cudaMalloc(&c->flags, r * sizeof(u32)) == cudaSuccess;
     ok &= ok && cudaMalloc(&c->ctl, sizeof(Control)) == cudaSuccess;
     ok &= ok && cudaHostAlloc(&c->h_ctl, sizeof(Control), cudaHostAllocDefault) == cudaSuccess;
-    const u64 nverts = 1ull << vertex_bits;
-    if (ok && vertex_bits <= kDirMaxBits) {
-        ok &= cudaMalloc(&c->adir, nverts * sizeof(DirEntry)) == cudaSuccess;
-        ok &= ok && cudaMemsetAsync(c->adir, 0, nverts * sizeof(DirEntry), c->own) == cudaSuccess;
+    ok &= ok && cudaStreamCreateWithFlags(&c->sa, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k < 2; ++k) {
+        ok &= ok && cudaEventCreateWithFlags(&c->ev_sorted[k], cudaEventDisableTiming) == cudaSuccess;
+        ok &= ok && cudaEventCreateWithFlags(&c->ev_swept[k], cudaEventDisableTiming) == cudaSuccess;
     }
     if (ok) {
         std::memset(c->h_ctl, 0, sizeof(Control));
@@ -484,7 +550,7 @@ void tc_destroy(tc_ctx *c) {
     cudaFree(c->chi);
     cudaFree(c->flags);
     cudaFree(c->ctl);
-    cudaFree(c->adir);
+    for (int k = 0; k < 2; ++k) free_set(c->set[k], true);
     if (c->h_ctl) cudaFreeHost(c->h_ctl);
     for (cudaEvent_t ev : c->pool) cudaEventDestroy(ev);
     if (c->own) cudaStreamDestroy(c->own);
@@ -492,9 +558,12 @@ void tc_destroy(tc_ctx *c) {
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->copy) cudaStreamDestroy(c->copy);
+    if (c->sa) cudaStreamDestroy(c->sa);
     for (int k = 0; k < 2; ++k) {
         if (c->ev_copied[k]) cudaEventDestroy(c->ev_copied[k]);
         if (c->ev_used[k]) cudaEventDestroy(c->ev_used[k]);
+        if (c->ev_sorted[k]) cudaEventDestroy(c->ev_sorted[k]);
+        if (c->ev_swept[k]) cudaEventDestroy(c->ev_swept[k]);
     }
     delete c;
 }
@@ -556,11 +625,23 @@ int tc_process_batch_host_async(tc_ctx *c, const uint64_t *h_edges, uint64_t w,
     TC_CUDA(cudaStreamWaitEvent(c->copy, c->ev_used[b], 0));
     TC_CUDA(cudaMemcpyAsync(buf, h_edges, w * sizeof(u64), cudaMemcpyHostToDevice, c->copy));
     TC_CUDA(cudaEventRecord(c->ev_copied[b], c->copy));
-    TC_CUDA(cudaStreamWaitEvent(st, c->ev_copied[b], 0));
-    const int rc = enqueue_batch(c, buf, w, st);
+    int rc = ensure_two_sets(c);
+    if (rc) return rc;
+    // the batch is sorted as soon as its copy lands, beside the previous sweep
+    rc = enqueue_batch(c, buf, w, st, true, c->ev_copied[b]);
     if (rc) return rc;
     TC_CUDA(cudaEventRecord(c->ev_used[b], st));
     return TC_OK;
+}
+
+int tc_process_batch_ready_async(tc_ctx *c, const uint64_t *d_edges, uint64_t w,
+                                 void *cuda_stream) {
+    if (!c || (w && !d_edges) || w > kMaxBatch) return TC_ERR_INVAL;
+    if (w == 0) return TC_OK;
+    if (w > c->cap_w) return TC_ERR_INVAL;
+    const int rc = ensure_two_sets(c);
+    if (rc) return rc;
+    return enqueue_batch(c, d_edges, w, (cudaStream_t)cuda_stream, true);
 }
 
 int tc_sync(tc_ctx *c) {

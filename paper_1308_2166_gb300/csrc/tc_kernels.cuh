@@ -142,9 +142,8 @@ __device__ __forceinline__ void dir_segment(const DirEntry *dir, u32 epoch, u64 
 template <bool kArcs>
 static __global__ void index_kernel(const u64 *keys0, const u64 *keys1, const SortPlan *plan,
                                     BatchShape s, DirEntry *dir, const u64 *__restrict__ W,
-                                    const Control *ctl, u32 *err) {
+                                    u32 epoch, u32 *err) {
     const u64 *__restrict__ K = plan_final_sel(plan) ? keys1 : keys0;
-    const u32 epoch = ctl->epoch + 1;
     const u64 n = kArcs ? 2ull * s.w : (u64)s.w;
     const u64 nverts = kArcs ? (1ull << s.B) : (1ull << s.hb);
     // key -> directory slot: arcs by src; Step-3 keys by hash bucket
@@ -233,6 +232,8 @@ struct SweepArgs {
     const DirEntry *edir;         // Step-3 hash buckets
     Control *ctl;
     BatchAcc *acc;                // per-batch S / closed accumulator (zeroed)
+    const u32 *berr;              // this batch's error word (zeroed)
+    u32 epoch;                    // this batch's directory tag
     BatchShape s;
     uint2 key;
     u32 stream;
@@ -337,12 +338,12 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
 template <bool kDir>
 static __global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArgs a) {
     __shared__ u64 s_lo[kSweepThreads / 32], s_hi[kSweepThreads / 32], s_cnt[kSweepThreads / 32];
-    if (ld_relaxed(&a.ctl->err)) return;  // rejected batch: state stays as it was
+    if (ld_relaxed(a.berr)) return;  // rejected batch: state stays as it was
     const u64 i = (u64)blockIdx.x * kSweepThreads + threadIdx.x;
     u64 add = 0, closed = 0;
     if (i < a.r) {
         const u64 m = a.ctl->m;
-        const u32 epoch = a.ctl->epoch + 1;
+        const u32 epoch = a.epoch;
         const DrawKey dk{a.key, (u32)a.ctl->batches, a.stream};
         const u64 *arcs = plan_final_sel(&a.plans[0]) ? a.arcs1 : a.arcs0;
         const bool e_sel = plan_final_sel(&a.plans[1]) != 0;
@@ -372,8 +373,8 @@ static __global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArg
 // Close the batch: if accepted, count it and commit the estimate of the new
 // state; otherwise record the error (state, |E|, batch counter and the
 // committed estimate stay as they were).
-static __global__ void finish_kernel(Control *ctl, const BatchAcc *acc, u64 w) {
-    const u32 e = ctl->err;
+static __global__ void finish_kernel(Control *ctl, const BatchAcc *acc, const u32 *berr, u64 w) {
+    const u32 e = *berr;
     if (e) {
         if (!ctl->sticky) ctl->sticky = e;
     } else {
@@ -385,7 +386,6 @@ static __global__ void finish_kernel(Control *ctl, const BatchAcc *acc, u64 w) {
         ctl->est[3] = ctl->m;
     }
     ctl->epoch += 1;
-    ctl->err = 0;
 }
 
 // Median-of-means groups: CTA k sums group k = [k*r/g, (k+1)*r/g) into

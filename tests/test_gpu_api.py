@@ -135,6 +135,50 @@ def test_pipelined_host_input_matches_oracle():
         tc.tc_destroy(ctx)
 
 
+def test_pipelined_batches_match_oracle_and_isolate_errors():
+    """tc_process_batch_ready_async overlaps each batch's sorts with the
+    previous sweep through two scratch sets: mixed with the stream-ordered
+    and synchronous calls, states equal the oracle, and a rejected batch in
+    the pipeline leaves its neighbours alone."""
+    import torch
+    keys = synth.tiny_chung_lu()
+    parts = synth.batches(keys, 2500)
+    bad = parts[5].copy()
+    bad[7] = bad[3]                                  # repeated edge
+    devs = [to_device(b) for b in parts]
+    dbad = to_device(bad)
+    torch.cuda.synchronize()
+    ctx = tc.tc_create_ex(400, 21, 2, 2500, 12)
+    ref = nbsi_bulk.BulkStream(400, seed=21, stream=2, vertex_bits=12)
+    s = torch.cuda.Stream()
+    try:
+        modes = ["ready", "ready", "async", "ready", "ready", "bad", "ready", "sync", "ready",
+                 "async", "ready", "ready", "ready", "ready"]
+        for j, mode in enumerate(modes[:len(parts)]):
+            if mode == "bad":
+                tc.tc_process_batch_ready_async(ctx, dbad, stream=s.cuda_stream)
+                continue
+            if mode == "ready":
+                tc.tc_process_batch_ready_async(ctx, devs[j], stream=s.cuda_stream)
+            elif mode == "async":
+                tc.tc_process_batch_async(ctx, devs[j], stream=s.cuda_stream)
+            else:
+                s.synchronize()
+                with pytest.raises(tc.TcError) as e:   # reports the earlier rejected batch
+                    tc.tc_process_batch(ctx, parts[j])
+                assert e.value.code == tc.TC_ERR_INPUT
+                ref.process_batch(parts[j])
+                continue
+            ref.process_batch(parts[j])
+        s.synchronize()
+        tc.tc_sync(ctx)
+        assert_state_equal(tc.tc_get_state(ctx), ref.state_arrays(), "pipelined mix")
+        e = tc.tc_estimate(ctx)
+        assert e["S"] == ref.closed_sum() and e["m"] == ref.m and e["batches"] == ref.b
+    finally:
+        tc.tc_destroy(ctx)
+
+
 def test_bounded_wait_gives_up_and_device_stays_usable():
     """A look-back wait whose predecessor never publishes runs out (about a
     second) and reports TC_ERR_TIMEOUT; afterwards a batch still matches the
