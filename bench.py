@@ -507,7 +507,7 @@ def run_multi(args, rank, world, local_rank):
             parts_all.append(parts)
         return ws, offs, rounds, parts_all
 
-    def time_batched(cap, nrounds, graph=False, tuning=None):
+    def time_batched(cap, nrounds, graph=False, tuning=None, ready=False):
         ws, offs, rounds, _ = rounds_for(cap)
         M = tc.MultiStream(r, seeds, sids, w_max_round=int(offs[-1]), vertex_bits=B)
         if tuning:
@@ -523,6 +523,8 @@ def run_multi(args, rank, world, local_rank):
                 if graph:
                     buf.copy_(rounds[k], non_blocking=True)
                     M.replay(sh)
+                elif ready:
+                    M.process_ready_async(rounds[k], offs, sh)
                 else:
                     M.process_async(rounds[k], offs, sh)
             ev1.record(stream)
@@ -553,6 +555,7 @@ def run_multi(args, rank, world, local_rank):
     Mg, ms_graph, _, launches_graph = time_batched(cap, T, graph=True, tuning=tuning)
     clocks = sampler.stop()
     Mb, ms_batched, _, launches_b = time_batched(cap, T, graph=False, tuning=tuning)
+    Mp, ms_piped, _, _ = time_batched(cap, T, graph=False, tuning=tuning, ready=True)
 
     # back to back: one single-stream context per stream
     ctxs = [tc.tc_create_ex(int(r[s]), int(seeds[s]), int(sids[s]), max(1, ws[s]), B)
@@ -583,13 +586,15 @@ def run_multi(args, rank, world, local_rank):
         a = Mg.state(s)
         b = Mb.state(s)
         c = tc.tc_get_state(ctxs[s])
-        for x, y, z in zip(a, b, c):
-            if not (np.array_equal(x, y) and np.array_equal(x, z)):
+        d = Mp.state(s)
+        for x, y, z, t in zip(a, b, c, d):
+            if not (np.array_equal(x, y) and np.array_equal(x, z) and np.array_equal(x, t)):
                 identical = False
     for cx in ctxs:
         tc.tc_destroy(cx)
     Mg.close()
     Mb.close()
+    Mp.close()
     val = edges_total / (ms_graph / 1e3)
     line = {
         "metric": "aggregate edges/s, 512 streams advanced together (round = one CUDA graph)",
@@ -609,6 +614,10 @@ def run_multi(args, rank, world, local_rank):
         "updates_per_s": float(sum(int(r[s2]) * ws[s2] for s2 in range(S))) * T / (ms_graph / 1e3),
         "batched_plain": {"value": edges_total / (ms_batched / 1e3), "ms_per_round": ms_batched / T,
                           "launches_per_round": launches_b / T},
+        "batched_pipelined": {"value": edges_total / (ms_piped / 1e3),
+                              "ms_per_round": ms_piped / T,
+                              "how": "tc_multi_process_ready_async: each round's sorts beside "
+                                     "the previous round's sweep"},
         "back_to_back": {"value": edges_total / (ms_b2b / 1e3), "ms_per_round": ms_b2b / T,
                          "launches_per_round": sum(1 for w in ws if w) * (5 + -(-B // 8) + -(-2 * B // 8))},
         "speedup_vs_back_to_back": ms_b2b / ms_graph,

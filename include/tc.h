@@ -269,6 +269,14 @@ int tc_multi_create(uint32_t n_streams, const uint64_t *r, const uint64_t *seeds
 int tc_multi_process_async(tc_multi *M, const uint64_t *d_edges, const uint64_t *offsets,
                            void *cuda_stream);
 
+/* Pipelined form of tc_multi_process_async for batches already in place in
+ * d_edges when the call is made: the round's sort phase runs on the
+ * engine's own streams, into a second round scratch set (allocated by the
+ * first call), beside the previous round's sweep; the sweep and bookkeeping
+ * stay ordered on `cuda_stream`, so results are bit-identical. */
+int tc_multi_process_ready_async(tc_multi *M, const uint64_t *d_edges, const uint64_t *offsets,
+                                 void *cuda_stream);
+
 /* As tc_multi_process_async, with each stream's batch in its own DEVICE
  * buffer: d_batches (HOST array of S device pointers) and w (HOST array of
  * S batch lengths; w[s] = 0 sits stream s out and d_batches[s] may then be

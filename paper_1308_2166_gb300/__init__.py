@@ -39,6 +39,7 @@ EXPORTS = (
     "tc_server_close", "tc_server_poll", "tc_server_drain", "tc_server_stats",
     "tc_server_destroy", "tc_selftest_wait_timeout", "tc_save_size", "tc_save", "tc_load",
     "tc_process_batch_host_async", "tc_process_batch_ready_async",
+    "tc_multi_process_ready_async",
 )
 
 TC_REQ_OPEN, TC_REQ_BATCH, TC_REQ_QUERY, TC_REQ_CLOSE = 1, 2, 3, 4
@@ -152,6 +153,7 @@ def load(path: str | None = None):
         "tc_selftest_wait_timeout": (I, []),
         "tc_process_batch_host_async": (I, [P, P, U64, P]),
         "tc_process_batch_ready_async": (I, [P, P, U64, P]),
+        "tc_multi_process_ready_async": (I, [P, P, P, P]),
         "tc_save_size": (U64, [P]),
         "tc_save": (I, [P, P, U64]),
         "tc_load": (I, [P, U64, U64, ctypes.POINTER(P)]),
@@ -425,6 +427,17 @@ class MultiStream:
         ptr = _ptr(d_edges) if int(off[-1]) else None
         _check(load().tc_multi_process_async(self.h, ptr, off.ctypes.data, stream or None),
                "tc_multi_process_async")
+
+    def process_ready_async(self, d_edges, offsets, stream: int = 0):
+        """Pipelined round for batches already in place: sorted beside the
+        previous round's sweep (bit-identical results)."""
+        import numpy as np
+        off = np.ascontiguousarray(offsets, dtype=np.uint64)
+        if off.size != self.S + 1:
+            raise ValueError("offsets needs S+1 entries")
+        ptr = _ptr(d_edges) if int(off[-1]) else None
+        _check(load().tc_multi_process_ready_async(self.h, ptr, off.ctypes.data, stream or None),
+               "tc_multi_process_ready_async")
 
     def process_ptrs_async(self, d_batches, stream: int = 0):
         """One round with each stream's batch in its own device tensor

@@ -93,7 +93,7 @@ __device__ __forceinline__ u32 segment_of(const u64 *__restrict__ off, u32 K, u6
 constexpr int kMThreads = 256;
 
 __global__ void __launch_bounds__(kMThreads) mprep_kernel(const u64 *__restrict__ desc,
-                                                           RoundShape rs, MStream *ms,
+                                                           RoundShape rs, u32 *perr,
                                                            u64 *__restrict__ arcs0,
                                                            u64 *__restrict__ ekeys0,
                                                            u32 *__restrict__ evals0,
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(kMThreads) mprep_kernel(const u64 *__restrict_
         const u64 jl = j - e0;
         const u64 e = d.ebase[k][jl];
         const u64 u = e >> 32, v = e & kMask32;
-        if (!(u < v) || v >= id_lim) atomicOr(&ms[__ldg(d.slot + k)].err, kErrInput);
+        if (!(u < v) || v >= id_lim) atomicOr(&perr[k], kErrInput);
         const u64 sp = (u64)k << (rs.B + rs.sha);
         const u64 rpos = (ws - 1 - jl) << 1;
         const u64 au = sp | (u << rs.sha) | rpos;
@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kMThreads) mprep_kernel(const u64 *__restrict_
 // empty).
 __global__ void mdups_kernel(const u64 *ekeys0, const u64 *ekeys1, const u32 *evals0,
                              const u32 *evals1, const SortPlan *plans,
-                             const u64 *__restrict__ desc, RoundShape rs, MStream *ms) {
+                             const u64 *__restrict__ desc, RoundShape rs, u32 *perr) {
     const Desc d = desc_view(desc, rs.K);
     const bool sel = plan_final_sel(&plans[1]) != 0;
     const u64 *E = sel ? ekeys1 : ekeys0;
@@ -162,7 +162,7 @@ __global__ void mdups_kernel(const u64 *ekeys0, const u64 *ekeys1, const u32 *ev
             const u64 b = __ldg(E + j);
             if (mkey_prefix(rs, b) != pa) break;
             if (__ldg(D + (rs.eko ? (b & jmask) : __ldg(EV + j))) == ea) {
-                atomicOr(&ms[__ldg(d.slot + k)].err, kErrInput);
+                atomicOr(&perr[k], kErrInput);
                 break;
             }
         }
@@ -177,6 +177,7 @@ struct MSweepArgs {
     const SortPlan *plans;
     MStream *ms;
     const u32 *gerr;     // round-wide error (a timed-out sort)
+    const u32 *perr;     // each participant's error this round
     RoundShape rs;
 };
 
@@ -212,7 +213,7 @@ __global__ void __launch_bounds__(kMThreads, 5) msweep_kernel(MSweepArgs a) {
         k = segment_of(d.roff, rs.K, g);
         const u64 e0 = __ldg(d.eoff + k), ws = __ldg(d.eoff + k + 1) - e0;
         MStream &st = a.ms[__ldg(d.slot + k)];
-        if (ws > 0 && !ld_relaxed(&st.err)) {
+        if (ws > 0 && !ld_relaxed(a.perr + k)) {
             const u64 i = g - __ldg(d.roff + k);
             const u64 m = st.m;
             const DrawKey dk{st.key, (u32)st.batches, st.stream_id};
@@ -321,13 +322,14 @@ __device__ __forceinline__ void write_record(u64 *o, u32 status, const MStream &
 
 // Close the round for every participant.
 __global__ void mfinish_kernel(MStream *ms, const u64 *__restrict__ desc, u32 K, u32 *gerr,
+                               const u32 *perr,
                                u64 *out) {
     const u32 k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
     const Desc d = desc_view(desc, K);
     MStream &st = ms[d.slot[k]];
     const u64 ws = d.eoff[k + 1] - d.eoff[k];
-    const u32 e = st.err ? st.err : *gerr;
+    const u32 e = perr[k] ? perr[k] : *gerr;
     if (e) {
         if (!st.sticky) st.sticky = e;
     } else if (ws > 0) {
@@ -339,7 +341,6 @@ __global__ void mfinish_kernel(MStream *ms, const u64 *__restrict__ desc, u32 K,
         st.est[3] = st.m;
     }
     if (out) write_record(out + (u64)k * kRecordWords, e, st);
-    st.err = 0;
     st.acc[0] = st.acc[1] = st.acc[2] = 0;
 }
 
@@ -455,6 +456,9 @@ u64 zeroed_bytes_for(u32 sb, u64 w_max_round, u32 vertex_bits) {
     return 2 * sizeof(SortPlan) + lb * sizeof(u32) + 256;
 }
 
+// Participant error words at the end of the zeroed block, one per slot at most.
+u64 perr_bytes(u32 S) { return ((u64)S * 4 + 255) & ~255ull; }
+
 // Per-stream state block bytes (f1, f2, chi, flags), padded to 256 bytes.
 u64 state_bytes(u64 r) { return (28 * r + 255) & ~255ull; }
 
@@ -462,22 +466,30 @@ u64 state_bytes(u64 r) { return (28 * r + 255) & ~255ull; }
 
 namespace tc {
 
-u64 multi_scratch_bytes(u32 S, u64 w_max_round, u32 vertex_bits) {
+u64 multi_scratch_bytes(u32 S, u64 w_max_round, u32 vertex_bits, int sets) {
     const u32 sb = mbits_for(S - 1);
-    return (u64)S * sizeof(MStream) + 2 * (2 * w_max_round * 8 + w_max_round * 8 + w_max_round * 4) +
-           zeroed_bytes_for(sb, w_max_round, vertex_bits) + kRing * desc_words(S) * 8;
+    const u64 per_set = 2 * (2 * w_max_round * 8 + w_max_round * 8 + w_max_round * 4) +
+                        zeroed_bytes_for(sb, w_max_round, vertex_bits) + perr_bytes(S);
+    return (u64)S * sizeof(MStream) + (u64)sets * per_set + kRing * desc_words(S) * 8;
 }
 
 void multi_free(tc_multi *M) {
     cudaDeviceSynchronize();
     cudaFree(M->state);
     cudaFree(M->ms);
-    for (int k = 0; k < 2; ++k) {
-        cudaFree(M->arcs[k]);
-        cudaFree(M->ekeys[k]);
-        cudaFree(M->evals[k]);
+    for (tc_multi::RoundSet &z : M->rset) {
+        for (int k = 0; k < 2; ++k) {
+            cudaFree(z.arcs[k]);
+            cudaFree(z.ekeys[k]);
+            cudaFree(z.evals[k]);
+        }
+        cudaFree(z.zeroed);
     }
-    cudaFree(M->zeroed);
+    if (M->sa) cudaStreamDestroy(M->sa);
+    for (int k = 0; k < 2; ++k) {
+        if (M->ev_sorted[k]) cudaEventDestroy(M->ev_sorted[k]);
+        if (M->ev_swept[k]) cudaEventDestroy(M->ev_swept[k]);
+    }
     for (int k = 0; k < kRing; ++k) {
         cudaFree(M->desc[k]);
         if (M->h_desc[k]) cudaFreeHost(M->h_desc[k]);
@@ -492,7 +504,7 @@ void multi_free(tc_multi *M) {
     delete M;
 }
 
-int multi_alloc(u32 S, u64 w_max_round, u32 vertex_bits, tc_multi **out) {
+int multi_alloc(u32 S, u64 w_max_round, u32 vertex_bits, tc_multi **out, int sets) {
     *out = nullptr;
     if (S == 0 || w_max_round == 0 || w_max_round > (1ull << 28) || vertex_bits < 1 ||
         vertex_bits > 32)
@@ -510,14 +522,24 @@ int multi_alloc(u32 S, u64 w_max_round, u32 vertex_bits, tc_multi **out) {
     M->w_max = w_max_round;
     M->rank = kRankBallot;
     M->h_rec.assign(S, MStream{});
-    M->zeroed_bytes = zeroed_bytes_for(sb, w_max_round, vertex_bits);
+    M->zeroed_bytes = zeroed_bytes_for(sb, w_max_round, vertex_bits) + perr_bytes(S);
+    M->nsets = sets == 2 ? 2 : 1;
     bool ok = cudaMalloc(&M->ms, S * sizeof(MStream)) == cudaSuccess;
-    for (int k = 0; k < 2 && ok; ++k) {
-        ok &= cudaMalloc(&M->arcs[k], 2 * w_max_round * sizeof(u64)) == cudaSuccess;
-        ok &= ok && cudaMalloc(&M->ekeys[k], w_max_round * sizeof(u64)) == cudaSuccess;
-        ok &= ok && cudaMalloc(&M->evals[k], w_max_round * sizeof(u32)) == cudaSuccess;
+    for (int z = 0; z < M->nsets && ok; ++z) {
+        tc_multi::RoundSet &rs = M->rset[z];
+        for (int k = 0; k < 2 && ok; ++k) {
+            ok &= cudaMalloc(&rs.arcs[k], 2 * w_max_round * sizeof(u64)) == cudaSuccess;
+            ok &= ok && cudaMalloc(&rs.ekeys[k], w_max_round * sizeof(u64)) == cudaSuccess;
+            ok &= ok && cudaMalloc(&rs.evals[k], w_max_round * sizeof(u32)) == cudaSuccess;
+        }
+        ok &= ok && cudaMalloc(&rs.zeroed, M->zeroed_bytes) == cudaSuccess;
+        ok &= ok && cudaMemset(rs.zeroed, 0, M->zeroed_bytes) == cudaSuccess;
     }
-    ok &= ok && cudaMalloc(&M->zeroed, M->zeroed_bytes) == cudaSuccess;
+    ok &= ok && cudaStreamCreateWithFlags(&M->sa, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k < 2 && ok; ++k) {
+        ok &= cudaEventCreateWithFlags(&M->ev_sorted[k], cudaEventDisableTiming) == cudaSuccess;
+        ok &= ok && cudaEventCreateWithFlags(&M->ev_swept[k], cudaEventDisableTiming) == cudaSuccess;
+    }
     for (int k = 0; k < kRing && ok; ++k) {
         ok &= cudaMalloc(&M->desc[k], desc_words(S) * sizeof(u64)) == cudaSuccess;
         ok &= ok && cudaHostAlloc(&M->h_desc[k], desc_words(S) * sizeof(u64),
@@ -530,7 +552,6 @@ int multi_alloc(u32 S, u64 w_max_round, u32 vertex_bits, tc_multi **out) {
     ok &= ok && cudaEventCreateWithFlags(&M->ev_join, cudaEventDisableTiming) == cudaSuccess;
     if (ok) {
         ok &= cudaMemset(M->ms, 0, S * sizeof(MStream)) == cudaSuccess;
-        ok &= cudaMemset(M->zeroed, 0, M->zeroed_bytes) == cudaSuccess;
         ok &= cudaDeviceSynchronize() == cudaSuccess;
     }
     if (!ok) {
@@ -585,8 +606,8 @@ int multi_gather(tc_multi *M, const u32 *d_slots, u32 Q, u64 *out, cudaStream_t 
     return TC_OK;
 }
 
-int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, const u64 *desc, u64 *out,
-                  cudaStream_t st) {
+int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u64 *h_desc,
+                  u64 *out, cudaStream_t st, bool pipelined, cudaEvent_t wait_ev) {
     const NvtxRange range("tc round");
     u64 Wt = 0, wmax = 0, R = 0;
     for (u32 k = 0; k < K; ++k) {
@@ -595,6 +616,7 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, const u64 *desc, u
         R += M->h_rec[items[k].slot].r;
     }
     if (K == 0 || Wt == 0 || Wt > M->w_max) return TC_ERR_INVAL;
+    if (pipelined && M->nsets != 2) return TC_ERR_INVAL;
     RoundShape rs{};
     rs.K = K;
     rs.kb = mbits_for(K - 1);
@@ -606,57 +628,75 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, const u64 *desc, u
     rs.bits_e = mpick(32 + rs.kb, M->force_e, rs.npe);
     rs.eko = rs.kb + 32 + rs.bw <= 64 ? 1u : 0u;
     rs.she = rs.eko ? rs.bw : 0u;
-    SortPlan *plans = reinterpret_cast<SortPlan *>(M->zeroed);
-    u32 *lb = reinterpret_cast<u32 *>(M->zeroed + 2 * sizeof(SortPlan));
+    const int b = M->nsets == 2 ? (int)(M->rseq & 1) : 0;
+    M->rseq++;
+    tc_multi::RoundSet &z = M->rset[b];
+    SortPlan *plans = reinterpret_cast<SortPlan *>(z.zeroed);
+    u32 *lb = reinterpret_cast<u32 *>(z.zeroed + 2 * sizeof(SortPlan));
     const u64 la = mlookback(2 * Wt, rs.bits_a), le = mlookback(Wt, rs.bits_e);
     const u64 lwords = (u64)rs.npa * la + (u64)rs.npe * le;
-    u32 *gerr = reinterpret_cast<u32 *>(M->zeroed + M->zeroed_bytes - 256);
-    TCM_CUDA(cudaMemsetAsync(M->zeroed, 0, 2 * sizeof(SortPlan) + lwords * sizeof(u32), st));
-    TCM_CUDA(cudaMemsetAsync(gerr, 0, sizeof(u32), st));
+    u32 *perr = reinterpret_cast<u32 *>(z.zeroed + M->zeroed_bytes - perr_bytes(M->S));
+    u32 *gerr = reinterpret_cast<u32 *>(reinterpret_cast<unsigned char *>(perr) - 256);
+    // the sort phase's stream: the caller's, or the engine's own when pipelined
+    cudaStream_t ms = pipelined ? M->sa : st;
+    // with two sets, the set's previous round may have been swept on another
+    // stream (one set: every round runs in the order of its stream)
+    if (M->nsets == 2) TCM_CUDA(cudaStreamWaitEvent(ms, M->ev_swept[b], 0));
+    if (wait_ev) TCM_CUDA(cudaStreamWaitEvent(ms, wait_ev, 0));
+    if (h_desc)
+        TCM_CUDA(cudaMemcpyAsync(desc, h_desc, desc_words(K) * sizeof(u64),
+                                 cudaMemcpyHostToDevice, ms));
+    TCM_CUDA(cudaMemsetAsync(z.zeroed, 0, 2 * sizeof(SortPlan) + lwords * sizeof(u32), ms));
+    TCM_CUDA(cudaMemsetAsync(gerr, 0, 256 + (u64)K * 4, ms));
 
     const size_t hsm = (((size_t)rs.npa << rs.bits_a) + ((size_t)rs.npe << rs.bits_e)) * 4;
     const u64 pb = std::min<u64>((Wt + kMThreads * 8 - 1) / (kMThreads * 8), 1216);
-    mprep_kernel<<<(unsigned)pb, kMThreads, hsm, st>>>(desc, rs, M->ms, M->arcs[0], M->ekeys[0],
-                                                       M->evals[0], plans);
-    sort_plan_kernel<<<dim3((unsigned)std::max(rs.npa, rs.npe), 2), 256, 0, st>>>(
+    mprep_kernel<<<(unsigned)pb, kMThreads, hsm, ms>>>(desc, rs, perr, z.arcs[0], z.ekeys[0],
+                                                       z.evals[0], plans);
+    sort_plan_kernel<<<dim3((unsigned)std::max(rs.npa, rs.npe), 2), 256, 0, ms>>>(
         plans, rs.npa, (u32)(2 * Wt), rs.bits_a, rs.npe, (u32)Wt, rs.bits_e);
     const PassK ka = mselect(rs.bits_a, false, M->rank);
     const PassK ke = mselect(rs.bits_e, !rs.eko, M->rank);
     const u64 ta = mtiles(2 * Wt), te = mtiles(Wt);
     // the two sorts are independent: the edge sort forks onto the side stream
-    TCM_CUDA(cudaEventRecord(M->ev_fork, st));
+    TCM_CUDA(cudaEventRecord(M->ev_fork, ms));
     TCM_CUDA(cudaStreamWaitEvent(M->side, M->ev_fork, 0));
     u32 *lbe = lb + (u64)rs.npa * la;
     for (int p = 0; p < rs.npe; ++p)
         ke.fn<<<(unsigned)te, ke.threads, ke.smem, M->side>>>(
-            M->ekeys[0], M->ekeys[1], rs.eko ? nullptr : M->evals[0],
-            rs.eko ? nullptr : M->evals[1], (u32)Wt, rs.she + p * rs.bits_e,
-            mlive(32 + rs.kb, rs.bits_e, p), p, &plans[1], lbe + (u64)p * le, gerr,
-            nullptr);
+            z.ekeys[0], z.ekeys[1], rs.eko ? nullptr : z.evals[0], rs.eko ? nullptr : z.evals[1],
+            (u32)Wt, rs.she + p * rs.bits_e, mlive(32 + rs.kb, rs.bits_e, p), p, &plans[1],
+            lbe + (u64)p * le, gerr, nullptr);
     const u64 db = std::min<u64>((Wt + 255) / 256, 1216);
-    mdups_kernel<<<(unsigned)db, 256, 0, M->side>>>(M->ekeys[0], M->ekeys[1], M->evals[0],
-                                                    M->evals[1], plans, desc, rs, M->ms);
+    mdups_kernel<<<(unsigned)db, 256, 0, M->side>>>(z.ekeys[0], z.ekeys[1], z.evals[0],
+                                                    z.evals[1], plans, desc, rs, perr);
     TCM_CUDA(cudaEventRecord(M->ev_join, M->side));
     for (int p = 0; p < rs.npa; ++p)
-        ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(
-            M->arcs[0], M->arcs[1], nullptr, nullptr, (u32)(2 * Wt), rs.sha + p * rs.bits_a,
+        ka.fn<<<(unsigned)ta, ka.threads, ka.smem, ms>>>(
+            z.arcs[0], z.arcs[1], nullptr, nullptr, (u32)(2 * Wt), rs.sha + p * rs.bits_a,
             mlive(M->B + rs.kb, rs.bits_a, p), p, &plans[0], lb + (u64)p * la, gerr, nullptr);
-    TCM_CUDA(cudaStreamWaitEvent(st, M->ev_join, 0));
+    TCM_CUDA(cudaStreamWaitEvent(ms, M->ev_join, 0));
+    if (pipelined) {
+        TCM_CUDA(cudaEventRecord(M->ev_sorted[b], ms));
+        TCM_CUDA(cudaStreamWaitEvent(st, M->ev_sorted[b], 0));
+    }
     MSweepArgs a{};
     a.desc = desc;
     a.R = R;
-    a.arcs0 = M->arcs[0];
-    a.arcs1 = M->arcs[1];
-    a.ekeys0 = M->ekeys[0];
-    a.ekeys1 = M->ekeys[1];
-    a.evals0 = M->evals[0];
-    a.evals1 = M->evals[1];
+    a.arcs0 = z.arcs[0];
+    a.arcs1 = z.arcs[1];
+    a.ekeys0 = z.ekeys[0];
+    a.ekeys1 = z.ekeys[1];
+    a.evals0 = z.evals[0];
+    a.evals1 = z.evals[1];
     a.plans = plans;
     a.ms = M->ms;
     a.gerr = gerr;
+    a.perr = perr;
     a.rs = rs;
     msweep_kernel<<<(unsigned)((R + kMThreads - 1) / kMThreads), kMThreads, 0, st>>>(a);
-    mfinish_kernel<<<(K + 255) / 256, 256, 0, st>>>(M->ms, desc, K, gerr, out);
+    mfinish_kernel<<<(K + 255) / 256, 256, 0, st>>>(M->ms, desc, K, gerr, perr, out);
+    if (M->nsets == 2) TCM_CUDA(cudaEventRecord(M->ev_swept[b], st));  // the set is free again
     TCM_CUDA(cudaGetLastError());
     M->launches += 5 + (u64)rs.npa + (u64)rs.npe;
     return TC_OK;
@@ -691,7 +731,7 @@ static int upload_and_enqueue(tc_multi *M, const std::vector<RoundItem> &items,
     TCM_CUDA(cudaMemcpyAsync(M->desc[slot], M->h_desc[slot], desc_words(K) * sizeof(u64),
                              cudaMemcpyHostToDevice, st));
     TCM_CUDA(cudaEventRecord(M->ring_ev[slot], st));
-    return multi_enqueue(M, items.data(), K, M->desc[slot], nullptr, st);
+    return multi_enqueue(M, items.data(), K, M->desc[slot], nullptr, nullptr, st);
 }
 
 extern "C" {
@@ -753,6 +793,54 @@ int tc_multi_process_async(tc_multi *M, const uint64_t *d_edges, const uint64_t 
     return upload_and_enqueue(M, items, (cudaStream_t)cuda_stream);
 }
 
+// The second round scratch set, for pipelined rounds.
+static int ensure_two_round_sets(tc_multi *M) {
+    if (M->nsets == 2) return TC_OK;
+    tc_multi::RoundSet &z = M->rset[1];
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k) {
+        ok &= cudaMalloc(&z.arcs[k], 2 * M->w_max * sizeof(u64)) == cudaSuccess;
+        ok &= ok && cudaMalloc(&z.ekeys[k], M->w_max * sizeof(u64)) == cudaSuccess;
+        ok &= ok && cudaMalloc(&z.evals[k], M->w_max * sizeof(u32)) == cudaSuccess;
+    }
+    ok &= ok && cudaMalloc(&z.zeroed, M->zeroed_bytes) == cudaSuccess;
+    ok &= ok && cudaMemset(z.zeroed, 0, M->zeroed_bytes) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        for (int k = 0; k < 2; ++k) {
+            cudaFree(z.arcs[k]);
+            cudaFree(z.ekeys[k]);
+            cudaFree(z.evals[k]);
+            z.arcs[k] = z.ekeys[k] = nullptr;
+            z.evals[k] = nullptr;
+        }
+        cudaFree(z.zeroed);
+        z.zeroed = nullptr;
+        return TC_ERR_NOMEM;
+    }
+    M->nsets = 2;
+    return TC_OK;
+}
+
+int tc_multi_process_ready_async(tc_multi *M, const uint64_t *d_edges, const uint64_t *offsets,
+                                 void *cuda_stream) {
+    if (!M) return TC_ERR_INVAL;
+    std::vector<RoundItem> items;
+    int rc = items_from_offsets(M, d_edges, offsets, items);
+    if (rc || items.empty()) return rc;
+    rc = ensure_two_round_sets(M);
+    if (rc) return rc;
+    const int slot = M->ring;
+    M->ring = (M->ring + 1) % kRing;
+    TCM_CUDA(cudaEventSynchronize(M->ring_ev[slot]));
+    write_descriptor(M, items.data(), (u32)items.size(), M->h_desc[slot]);
+    rc = multi_enqueue(M, items.data(), (u32)items.size(), M->desc[slot], M->h_desc[slot],
+                       nullptr, (cudaStream_t)cuda_stream, true, nullptr);
+    if (rc) return rc;
+    TCM_CUDA(cudaEventRecord(M->ring_ev[slot], M->sa));  // after the descriptor's upload
+    return TC_OK;
+}
+
 int tc_multi_process_ptrs_async(tc_multi *M, const uint64_t *const *d_batches,
                                 const uint64_t *w, void *cuda_stream) {
     if (!M || !d_batches || !w) return TC_ERR_INVAL;
@@ -787,7 +875,7 @@ int tc_multi_capture(tc_multi *M, const uint64_t *d_edges, const uint64_t *offse
     TCM_CUDA(cudaMemcpy(M->g_desc, h.data(), h.size() * sizeof(u64), cudaMemcpyHostToDevice));
     TCM_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const u64 before = M->launches;
-    rc = multi_enqueue(M, items.data(), (u32)items.size(), M->g_desc, nullptr, st);
+    rc = multi_enqueue(M, items.data(), (u32)items.size(), M->g_desc, nullptr, nullptr, st);
     cudaGraph_t graph = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(st, &graph);
     if (rc || ec != cudaSuccess) {

@@ -24,7 +24,7 @@ struct MStream {
     u64 batches;
     uint2 key;           // Philox key (seed lo, seed hi)
     u32 stream_id;
-    u32 err;             // error of the round in flight
+    u32 pad0;            // (a round's errors live in its scratch, one word per participant)
     u32 sticky;          // first error since the host last looked
     u32 pad;
     u64 est[4];          // committed estimate: S lo, S hi, closed, m
@@ -57,12 +57,20 @@ struct tc_multi {
     tc::u64 *state = nullptr;            // state block of tc_multi_create's streams
     std::vector<tc::MStream> h_rec;      // host copy of each slot's static fields
     tc::MStream *ms = nullptr;           // device records, S
-    // round scratch
-    tc::u64 *arcs[2] = {nullptr, nullptr};
-    tc::u64 *ekeys[2] = {nullptr, nullptr};
-    tc::u32 *evals[2] = {nullptr, nullptr};
-    unsigned char *zeroed = nullptr;     // SortPlan[2], look-back, global error
+    // round scratch: one set, or two when rounds are pipelined (round k+1
+    // sorts into the set that round k's sweep is not reading)
+    struct RoundSet {
+        tc::u64 *arcs[2] = {nullptr, nullptr};
+        tc::u64 *ekeys[2] = {nullptr, nullptr};
+        tc::u32 *evals[2] = {nullptr, nullptr};
+        unsigned char *zeroed = nullptr;  // SortPlan[2], look-back, round error, participant errors
+    };
+    RoundSet rset[2];
+    int nsets = 1;
+    tc::u32 rseq = 0;                    // rounds enqueued: set parity
     tc::u64 zeroed_bytes = 0;
+    cudaStream_t sa = nullptr;           // a pipelined round's sort phase (with `side`)
+    cudaEvent_t ev_sorted[2] = {}, ev_swept[2] = {};
     tc::u64 *desc[tc::kRing] = {};       // device round descriptors
     tc::u64 *h_desc[tc::kRing] = {};     // pinned staging
     cudaEvent_t ring_ev[tc::kRing] = {};
@@ -81,13 +89,14 @@ namespace tc {
 // Words of a round descriptor for K participants.
 inline u64 desc_words(u32 K) { return 4 * (u64)K + 2; }
 
-// Allocate an engine with S slots and round scratch for w_max_round edges;
-// slots start unused (r = 0).  Returns a TC_* code.
-int multi_alloc(u32 S, u64 w_max_round, u32 vertex_bits, tc_multi **out);
+// Allocate an engine with S slots and `sets` (1 or 2; 2 allows pipelined
+// rounds) of round scratch for w_max_round edges; slots start unused
+// (r = 0).  Returns a TC_* code.
+int multi_alloc(u32 S, u64 w_max_round, u32 vertex_bits, tc_multi **out, int sets = 1);
 void multi_free(tc_multi *M);
 
 // Bytes of device memory multi_alloc holds for these sizes.
-u64 multi_scratch_bytes(u32 S, u64 w_max_round, u32 vertex_bits);
+u64 multi_scratch_bytes(u32 S, u64 w_max_round, u32 vertex_bits, int sets = 1);
 
 // Open slot `slot` with r estimators whose state lives at `state` (device,
 // 28 r bytes, 8-byte aligned: f1, f2, chi as u64[r], then flags as u32[r]),
@@ -97,12 +106,17 @@ u64 multi_scratch_bytes(u32 S, u64 w_max_round, u32 vertex_bits);
 int multi_open_slot(tc_multi *M, u32 slot, u64 r, u64 seed, u32 stream_id, void *state,
                     cudaStream_t st);
 
-// Enqueue one round on st.  desc: a device descriptor of desc_words(K)
-// words written by write_descriptor (host copy in h_desc); out: optional
-// device array of K * kRecordWords words receiving each participant's
-// record after the round.
-int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, const u64 *desc, u64 *out,
-                  cudaStream_t st);
+// Enqueue one round whose sweep and bookkeeping land on st.  desc: the
+// device descriptor of desc_words(K) words; h_desc: if not null, its pinned
+// host copy (written by write_descriptor), uploaded by the round itself
+// ahead of the key build; out: optional device array of K * kRecordWords
+// words receiving each participant's record after the round.  Pipelined
+// (two sets): the sort phase runs on the engine's own streams once wait_ev
+// (if any; e.g. the batches' copies) has fired and the round's set is free,
+// beside the previous round's sweep.
+int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u64 *h_desc,
+                  u64 *out, cudaStream_t st, bool pipelined = false,
+                  cudaEvent_t wait_ev = nullptr);
 
 // Fill a host descriptor for the given participants; returns the largest w.
 u64 write_descriptor(const tc_multi *M, const RoundItem *items, u32 K, u64 *h_desc);

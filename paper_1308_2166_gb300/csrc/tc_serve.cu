@@ -355,12 +355,13 @@ bool tc_server::form_round() {
         ok &= ok && multi_gather(M, d_qs[b], Q, d_out[b], cs) == TC_OK;
     }
     if (K && ok) {
-        if (wait_ev >= 0) ok &= cudaStreamWaitEvent(cs, ev_pool[wait_ev], 0) == cudaSuccess;
+        // pipelined: the round is sorted on the engine's own streams as soon as
+        // its batches' copies have landed, beside the previous round's sweep;
+        // its sweep and records are ordered on cs
         write_descriptor(M, items.data(), K, h_desc[b]);
-        ok &= ok && cudaMemcpyAsync(d_desc[b], h_desc[b], desc_words(K) * sizeof(u64),
-                                    cudaMemcpyHostToDevice, cs) == cudaSuccess;
-        ok &= ok && multi_enqueue(M, items.data(), K, d_desc[b],
-                                  d_out[b] + (u64)Q * kRecordWords, cs) == TC_OK;
+        ok &= multi_enqueue(M, items.data(), K, d_desc[b], h_desc[b],
+                            d_out[b] + (u64)Q * kRecordWords, cs, true,
+                            wait_ev >= 0 ? ev_pool[wait_ev] : nullptr) == TC_OK;
         for (Req &q : R.batches) {
             ok &= ok && cudaFreeAsync(q.d_edges, cs) == cudaSuccess;
             q.d_edges = nullptr;
@@ -552,7 +553,7 @@ int tc_server_create(const tc_server_config_t *cfg, tc_server **out) {
     const int depth = cfg->depth ? (int)cfg->depth : 2;
     const int nbuf = depth + 1;
     const u64 ring_bytes = (u64)nbuf * (2ull * S * kRecordWords * 8 + desc_words(S) * 8 + S * 4);
-    const u64 fixed = multi_scratch_bytes(S, cfg->w_max_round, cfg->vertex_bits) + ring_bytes;
+    const u64 fixed = multi_scratch_bytes(S, cfg->w_max_round, cfg->vertex_bits, 2) + ring_bytes;
     if (fixed >= cfg->budget_bytes) return TC_ERR_RANGE;
 
     tc_server *Sv = new (std::nothrow) tc_server();
@@ -568,7 +569,7 @@ int tc_server_create(const tc_server_config_t *cfg, tc_server **out) {
     Sv->t0 = std::chrono::steady_clock::now();
     int rc = TC_OK;
     if (cudaGetDevice(&Sv->dev) != cudaSuccess) rc = TC_ERR_CUDA;
-    if (!rc) rc = multi_alloc(S, cfg->w_max_round, cfg->vertex_bits, &Sv->M);
+    if (!rc) rc = multi_alloc(S, cfg->w_max_round, cfg->vertex_bits, &Sv->M, 2);
     bool ok = rc == TC_OK;
     ok &= ok && cudaStreamCreateWithFlags(&Sv->cs, cudaStreamNonBlocking) == cudaSuccess;
     ok &= ok && cudaStreamCreateWithFlags(&Sv->xs, cudaStreamNonBlocking) == cudaSuccess;

@@ -65,8 +65,13 @@ def test_rounds_match_oracle_and_single_stream(S, vertex_bits):
             cat, offs, parts = _round(streams, cur, sizes)
             if offs[-1] == 0:
                 continue
-            if rnd % 2:
+            if rnd % 3 == 1:
                 M.process_ptrs_async([to_device(b) if b.size else None for b in parts])
+            elif rnd % 3 == 2:
+                dcat = to_device(cat)
+                import torch
+                torch.cuda.synchronize()          # in place before the pipelined call
+                M.process_ready_async(dcat, offs)
             else:
                 M.process_async(to_device(cat), offs)
             for s in range(S):
