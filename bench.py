@@ -377,6 +377,30 @@ def run_gpu(args, rank, world, local_rank):
     e2e_s, e2e_all = reduce_over_ranks(dist, time.perf_counter() - t0, e2e_edges, "cuda")
     e2e_value = e2e_all / e2e_s
 
+    # ---- stage split: pipelined, a batch's sort phase overlaps the previous
+    # batch's sweep, so per-stage times do not partition the step; a short
+    # stream-ordered pass after the timed run gives the split
+    if args.pipeline == "on":
+        tc.tc_sync(ctx)
+        torch.cuda.synchronize()
+        stage_steps = min(args.steps, 20)
+        tc.tc_profile_begin(ctx)
+        with torch.cuda.stream(stream):
+            for j in range(stage_steps):
+                tc.tc_process_batch_async(ctx, dev_batches[k % nb], stream=sh)
+                tc.tc_estimate_async(ctx, est_words, stream=sh)
+                k += 1
+        stream.synchronize()
+        sprof = tc.tc_profile_end(ctx)
+        stage_how = (f"stream-ordered pass of {stage_steps} steps (tc_process_batch_async) "
+                     "after the timed run; the two sorts run side by side on two streams: "
+                     "ms_arc_sort = the arc passes with the Step-3 passes beside them, "
+                     "ms_dups = the arc directory, ms_edge_sort = what is left of the Step-3 "
+                     "branch (its directory and repeat check)")
+    else:
+        sprof, stage_steps = prof, args.steps
+        stage_how = "the timed run itself"
+
     if rank != 0:
         tc.tc_destroy(ctx)
         if dist:
@@ -387,8 +411,9 @@ def run_gpu(args, rank, world, local_rank):
     ms_sort = prof["ms_sort_wall"]   # both sorts' passes, run side by side
     # stream-ordered: the stages partition the step; pipelined: the sort
     # phase runs on the library's own streams (ms_sort_wall), the rest on sh
-    stages = {k2: prof[k2] for k2 in ("ms_prep", "ms_arc_sort", "ms_edge_sort", "ms_dups",
-                                        "ms_sweep", "ms_finish", "ms_estimate", "ms_sort_wall")}
+    stages = {k2: sprof[k2] / stage_steps for k2 in ("ms_prep", "ms_arc_sort", "ms_edge_sort",
+                                                    "ms_dups", "ms_sweep", "ms_finish",
+                                                    "ms_estimate", "ms_sort_wall")}
     sort_gbs = prof["sort_pass_bytes"] / (ms_sort / 1e3) / 1e9 if ms_sort > 0 else 0.0
     launched = max(1, prof["sort_pass_launches"] - prof["sort_pass_skipped"])
     roofline = {
@@ -407,13 +432,15 @@ def run_gpu(args, rank, world, local_rank):
     if tr and tr.get("src_hash") == _src_hash():
         roofline["traffic"] = tr["bytes_per_algorithmic_byte"] * roofline["bytes_per_launch"]
     # algorithmic bytes of the whole step: this design's minimal passes (arcs
-    # on the src bits, Step-3 keys on a 32-bit edge hash with the position
+    # on the src bits, Step-3 keys on the top bits of a 32-bit edge hash --
+    # whole 8-bit digits covering the bw - 2 bucket bits -- with the position
     # packed below it) and the survey's formula (arcs on src + position,
     # Step-3 keys on (u, v), a u32 position value once 2B + bw > 64)
     bw = max(1, (w - 1).bit_length())
     B = cfg["vertex_bits"]
     pa = -(-B // 8)
-    own_bytes = 32 * w + pa * 2 * w * 16 + 4 * w * 16 + 8 * w + 2 * 28 * r
+    pe = -(-(bw - 2 if bw > 3 else 1) // 8)
+    own_bytes = 32 * w + pa * 2 * w * 16 + pe * w * 16 + 8 * w + 2 * 28 * r
     pe_s = -(-2 * B // 8)
     e_bytes_s = 16 if 2 * B + bw <= 64 else 24
     survey_bytes = 8 * w + (2 * w * 8 + (-(-(B + bw) // 8)) * 2 * w * 16) + \
@@ -437,7 +464,7 @@ def run_gpu(args, rank, world, local_rank):
         "updates_per_s": value * r,
         "p50_ms": statistics.median(per_step),
         "p99_ms": float(np.percentile(per_step, 99)),
-        "stage_ms_per_step": {k2: v / args.steps for k2, v in stages.items()},
+        "stage_ms_per_step": dict(stages, how=stage_how),
         "step_hbm_frac": {
             "own_min_bytes_per_step": own_bytes,
             "frac_own": own_bytes / step_s / 1e9 / peak,
@@ -703,6 +730,7 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
     t0 = time.perf_counter()
     t_end = t0 + seconds
     st0 = srv.stats()
+    lags = []                         # Poisson: how late each submit left the client (s)
     if rate:
         nxt = t0
         while True:
@@ -710,6 +738,7 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
             if now >= t_end:
                 break
             while nxt <= now:
+                lags.append(time.perf_counter() - nxt)
                 cl.one()
                 nxt += rng.exponential(1.0 / rate)
             cl.poll(wait_us=int(max(0, min(nxt - time.perf_counter(), 5e-4)) * 1e6))
@@ -736,8 +765,17 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
     span = (int(phase["t_done_ns"].max()) - first) / 1e9 if phase.size else 1.0
     lat_b = (batches["t_done_ns"] - batches["t_submit_ns"]) / 1e6
     lat_q = (queries["t_done_ns"] - queries["t_submit_ns"]) / 1e6
+    wait_b = (batches["t_admit_ns"] - batches["t_submit_ns"]) / 1e6
+    serv_b = (batches["t_done_ns"] - batches["t_admit_ns"]) / 1e6
     pct = (lambda a, q: float(np.percentile(a, q)) if a.size else None)
-    return {
+    lags = np.asarray(lags) * 1e3
+    extra = {}
+    if rate:
+        extra = {"client_lag_ms": {"p50": pct(lags, 50), "p99": pct(lags, 99),
+                                   "max": float(lags.max()) if lags.size else None},
+                 "batch_wait_ms": {"p50": pct(wait_b, 50), "p99": pct(wait_b, 99)},
+                 "batch_service_ms": {"p50": pct(serv_b, 50), "p99": pct(serv_b, 99)}}
+    return {**extra,
         "edges_per_s": float(ws.sum()) / span,
         "updates_per_s": float((ws * rs).sum()) / span,
         "seconds": span, "batches": int(batches.size), "queries": int(queries.size),

@@ -124,7 +124,11 @@ BatchShape make_shape(u64 w, u32 B, u32 force_a = 0, u32 force_e = 0) {
     s.sha = s.bw + 1;
     s.hb = hash_bucket_bits(w);
     s.bits_a = pick_digits(B, force_a, s.npa);
-    s.bits_e = pick_digits(32, force_e, s.npe);  // the 32-bit edge hash
+    // the Step-3 keys sort on whole digits covering the bucket bits, at
+    // most the 32 hash bits
+    s.bits_e = pick_digits(s.hb, force_e, s.npe);
+    s.hs = std::min(32u, (u32)s.npe * s.bits_e);
+    s.she = s.bw + 32 - s.hs;
     return s;
 }
 
@@ -376,8 +380,8 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
     u32 *lbe = lb + (u64)s.npa * la;
     for (int p = 0; p < s.npe; ++p)
         ke.fn<<<(unsigned)te, ke.threads, ke.smem, c->side>>>(
-            z.ekeys[0], z.ekeys[1], nullptr, nullptr, (u32)w, s.bw + p * s.bits_e,
-            live_bits(32, s.bits_e, p), p, &plans[1], lbe + (u64)p * le, berr, c->ctl);
+            z.ekeys[0], z.ekeys[1], nullptr, nullptr, (u32)w, s.she + p * s.bits_e,
+            live_bits(s.hs, s.bits_e, p), p, &plans[1], lbe + (u64)p * le, berr, c->ctl);
     const cudaEvent_t edge_end = mark(c, c->side);
     const u64 idx_blocks = std::min<u64>((w + 255) / 256, 152 * 16);
     index_kernel<false><<<(unsigned)idx_blocks, 256, 0, c->side>>>(

@@ -12,15 +12,17 @@
 //                   decreasing pos order and sorted stably on the src bits
 //                   only, which yields Lemma 4.3's order (src asc, pos desc)
 //                   and makes the arc's rank its offset in the src segment.
-//     ekeys[2][w]   uint64 Step-3 keys  h(u, v) << bw | pos, sorted on the
-//                   32-bit mix h of the packed edge (edge_hash): equal edges
-//                   are adjacent and every edge is found by its hash bucket.
+//     ekeys[2][w]   uint64 Step-3 keys  h(u, v) << bw | pos, h the 32-bit mix
+//                   of the packed edge (edge_hash), sorted on the top hs bits
+//                   of h only (hs >= hb: whole digits covering the bucket
+//                   bits): every edge lies in its hash bucket, in the run of
+//                   keys sharing its top hs bits, and so does a repeat.
 //     adir          per-vertex directory over the sorted arcs (vertex ids
 //                   < 2^kDirMaxBits), epoch-tagged;
 //     edir          directory of the 2^hb hash buckets (top hb bits of h)
 //                   over the sorted Step-3 keys, epoch-tagged.
 //   bw = bits of w-1, B = vertex id bits, hb = bucket bits (about w/4
-//   buckets).
+//   buckets), she = bw + 32 - hs the first sorted bit of a Step-3 key.
 #pragma once
 
 #include "tc_common.cuh"
@@ -36,6 +38,8 @@ struct BatchShape {
     u32 B;          // vertex id bits
     u32 sha;        // arc key: src shift = bw + 1
     u32 hb;         // Step-3 hash bucket bits
+    u32 hs;         // Step-3 hash bits sorted (top of h, hb <= hs <= 32)
+    u32 she;        // Step-3 key: first sorted bit, bw + 32 - hs
     int npa;        // arc sort passes
     int npe;        // edge sort passes
     u32 bits_a;     // arc sort digit width
@@ -95,7 +99,7 @@ static __global__ void __launch_bounds__(kPrepThreads) prep_kernel(
             const u64 ek = ((u64)edge_hash(e) << s.bw) | j;
             ekeys0[j] = ek;
             for (int p = 0; p < s.npe; ++p)
-                atomicAdd(&he[p * re + digit_bits(ek, s.bw + p * s.bits_e, me)], 1u);
+                atomicAdd(&he[p * re + digit_bits(ek, s.she + p * s.bits_e, me)], 1u);
         }
     }
     if (bad) set_error(err, kErrInput);
@@ -157,14 +161,15 @@ static __global__ void index_kernel(const u64 *keys0, const u64 *keys1, const So
         const u64 prev = k ? __ldg(K + k - 1) >> sh : ~0ull;
         const u64 next = k + 1 < n ? __ldg(K + k + 1) >> sh : ~0ull;
         if constexpr (!kArcs) {
-            // a repeated edge has the repeated hash: compare the edges of the
-            // run of equal hashes that follows (almost always empty)
-            const u64 h = key >> s.bw;
+            // a repeated edge has the repeated hash, so it lies in the run of
+            // keys sharing the sorted hash bits that follows (almost always
+            // empty): compare the edges whose whole hash matches
+            const u64 hp = key >> s.she, h = key >> s.bw;
             const u64 e = __ldg(W + (key & pmask));
             for (u64 j = k + 1; j < n; ++j) {
                 const u64 kj = __ldg(K + j);
-                if ((kj >> s.bw) != h) break;
-                dup |= __ldg(W + (kj & pmask)) == e;
+                if ((kj >> s.she) != hp) break;
+                if ((kj >> s.bw) == h) dup |= __ldg(W + (kj & pmask)) == e;
             }
         }
         if (x >= nverts) continue;  // invalid batch (already flagged by the key build)
@@ -312,17 +317,20 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
     chi += chi_plus;
 
     // ---- Step 3 (Sec. 4.4): closing edge after f2, looked up by its hash
-    // bucket; the candidates with its hash are checked against W itself
+    // bucket and sorted hash bits; the candidates with its whole hash are
+    // checked against W itself
     if (f2 != kEmpty && !(fl & TC_FLAG_CLOSED)) {
         u64 gu, gv, lo, hi;
         closing_pair(f1, f2, gu, gv);
         const u64 g = (gu << 32) | gv;
         const u64 h = edge_hash(g);
+        const u64 hp = h >> (32 - s.hs);  // the sorted bits
         dir_segment(a.edir, epoch, h >> (32 - s.hb), s.w, lo, hi);
-        u64 k = lower_bound_range(E, lo, hi, h << s.bw);
+        u64 k = lower_bound_range(E, lo, hi, hp << s.she);
         for (; k < hi; ++k) {
             const u64 ek = __ldg(E + k);
-            if ((ek >> s.bw) != h) break;
+            if ((ek >> s.she) != hp) break;
+            if ((ek >> s.bw) != h) continue;
             const u32 q = (u32)(ek & wmask);
             if (__ldg(a.W + q) == g) {
                 if (!new2 || q > p2) fl |= TC_FLAG_CLOSED;

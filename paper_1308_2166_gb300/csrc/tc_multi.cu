@@ -15,9 +15,11 @@
 //               on the (k, src) bits: every participant's arcs end up in its
 //               own range [2 eoff_k, 2 eoff_k + 2 w_k), in Lemma 4.3's order;
 //   edge keys   k << (32+bw) | h << bw | j, h = edge_hash(u, v) (or k << 32 | h
-//               with value j when kb + 32 + bw > 64): participant k's keys
-//               end up in [eoff_k, eoff_k + w_k) sorted by hash; a lookup
-//               checks each candidate with the probe's hash against D_k;
+//               with value j when kb + 32 + bw > 64), sorted on k and the top
+//               hs bits of h (whole digits, hs >= bw + 1 where they fit):
+//               participant k's keys end up in [eoff_k, eoff_k + w_k), and
+//               a lookup scans the short run sharing the probe's sorted bits,
+//               checking each candidate with its whole hash against D_k;
 //   sweep       one thread per estimator of the participants only (roff).
 //   bw = bits of (max_k w_k) - 1, kb = bits of K-1, B = vertex id bits.
 #include <algorithm>
@@ -49,7 +51,8 @@ struct RoundShape {
     int npa, npe;
     u32 bits_a, bits_e;
     u32 eko;    // 1: Step-3 keys carry j in their low bw bits (else as a value)
-    u32 she;    // Step-3 key: sort bits start (bw or 0)
+    u32 hs;     // Step-3 hash bits sorted (the top of h)
+    u32 she;    // Step-3 key: first sorted bit ((bw or 0) + 32 - hs)
 };
 
 // Step-3 key of participant k's edge at local position j with hash h.
@@ -60,6 +63,11 @@ __device__ __forceinline__ u64 mkey(const RoundShape &rs, u64 k, u64 h, u64 j) {
 // (participant, hash) part of a Step-3 key.
 __device__ __forceinline__ u64 mkey_prefix(const RoundShape &rs, u64 key) {
     return rs.eko ? key >> rs.bw : key;
+}
+
+// The sorted part of a Step-3 key: participant and the top hs hash bits.
+__device__ __forceinline__ u64 mkey_sorted(const RoundShape &rs, u64 key) {
+    return key >> rs.she;
 }
 
 // Views of a round descriptor.
@@ -153,14 +161,17 @@ __global__ void mdups_kernel(const u64 *ekeys0, const u64 *ekeys1, const u32 *ev
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < rs.Wt;
          i += (u64)gridDim.x * blockDim.x) {
         const u64 a = __ldg(E + i);
-        const u64 pa = mkey_prefix(rs, a);
-        if (i + 1 >= rs.Wt || mkey_prefix(rs, __ldg(E + i + 1)) != pa) continue;
+        const u64 sa = mkey_sorted(rs, a), pa = mkey_prefix(rs, a);
+        if (i + 1 >= rs.Wt || mkey_sorted(rs, __ldg(E + i + 1)) != sa) continue;
         const u64 k = rs.eko ? a >> (32 + rs.bw) : a >> 32;
         const u64 *D = d.ebase[k];
         const u64 ea = __ldg(D + (rs.eko ? (a & jmask) : __ldg(EV + i)));
+        // a repeat shares the whole hash, so it lies in the run of equal
+        // sorted bits that follows
         for (u64 j = i + 1; j < rs.Wt; ++j) {
             const u64 b = __ldg(E + j);
-            if (mkey_prefix(rs, b) != pa) break;
+            if (mkey_sorted(rs, b) != sa) break;
+            if (mkey_prefix(rs, b) != pa) continue;
             if (__ldg(D + (rs.eko ? (b & jmask) : __ldg(EV + j))) == ea) {
                 atomicOr(&perr[k], kErrInput);
                 break;
@@ -280,10 +291,11 @@ __global__ void __launch_bounds__(kMThreads, 5) msweep_kernel(MSweepArgs a) {
                 const u64 gu = x1 < x2 ? x1 : x2, gv = x1 < x2 ? x2 : x1;
                 const u64 gkey = (gu << 32) | gv;
                 const u64 probe = mkey(rs, k, edge_hash(gkey), 0);
-                const u64 pp = mkey_prefix(rs, probe);
-                for (u64 q = lower_bound_range(E, e0, e0 + ws, probe); q < e0 + ws; ++q) {
+                const u64 pp = mkey_prefix(rs, probe), ps = mkey_sorted(rs, probe);
+                for (u64 q = lower_bound_range(E, e0, e0 + ws, ps << rs.she); q < e0 + ws; ++q) {
                     const u64 ek = __ldg(E + q);
-                    if (mkey_prefix(rs, ek) != pp) break;
+                    if (mkey_sorted(rs, ek) != ps) break;
+                    if (mkey_prefix(rs, ek) != pp) continue;
                     const u64 pq = rs.eko ? (ek & wmask) : __ldg(EV + q);
                     if (__ldg(D + pq) == gkey) {
                         if (!new2 || pq > p2) fl |= TC_FLAG_CLOSED;
@@ -625,9 +637,13 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u
     rs.sha = rs.bw + 1;
     rs.Wt = Wt;
     rs.bits_a = mpick(M->B + rs.kb, M->force_a, rs.npa);
-    rs.bits_e = mpick(32 + rs.kb, M->force_e, rs.npe);
+    // Step-3 keys: whole digits covering k and at least bw + 1 hash bits
+    // (runs of equal sorted bits then hold half a key on average in the
+    // largest batch), at most all 32
+    rs.bits_e = mpick(rs.kb + std::min(32u, rs.bw + 1), M->force_e, rs.npe);
+    rs.hs = std::min(32u, (u32)rs.npe * rs.bits_e - rs.kb);
     rs.eko = rs.kb + 32 + rs.bw <= 64 ? 1u : 0u;
-    rs.she = rs.eko ? rs.bw : 0u;
+    rs.she = (rs.eko ? rs.bw : 0u) + 32 - rs.hs;
     const int b = M->nsets == 2 ? (int)(M->rseq & 1) : 0;
     M->rseq++;
     tc_multi::RoundSet &z = M->rset[b];
@@ -665,7 +681,7 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u
     for (int p = 0; p < rs.npe; ++p)
         ke.fn<<<(unsigned)te, ke.threads, ke.smem, M->side>>>(
             z.ekeys[0], z.ekeys[1], rs.eko ? nullptr : z.evals[0], rs.eko ? nullptr : z.evals[1],
-            (u32)Wt, rs.she + p * rs.bits_e, mlive(32 + rs.kb, rs.bits_e, p), p, &plans[1],
+            (u32)Wt, rs.she + p * rs.bits_e, mlive(rs.hs + rs.kb, rs.bits_e, p), p, &plans[1],
             lbe + (u64)p * le, gerr, nullptr);
     const u64 db = std::min<u64>((Wt + 255) / 256, 1216);
     mdups_kernel<<<(unsigned)db, 256, 0, M->side>>>(z.ekeys[0], z.ekeys[1], z.evals[0],
