@@ -743,11 +743,14 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
                 nxt += rng.exponential(1.0 / rate)
             cl.poll(wait_us=int(max(0, min(nxt - time.perf_counter(), 5e-4)) * 1e6))
     else:
+        loops = capped = 0            # client passes; passes that found the cap reached
         while time.perf_counter() < t_end:
             sub = 0
             while cl.out_edges < cap_edges and sub < 64:
                 cl.one()
                 sub += 1
+            loops += 1
+            capped += sub == 0
             cl.poll(wait_us=0 if sub else 200)
     srv.drain(600000)
     cl.poll()
@@ -770,11 +773,25 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
     pct = (lambda a, q: float(np.percentile(a, q)) if a.size else None)
     lags = np.asarray(lags) * 1e3
     extra = {}
+    if not rate:
+        extra["client_passes_at_cap"] = capped / max(1, loops)
     if rate:
         extra = {"client_lag_ms": {"p50": pct(lags, 50), "p99": pct(lags, 99),
                                    "max": float(lags.max()) if lags.size else None},
                  "batch_wait_ms": {"p50": pct(wait_b, 50), "p99": pct(wait_b, 99)},
                  "batch_service_ms": {"p50": pct(serv_b, 50), "p99": pct(serv_b, 99)}}
+        # where the slow batches sit in the phase (admission time, 50 ms bins)
+        lat_all = (batches["t_done_ns"] - batches["t_submit_ns"]) / 1e6
+        slow = lat_all > 5.0
+        if slow.any():
+            at = (batches["t_admit_ns"][slow].astype(np.int64) - first) / 1e6
+            bins, cnt = np.unique((at // 50).astype(np.int64), return_counts=True)
+            extra["slow_batches"] = {"over_ms": 5.0, "count": int(slow.sum()),
+                                     "admit_bins_50ms": {str(int(k) * 50): int(c)
+                                                         for k, c in zip(bins[:20], cnt[:20])},
+                                     "max_ms": float(lat_all.max()),
+                                     "w_mean": float(ws[slow].mean()),
+                                     "r_mean": float(rs[slow].mean())}
     return {**extra,
         "edges_per_s": float(ws.sum()) / span,
         "updates_per_s": float((ws * rs).sum()) / span,

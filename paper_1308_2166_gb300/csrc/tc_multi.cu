@@ -10,16 +10,27 @@
 // D_k[0..w_k) into slot slot_k; eoff = exclusive prefix sums of w_k, roff =
 // exclusive prefix sums of the participants' estimator counts r_k):
 //   descriptor  u64 words: eoff[K+1], D_k pointers[K], roff[K+1], slot_k[K]
-//   arc keys    k << (B+bw+1) | src << (bw+1) | (w_k-1-j) << 1 | side, written
-//               participant-major in decreasing local position j and sorted
-//               on the (k, src) bits: every participant's arcs end up in its
-//               own range [2 eoff_k, 2 eoff_k + 2 w_k), in Lemma 4.3's order;
+//   arc keys    k << (B+bw+1) | pi(src) << (bw+1) | (w_k-1-j) << 1 | side,
+//               pi a bijection of [0, 2^B) (multiplication by an odd
+//               Fibonacci-hashing constant mod 2^B) that spreads any set of
+//               ids evenly over the range; written participant-major in
+//               decreasing local position j and sorted on the (k, pi(src))
+//               bits: every participant's arcs end up in its own range
+//               [2 eoff_k, 2 eoff_k + 2 w_k), each vertex's arcs contiguous
+//               in Lemma 4.3's order;
 //   edge keys   k << (32+bw) | h << bw | j, h = edge_hash(u, v) (or k << 32 | h
 //               with value j when kb + 32 + bw > 64), sorted on k and the top
 //               hs bits of h (whole digits, hs >= bw + 1 where they fit):
 //               participant k's keys end up in [eoff_k, eoff_k + w_k), and
 //               a lookup scans the short run sharing the probe's sorted bits,
 //               checking each candidate with its whole hash against D_k;
+//   directories bucket directories over the two sorted arrays, like the
+//               single-stream Step-3 directory: arcs by the top hA bits of
+//               (k, pi(src)), Step-3 keys by the top hE bits of their sorted
+//               (k, hash) bits; a lookup reads its bucket's [start, end) and
+//               searches only there.  Entries carry the round set's tag, a
+//               device word that each round's bookkeeping advances (so a
+//               replayed CUDA graph gets a fresh tag every time);
 //   sweep       one thread per estimator of the participants only (roff).
 //   bw = bits of (max_k w_k) - 1, kb = bits of K-1, B = vertex id bits.
 #include <algorithm>
@@ -53,7 +64,16 @@ struct RoundShape {
     u32 eko;    // 1: Step-3 keys carry j in their low bw bits (else as a value)
     u32 hs;     // Step-3 hash bits sorted (the top of h)
     u32 she;    // Step-3 key: first sorted bit ((bw or 0) + 32 - hs)
+    u32 ha_sh;  // arc bucket: (k, pi(src)) >> ha_sh, 2^hA buckets
+    u32 he_sh;  // Step-3 bucket: sorted bits >> he_sh, 2^hE buckets
+    u64 nba, nbe;   // 2^hA, 2^hE
+    u64 pmul;   // pi: x -> x * pmul mod 2^B (pmul odd)
 };
+
+// pi(x): the vertex id bijection of the arc keys.
+__device__ __forceinline__ u64 vperm(const RoundShape &rs, u64 x) {
+    return (x * rs.pmul) & ((rs.B >= 64) ? ~0ull : ((1ull << rs.B) - 1));
+}
 
 // Step-3 key of participant k's edge at local position j with hash h.
 __device__ __forceinline__ u64 mkey(const RoundShape &rs, u64 k, u64 h, u64 j) {
@@ -124,8 +144,8 @@ __global__ void __launch_bounds__(kMThreads) mprep_kernel(const u64 *__restrict_
         if (!(u < v) || v >= id_lim) atomicOr(&perr[k], kErrInput);
         const u64 sp = (u64)k << (rs.B + rs.sha);
         const u64 rpos = (ws - 1 - jl) << 1;
-        const u64 au = sp | (u << rs.sha) | rpos;
-        const u64 av = sp | (v << rs.sha) | rpos | 1ull;
+        const u64 au = sp | (vperm(rs, u) << rs.sha) | rpos;
+        const u64 av = sp | (vperm(rs, v) << rs.sha) | rpos | 1ull;
         reinterpret_cast<ulonglong2 *>(arcs0)[e0 + ws - 1 - jl] = make_ulonglong2(au, av);
         for (int p = 0; p < rs.npa; ++p) {
             atomicAdd(&h[p * ra + digit_bits(au, rs.sha + p * rs.bits_a, ra - 1)], 1u);
@@ -150,17 +170,45 @@ __global__ void __launch_bounds__(kMThreads) mprep_kernel(const u64 *__restrict_
 // they lie in one run of equal (participant, hash) after the edge sort: each
 // key compares its edge with those of the rest of its run (almost always
 // empty).
+// Bucket directory over a sorted array: the first key of bucket x writes
+// (tag, start), the last one writes end; x = key >> shift.
+__device__ __forceinline__ void dir_mark(DirEntry *dir, u64 nb, u32 tag, const u64 *K, u64 n,
+                                         u64 i, u64 key, u32 shift) {
+    const u64 x = key >> shift;
+    if (x >= nb) return;  // only keys of a rejected batch; never looked up
+    const u64 prev = i ? __ldg(K + i - 1) >> shift : ~0ull;
+    const u64 next = i + 1 < n ? __ldg(K + i + 1) >> shift : ~0ull;
+    if (x != prev) *reinterpret_cast<u64 *>(&dir[x].epoch) = (i << 32) | tag;
+    if (x != next) dir[x].end = (u32)(i + 1);
+}
+
+// Arc bucket directory (after the arc sort).
+__global__ void marc_index_kernel(const u64 *arcs0, const u64 *arcs1, const SortPlan *plans,
+                                  RoundShape rs, DirEntry *adir, const u32 *tagp) {
+    const u64 *A = plan_final_sel(&plans[0]) ? arcs1 : arcs0;
+    const u32 tag = *tagp;
+    const u64 n = 2 * rs.Wt;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (u64)gridDim.x * blockDim.x)
+        dir_mark(adir, rs.nba, tag, A, n, i, __ldg(A + i), rs.sha + rs.ha_sh);
+}
+
+// Step-3 bucket directory and the in-round repeat check (after the Step-3
+// sort).
 __global__ void mdups_kernel(const u64 *ekeys0, const u64 *ekeys1, const u32 *evals0,
                              const u32 *evals1, const SortPlan *plans,
-                             const u64 *__restrict__ desc, RoundShape rs, u32 *perr) {
+                             const u64 *__restrict__ desc, RoundShape rs, u32 *perr,
+                             DirEntry *edir, const u32 *tagp) {
     const Desc d = desc_view(desc, rs.K);
     const bool sel = plan_final_sel(&plans[1]) != 0;
     const u64 *E = sel ? ekeys1 : ekeys0;
     const u32 *EV = sel ? evals1 : evals0;
     const u64 jmask = (1ull << rs.bw) - 1;
+    const u32 tag = *tagp;
     for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < rs.Wt;
          i += (u64)gridDim.x * blockDim.x) {
         const u64 a = __ldg(E + i);
+        dir_mark(edir, rs.nbe, tag, E, rs.Wt, i, a, rs.she + rs.he_sh);
         const u64 sa = mkey_sorted(rs, a), pa = mkey_prefix(rs, a);
         if (i + 1 >= rs.Wt || mkey_sorted(rs, __ldg(E + i + 1)) != sa) continue;
         const u64 k = rs.eko ? a >> (32 + rs.bw) : a >> 32;
@@ -189,6 +237,8 @@ struct MSweepArgs {
     MStream *ms;
     const u32 *gerr;     // round-wide error (a timed-out sort)
     const u32 *perr;     // each participant's error this round
+    const DirEntry *adir, *edir;
+    const u32 *tag;      // the round set's directory tag
     RoundShape rs;
 };
 
@@ -213,6 +263,28 @@ __device__ __forceinline__ bool warp_segment_sum(u32 key, u64 &lo, u64 &hi, u64 
     return lane == __ffs(grp) - 1;
 }
 
+// The arcs [start, end) of vertex prefix x = (k, pi(src)): its bucket's
+// range from the directory, then the run of keys with that prefix in it.
+__device__ __forceinline__ void vertex_arcs(const DirEntry *adir, u32 tag, const u64 *arcs,
+                                            const RoundShape &rs, u64 x, u64 &start, u64 &end) {
+    u64 lo, hi;
+    dir_segment(adir, tag, x >> rs.ha_sh, 2 * rs.Wt, lo, hi);
+    start = lower_bound_range(arcs, lo, hi, x << rs.sha);
+    // first key past the prefix: compare prefixes (x + 1 << sha may not fit)
+    u64 n = hi - start;
+    const u64 *base = arcs + start;
+    while (n > 0) {
+        const u64 half = n >> 1;
+        if ((__ldg(base + half) >> rs.sha) <= x) {
+            base += half + 1;
+            n -= half + 1;
+        } else {
+            n = half;
+        }
+    }
+    end = (u64)(base - arcs);
+}
+
 __global__ void __launch_bounds__(kMThreads, 5) msweep_kernel(MSweepArgs a) {
     if (ld_relaxed(a.gerr)) return;
     const u64 g = (u64)blockIdx.x * kMThreads + threadIdx.x;
@@ -235,11 +307,12 @@ __global__ void __launch_bounds__(kMThreads, 5) msweep_kernel(MSweepArgs a) {
             const bool es = plan_final_sel(&a.plans[1]) != 0;
             const u64 *E = es ? a.ekeys1 : a.ekeys0;
             const u32 *EV = es ? a.evals1 : a.evals0;
-            const u64 a_lo = 2 * e0, a_hi = 2 * (e0 + ws);
-            const u64 sp = (u64)k << (rs.B + rs.sha);
             const u64 wmask = (1ull << rs.bw) - 1;
-            u64 f1 = F1[i], f2 = F2[i], chi = CHI[i];
-            u32 fl = FL[i];
+            const u32 tag = *a.tag;
+            // the state streams through once: evict-first, so that L2 keeps
+            // the directories and sorted arrays the searches hit at random
+            u64 f1 = __ldcs(F1 + i), f2 = __ldcs(F2 + i), chi = __ldcs(CHI + i);
+            u32 fl = __ldcs(FL + i);
             // ---- Step 1 (Sec. 4.2)
             const u64 x = draw_bounded(dk, (u32)i, kStep1, m + ws);
             const bool new1 = x >= m;
@@ -251,18 +324,17 @@ __global__ void __launch_bounds__(kMThreads, 5) msweep_kernel(MSweepArgs a) {
                 f2 = kEmpty;
                 fl = 0;
             }
-            // ---- Step 2 (Sec. 4.3)
+            // ---- Step 2 (Sec. 4.3): each endpoint's arcs, from its bucket
             const u64 u = f1 >> 32, v = f1 & kMask32;
-            // (x + 1) << sha may carry into the participant bits: add, do not OR
-            const u64 su = lower_bound_range(arcs, a_lo, a_hi, sp + (u << rs.sha));
-            const u64 eu = lower_bound_range(arcs, su, a_hi, sp + ((u + 1) << rs.sha));
-            const u64 sv = lower_bound_range(arcs, a_lo, a_hi, sp + (v << rs.sha));
-            const u64 ev = lower_bound_range(arcs, sv, a_hi, sp + ((v + 1) << rs.sha));
+            const u64 xu = ((u64)k << rs.B) | vperm(rs, u), xv = ((u64)k << rs.B) | vperm(rs, v);
+            u64 su, eu, sv, ev;
+            vertex_arcs(a.adir, tag, arcs, rs, xu, su, eu);
+            vertex_arcs(a.adir, tag, arcs, rs, xv, sv, ev);
             u64 ld, rd;
             if (new1) {
                 const u64 rp = (ws - 1 - p1) << 1;
-                ld = lower_bound_range(arcs, su, eu, sp | (u << rs.sha) | rp) - su;
-                rd = lower_bound_range(arcs, sv, ev, sp | (v << rs.sha) | rp) - sv;
+                ld = lower_bound_range(arcs, su, eu, (xu << rs.sha) | rp) - su;
+                rd = lower_bound_range(arcs, sv, ev, (xv << rs.sha) | rp) - sv;
             } else {
                 ld = eu - su;
                 rd = ev - sv;
@@ -292,7 +364,9 @@ __global__ void __launch_bounds__(kMThreads, 5) msweep_kernel(MSweepArgs a) {
                 const u64 gkey = (gu << 32) | gv;
                 const u64 probe = mkey(rs, k, edge_hash(gkey), 0);
                 const u64 pp = mkey_prefix(rs, probe), ps = mkey_sorted(rs, probe);
-                for (u64 q = lower_bound_range(E, e0, e0 + ws, ps << rs.she); q < e0 + ws; ++q) {
+                u64 lo, hi;
+                dir_segment(a.edir, tag, ps >> rs.he_sh, rs.Wt, lo, hi);
+                for (u64 q = lower_bound_range(E, lo, hi, ps << rs.she); q < hi; ++q) {
                     const u64 ek = __ldg(E + q);
                     if (mkey_sorted(rs, ek) != ps) break;
                     if (mkey_prefix(rs, ek) != pp) continue;
@@ -303,10 +377,10 @@ __global__ void __launch_bounds__(kMThreads, 5) msweep_kernel(MSweepArgs a) {
                     }
                 }
             }
-            F1[i] = f1;
-            F2[i] = f2;
-            CHI[i] = chi;
-            FL[i] = fl;
+            __stcs(F1 + i, f1);
+            __stcs(F2 + i, f2);
+            __stcs(CHI + i, chi);
+            __stcs(FL + i, fl);
             if (fl & TC_FLAG_CLOSED) {
                 add = chi;
                 closed = 1;
@@ -334,10 +408,13 @@ __device__ __forceinline__ void write_record(u64 *o, u32 status, const MStream &
 
 // Close the round for every participant.
 __global__ void mfinish_kernel(MStream *ms, const u64 *__restrict__ desc, u32 K, u32 *gerr,
-                               const u32 *perr,
-                               u64 *out) {
+                               const u32 *perr, u64 *out, u32 *tag) {
     const u32 k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= K) return;
+    if (k == 0) {  // the set's next round writes its directories under a new tag
+        const u32 t = *tag + 1;
+        *tag = t ? t : 1;
+    }
     const Desc d = desc_view(desc, K);
     MStream &st = ms[d.slot[k]];
     const u64 ws = d.eoff[k + 1] - d.eoff[k];
@@ -468,6 +545,30 @@ u64 zeroed_bytes_for(u32 sb, u64 w_max_round, u32 vertex_bits) {
     return 2 * sizeof(SortPlan) + lb * sizeof(u32) + 256;
 }
 
+// Bucket bits of the two round directories for Wt edges (at most, before
+// the clamp to the sorted bits): about 2 Wt / 4 arc buckets and Wt / 4
+// Step-3 buckets.
+u32 arc_dir_bits(u64 Wt) {
+    const u32 b = mbits_for(2 * Wt - 1);
+    return b > 3 ? b - 2 : 1;
+}
+u32 edge_dir_bits(u64 Wt) {
+    const u32 b = mbits_for(Wt - 1);
+    return b > 3 ? b - 2 : 1;
+}
+
+// pi's multiplier for B-bit ids: the odd integer next to 2^B / phi
+// (Fibonacci hashing, Knuth TAOCP vol. 3, 6.4).
+u64 fib_multiplier(u32 B) {
+    return (u64)(0.6180339887498949 * (double)(1ull << B)) | 1ull;
+}
+
+// Bytes of one round set's directories and tag word.
+u64 dir_bytes(u64 w_max_round) {
+    return ((1ull << arc_dir_bits(w_max_round)) + (1ull << edge_dir_bits(w_max_round))) *
+               sizeof(DirEntry) + 256;
+}
+
 // Participant error words at the end of the zeroed block, one per slot at most.
 u64 perr_bytes(u32 S) { return ((u64)S * 4 + 255) & ~255ull; }
 
@@ -481,22 +582,53 @@ namespace tc {
 u64 multi_scratch_bytes(u32 S, u64 w_max_round, u32 vertex_bits, int sets) {
     const u32 sb = mbits_for(S - 1);
     const u64 per_set = 2 * (2 * w_max_round * 8 + w_max_round * 8 + w_max_round * 4) +
-                        zeroed_bytes_for(sb, w_max_round, vertex_bits) + perr_bytes(S);
+                        zeroed_bytes_for(sb, w_max_round, vertex_bits) + perr_bytes(S) +
+                        dir_bytes(w_max_round);
     return (u64)S * sizeof(MStream) + (u64)sets * per_set + kRing * desc_words(S) * 8;
+}
+
+static void free_round_set(tc_multi::RoundSet &z) {
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(z.arcs[k]);
+        cudaFree(z.ekeys[k]);
+        cudaFree(z.evals[k]);
+    }
+    cudaFree(z.zeroed);
+    cudaFree(z.adir);
+    cudaFree(z.edir);
+    cudaFree(z.tag);
+    z = tc_multi::RoundSet{};
+}
+
+// Allocate one set of round scratch: the sort buffers, the zeroed block,
+// the two directories (tag 0 everywhere) and the tag word (1: the first
+// round's tag).  On failure the set is freed and false returned.
+static bool alloc_round_set(tc_multi::RoundSet &z, u64 w_max, u64 zeroed_bytes) {
+    bool ok = true;
+    for (int k = 0; k < 2 && ok; ++k) {
+        ok &= cudaMalloc(&z.arcs[k], 2 * w_max * sizeof(u64)) == cudaSuccess;
+        ok &= ok && cudaMalloc(&z.ekeys[k], w_max * sizeof(u64)) == cudaSuccess;
+        ok &= ok && cudaMalloc(&z.evals[k], w_max * sizeof(u32)) == cudaSuccess;
+    }
+    ok &= ok && cudaMalloc(&z.zeroed, zeroed_bytes) == cudaSuccess;
+    ok &= ok && cudaMemset(z.zeroed, 0, zeroed_bytes) == cudaSuccess;
+    const u64 na = 1ull << arc_dir_bits(w_max), ne = 1ull << edge_dir_bits(w_max);
+    ok &= ok && cudaMalloc(&z.adir, na * sizeof(DirEntry)) == cudaSuccess;
+    ok &= ok && cudaMemset(z.adir, 0, na * sizeof(DirEntry)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&z.edir, ne * sizeof(DirEntry)) == cudaSuccess;
+    ok &= ok && cudaMemset(z.edir, 0, ne * sizeof(DirEntry)) == cudaSuccess;
+    const u32 one = 1;
+    ok &= ok && cudaMalloc(&z.tag, 256) == cudaSuccess;
+    ok &= ok && cudaMemcpy(z.tag, &one, sizeof(one), cudaMemcpyHostToDevice) == cudaSuccess;
+    if (!ok) free_round_set(z);
+    return ok;
 }
 
 void multi_free(tc_multi *M) {
     cudaDeviceSynchronize();
     cudaFree(M->state);
     cudaFree(M->ms);
-    for (tc_multi::RoundSet &z : M->rset) {
-        for (int k = 0; k < 2; ++k) {
-            cudaFree(z.arcs[k]);
-            cudaFree(z.ekeys[k]);
-            cudaFree(z.evals[k]);
-        }
-        cudaFree(z.zeroed);
-    }
+    for (tc_multi::RoundSet &z : M->rset) free_round_set(z);
     if (M->sa) cudaStreamDestroy(M->sa);
     for (int k = 0; k < 2; ++k) {
         if (M->ev_sorted[k]) cudaEventDestroy(M->ev_sorted[k]);
@@ -537,16 +669,8 @@ int multi_alloc(u32 S, u64 w_max_round, u32 vertex_bits, tc_multi **out, int set
     M->zeroed_bytes = zeroed_bytes_for(sb, w_max_round, vertex_bits) + perr_bytes(S);
     M->nsets = sets == 2 ? 2 : 1;
     bool ok = cudaMalloc(&M->ms, S * sizeof(MStream)) == cudaSuccess;
-    for (int z = 0; z < M->nsets && ok; ++z) {
-        tc_multi::RoundSet &rs = M->rset[z];
-        for (int k = 0; k < 2 && ok; ++k) {
-            ok &= cudaMalloc(&rs.arcs[k], 2 * w_max_round * sizeof(u64)) == cudaSuccess;
-            ok &= ok && cudaMalloc(&rs.ekeys[k], w_max_round * sizeof(u64)) == cudaSuccess;
-            ok &= ok && cudaMalloc(&rs.evals[k], w_max_round * sizeof(u32)) == cudaSuccess;
-        }
-        ok &= ok && cudaMalloc(&rs.zeroed, M->zeroed_bytes) == cudaSuccess;
-        ok &= ok && cudaMemset(rs.zeroed, 0, M->zeroed_bytes) == cudaSuccess;
-    }
+    for (int z = 0; z < M->nsets && ok; ++z)
+        ok &= alloc_round_set(M->rset[z], w_max_round, M->zeroed_bytes);
     ok &= ok && cudaStreamCreateWithFlags(&M->sa, cudaStreamNonBlocking) == cudaSuccess;
     for (int k = 0; k < 2 && ok; ++k) {
         ok &= cudaEventCreateWithFlags(&M->ev_sorted[k], cudaEventDisableTiming) == cudaSuccess;
@@ -644,6 +768,14 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u
     rs.hs = std::min(32u, (u32)rs.npe * rs.bits_e - rs.kb);
     rs.eko = rs.kb + 32 + rs.bw <= 64 ? 1u : 0u;
     rs.she = (rs.eko ? rs.bw : 0u) + 32 - rs.hs;
+    // bucket directories: at most the sorted bits
+    const u32 ha = std::min(arc_dir_bits(Wt), rs.kb + rs.B);
+    const u32 he = std::min(edge_dir_bits(Wt), rs.kb + rs.hs);
+    rs.ha_sh = rs.kb + rs.B - ha;
+    rs.he_sh = rs.kb + rs.hs - he;
+    rs.nba = 1ull << ha;
+    rs.nbe = 1ull << he;
+    rs.pmul = fib_multiplier(rs.B);
     const int b = M->nsets == 2 ? (int)(M->rseq & 1) : 0;
     M->rseq++;
     tc_multi::RoundSet &z = M->rset[b];
@@ -685,12 +817,16 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u
             lbe + (u64)p * le, gerr, nullptr);
     const u64 db = std::min<u64>((Wt + 255) / 256, 1216);
     mdups_kernel<<<(unsigned)db, 256, 0, M->side>>>(z.ekeys[0], z.ekeys[1], z.evals[0],
-                                                    z.evals[1], plans, desc, rs, perr);
+                                                    z.evals[1], plans, desc, rs, perr, z.edir,
+                                                    z.tag);
     TCM_CUDA(cudaEventRecord(M->ev_join, M->side));
     for (int p = 0; p < rs.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, ms>>>(
             z.arcs[0], z.arcs[1], nullptr, nullptr, (u32)(2 * Wt), rs.sha + p * rs.bits_a,
             mlive(M->B + rs.kb, rs.bits_a, p), p, &plans[0], lb + (u64)p * la, gerr, nullptr);
+    const u64 ib = std::min<u64>((2 * Wt + 255) / 256, 152 * 16);
+    marc_index_kernel<<<(unsigned)ib, 256, 0, ms>>>(z.arcs[0], z.arcs[1], plans, rs, z.adir,
+                                                    z.tag);
     TCM_CUDA(cudaStreamWaitEvent(ms, M->ev_join, 0));
     if (pipelined) {
         TCM_CUDA(cudaEventRecord(M->ev_sorted[b], ms));
@@ -709,12 +845,15 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u
     a.ms = M->ms;
     a.gerr = gerr;
     a.perr = perr;
+    a.adir = z.adir;
+    a.edir = z.edir;
+    a.tag = z.tag;
     a.rs = rs;
     msweep_kernel<<<(unsigned)((R + kMThreads - 1) / kMThreads), kMThreads, 0, st>>>(a);
-    mfinish_kernel<<<(K + 255) / 256, 256, 0, st>>>(M->ms, desc, K, gerr, perr, out);
+    mfinish_kernel<<<(K + 255) / 256, 256, 0, st>>>(M->ms, desc, K, gerr, perr, out, z.tag);
     if (M->nsets == 2) TCM_CUDA(cudaEventRecord(M->ev_swept[b], st));  // the set is free again
     TCM_CUDA(cudaGetLastError());
-    M->launches += 5 + (u64)rs.npa + (u64)rs.npe;
+    M->launches += 6 + (u64)rs.npa + (u64)rs.npe;
     return TC_OK;
 }
 
@@ -812,26 +951,8 @@ int tc_multi_process_async(tc_multi *M, const uint64_t *d_edges, const uint64_t 
 // The second round scratch set, for pipelined rounds.
 static int ensure_two_round_sets(tc_multi *M) {
     if (M->nsets == 2) return TC_OK;
-    tc_multi::RoundSet &z = M->rset[1];
-    bool ok = true;
-    for (int k = 0; k < 2 && ok; ++k) {
-        ok &= cudaMalloc(&z.arcs[k], 2 * M->w_max * sizeof(u64)) == cudaSuccess;
-        ok &= ok && cudaMalloc(&z.ekeys[k], M->w_max * sizeof(u64)) == cudaSuccess;
-        ok &= ok && cudaMalloc(&z.evals[k], M->w_max * sizeof(u32)) == cudaSuccess;
-    }
-    ok &= ok && cudaMalloc(&z.zeroed, M->zeroed_bytes) == cudaSuccess;
-    ok &= ok && cudaMemset(z.zeroed, 0, M->zeroed_bytes) == cudaSuccess;
-    if (!ok) {
+    if (!alloc_round_set(M->rset[1], M->w_max, M->zeroed_bytes)) {
         cudaGetLastError();
-        for (int k = 0; k < 2; ++k) {
-            cudaFree(z.arcs[k]);
-            cudaFree(z.ekeys[k]);
-            cudaFree(z.evals[k]);
-            z.arcs[k] = z.ekeys[k] = nullptr;
-            z.evals[k] = nullptr;
-        }
-        cudaFree(z.zeroed);
-        z.zeroed = nullptr;
         return TC_ERR_NOMEM;
     }
     M->nsets = 2;

@@ -64,6 +64,9 @@ struct tc_multi {
         tc::u64 *ekeys[2] = {nullptr, nullptr};
         tc::u32 *evals[2] = {nullptr, nullptr};
         unsigned char *zeroed = nullptr;  // SortPlan[2], look-back, round error, participant errors
+        tc::DirEntry *adir = nullptr;     // arc bucket directory
+        tc::DirEntry *edir = nullptr;     // Step-3 bucket directory
+        tc::u32 *tag = nullptr;           // device word: the directories' current tag
     };
     RoundSet rset[2];
     int nsets = 1;
