@@ -661,56 +661,82 @@ class _ServeClient:
     a rotation of one of the R-MAT base graphs (scale 14..22) read in batches
     of log-uniform [1e3, 1e6] edges; a stream that has delivered its whole
     graph closes and a fresh stream (new scale, r, seed) takes its place.
-    10% of requests are estimate queries."""
+    10% of requests are estimate queries.  Requests go to the server in
+    chunks through tc_server_submit_many (one call per chunk)."""
 
     def __init__(self, srv, graphs, S, seed):
         self.srv, self.graphs, self.S = srv, graphs, S
         self.rng = np.random.default_rng(seed)
+        self.ptr0 = {sc: g.data_ptr() for sc, g in graphs.items()}
         self.streams = [None] * S
         self.sid = 0
         self.out_edges = 0            # submitted, not yet completed batch edges
-        self.w_of = {}                # ticket -> (edges, r) of a batch
-        self.kind_of = {}
+        self.w_t = np.zeros(1 << 20, dtype=np.int64)   # ticket -> batch edges
+        self.r_t = np.zeros(1 << 20, dtype=np.int64)   # ticket -> r of its stream
         self.done = []                # completion arrays
         for i in range(S):
             self._open(i)
 
     def _open(self, i):
         sc = int(self.rng.integers(14, 23))
-        g = self.graphs[sc]
+        m = int(self.graphs[sc].numel())
         r = int(round(2 ** self.rng.uniform(10, 16)))
-        h, t = self.srv.open(r, int(self.rng.integers(1, 2**63)), self.sid)
+        h, _ = self.srv.open(r, int(self.rng.integers(1, 2**63)), self.sid)
         self.sid += 1
-        m = g.numel()
-        self.streams[i] = {"h": h, "g": g, "m": m, "pos": int(self.rng.integers(0, m)),
-                           "left": m, "r": r}
+        self.streams[i] = [h, self.ptr0[sc], m, int(self.rng.integers(0, m)), m, r]
 
-    def one(self):
-        """Submit one request (query or batch; close + reopen when spent)."""
-        i = int(self.rng.integers(0, self.S))
-        st = self.streams[i]
-        if self.rng.random() < 0.1:
-            t = self.srv.query(st["h"])
-            self.kind_of[t] = 3
+    def _send(self, kinds, handles, ptrs, ws, rs):
+        if not kinds:
             return
-        if st["left"] == 0:
-            self.srv.close(st["h"])
-            self._open(i)
-            st = self.streams[i]
-        w = int(round(10 ** self.rng.uniform(3, 6)))
-        w = min(w, st["left"], st["m"] - st["pos"])
-        t = self.srv.submit(st["h"], st["g"][st["pos"]:st["pos"] + w])
-        st["pos"] = (st["pos"] + w) % st["m"]
-        st["left"] -= w
-        self.w_of[t] = (w, st["r"])
-        self.out_edges += w
+        t = self.srv.submit_many(kinds, handles, ptrs, ws).astype(np.int64)
+        top = int(t.max()) + 1
+        if top > self.w_t.size:
+            n = max(top, 2 * self.w_t.size)
+            self.w_t = np.concatenate([self.w_t, np.zeros(n - self.w_t.size, np.int64)])
+            self.r_t = np.concatenate([self.r_t, np.zeros(n - self.r_t.size, np.int64)])
+        w = np.asarray(ws, dtype=np.int64)
+        self.w_t[t] = w
+        self.r_t[t] = np.asarray(rs, dtype=np.int64)
+        self.out_edges += int(w.sum())
+
+    def many(self, n):
+        """Submit n requests (query or batch, to uniformly drawn streams)."""
+        idx = self.rng.integers(0, self.S, size=n).tolist()
+        isq = (self.rng.random(n) < 0.1).tolist()
+        wv = np.round(10 ** self.rng.uniform(3, 6, size=n)).astype(np.int64).tolist()
+        kinds, handles, ptrs, ws, rs = [], [], [], [], []
+        for j in range(n):
+            st = self.streams[idx[j]]
+            if isq[j]:
+                kinds.append(3)
+                handles.append(st[0])
+                ptrs.append(0)
+                ws.append(0)
+                rs.append(0)
+                continue
+            if st[4] == 0:
+                # spent: its earlier requests go first, then close and reopen
+                self._send(kinds, handles, ptrs, ws, rs)
+                kinds, handles, ptrs, ws, rs = [], [], [], [], []
+                self.srv.close(st[0])
+                self._open(idx[j])
+                st = self.streams[idx[j]]
+            h, p0, m, pos, left, r = st
+            w = min(wv[j], left, m - pos)
+            kinds.append(2)
+            handles.append(h)
+            ptrs.append(p0 + 8 * pos)
+            ws.append(w)
+            rs.append(r)
+            st[3] = (pos + w) % m
+            st[4] = left - w
+        self._send(kinds, handles, ptrs, ws, rs)
 
     def poll(self, wait_us=0):
         c = self.srv.poll(wait_us)
         if c.size:
-            for t in c["ticket"][c["kind"] == 2]:
-                w, _ = self.w_of.get(int(t), (0, 0))
-                self.out_edges -= w
+            t = c["ticket"][c["kind"] == 2].astype(np.int64)
+            self.out_edges -= int(self.w_t[t].sum())
             self.done.append(c)
         return c.size
 
@@ -737,18 +763,21 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
             now = time.perf_counter()
             if now >= t_end:
                 break
-            while nxt <= now:
-                lags.append(time.perf_counter() - nxt)
-                cl.one()
+            k = 0
+            while nxt <= now and k < 256:
+                lags.append(now - nxt)
                 nxt += rng.exponential(1.0 / rate)
+                k += 1
+            if k:
+                cl.many(k)
             cl.poll(wait_us=int(max(0, min(nxt - time.perf_counter(), 5e-4)) * 1e6))
     else:
         loops = capped = 0            # client passes; passes that found the cap reached
         while time.perf_counter() < t_end:
             sub = 0
             while cl.out_edges < cap_edges and sub < 64:
-                cl.one()
-                sub += 1
+                cl.many(16)
+                sub += 16
             loops += 1
             capped += sub == 0
             cl.poll(wait_us=0 if sub else 200)
@@ -763,8 +792,9 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
     phase = comp[(comp["kind"] != 1) & (sub_ns >= first)]
     batches = phase[phase["kind"] == 2]
     queries = phase[phase["kind"] == 3]
-    ws = np.array([cl.w_of.get(int(t), (0, 0))[0] for t in batches["ticket"]], dtype=np.float64)
-    rs = np.array([cl.w_of.get(int(t), (0, 0))[1] for t in batches["ticket"]], dtype=np.float64)
+    bt = batches["ticket"].astype(np.int64)
+    ws = cl.w_t[bt].astype(np.float64)
+    rs = cl.r_t[bt].astype(np.float64)
     span = (int(phase["t_done_ns"].max()) - first) / 1e9 if phase.size else 1.0
     lat_b = (batches["t_done_ns"] - batches["t_submit_ns"]) / 1e6
     lat_q = (queries["t_done_ns"] - queries["t_submit_ns"]) / 1e6

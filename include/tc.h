@@ -412,6 +412,17 @@ int tc_server_submit(tc_server *S, uint32_t handle, const uint64_t *h_edges, uin
 /* Ask for the stream's estimate after every batch submitted before this call. */
 int tc_server_query(tc_server *S, uint32_t handle, uint64_t *ticket);
 
+/* Submit n requests in one call, in array order, as if by n calls of
+ * tc_server_submit (kinds[i] = TC_REQ_BATCH) or tc_server_query
+ * (TC_REQ_QUERY), under one lock and one wake-up of the scheduler.  All HOST
+ * arrays of n entries; h_edges[i] and w[i] are ignored for queries.
+ * tickets[i] receives request i's ticket.  Every request is checked first:
+ * on an error (as those calls give, or TC_ERR_INVAL for another kind) none is
+ * submitted. */
+int tc_server_submit_many(tc_server *S, uint32_t n, const uint32_t *kinds,
+                          const uint32_t *handles, const uint64_t *const *h_edges,
+                          const uint64_t *w, uint64_t *tickets);
+
 /* Close the stream after its earlier requests; its slot and state memory
  * return to the server.  The handle is invalid from this call on. */
 int tc_server_close(tc_server *S, uint32_t handle, uint64_t *ticket);

@@ -39,7 +39,7 @@ EXPORTS = (
     "tc_server_close", "tc_server_poll", "tc_server_drain", "tc_server_stats",
     "tc_server_destroy", "tc_selftest_wait_timeout", "tc_save_size", "tc_save", "tc_load",
     "tc_process_batch_host_async", "tc_process_batch_ready_async",
-    "tc_multi_process_ready_async",
+    "tc_multi_process_ready_async", "tc_server_submit_many",
 )
 
 TC_REQ_OPEN, TC_REQ_BATCH, TC_REQ_QUERY, TC_REQ_CLOSE = 1, 2, 3, 4
@@ -145,6 +145,7 @@ def load(path: str | None = None):
         "tc_server_open": (I, [P, U64, U64, U32, ctypes.POINTER(U32), ctypes.POINTER(U64)]),
         "tc_server_submit": (I, [P, U32, P, U64, ctypes.POINTER(U64)]),
         "tc_server_query": (I, [P, U32, ctypes.POINTER(U64)]),
+        "tc_server_submit_many": (I, [P, U32, P, P, P, P, P]),
         "tc_server_close": (I, [P, U32, ctypes.POINTER(U64)]),
         "tc_server_poll": (I, [P, P, U32, U32, ctypes.POINTER(U32)]),
         "tc_server_drain": (I, [P, U32]),
@@ -579,6 +580,26 @@ class Server:
         _check(load().tc_server_query(self.h, handle, ctypes.byref(t)), "tc_server_query")
         return t.value
 
+    def submit_many(self, kinds, handles, ptrs, ws):
+        """Submit many batches and queries in one call (tc_server_submit_many).
+        kinds: TC_REQ_BATCH / TC_REQ_QUERY per request; ptrs: host addresses
+        of the batches (ints; ignored for queries), ws: their lengths.  The
+        caller keeps every batch buffer alive until its completion.  Returns
+        the tickets (numpy uint64)."""
+        import numpy as np
+        kinds = np.ascontiguousarray(kinds, dtype=np.uint32)
+        handles = np.ascontiguousarray(handles, dtype=np.uint32)
+        ptrs = np.ascontiguousarray(ptrs, dtype=np.uint64)
+        ws = np.ascontiguousarray(ws, dtype=np.uint64)
+        n = kinds.size
+        if not (handles.size == ptrs.size == ws.size == n):
+            raise ValueError("submit_many: arrays of different lengths")
+        tickets = np.zeros(n, dtype=np.uint64)
+        _check(load().tc_server_submit_many(self.h, n, kinds.ctypes.data, handles.ctypes.data,
+                                            ptrs.ctypes.data, ws.ctypes.data,
+                                            tickets.ctypes.data), "tc_server_submit_many")
+        return tickets
+
     def close(self, handle: int) -> int:
         t = ctypes.c_uint64()
         _check(load().tc_server_close(self.h, handle, ctypes.byref(t)), "tc_server_close")
@@ -590,8 +611,9 @@ class Server:
         _check(load().tc_server_poll(self.h, self._buf.ctypes.data, self._buf.size, wait_us,
                                      ctypes.byref(n)), "tc_server_poll")
         out = self._buf[:n.value].copy()
-        for t in out["ticket"]:
-            self._keep.pop(int(t), None)
+        if self._keep:
+            for t in out["ticket"]:
+                self._keep.pop(int(t), None)
         return out
 
     def drain(self, timeout_ms: int = 600000):

@@ -688,6 +688,45 @@ int tc_server_query(tc_server *S, uint32_t handle, uint64_t *ticket) {
     return submit(S, std::move(q), ticket);
 }
 
+int tc_server_submit_many(tc_server *S, uint32_t n, const uint32_t *kinds,
+                          const uint32_t *handles, const uint64_t *const *h_edges,
+                          const uint64_t *w, uint64_t *tickets) {
+    if (!S) return TC_ERR_INVAL;
+    if (n == 0) return TC_OK;
+    if (!kinds || !handles || !tickets) return TC_ERR_INVAL;
+    for (u32 i = 0; i < n; ++i) {
+        if (kinds[i] == TC_REQ_BATCH) {
+            if (!w || !h_edges || (w[i] && !h_edges[i])) return TC_ERR_INVAL;
+            if (w[i] > S->cfg.w_max_round || w[i] > (1ull << 28) ||
+                S->fixed + round_up(8 * w[i]) > S->cfg.budget_bytes)
+                return TC_ERR_RANGE;
+        } else if (kinds[i] != TC_REQ_QUERY) {
+            return TC_ERR_INVAL;
+        }
+    }
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->fatal) return S->fatal;
+    for (u32 i = 0; i < n; ++i)
+        if (S->handles.find(handles[i]) == S->handles.end()) return TC_ERR_INVAL;
+    const u64 t = S->now();
+    for (u32 i = 0; i < n; ++i) {
+        Req q;
+        q.kind = kinds[i];
+        q.handle = handles[i];
+        if (q.kind == TC_REQ_BATCH) {
+            q.h_edges = h_edges[i];
+            q.w = w[i];
+        }
+        q.ticket = S->next_ticket++;
+        q.t_submit = t;
+        tickets[i] = q.ticket;
+        S->inbox.push_back(std::move(q));
+    }
+    S->submitted += n;
+    S->cv_in.notify_one();
+    return TC_OK;
+}
+
 int tc_server_close(tc_server *S, uint32_t handle, uint64_t *ticket) {
     if (!S) return TC_ERR_INVAL;
     if (!handle_open(S, handle, true)) return TC_ERR_INVAL;

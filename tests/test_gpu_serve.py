@@ -87,6 +87,59 @@ def _run_mix(srv, specs, plans, rng):
     return where, done
 
 
+def _run_mix_many(srv, specs, plans, rng, chunk=7):
+    """As _run_mix, but batches and queries go in chunks through
+    tc_server_submit_many (opens and closes flush the chunk first)."""
+    left = {s: 0 for s in range(len(specs))}
+    handles, where = {}, {}
+    order = []
+    for s, (r, seed, sid) in enumerate(specs):
+        order += [s] * (len(plans[s]) + 1)
+    rng.shuffle(order)
+    done = {}
+    pend = []   # (stream, op index, kind, handle, ptr, w)
+
+    def flush():
+        if not pend:
+            return
+        t = srv.submit_many([p[2] for p in pend], [p[3] for p in pend],
+                            [p[4] for p in pend], [p[5] for p in pend])
+        for (s, i, *_), tk in zip(pend, t):
+            where[int(tk)] = (s, i)
+        pend.clear()
+
+    for s in order:
+        k = left[s]
+        left[s] += 1
+        if k == 0:
+            flush()
+            h, t = srv.open(*specs[s])
+            handles[s] = h
+            where[t] = (s, -1)
+            continue
+        op = plans[s][k - 1]
+        if op[0] == "b":
+            pend.append((s, k - 1, tc.TC_REQ_BATCH, handles[s], op[1].ctypes.data, op[1].size))
+        elif op[0] == "q":
+            pend.append((s, k - 1, tc.TC_REQ_QUERY, handles[s], 0, 0))
+        else:
+            flush()
+            where[srv.close(handles[s])] = (s, k - 1)
+        if len(pend) >= chunk:
+            flush()
+        for c in srv.poll():
+            done[int(c["ticket"])] = c
+    flush()
+    srv.drain(120000)
+    while True:
+        more = srv.poll(wait_us=1000)
+        if more.size == 0:
+            break
+        for c in more:
+            done[int(c["ticket"])] = c
+    return where, done
+
+
 def _alone(spec, plan, vertex_bits, bad=()):
     """Expected (batches, S, closed, m) after each op of the plan, alone."""
     r, seed, sid = spec
@@ -157,6 +210,31 @@ def test_mix_equals_alone_with_slot_waits():
                 ref.process_batch(op[1])
             if op[0] != "c":
                 assert exp[i][1] == ref.closed_sum() and exp[i][3] == ref.m
+
+
+def test_submit_many_equals_alone():
+    """The same kind of mix with batches and queries submitted in chunks."""
+    rng = np.random.default_rng(15)
+    specs, plans = [], []
+    for s in range(16):
+        keys = _graph(2000 + s)
+        specs.append((int(rng.integers(1, 700)), int(rng.integers(0, 2**63)),
+                      int(rng.integers(0, 2**32))))
+        plans.append(_plan(rng, keys, int(rng.integers(3, 14))))
+    srv = tc.Server(max_streams=6, vertex_bits=12, budget_bytes=2 << 30, w_max_round=4096,
+                    depth=2)
+    try:
+        where, done = _run_mix_many(srv, specs, plans, rng)
+        # an unknown handle or another kind fails the whole call
+        with pytest.raises(tc.TcError):
+            srv.submit_many([tc.TC_REQ_QUERY, tc.TC_REQ_QUERY], [0, 0xFFFFFF], [0, 0], [0, 0])
+        with pytest.raises(tc.TcError):
+            srv.submit_many([tc.TC_REQ_OPEN], [0], [0], [0])
+        st = srv.stats()
+    finally:
+        srv.destroy()
+    _check(where, done, specs, plans, 12)
+    assert st["opens"] == 16 and st["closes"] == 16
 
 
 def test_memory_budget_limits_admission():
