@@ -561,20 +561,22 @@ def run_multi(args, rank, world, local_rank):
         assert not errs.any(), "batched round rejected a stream"
         return M, ms, int(offs[-1]) * nrounds, M.launches()
 
-    # autotune the per-stream batch cap on a few rounds (untimed for the result)
-    tune = {}
-    for cap in caps:
-        M, ms, edges, _ = time_batched(cap, 3)
-        tune[cap] = edges / (ms / 1e3)
-        M.close()
-    cap = max(tune, key=tune.get)
-    # then the sort tuning (digit widths, warp ranking) at that cap
-    dtune = {}
-    for cand in ((8, 8, 2), (8, 8, 1), (8, 10, 2), (10, 8, 2), (10, 10, 2)):
-        M, ms, edges, _ = time_batched(cap, 3, tuning=cand)
-        dtune[cand] = edges / (ms / 1e3)
-        M.close()
-    tuning = max(dtune, key=dtune.get)
+    tune, dtune = {}, {}
+    if args.no_autotune:
+        cap, tuning = max(caps), (8, 8, 2)
+    else:
+        # autotune the per-stream batch cap on a few rounds (untimed for the result)
+        for cap in caps:
+            M, ms, edges, _ = time_batched(cap, 3)
+            tune[cap] = edges / (ms / 1e3)
+            M.close()
+        cap = max(tune, key=tune.get)
+        # then the sort tuning (digit widths, warp ranking) at that cap
+        for cand in ((8, 8, 2), (8, 8, 1), (8, 10, 2), (10, 8, 2), (10, 10, 2)):
+            M, ms, edges, _ = time_batched(cap, 3, tuning=cand)
+            dtune[cand] = edges / (ms / 1e3)
+            M.close()
+        tuning = max(dtune, key=dtune.get)
     ws, offs, rounds, parts_all = rounds_for(cap)
     edges_total = int(offs[-1]) * T
 

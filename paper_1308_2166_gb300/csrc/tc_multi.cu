@@ -286,14 +286,27 @@ __device__ __forceinline__ void vertex_arcs(const DirEntry *adir, u32 tag, const
 }
 
 __global__ void __launch_bounds__(kMThreads, 5) msweep_kernel(MSweepArgs a) {
+    __shared__ u32 s_k[2];
     if (ld_relaxed(a.gerr)) return;
-    const u64 g = (u64)blockIdx.x * kMThreads + threadIdx.x;
+    const u64 g0 = (u64)blockIdx.x * kMThreads;
+    const u64 g = g0 + threadIdx.x;
     const RoundShape &rs = a.rs;
     const Desc d = desc_view(a.desc, rs.K);
+    // participants of the block's first and last estimators: usually the
+    // same, else every thread searches only between them
+    if (threadIdx.x == 0) s_k[0] = segment_of(d.roff, rs.K, g0);
+    if (threadIdx.x == 32) s_k[1] = segment_of(d.roff, rs.K, min(g0 + kMThreads, a.R) - 1);
+    __syncthreads();
     u32 k = 0xFFFFFFFFu;
     u64 add = 0, closed = 0;
     if (g < a.R) {
-        k = segment_of(d.roff, rs.K, g);
+        u32 lo = s_k[0], hi = s_k[1] + 1;  // last k in [lo, hi) with roff[k] <= g
+        while (hi - lo > 1) {
+            const u32 mid = (lo + hi) >> 1;
+            if (__ldg(d.roff + mid) <= g) lo = mid;
+            else hi = mid;
+        }
+        k = lo;
         const u64 e0 = __ldg(d.eoff + k), ws = __ldg(d.eoff + k + 1) - e0;
         MStream &st = a.ms[__ldg(d.slot + k)];
         if (ws > 0 && !ld_relaxed(a.perr + k)) {
