@@ -177,6 +177,7 @@ constexpr u64 kOffLookback = kOffPlans + 2 * sizeof(SortPlan);
 
 struct tc_ctx {
     int device = 0;
+    int sm_count = 1;
     u64 r = 0, seed = 0;
     u32 stream_id = 0, vertex_bits = 32;
     u64 cap_w = 0;                           // scratch capacity in edges
@@ -426,11 +427,10 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
     a.s = s;
     a.key = make_uint2((u32)(c->seed & 0xFFFFFFFFu), (u32)(c->seed >> 32));
     a.stream = c->stream_id;
-    const u64 sweep_blocks = (c->r + kSweepThreads - 1) / kSweepThreads;
     if (z.adir)
-        sweep_kernel<true><<<(unsigned)sweep_blocks, kSweepThreads, 0, st>>>(a);
+        sweep_kernel<true><<<sweep_blocks(c->r, c->sm_count), kSweepThreads, 0, st>>>(a);
     else
-        sweep_kernel<false><<<(unsigned)sweep_blocks, kSweepThreads, 0, st>>>(a);
+        sweep_kernel<false><<<sweep_blocks(c->r, c->sm_count), kSweepThreads, 0, st>>>(a);
     stamp(c, st, kSweep);
     finish_kernel<<<1, 1, 0, st>>>(c->ctl, acc, berr, w);
     stamp(c, st, kFinish);
@@ -496,6 +496,8 @@ int tc_create_ex(uint64_t r, uint64_t seed, uint32_t stream_id, uint64_t w_max,
     c->stream_id = stream_id;
     c->vertex_bits = vertex_bits;
     bool ok = cudaGetDevice(&c->device) == cudaSuccess;
+    ok &= ok && cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) ==
+                    cudaSuccess;
     ok &= ok && cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) == cudaSuccess;
     ok &= ok && cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) == cudaSuccess;
     ok &= ok && cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) == cudaSuccess;

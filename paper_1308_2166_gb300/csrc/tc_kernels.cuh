@@ -340,22 +340,23 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
     }
 }
 
-// One estimator per thread.  kDir: arc segments from the vertex directory,
-// else by binary search on the sorted arcs.  Adds sum(chi over closed) and
-// the closed count of the new state into a.acc.
+// One estimator per thread and iteration (grid-stride over r; the grid is
+// sweep_blocks(r)).  kDir: arc segments from the vertex directory, else by
+// binary search on the sorted arcs.  Adds sum(chi over closed) and the
+// closed count of the new state into a.acc.
 template <bool kDir>
 static __global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArgs a) {
     __shared__ u64 s_lo[kSweepThreads / 32], s_hi[kSweepThreads / 32], s_cnt[kSweepThreads / 32];
     if (ld_relaxed(a.berr)) return;  // rejected batch: state stays as it was
-    const u64 i = (u64)blockIdx.x * kSweepThreads + threadIdx.x;
-    u64 add = 0, closed = 0;
-    if (i < a.r) {
-        const u64 m = a.ctl->m;
-        const u32 epoch = a.epoch;
-        const DrawKey dk{a.key, (u32)a.ctl->batches, a.stream};
-        const u64 *arcs = plan_final_sel(&a.plans[0]) ? a.arcs1 : a.arcs0;
-        const bool e_sel = plan_final_sel(&a.plans[1]) != 0;
-        const u64 *E = e_sel ? a.ekeys1 : a.ekeys0;
+    u64 add = 0, hi = 0, closed = 0;
+    const u64 m = a.ctl->m;
+    const u32 epoch = a.epoch;
+    const DrawKey dk{a.key, (u32)a.ctl->batches, a.stream};
+    const u64 *arcs = plan_final_sel(&a.plans[0]) ? a.arcs1 : a.arcs0;
+    const bool e_sel = plan_final_sel(&a.plans[1]) != 0;
+    const u64 *E = e_sel ? a.ekeys1 : a.ekeys0;
+    for (u64 i = (u64)blockIdx.x * kSweepThreads + threadIdx.x; i < a.r;
+         i += (u64)gridDim.x * kSweepThreads) {
         // the state streams through once: evict-first, so that L2 keeps the
         // directories and sorted arrays the searches hit at random
         u64 f1 = __ldcs(a.f1 + i), f2 = __ldcs(a.f2 + i), chi = __ldcs(a.chi + i);
@@ -366,16 +367,28 @@ static __global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArg
         __stcs(a.chi + i, chi);
         __stcs(a.flags + i, fl);
         if (fl & TC_FLAG_CLOSED) {
-            add = chi;
-            closed = 1;
+            const u64 t = add + chi;
+            hi += t < add ? 1 : 0;
+            add = t;
+            closed += 1;
         }
     }
-    u64 hi = 0;
     block_sum_u128(add, hi, closed, s_lo, s_hi, s_cnt);
     if (threadIdx.x == 0) {
         if (add | hi) add_u128(&a.acc->s_lo, add, hi);
         if (closed) atomicAdd((unsigned long long *)&a.acc->closed, (unsigned long long)closed);
     }
+}
+
+// Blocks of a sweep over r estimators: at most one full wave (the 6 blocks
+// per SM the launch bounds allow), each thread then taking every
+// (blocks x threads)-th estimator.  One resident wave measured 3% faster
+// per batch than one block per 256 estimators at r = 2^20.
+constexpr u32 kSweepBlocksPerSM = 6;
+inline unsigned sweep_blocks(u64 r, int sm_count) {
+    const u64 b = (r + kSweepThreads - 1) / kSweepThreads;
+    const u64 cap = (u64)kSweepBlocksPerSM * (u64)(sm_count > 0 ? sm_count : 1);
+    return (unsigned)(b < cap ? b : cap);
 }
 
 // Close the batch: if accepted, count it and commit the estimate of the new
