@@ -77,6 +77,9 @@ def _args():
                         "(tc_process_batch_ready_async) or fully stream-ordered")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the library's default sort tuning (8-bit digits, ballot ranking)")
+    p.add_argument("--sort-tuning", default=None,
+                   help="A,E,R: fix the sort tuning (arc and Step-3 digit bits, ranking "
+                        "1 match / 2 ballot / 3 atomic-or) instead of autotuning")
     return p.parse_args()
 
 
@@ -289,7 +292,9 @@ def run_gpu(args, rank, world, local_rank):
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
     from paper_1308_2166_gb300 import autotune
-    if args.no_autotune:
+    if args.sort_tuning:
+        tuning, tune_table = tuple(int(x) for x in args.sort_tuning.split(",")), {}
+    elif args.no_autotune:
         tuning, tune_table = (8, 8, 2), {}
     else:
         tuning, tune_table = autotune.tune(dev_batches, r, cfg["vertex_bits"],

@@ -384,8 +384,7 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
             z.ekeys[0], z.ekeys[1], nullptr, nullptr, (u32)w, s.she + p * s.bits_e,
             live_bits(s.hs, s.bits_e, p), p, &plans[1], lbe + (u64)p * le, berr, c->ctl);
     const cudaEvent_t edge_end = mark(c, c->side);
-    const u64 idx_blocks = std::min<u64>((w + 255) / 256, 152 * 16);
-    index_kernel<false><<<(unsigned)idx_blocks, 256, 0, c->side>>>(
+    index_kernel<false><<<index_blocks(w), kIdxThreads, 0, c->side>>>(
         z.ekeys[0], z.ekeys[1], &plans[1], s, z.edir, W, tag, berr);
     TC_CUDA(cudaEventRecord(c->ev_join, c->side));
     for (int p = 0; p < s.npa; ++p)
@@ -396,8 +395,8 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
     if (sort_begin && edge_end && arc_end) c->spans.push_back({sort_begin, arc_end, edge_end});
     if (stages) stamp(c, ms, kArcSort);  // arc passes, with the edge passes beside them
     if (z.adir)
-        index_kernel<true><<<(unsigned)std::min<u64>((2 * w + 255) / 256, 152 * 16), 256, 0,
-                             ms>>>(z.arcs[0], z.arcs[1], &plans[0], s, z.adir, W, tag, berr);
+        index_kernel<true><<<index_blocks(2 * w), kIdxThreads, 0, ms>>>(
+            z.arcs[0], z.arcs[1], &plans[0], s, z.adir, W, tag, berr);
     if (stages) stamp(c, ms, kDups);  // the arc index, beside the rest of the edge branch
     TC_CUDA(cudaStreamWaitEvent(ms, c->ev_join, 0));
     if (stages) stamp(c, ms, kEdgeSort);  // what is left of the edge passes and their index

@@ -171,60 +171,102 @@ __global__ void __launch_bounds__(kMThreads) mprep_kernel(const u64 *__restrict_
 // key compares its edge with those of the rest of its run (almost always
 // empty).
 // Bucket directory over a sorted array: the first key of bucket x writes
-// (tag, start), the last one writes end; x = key >> shift.
-__device__ __forceinline__ void dir_mark(DirEntry *dir, u64 nb, u32 tag, const u64 *K, u64 n,
-                                         u64 i, u64 key, u32 shift) {
+// (tag, start), the last one writes end; x = key >> shift.  prev / next: the
+// neighbouring keys (ignored at the array's ends).
+__device__ __forceinline__ void dir_mark(DirEntry *dir, u64 nb, u32 tag, u64 n, u64 i, u64 key,
+                                         u64 prev_key, u64 next_key, u32 shift) {
     const u64 x = key >> shift;
     if (x >= nb) return;  // only keys of a rejected batch; never looked up
-    const u64 prev = i ? __ldg(K + i - 1) >> shift : ~0ull;
-    const u64 next = i + 1 < n ? __ldg(K + i + 1) >> shift : ~0ull;
+    const u64 prev = i ? prev_key >> shift : ~0ull;
+    const u64 next = i + 1 < n ? next_key >> shift : ~0ull;
     if (x != prev) *reinterpret_cast<u64 *>(&dir[x].epoch) = (i << 32) | tag;
     if (x != next) dir[x].end = (u32)(i + 1);
 }
 
+// Stage keys [t0 - 1, t0 + kIdxTile] of K (n keys) into st[0 .. kIdxTile + 1]
+// with coalesced loads; keys outside the array read as 0.
+__device__ __forceinline__ void stage_tile(u64 *st, const u64 *K, u64 n, u64 t0) {
+    const int tid = threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < kIdxItems; ++j) {
+        const u64 k = t0 + (u64)(j * kIdxThreads + tid);
+        st[1 + j * kIdxThreads + tid] = k < n ? __ldg(K + k) : 0ull;
+    }
+    if (tid == 0) st[0] = t0 ? __ldg(K + t0 - 1) : 0ull;
+    if (tid == 1) st[kIdxTile + 1] = t0 + kIdxTile < n ? __ldg(K + t0 + kIdxTile) : 0ull;
+}
+
 // Arc bucket directory (after the arc sort).
-__global__ void marc_index_kernel(const u64 *arcs0, const u64 *arcs1, const SortPlan *plans,
-                                  RoundShape rs, DirEntry *adir, const u32 *tagp) {
+__global__ void __launch_bounds__(kIdxThreads) marc_index_kernel(const u64 *arcs0,
+                                                                 const u64 *arcs1,
+                                                                 const SortPlan *plans,
+                                                                 RoundShape rs, DirEntry *adir,
+                                                                 const u32 *tagp) {
+    __shared__ u64 st[kIdxTile + 2];
     const u64 *A = plan_final_sel(&plans[0]) ? arcs1 : arcs0;
     const u32 tag = *tagp;
     const u64 n = 2 * rs.Wt;
-    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (u64)gridDim.x * blockDim.x)
-        dir_mark(adir, rs.nba, tag, A, n, i, __ldg(A + i), rs.sha + rs.ha_sh);
+    for (u64 t0 = (u64)blockIdx.x * kIdxTile; t0 < n; t0 += (u64)gridDim.x * kIdxTile) {
+        stage_tile(st, A, n, t0);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kIdxItems; ++j) {
+            const int i = j * kIdxThreads + threadIdx.x;
+            if (t0 + i >= n) break;
+            dir_mark(adir, rs.nba, tag, n, t0 + i, st[1 + i], st[i], st[i + 2],
+                     rs.sha + rs.ha_sh);
+        }
+        __syncthreads();  // the tile is restaged next
+    }
 }
 
 // Step-3 bucket directory and the in-round repeat check (after the Step-3
 // sort).
-__global__ void mdups_kernel(const u64 *ekeys0, const u64 *ekeys1, const u32 *evals0,
-                             const u32 *evals1, const SortPlan *plans,
-                             const u64 *__restrict__ desc, RoundShape rs, u32 *perr,
-                             DirEntry *edir, const u32 *tagp) {
+__global__ void __launch_bounds__(kIdxThreads) mdups_kernel(
+    const u64 *ekeys0, const u64 *ekeys1, const u32 *evals0, const u32 *evals1,
+    const SortPlan *plans, const u64 *__restrict__ desc, RoundShape rs, u32 *perr,
+    DirEntry *edir, const u32 *tagp) {
+    __shared__ u64 st[kIdxTile + 2];
     const Desc d = desc_view(desc, rs.K);
     const bool sel = plan_final_sel(&plans[1]) != 0;
     const u64 *E = sel ? ekeys1 : ekeys0;
     const u32 *EV = sel ? evals1 : evals0;
     const u64 jmask = (1ull << rs.bw) - 1;
     const u32 tag = *tagp;
-    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < rs.Wt;
-         i += (u64)gridDim.x * blockDim.x) {
-        const u64 a = __ldg(E + i);
-        dir_mark(edir, rs.nbe, tag, E, rs.Wt, i, a, rs.she + rs.he_sh);
-        const u64 sa = mkey_sorted(rs, a), pa = mkey_prefix(rs, a);
-        if (i + 1 >= rs.Wt || mkey_sorted(rs, __ldg(E + i + 1)) != sa) continue;
-        const u64 k = rs.eko ? a >> (32 + rs.bw) : a >> 32;
-        const u64 *D = d.ebase[k];
-        const u64 ea = __ldg(D + (rs.eko ? (a & jmask) : __ldg(EV + i)));
-        // a repeat shares the whole hash, so it lies in the run of equal
-        // sorted bits that follows
-        for (u64 j = i + 1; j < rs.Wt; ++j) {
-            const u64 b = __ldg(E + j);
-            if (mkey_sorted(rs, b) != sa) break;
-            if (mkey_prefix(rs, b) != pa) continue;
-            if (__ldg(D + (rs.eko ? (b & jmask) : __ldg(EV + j))) == ea) {
-                atomicOr(&perr[k], kErrInput);
-                break;
+    const u64 n = rs.Wt;
+    for (u64 t0 = (u64)blockIdx.x * kIdxTile; t0 < n; t0 += (u64)gridDim.x * kIdxTile) {
+        stage_tile(st, E, n, t0);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kIdxItems; ++j) {
+            const int ti = j * kIdxThreads + threadIdx.x;
+            const u64 i = t0 + ti;
+            if (i >= n) break;
+            const u64 a = st[1 + ti];
+            dir_mark(edir, rs.nbe, tag, n, i, a, st[ti], st[ti + 2], rs.she + rs.he_sh);
+            const u64 sa = mkey_sorted(rs, a), pa = mkey_prefix(rs, a);
+            if (i + 1 >= n || mkey_sorted(rs, st[ti + 2]) != sa) continue;
+            // a repeat shares the whole hash, so it lies in the run of equal
+            // sorted bits that follows (almost always empty)
+            const u64 k = rs.eko ? a >> (32 + rs.bw) : a >> 32;
+            const u64 *D = d.ebase[k];
+            u64 ea = 0;
+            bool have = false;
+            for (u64 q = i + 1; q < n; ++q) {
+                const u64 b = __ldg(E + q);
+                if (mkey_sorted(rs, b) != sa) break;
+                if (mkey_prefix(rs, b) != pa) continue;
+                if (!have) {
+                    ea = __ldg(D + (rs.eko ? (a & jmask) : __ldg(EV + i)));
+                    have = true;
+                }
+                if (__ldg(D + (rs.eko ? (b & jmask) : __ldg(EV + q))) == ea) {
+                    atomicOr(&perr[k], kErrInput);
+                    break;
+                }
             }
         }
+        __syncthreads();  // the tile is restaged next
     }
 }
 
@@ -828,18 +870,15 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u
             z.ekeys[0], z.ekeys[1], rs.eko ? nullptr : z.evals[0], rs.eko ? nullptr : z.evals[1],
             (u32)Wt, rs.she + p * rs.bits_e, mlive(rs.hs + rs.kb, rs.bits_e, p), p, &plans[1],
             lbe + (u64)p * le, gerr, nullptr);
-    const u64 db = std::min<u64>((Wt + 255) / 256, 1216);
-    mdups_kernel<<<(unsigned)db, 256, 0, M->side>>>(z.ekeys[0], z.ekeys[1], z.evals[0],
-                                                    z.evals[1], plans, desc, rs, perr, z.edir,
-                                                    z.tag);
+    mdups_kernel<<<index_blocks(Wt), kIdxThreads, 0, M->side>>>(
+        z.ekeys[0], z.ekeys[1], z.evals[0], z.evals[1], plans, desc, rs, perr, z.edir, z.tag);
     TCM_CUDA(cudaEventRecord(M->ev_join, M->side));
     for (int p = 0; p < rs.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, ms>>>(
             z.arcs[0], z.arcs[1], nullptr, nullptr, (u32)(2 * Wt), rs.sha + p * rs.bits_a,
             mlive(M->B + rs.kb, rs.bits_a, p), p, &plans[0], lb + (u64)p * la, gerr, nullptr);
-    const u64 ib = std::min<u64>((2 * Wt + 255) / 256, 152 * 16);
-    marc_index_kernel<<<(unsigned)ib, 256, 0, ms>>>(z.arcs[0], z.arcs[1], plans, rs, z.adir,
-                                                    z.tag);
+    marc_index_kernel<<<index_blocks(2 * Wt), kIdxThreads, 0, ms>>>(z.arcs[0], z.arcs[1], plans,
+                                                                   rs, z.adir, z.tag);
     TCM_CUDA(cudaStreamWaitEvent(ms, M->ev_join, 0));
     if (pipelined) {
         TCM_CUDA(cudaEventRecord(M->ev_sorted[b], ms));
