@@ -67,6 +67,7 @@ __host__ __device__ __forceinline__ u32 edge_hash(u64 x) {
 // counters.
 // ---------------------------------------------------------------------------
 constexpr int kPrepThreads = 256;
+constexpr int kPrepItems = 4;  // edges per thread whose loads are issued together
 
 static __global__ void __launch_bounds__(kPrepThreads) prep_kernel(
     const u64 *__restrict__ W, BatchShape s, u64 *__restrict__ arcs0, u64 *__restrict__ ekeys0,
@@ -82,24 +83,37 @@ static __global__ void __launch_bounds__(kPrepThreads) prep_kernel(
     const u64 id_lim = (s.B >= 32) ? (1ull << 32) : (1ull << s.B);
     const u32 wm1 = s.w - 1;
     bool bad = false;
-    for (u64 j = (u64)blockIdx.x * kPrepThreads + threadIdx.x; j < s.w;
-         j += (u64)gridDim.x * kPrepThreads) {
-        const u64 e = W[j];
-        const u64 u = e >> 32, v = e & kMask32;
-        bad |= !(u < v) || v >= id_lim;
-        const u64 rpos = (u64)(wm1 - (u32)j) << 1;
-        const u64 au = (u << s.sha) | rpos;
-        const u64 av = (v << s.sha) | rpos | 1ull;
-        reinterpret_cast<ulonglong2 *>(arcs0)[wm1 - (u32)j] = make_ulonglong2(au, av);
-        for (int p = 0; p < s.npa; ++p) {
-            atomicAdd(&h[p * ra + digit_bits(au, s.sha + p * s.bits_a, ma)], 1u);
-            atomicAdd(&h[p * ra + digit_bits(av, s.sha + p * s.bits_a, ma)], 1u);
+    const u64 stride = (u64)gridDim.x * kPrepThreads;
+    for (u64 j0 = (u64)blockIdx.x * kPrepThreads + threadIdx.x; j0 < s.w;
+         j0 += kPrepItems * stride) {
+        // the group's loads first, all in flight together
+        u64 eg[kPrepItems];
+#pragma unroll
+        for (int t = 0; t < kPrepItems; ++t) {
+            const u64 j = j0 + t * stride;
+            eg[t] = j < s.w ? W[j] : 0ull;
         }
-        if (build_edges) {
-            const u64 ek = ((u64)edge_hash(e) << s.bw) | j;
-            ekeys0[j] = ek;
-            for (int p = 0; p < s.npe; ++p)
-                atomicAdd(&he[p * re + digit_bits(ek, s.she + p * s.bits_e, me)], 1u);
+#pragma unroll
+        for (int t = 0; t < kPrepItems; ++t) {
+            const u64 j = j0 + t * stride;
+            if (j >= s.w) break;
+            const u64 e = eg[t];
+            const u64 u = e >> 32, v = e & kMask32;
+            bad |= !(u < v) || v >= id_lim;
+            const u64 rpos = (u64)(wm1 - (u32)j) << 1;
+            const u64 au = (u << s.sha) | rpos;
+            const u64 av = (v << s.sha) | rpos | 1ull;
+            reinterpret_cast<ulonglong2 *>(arcs0)[wm1 - (u32)j] = make_ulonglong2(au, av);
+            for (int p = 0; p < s.npa; ++p) {
+                atomicAdd(&h[p * ra + digit_bits(au, s.sha + p * s.bits_a, ma)], 1u);
+                atomicAdd(&h[p * ra + digit_bits(av, s.sha + p * s.bits_a, ma)], 1u);
+            }
+            if (build_edges) {
+                const u64 ek = ((u64)edge_hash(e) << s.bw) | j;
+                ekeys0[j] = ek;
+                for (int p = 0; p < s.npe; ++p)
+                    atomicAdd(&he[p * re + digit_bits(ek, s.she + p * s.bits_e, me)], 1u);
+            }
         }
     }
     if (bad) set_error(err, kErrInput);
