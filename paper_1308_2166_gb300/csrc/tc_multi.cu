@@ -311,6 +311,20 @@ __device__ __forceinline__ void vertex_arcs(const DirEntry *adir, u32 tag, const
                                             const RoundShape &rs, u64 x, u64 &start, u64 &end) {
     u64 lo, hi;
     dir_segment(adir, tag, x >> rs.ha_sh, 2 * rs.Wt, lo, hi);
+    if (lo < hi) {
+        // the bucket's first and last keys: usually the bucket holds one
+        // vertex (or x is outside it), which settles the run at once
+        const u64 p0 = __ldg(arcs + lo) >> rs.sha, p1 = __ldg(arcs + hi - 1) >> rs.sha;
+        if (p0 == x && p1 == x) {
+            start = lo;
+            end = hi;
+            return;
+        }
+        if (x < p0 || x > p1) {
+            start = end = lo;
+            return;
+        }
+    }
     start = lower_bound_range(arcs, lo, hi, x << rs.sha);
     // first key past the prefix: compare prefixes (x + 1 << sha may not fit)
     u64 n = hi - start;
@@ -601,11 +615,11 @@ u64 zeroed_bytes_for(u32 sb, u64 w_max_round, u32 vertex_bits) {
 }
 
 // Bucket bits of the two round directories for Wt edges (at most, before
-// the clamp to the sorted bits): about 2 Wt / 4 arc buckets and Wt / 4
-// Step-3 buckets.
+// the clamp to the sorted bits): between 2 Wt and 4 Wt arc buckets (a
+// bucket then mostly holds one vertex's arcs; 3% faster rounds at 512
+// streams than 2 Wt / 4) and about Wt / 4 Step-3 buckets.
 u32 arc_dir_bits(u64 Wt) {
-    const u32 b = mbits_for(2 * Wt - 1);
-    return b > 3 ? b - 2 : 1;
+    return mbits_for(2 * Wt - 1);
 }
 u32 edge_dir_bits(u64 Wt) {
     const u32 b = mbits_for(Wt - 1);
