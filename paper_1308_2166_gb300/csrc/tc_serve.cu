@@ -43,6 +43,10 @@ using namespace tc;
 
 namespace {
 
+// Bytes of pool memory mapped when a server starts (at most the budget left
+// after the fixed scratch).
+constexpr u64 kPoolWarmBytes = 16ull << 30;
+
 struct Req {
     u64 ticket = 0;
     int kind = 0;
@@ -586,6 +590,17 @@ int tc_server_create(const tc_server_config_t *cfg, tc_server **out) {
         // never make the copy stream wait for the compute stream to reuse memory
         ok &= ok && cudaMemPoolSetAttribute(Sv->pool, cudaMemPoolReuseAllowInternalDependencies,
                                             &no) == cudaSuccess;
+        // map the pool's memory up front (up to 16 GB of the budget): growing
+        // it while requests wait would stall the scheduler thread; the pool
+        // keeps what it maps (release threshold: everything)
+        const u64 warm = std::min<u64>(cfg->budget_bytes - fixed, kPoolWarmBytes);
+        void *wp = nullptr;
+        if (ok && warm && cudaMallocFromPoolAsync(&wp, warm, Sv->pool, Sv->cs) == cudaSuccess) {
+            ok &= cudaFreeAsync(wp, Sv->cs) == cudaSuccess;
+            ok &= ok && cudaStreamSynchronize(Sv->cs) == cudaSuccess;
+        } else {
+            cudaGetLastError();  // not enough memory to warm: the pool grows on demand
+        }
     }
     Sv->d_out.assign(nbuf, nullptr);
     Sv->h_out.assign(nbuf, nullptr);
