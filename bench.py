@@ -432,6 +432,9 @@ def run_gpu(args, rank, world, local_rank):
                   "pass's start to the later sort's end (CUDA events on both streams)",
         "traffic": None,
         "share_of_step": ms_sort / t_ms if t_ms else None,
+        "limiter": "integer issue: the pass's ALU pipe is 69-71% busy while DRAM is ~20% busy "
+                   "(ncu, profiles/onesweep_pass_rmat20.md); HBM is the bound the pass's data "
+                   "movement allows, the fraction shows the distance to it",
     }
     tr = TRAFFIC.get("onesweep_pass_kernel")
     if tr and tr.get("src_hash") == _src_hash():
