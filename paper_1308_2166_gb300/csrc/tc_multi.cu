@@ -341,7 +341,9 @@ __device__ __forceinline__ void vertex_arcs(const DirEntry *adir, u32 tag, const
     end = (u64)(base - arcs);
 }
 
-__global__ void __launch_bounds__(kMThreads, 5) msweep_kernel(MSweepArgs a) {
+// 6 blocks per SM (40 registers, with some spills to local memory) measured
+// 2% faster rounds than 5 (48 registers) or 4 (64).
+__global__ void __launch_bounds__(kMThreads, 6) msweep_kernel(MSweepArgs a) {
     __shared__ u32 s_k[2];
     if (ld_relaxed(a.gerr)) return;
     const u64 g0 = (u64)blockIdx.x * kMThreads;
