@@ -150,7 +150,7 @@ class ClockSampler:
                     reasons.add(name)
         return {"sm_mhz": statistics.median(r["sm"] for r in rows),
                 "sm_max_mhz": max(r["smax"] for r in rows), "reasons": sorted(reasons),
-                "samples": len(rows)}
+                "samples": len(rows), "sm_mhz_min": min(r["sm"] for r in rows)}
 
 
 def _cpu_baseline(keys, cfg, budget_s=20.0):
@@ -889,8 +889,10 @@ def run_serve(args, rank, world, local_rank):
     b2b = _serve_phase(tc, graphs, cfg, S, max(3.0, secs / 2), cap_edges=3 * cfg["w_max_round"],
                        max_round_streams=1)
     req_rate = 0.7 * sat["edges_per_s"] / max(1.0, sat["mean_batch"]) / 0.9
+    sampler = ClockSampler(local_rank)
     poi = _serve_phase(tc, graphs, cfg, S, secs, rate=req_rate)
     poi50 = _serve_phase(tc, graphs, cfg, S, secs, rate=req_rate * 5 / 7)
+    clocks_poisson = sampler.stop()
     line = {
         "metric": "aggregate edges/s served: 4096 concurrent streams, continuous batching",
         "value": sat["edges_per_s"], "unit": UNIT, "n_gpus": 1, "steps": sat["rounds"],
@@ -910,6 +912,7 @@ def run_serve(args, rank, world, local_rank):
         "speedup_vs_back_to_back": sat["edges_per_s"] / max(1.0, b2b["edges_per_s"]),
         "poisson": dict(poi, offered_requests_per_s=req_rate),
         "poisson_50": dict(poi50, offered_requests_per_s=req_rate * 5 / 7),
+        "clocks_poisson": clocks_poisson,
         "p50_ms": poi["p50_batch_ms"], "p99_ms": poi["p99_batch_ms"],
         "e2e": {"value": sat["edges_per_s"], "unit": UNIT, "h2d_bytes_per_step":
                 8 * sat["edges"] // max(1, sat["rounds"]),
