@@ -442,17 +442,18 @@ def run_gpu(args, rank, world, local_rank):
     # algorithmic bytes of the whole step: this design's minimal passes (arcs
     # on the src bits, Step-3 keys on the top bits of a 32-bit edge hash --
     # whole 8-bit digits covering the bw - 2 bucket bits -- with the position
-    # packed below it) and the survey's formula (arcs on src + position,
-    # Step-3 keys on (u, v), a u32 position value once 2B + bw > 64)
+    # packed below it) and the paper's layout (arcs sorted on src + position,
+    # the Step-3 `edges` array on (u, v), a u32 position value once
+    # 2B + bw > 64; 8-bit digits, 32-byte state read and written once)
     bw = max(1, (w - 1).bit_length())
     B = cfg["vertex_bits"]
     pa = -(-B // 8)
     pe = -(-(bw - 2 if bw > 3 else 1) // 8)
     own_bytes = 32 * w + pa * 2 * w * 16 + pe * w * 16 + 8 * w + 2 * 28 * r
-    pe_s = -(-2 * B // 8)
-    e_bytes_s = 16 if 2 * B + bw <= 64 else 24
-    survey_bytes = 8 * w + (2 * w * 8 + (-(-(B + bw) // 8)) * 2 * w * 16) + \
-        (w * 8 + pe_s * w * e_bytes_s) + 64 * r
+    pe_p = -(-2 * B // 8)
+    e_bytes_p = 16 if 2 * B + bw <= 64 else 24
+    paper_bytes = 8 * w + (2 * w * 8 + (-(-(B + bw) // 8)) * 2 * w * 16) + \
+        (w * 8 + pe_p * w * e_bytes_p) + 64 * r
     step_s = (t_ms / 1e3) / args.steps
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -476,8 +477,8 @@ def run_gpu(args, rank, world, local_rank):
         "step_hbm_frac": {
             "own_min_bytes_per_step": own_bytes,
             "frac_own": own_bytes / step_s / 1e9 / peak,
-            "survey_min_bytes_per_step": survey_bytes,
-            "frac_survey": survey_bytes / step_s / 1e9 / peak,
+            "paper_layout_min_bytes_per_step": paper_bytes,
+            "frac_paper_layout": paper_bytes / step_s / 1e9 / peak,
         },
         "roofline": roofline,
         "gpu_launches": prof["launches"],
