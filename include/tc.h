@@ -202,13 +202,17 @@ typedef struct {
     double ms_sort_wall;          /* wall time of both sorts' digit passes:
                                      from their start to the later end */
 } tc_profile_t;
+/* Batches enqueued by the pipelined calls (tc_process_batch_ready_async,
+ * tc_process_batch_host_async) run their sort phase on the library's own
+ * streams: for them only ms_sweep, ms_finish, ms_estimate and ms_sort_wall
+ * are recorded. */
 
 int tc_profile_begin(tc_ctx *c);
 int tc_profile_end(tc_ctx *c, tc_profile_t *out);
 
 /* Launch tuning of the two radix sorts (rankAll's arcs, Lemma 4.3; Step 3's
- * edges, Sec. 4.4).  arc_digit_bits / edge_digit_bits: 0 (automatic: the
- * fewest passes over the live key bits), 8, 10 or 11.  ranking (how a warp
+ * edges, Sec. 4.4).  arc_digit_bits / edge_digit_bits: 0 (automatic: 8-bit
+ * digits over the live key bits, measured fastest), 8, 10 or 11.  ranking (how a warp
  * finds the lanes holding equal digits): 0 or 2 = one ballot per digit bit
  * (the default), 1 = one match.any per key, 3 = lanes OR their bit into a
  * shared-memory word per (warp, digit; 8-bit digits only, else match.any).
@@ -391,7 +395,10 @@ typedef struct {
 
 /* Errors: TC_ERR_INVAL (bad config; key bits as tc_multi_create with
  * S = max_streams), TC_ERR_RANGE (budget below the fixed scratch),
- * TC_ERR_NOMEM, TC_ERR_CUDA.  Uses the current CUDA device. */
+ * TC_ERR_NOMEM, TC_ERR_CUDA.  Uses the current CUDA device.  The server's
+ * memory pool (stream state and batch copies) maps min(16 GB, budget minus
+ * the fixed scratch) at creation, so admitting requests never waits for the
+ * pool to grow that far; it keeps what it maps until tc_server_destroy. */
 int tc_server_create(const tc_server_config_t *cfg, tc_server **out);
 
 /* Request a new stream with r estimators (1..2^32-1), Philox seed and stream
