@@ -307,10 +307,32 @@ __device__ __forceinline__ bool warp_segment_sum(u32 key, u64 &lo, u64 &hi, u64 
 
 // The arcs [start, end) of vertex prefix x = (k, pi(src)): its bucket's
 // range from the directory, then the run of keys with that prefix in it.
+// First index in [lo, hi) of the sorted array a with a[idx] >= key (hi if
+// none).  Indices are 32-bit: a round holds fewer than 2^29 arcs.
+__device__ __forceinline__ u32 lower_bound32(const u64 *__restrict__ a, u32 lo, u32 hi,
+                                             u64 key) {
+    u32 n = hi - lo;
+    while (n > 0) {
+        const u32 half = n >> 1;
+        if (__ldg(a + lo + half) < key) {
+            lo += half + 1;
+            n -= half + 1;
+        } else {
+            n = half;
+        }
+    }
+    return lo;
+}
+
+// The arcs [start, end) of vertex prefix x = (k, pi(src)): its bucket's
+// range from the directory, then the run of keys with that prefix in it.
 __device__ __forceinline__ void vertex_arcs(const DirEntry *adir, u32 tag, const u64 *arcs,
-                                            const RoundShape &rs, u64 x, u64 &start, u64 &end) {
-    u64 lo, hi;
-    dir_segment(adir, tag, x >> rs.ha_sh, 2 * rs.Wt, lo, hi);
+                                            const RoundShape &rs, u64 x, u32 &start, u32 &end) {
+    const uint4 e = __ldg(reinterpret_cast<const uint4 *>(adir + (x >> rs.ha_sh)));
+    const u32 n_arcs = (u32)(2 * rs.Wt);
+    const bool hit = e.x == tag;
+    // (clamped to start <= end <= n, as dir_segment)
+    const u32 hi = hit ? min(e.z, n_arcs) : 0u, lo = hit ? min(e.y, hi) : 0u;
     if (lo < hi) {
         // the bucket's first and last keys: usually the bucket holds one
         // vertex (or x is outside it), which settles the run at once
@@ -325,24 +347,24 @@ __device__ __forceinline__ void vertex_arcs(const DirEntry *adir, u32 tag, const
             return;
         }
     }
-    start = lower_bound_range(arcs, lo, hi, x << rs.sha);
+    start = lower_bound32(arcs, lo, hi, x << rs.sha);
     // first key past the prefix: compare prefixes (x + 1 << sha may not fit)
-    u64 n = hi - start;
-    const u64 *base = arcs + start;
+    u32 b = start, n = hi - start;
     while (n > 0) {
-        const u64 half = n >> 1;
-        if ((__ldg(base + half) >> rs.sha) <= x) {
-            base += half + 1;
+        const u32 half = n >> 1;
+        if ((__ldg(arcs + b + half) >> rs.sha) <= x) {
+            b += half + 1;
             n -= half + 1;
         } else {
             n = half;
         }
     }
-    end = (u64)(base - arcs);
+    end = b;
 }
 
-// 6 blocks per SM (40 registers, with some spills to local memory) measured
-// 2% faster rounds than 5 (48 registers) or 4 (64).
+// 6 blocks per SM (40 registers) measured 2% faster rounds than 5 or 4.
+// Positions and indices are 32-bit (a round holds fewer than 2^29 arcs and a
+// stream fewer than 2^32 estimators), which keeps the live registers down.
 __global__ void __launch_bounds__(kMThreads, 6) msweep_kernel(MSweepArgs a) {
     __shared__ u32 s_k[2];
     if (ld_relaxed(a.gerr)) return;
@@ -365,60 +387,57 @@ __global__ void __launch_bounds__(kMThreads, 6) msweep_kernel(MSweepArgs a) {
             else hi = mid;
         }
         k = lo;
-        const u64 e0 = __ldg(d.eoff + k), ws = __ldg(d.eoff + k + 1) - e0;
+        const u32 ws = (u32)(__ldg(d.eoff + k + 1) - __ldg(d.eoff + k));
         MStream &st = a.ms[__ldg(d.slot + k)];
         if (ws > 0 && !ld_relaxed(a.perr + k)) {
-            const u64 i = g - __ldg(d.roff + k);
+            const u32 i = (u32)(g - __ldg(d.roff + k));
             const u64 m = st.m;
             const DrawKey dk{st.key, (u32)st.batches, st.stream_id};
             const u64 *D = d.ebase[k];
             u64 *const F1 = st.f1, *const F2 = st.f2, *const CHI = st.chi;
             u32 *const FL = st.flags;
             const u64 *arcs = plan_final_sel(&a.plans[0]) ? a.arcs1 : a.arcs0;
-            const bool es = plan_final_sel(&a.plans[1]) != 0;
-            const u64 *E = es ? a.ekeys1 : a.ekeys0;
-            const u32 *EV = es ? a.evals1 : a.evals0;
-            const u64 wmask = (1ull << rs.bw) - 1;
+            const u32 wmask = (u32)((1ull << rs.bw) - 1);
             const u32 tag = *a.tag;
             // the state streams through once: evict-first, so that L2 keeps
             // the directories and sorted arrays the searches hit at random
             u64 f1 = __ldcs(F1 + i), f2 = __ldcs(F2 + i), chi = __ldcs(CHI + i);
             u32 fl = __ldcs(FL + i);
             // ---- Step 1 (Sec. 4.2)
-            const u64 x = draw_bounded(dk, (u32)i, kStep1, m + ws);
+            const u64 x = draw_bounded(dk, i, kStep1, m + ws);
             const bool new1 = x >= m;
-            u64 p1 = 0;
+            u32 p1 = 0;
             if (new1) {
-                p1 = x - m;
+                p1 = (u32)(x - m);
                 f1 = __ldg(D + p1);
                 chi = 0;
                 f2 = kEmpty;
                 fl = 0;
             }
             // ---- Step 2 (Sec. 4.3): each endpoint's arcs, from its bucket
-            const u64 u = f1 >> 32, v = f1 & kMask32;
-            const u64 xu = ((u64)k << rs.B) | vperm(rs, u), xv = ((u64)k << rs.B) | vperm(rs, v);
-            u64 su, eu, sv, ev;
+            const u64 xu = ((u64)k << rs.B) | vperm(rs, f1 >> 32);
+            const u64 xv = ((u64)k << rs.B) | vperm(rs, f1 & kMask32);
+            u32 su, eu, sv, ev;
             vertex_arcs(a.adir, tag, arcs, rs, xu, su, eu);
             vertex_arcs(a.adir, tag, arcs, rs, xv, sv, ev);
-            u64 ld, rd;
+            u32 ld, rd;
             if (new1) {
-                const u64 rp = (ws - 1 - p1) << 1;
-                ld = lower_bound_range(arcs, su, eu, (xu << rs.sha) | rp) - su;
-                rd = lower_bound_range(arcs, sv, ev, (xv << rs.sha) | rp) - sv;
+                const u64 rp = (u64)(ws - 1 - p1) << 1;
+                ld = lower_bound32(arcs, su, eu, (xu << rs.sha) | rp) - su;
+                rd = lower_bound32(arcs, sv, ev, (xv << rs.sha) | rp) - sv;
             } else {
                 ld = eu - su;
                 rd = ev - sv;
             }
-            const u64 chi_plus = ld + rd;
+            const u64 chi_plus = (u64)ld + rd;
             bool new2 = false;
-            u64 p2 = 0;
+            u32 p2 = 0;
             if (chi_plus > 0) {
-                const u64 y = draw_bounded(dk, (u32)i, kStep2, chi + chi_plus);
+                const u64 y = draw_bounded(dk, i, kStep2, chi + chi_plus);
                 if (y >= chi) {
-                    const u64 phi = y - chi;
-                    const u64 q = (phi < ld) ? su + phi : sv + (phi - ld);
-                    p2 = ws - 1 - ((__ldg(arcs + q) >> 1) & wmask);
+                    const u32 phi = (u32)(y - chi);
+                    const u32 q = (phi < ld) ? su + phi : sv + (phi - ld);
+                    p2 = ws - 1 - ((u32)(__ldg(arcs + q) >> 1) & wmask);
                     f2 = __ldg(D + p2);
                     fl &= ~TC_FLAG_CLOSED;
                     new2 = true;
@@ -435,13 +454,17 @@ __global__ void __launch_bounds__(kMThreads, 6) msweep_kernel(MSweepArgs a) {
                 const u64 gkey = (gu << 32) | gv;
                 const u64 probe = mkey(rs, k, edge_hash(gkey), 0);
                 const u64 pp = mkey_prefix(rs, probe), ps = mkey_sorted(rs, probe);
-                u64 lo, hi;
-                dir_segment(a.edir, tag, ps >> rs.he_sh, rs.Wt, lo, hi);
-                for (u64 q = lower_bound_range(E, lo, hi, ps << rs.she); q < hi; ++q) {
+                const bool es = plan_final_sel(&a.plans[1]) != 0;
+                const u64 *E = es ? a.ekeys1 : a.ekeys0;
+                const u32 *EV = es ? a.evals1 : a.evals0;
+                u64 lo64, hi64;
+                dir_segment(a.edir, tag, ps >> rs.he_sh, rs.Wt, lo64, hi64);
+                const u32 qhi = (u32)hi64;
+                for (u32 q = lower_bound32(E, (u32)lo64, qhi, ps << rs.she); q < qhi; ++q) {
                     const u64 ek = __ldg(E + q);
                     if (mkey_sorted(rs, ek) != ps) break;
                     if (mkey_prefix(rs, ek) != pp) continue;
-                    const u64 pq = rs.eko ? (ek & wmask) : __ldg(EV + q);
+                    const u32 pq = rs.eko ? ((u32)ek & wmask) : __ldg(EV + q);
                     if (__ldg(D + pq) == gkey) {
                         if (!new2 || pq > p2) fl |= TC_FLAG_CLOSED;
                         break;
