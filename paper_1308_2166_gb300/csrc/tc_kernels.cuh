@@ -149,6 +149,29 @@ __device__ __forceinline__ void dir_segment(const DirEntry *dir, u32 epoch, u64 
     start = s0 < end ? s0 : end;
 }
 
+// The same with 32-bit bounds (n < 2^32).
+__device__ __forceinline__ void dir_segment32(const DirEntry *dir, u32 epoch, u64 x, u32 n,
+                                              u32 &start, u32 &end) {
+    const uint4 e = __ldg(reinterpret_cast<const uint4 *>(dir + x));
+    const bool hit = e.x == epoch;
+    end = hit ? min(e.z, n) : 0u;
+    start = hit ? min(e.y, end) : 0u;
+}
+
+// lower_bound_range with 32-bit indices (loop count depends only on the
+// range length, so a warp's lanes stay converged).
+__device__ __forceinline__ u32 lower_bound_idx32(const u64 *__restrict__ a, u32 lo, u32 hi,
+                                                 u64 key) {
+    const u64 *base = a + lo;
+    u32 len = hi - lo;
+    while (len > 1) {
+        const u32 half = len >> 1;
+        base = (__ldg(base + half - 1) < key) ? base + half : base;
+        len -= half;
+    }
+    return (u32)(base - a) + ((len == 1 && __ldg(base) < key) ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------------------
 // Directories over the two sorted arrays, plus the in-batch repeat check.
 // For the arcs, x = src; for the Step-3 keys, x = the smaller endpoint.  The
@@ -311,9 +334,9 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
                                           const u64 *__restrict__ E, u64 &f1, u64 &f2, u64 &chi,
                                           u32 &fl) {
     const BatchShape &s = a.s;
-    const u64 n_arcs = 2ull * s.w;
+    const u32 n_arcs = 2u * s.w;
     const u32 wm1 = s.w - 1;
-    const u64 wmask = (1ull << s.bw) - 1;
+    const u32 wmask = (u32)((1ull << s.bw) - 1);
 
     // ---- Step 1 (Sec. 4.2): level-1 reservoir over E u W
     const u64 x = draw_bounded(dk, (u32)i, kStep1, m + s.w);
@@ -328,35 +351,38 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
     }
 
     // ---- Step 2 (Sec. 4.3): chi+ = rank(u->v) + rank(v->u), coin, rank-select
+    // (positions and indices are 32-bit: a batch has fewer than 2^29 arcs)
     const u64 u = f1 >> 32, v = f1 & kMask32;
-    u64 su, eu, sv, ev;
+    u32 su, eu, sv, ev;
     if constexpr (kDir) {
-        dir_segment(a.adir, epoch, u, n_arcs, su, eu);
-        dir_segment(a.adir, epoch, v, n_arcs, sv, ev);
+        dir_segment32(a.adir, epoch, u, n_arcs, su, eu);
+        dir_segment32(a.adir, epoch, v, n_arcs, sv, ev);
     } else {
-        arc_segment(arcs, n_arcs, s.sha, u, su, eu);
-        arc_segment(arcs, n_arcs, s.sha, v, sv, ev);
+        u64 s0, e0, s1, e1;
+        arc_segment(arcs, n_arcs, s.sha, u, s0, e0);
+        arc_segment(arcs, n_arcs, s.sha, v, s1, e1);
+        su = (u32)s0, eu = (u32)e0, sv = (u32)s1, ev = (u32)e1;
     }
-    u64 ld, rd;
+    u32 ld, rd;
     if (new1) {
         // rank of the arc (x, p1): its offset inside the src segment
         const u64 rp = (u64)(wm1 - p1) << 1;
-        ld = lower_bound_range(arcs, su, eu, (u << s.sha) | rp) - su;
-        rd = lower_bound_range(arcs, sv, ev, (v << s.sha) | rp) - sv;
+        ld = lower_bound_idx32(arcs, su, eu, (u << s.sha) | rp) - su;
+        rd = lower_bound_idx32(arcs, sv, ev, (v << s.sha) | rp) - sv;
     } else {
         ld = eu - su;  // deg_W(u): Def. 4.2 for a pair outside W
         rd = ev - sv;
     }
-    const u64 chi_plus = ld + rd;
+    const u64 chi_plus = (u64)ld + rd;
     bool new2 = false;
     u32 p2 = 0;
     if (chi_plus > 0) {
         const u64 y = draw_bounded(dk, (u32)i, kStep2, chi + chi_plus);
         if (y >= chi) {
-            const u64 phi = y - chi;
-            const u64 k = (phi < ld) ? su + phi : sv + (phi - ld);
+            const u32 phi = (u32)(y - chi);
+            const u32 k = (phi < ld) ? su + phi : sv + (phi - ld);
             const u64 akey = __ldg(arcs + k);
-            p2 = wm1 - (u32)((akey >> 1) & wmask);
+            p2 = wm1 - ((u32)(akey >> 1) & wmask);
             f2 = __ldg(a.W + p2);
             fl &= ~TC_FLAG_CLOSED;
             new2 = true;
@@ -368,18 +394,18 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
     // bucket and sorted hash bits; the candidates with its whole hash are
     // checked against W itself
     if (f2 != kEmpty && !(fl & TC_FLAG_CLOSED)) {
-        u64 gu, gv, lo, hi;
+        u64 gu, gv;
+        u32 lo, hi;
         closing_pair(f1, f2, gu, gv);
         const u64 g = (gu << 32) | gv;
         const u64 h = edge_hash(g);
         const u64 hp = h >> (32 - s.hs);  // the sorted bits
-        dir_segment(a.edir, epoch, h >> (32 - s.hb), s.w, lo, hi);
-        u64 k = lower_bound_range(E, lo, hi, hp << s.she);
-        for (; k < hi; ++k) {
+        dir_segment32(a.edir, epoch, h >> (32 - s.hb), s.w, lo, hi);
+        for (u32 k = lower_bound_idx32(E, lo, hi, hp << s.she); k < hi; ++k) {
             const u64 ek = __ldg(E + k);
             if ((ek >> s.she) != hp) break;
             if ((ek >> s.bw) != h) continue;
-            const u32 q = (u32)(ek & wmask);
+            const u32 q = (u32)ek & wmask;
             if (__ldg(a.W + q) == g) {
                 if (!new2 || q > p2) fl |= TC_FLAG_CLOSED;
                 break;
