@@ -362,10 +362,11 @@ __device__ __forceinline__ void vertex_arcs(const DirEntry *adir, u32 tag, const
     end = b;
 }
 
-// 6 blocks per SM (40 registers) measured 2% faster rounds than 5 or 4.
 // Positions and indices are 32-bit (a round holds fewer than 2^29 arcs and a
-// stream fewer than 2^32 estimators), which keeps the live registers down.
-__global__ void __launch_bounds__(kMThreads, 6) msweep_kernel(MSweepArgs a) {
+// stream fewer than 2^32 estimators), which keeps the live registers down;
+// at 7 blocks per SM (32 registers, some spills to local memory) rounds were
+// 3% faster than at 6 and 5.
+__global__ void __launch_bounds__(kMThreads, 7) msweep_kernel(MSweepArgs a) {
     __shared__ u32 s_k[2];
     if (ld_relaxed(a.gerr)) return;
     const u64 g0 = (u64)blockIdx.x * kMThreads;
