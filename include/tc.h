@@ -56,15 +56,20 @@ typedef struct tc_ctx tc_ctx;
 /* Result of tc_estimate (Lemma 3.1 aggregated by the plain mean).
  *   S = sum of chi over the estimators whose wedge is closed (128-bit),
  *   N = |E| * S (128-bit, exact), tau_hat = N / r as a double computed as
- *   q + rem / r with q = N div r. */
+ *   q + rem / r with q = N div r (q rounded to nearest, rem / r one correctly
+ *   rounded division, then one rounded addition).  The first six fields are
+ *   the problem statement's result (N, r, |E|, closed count, tau_hat); S and
+ *   the batch count follow.  Every call that returns an estimate -- host or
+ *   device record, one stream or many -- forms it with the same arithmetic,
+ *   so the records agree bit for bit.  72 bytes, no padding. */
 typedef struct {
-    uint64_t sum_lo, sum_hi;   /* S */
     uint64_t num_lo, num_hi;   /* N = m * S */
     uint64_t r;                /* estimators */
     uint64_t m;                /* |E|: edges folded in so far */
     uint64_t n_closed;         /* estimators with a closed wedge */
-    uint64_t batches;          /* batches folded in so far */
     double tau_hat;            /* N / r (display value; N is exact) */
+    uint64_t sum_lo, sum_hi;   /* S */
+    uint64_t batches;          /* batches folded in so far */
 } tc_estimate_t;
 
 /* Create a stream of r >= 1 estimators (Sec. 4.1: est_1..est_r), all empty,
@@ -145,13 +150,13 @@ int tc_sync(tc_ctx *c);
  * Synchronises (returns a pending device-side error first, as tc_sync). */
 int tc_estimate(tc_ctx *c, tc_estimate_t *out);
 
-/* Enqueue, on `cuda_stream`, the copy of the current estimate to the DEVICE
- * array d_out without waiting: four uint64 -- S low word, S high word, the
- * closed count, and |E| -- as of the last batch enqueued before it on the
- * same stream (N = |E| * S and tau_hat = N / r are then formed by the
- * caller).  d_out is borrowed until the stream passes this point.  Errors:
- * TC_ERR_INVAL, TC_ERR_CUDA. */
-int tc_estimate_async(tc_ctx *c, uint64_t *d_out, void *cuda_stream);
+/* Enqueue, on `cuda_stream`, one small kernel that writes the current
+ * estimate -- as of the last batch enqueued before it on the same stream --
+ * to the DEVICE record *d_out, laid out as tc_estimate_t (N, tau_hat and
+ * all), without waiting.  The record equals what tc_estimate would return at
+ * that point.  d_out must be 8-byte aligned and is borrowed until the stream
+ * passes this point.  Errors: TC_ERR_INVAL, TC_ERR_CUDA. */
+int tc_estimate_async(tc_ctx *c, tc_estimate_t *d_out, void *cuda_stream);
 
 /* Median-of-means aggregate (Sec. 3.1; the paper's implementation, Sec. 5):
  * estimators are split into g contiguous groups, group k holding indices
@@ -310,10 +315,11 @@ int tc_multi_sync(tc_multi *M, int32_t *stream_errors);
 /* Lemma 3.1's estimate of stream s, as tc_estimate.  Synchronises. */
 int tc_multi_estimate(tc_multi *M, uint32_t s, tc_estimate_t *out);
 
-/* Enqueue the copy of every stream's estimate words (S low, S high, closed
- * count, |E|; four uint64 per stream, stream-major) to the DEVICE array
- * d_out[4*S] on `cuda_stream`. */
-int tc_multi_estimates_async(tc_multi *M, uint64_t *d_out, void *cuda_stream);
+/* Enqueue, on `cuda_stream`, one kernel that writes every stream's estimate
+ * record (as tc_multi_estimate would return it) to the DEVICE array
+ * d_out[S] of tc_estimate_t.  A slot that holds no stream gets a zero record
+ * with r = 0. */
+int tc_multi_estimates_async(tc_multi *M, tc_estimate_t *d_out, void *cuda_stream);
 
 /* Stream s's estimator state into HOST arrays of r[s] entries (as
  * tc_get_state), and its counters.  Synchronise. */
@@ -381,6 +387,10 @@ typedef struct {
     /* host steady-clock nanoseconds since tc_server_create: submitted,
      * admitted (slot/memory granted), completion recorded */
     uint64_t t_submit_ns, t_admit_ns, t_done_ns;
+    /* batch and query: N = m * S (128-bit) and tau_hat = N / r, formed as in
+     * tc_estimate_t; zero for open and close */
+    uint64_t num_lo, num_hi;
+    double tau_hat;
 } tc_completion_t;
 
 typedef struct {

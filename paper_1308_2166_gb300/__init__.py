@@ -52,11 +52,33 @@ class TcError(RuntimeError):
 
 
 class tc_estimate_t(ctypes.Structure):
-    _fields_ = [("sum_lo", ctypes.c_uint64), ("sum_hi", ctypes.c_uint64),
-                ("num_lo", ctypes.c_uint64), ("num_hi", ctypes.c_uint64),
+    _fields_ = [("num_lo", ctypes.c_uint64), ("num_hi", ctypes.c_uint64),
                 ("r", ctypes.c_uint64), ("m", ctypes.c_uint64),
-                ("n_closed", ctypes.c_uint64), ("batches", ctypes.c_uint64),
-                ("tau_hat", ctypes.c_double)]
+                ("n_closed", ctypes.c_uint64), ("tau_hat", ctypes.c_double),
+                ("sum_lo", ctypes.c_uint64), ("sum_hi", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64)]
+
+
+# Bytes of one tc_estimate_t record (tc_estimate_async writes one to device
+# memory, tc_multi_estimates_async one per stream).
+ESTIMATE_BYTES = ctypes.sizeof(tc_estimate_t)
+
+
+def _estimate_dict(out: tc_estimate_t) -> dict:
+    return {"N": out.num_lo | (out.num_hi << 64), "r": out.r, "m": out.m,
+            "n_closed": out.n_closed, "tau_hat": out.tau_hat,
+            "S": out.sum_lo | (out.sum_hi << 64), "batches": out.batches}
+
+
+def estimate_records(buf) -> list:
+    """Field view of tc_estimate_t records copied to host memory (a numpy
+    array or CPU tensor holding n * ESTIMATE_BYTES bytes): one dict per
+    record.  Reads the fields only; the library formed every value."""
+    import numpy as np
+    raw = np.ascontiguousarray(buf.numpy() if hasattr(buf, "numpy") else buf).view(np.uint8)
+    n = raw.size // ESTIMATE_BYTES
+    return [_estimate_dict(tc_estimate_t.from_buffer_copy(
+        raw[k * ESTIMATE_BYTES:(k + 1) * ESTIMATE_BYTES].tobytes())) for k in range(n)]
 
 
 class tc_profile_t(ctypes.Structure):
@@ -81,7 +103,9 @@ class tc_completion_t(ctypes.Structure):
                 ("batches", ctypes.c_uint64), ("sum_lo", ctypes.c_uint64),
                 ("sum_hi", ctypes.c_uint64), ("n_closed", ctypes.c_uint64),
                 ("m", ctypes.c_uint64), ("t_submit_ns", ctypes.c_uint64),
-                ("t_admit_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64)]
+                ("t_admit_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64),
+                ("num_lo", ctypes.c_uint64), ("num_hi", ctypes.c_uint64),
+                ("tau_hat", ctypes.c_double)]
 
 
 _STATS_FIELDS = ("rounds", "kernel_launches", "batches", "rejected", "edges", "queries", "opens",
@@ -256,23 +280,13 @@ def tc_sync(ctx: int) -> None:
 def tc_estimate(ctx: int) -> dict:
     out = tc_estimate_t()
     _check(load().tc_estimate(ctx, ctypes.byref(out)), "tc_estimate")
-    return {"S": out.sum_lo | (out.sum_hi << 64), "N": out.num_lo | (out.num_hi << 64),
-            "r": out.r, "m": out.m, "n_closed": out.n_closed, "batches": out.batches,
-            "tau_hat": out.tau_hat}
+    return _estimate_dict(out)
 
 
 def tc_estimate_async(ctx: int, d_out, stream: int = 0) -> None:
-    """Enqueue the reduction; d_out: device array of 4 uint64 (S lo, S hi, closed, m)."""
+    """Enqueue the estimate record; d_out: device buffer of at least
+    ESTIMATE_BYTES bytes (8-byte aligned), laid out as tc_estimate_t."""
     _check(load().tc_estimate_async(ctx, _ptr(d_out), stream or None), "tc_estimate_async")
-
-
-def estimate_from_words(words, r: int) -> dict:
-    """Host-side finish of tc_estimate_async's four words (N = m * S exactly)."""
-    S = int(words[0]) | (int(words[1]) << 64)
-    m = int(words[3])
-    N = m * S
-    q, rem = divmod(N, r)
-    return {"S": S, "N": N, "n_closed": int(words[2]), "m": m, "tau_hat": q + rem / r}
 
 
 def tc_profile_begin(ctx: int) -> None:
@@ -476,11 +490,11 @@ class MultiStream:
     def estimate(self, s: int) -> dict:
         out = tc_estimate_t()
         _check(load().tc_multi_estimate(self.h, s, ctypes.byref(out)), "tc_multi_estimate")
-        return {"S": out.sum_lo | (out.sum_hi << 64), "N": out.num_lo | (out.num_hi << 64),
-                "r": out.r, "m": out.m, "n_closed": out.n_closed, "batches": out.batches,
-                "tau_hat": out.tau_hat}
+        return _estimate_dict(out)
 
     def estimates_async(self, d_out, stream: int = 0):
+        """Every stream's tc_estimate_t record into the device buffer d_out
+        (at least S * ESTIMATE_BYTES bytes)."""
         _check(load().tc_multi_estimates_async(self.h, _ptr(d_out), stream or None),
                "tc_multi_estimates_async")
 
@@ -534,7 +548,7 @@ def _completion_dtype():
             ("ticket", "<u8"), ("handle", "<u4"), ("kind", "<i4"), ("status", "<i4"),
             ("pad", "<u4"), ("batches", "<u8"), ("sum_lo", "<u8"), ("sum_hi", "<u8"),
             ("n_closed", "<u8"), ("m", "<u8"), ("t_submit_ns", "<u8"), ("t_admit_ns", "<u8"),
-            ("t_done_ns", "<u8")])
+            ("t_done_ns", "<u8"), ("num_lo", "<u8"), ("num_hi", "<u8"), ("tau_hat", "<f8")])
         assert COMPLETION_DTYPE.itemsize == ctypes.sizeof(tc_completion_t)
     return COMPLETION_DTYPE
 

@@ -2,6 +2,8 @@
 // per-batch launch sequence of bulkUpdateAll (Sec. 4), the estimate of
 // Lemma 3.1, stage timing and the standalone rankAll (Lemma 4.3).
 #include <algorithm>
+#include <atomic>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -666,13 +668,15 @@ int tc_get_counters(tc_ctx *c, uint64_t *r, uint64_t *m, uint64_t *batches) {
     return TC_OK;
 }
 
-int tc_estimate_async(tc_ctx *c, uint64_t *d_out, void *cuda_stream) {
-    if (!c || !d_out) return TC_ERR_INVAL;
+int tc_estimate_async(tc_ctx *c, tc_estimate_t *d_out, void *cuda_stream) {
+    if (!c || !d_out || (reinterpret_cast<uintptr_t>(d_out) & 7)) return TC_ERR_INVAL;
     // The sweep reduced S and the closed count of the new state, and the
-    // batch's finish step committed them with |E|: copy the four words.
+    // batch's finish step committed them with |E|: form the record from them.
     cudaStream_t st = (cudaStream_t)cuda_stream;
     stamp(c, st, kStart);
-    TC_CUDA(cudaMemcpyAsync(d_out, c->ctl->est, 4 * sizeof(u64), cudaMemcpyDeviceToDevice, st));
+    estimate_record_kernel<<<1, 1, 0, st>>>(c->ctl, c->r, d_out);
+    TC_CUDA(cudaGetLastError());
+    c->launches += 1;
     stamp(c, st, kEstimate);
     return TC_OK;
 }
@@ -681,21 +685,8 @@ int tc_estimate(tc_ctx *c, tc_estimate_t *out) {
     if (!c || !out) return TC_ERR_INVAL;
     int rc = tc_sync(c);
     if (rc) return rc;
-    using u128 = unsigned __int128;
     const Control &h = *c->h_ctl;
-    const u128 S = ((u128)h.est[1] << 64) | h.est[0];
-    const u64 m = h.m;
-    const u128 N = S * (u128)m;
-    out->sum_lo = (u64)S;
-    out->sum_hi = (u64)(S >> 64);
-    out->num_lo = (u64)N;
-    out->num_hi = (u64)(N >> 64);
-    out->r = c->r;
-    out->m = m;
-    out->n_closed = h.est[2];
-    out->batches = h.batches;
-    const u128 q = N / c->r, rem = N % c->r;
-    out->tau_hat = (double)q + (double)rem / (double)c->r;
+    finish_estimate(h.est[0], h.est[1], h.est[2], h.est[3], c->r, h.batches, out);
     return TC_OK;
 }
 
@@ -895,8 +886,8 @@ namespace {
 
 constexpr u64 kNoAllocArcs = 2ull * TC_NOALLOC_MAX_EDGES;
 constexpr u64 kNoAllocPlanBytes = 2 * sizeof(SortPlan);
-// Look-back words for any vertex width: at most 3 passes of <= 11-bit digits
-// over the arcs (reserved for 4).
+// Look-back words for any vertex width: at most 4 passes (8-bit digits over
+// 32 vertex bits), each reserved for the widest (11-bit) digits.
 constexpr u64 kNoAllocLookbackWords =
     4ull * ((kNoAllocArcs / kSortTile + kLookWin - 1) / kLookWin * kLookWin) * kMaxRadix;
 constexpr u64 align256(u64 x) { return (x + 255) / 256 * 256; }
@@ -911,20 +902,25 @@ constexpr u64 kNoAllocScratchBytes = kNoAllocOffArcs1 + align256(kNoAllocArcs * 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kNoAllocMaxDevices = 64;
-unsigned char *g_noalloc_addr[kNoAllocMaxDevices] = {};
+// Per-device cache of the scratch's device address.  Host threads may make
+// their first calls at the same time: every one of them stores the same
+// value, through an atomic so that the race is well defined.
+std::atomic<unsigned char *> g_noalloc_addr[kNoAllocMaxDevices] = {};
 
 // Device address of the scratch on the current device (looked up once per
-// device, on that device's first call).
+// device, on that device's first call, with that device current).
 int noalloc_scratch(unsigned char **out) {
     int dev = 0;
     TC_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kNoAllocMaxDevices) return TC_ERR_INVAL;
-    if (!g_noalloc_addr[dev]) {
+    unsigned char *addr = g_noalloc_addr[dev].load(std::memory_order_relaxed);
+    if (!addr) {
         void *p = nullptr;
         TC_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
-        g_noalloc_addr[dev] = static_cast<unsigned char *>(p);
+        addr = static_cast<unsigned char *>(p);
+        g_noalloc_addr[dev].store(addr, std::memory_order_relaxed);
     }
-    *out = g_noalloc_addr[dev];
+    *out = addr;
     return TC_OK;
 }
 
@@ -954,26 +950,38 @@ extern "C" int tc_rank_all_noalloc(const uint64_t *d_edges, uint64_t w, uint32_t
     u64 *a0 = reinterpret_cast<u64 *>(z + kNoAllocOffArcs0);
     u64 *a1 = reinterpret_cast<u64 *>(z + kNoAllocOffArcs1);
     // The array keeps the previous call's contents: clear the histograms,
-    // tile counters, this call's look-back words and the error word.
-    TC_CUDA(cudaMemsetAsync(z, 0, kNoAllocPlanBytes, st));
-    TC_CUDA(cudaMemsetAsync(lb, 0, (u64)s.npa * la * sizeof(u32), st));
-    TC_CUDA(cudaMemsetAsync(err, 0, sizeof(u32), st));
-    const u64 prep_blocks = std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
-    prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, prep_smem(s, false), st>>>(
-        d_edges, s, a0, nullptr, plans, err, 0);
-    sort_plan_kernel<<<dim3((unsigned)s.npa, 1), 256, 0, st>>>(plans, s.npa, (u32)(2 * w),
-                                                               s.bits_a, 0, 0, 8);
-    for (int p = 0; p < s.npa; ++p)
-        ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(a0, a1, nullptr, nullptr, (u32)(2 * w),
-                                                         s.sha + p * s.bits_a, live_bits(s.B, s.bits_a, p), p, &plans[0],
-                                                         lb + (u64)p * la, err, nullptr);
-    const u64 rb = (2 * w + kRankTile - 1) / kRankTile;
-    rank_out_kernel<<<(unsigned)rb, kRankThreads, 0, st>>>(d_edges, a0, a1, &plans[0], s, d_src,
-                                                           d_dst, d_pos, d_rank);
-    TC_CUDA(cudaGetLastError());
+    // tile counters, this call's look-back words and the error word.  On a
+    // failure part-way, the stream is still drained before returning, so
+    // that no work of this call is left running on the shared array when
+    // the caller issues the next one.
+    cudaError_t e = cudaMemsetAsync(z, 0, kNoAllocPlanBytes, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(lb, 0, (u64)s.npa * la * sizeof(u32), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(u32), st);
     u32 h_err = 0;
-    TC_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(u32), cudaMemcpyDeviceToHost, st));
-    TC_CUDA(cudaStreamSynchronize(st));
+    if (e == cudaSuccess) {
+        const u64 prep_blocks =
+            std::min<u64>((w + kPrepThreads * 8 - 1) / (kPrepThreads * 8), 1216);
+        prep_kernel<<<(unsigned)prep_blocks, kPrepThreads, prep_smem(s, false), st>>>(
+            d_edges, s, a0, nullptr, plans, err, 0);
+        sort_plan_kernel<<<dim3((unsigned)s.npa, 1), 256, 0, st>>>(plans, s.npa, (u32)(2 * w),
+                                                                   s.bits_a, 0, 0, 8);
+        for (int p = 0; p < s.npa; ++p)
+            ka.fn<<<(unsigned)ta, ka.threads, ka.smem, st>>>(
+                a0, a1, nullptr, nullptr, (u32)(2 * w), s.sha + p * s.bits_a,
+                live_bits(s.B, s.bits_a, p), p, &plans[0], lb + (u64)p * la, err, nullptr);
+        const u64 rb = (2 * w + kRankTile - 1) / kRankTile;
+        rank_out_kernel<<<(unsigned)rb, kRankThreads, 0, st>>>(d_edges, a0, a1, &plans[0], s,
+                                                               d_src, d_dst, d_pos, d_rank);
+        e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&h_err, err, sizeof(u32), cudaMemcpyDeviceToHost, st);
+    }
+    const cudaError_t e_sync = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = e_sync;
+    if (e != cudaSuccess) {
+        last_cuda_error() = e;
+        return TC_ERR_CUDA;
+    }
     return map_device_error(h_err & kErrTimeout);
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cmath>
 #include <cuda_runtime.h>
 
 #include "tc.h"
@@ -88,6 +89,59 @@ __device__ __forceinline__ u64 lower_bound_u64(const u64 *__restrict__ a, u64 n,
 __device__ __forceinline__ u64 lower_bound_range(const u64 *__restrict__ a, u64 lo, u64 hi,
                                                  u64 key) {
     return lo + lower_bound_u64(a + lo, hi - lo, key);
+}
+
+// ---------------------------------------------------------------------------
+// Lemma 3.1's estimate from the committed sums, shared by host and device so
+// that every entry point returns the same record bit for bit: N = m * S
+// exactly in 128 bits, tau_hat = q + rem / r with q = N div r (q converted
+// to double with round-to-nearest-even, rem / r one correctly rounded
+// division of two exact doubles, then one rounded addition).
+// ---------------------------------------------------------------------------
+using u128 = unsigned __int128;
+
+__host__ __device__ __forceinline__ double u64_to_double_rn(u64 x) {
+#ifdef __CUDA_ARCH__
+    return __ull2double_rn(x);
+#else
+    return (double)x;  // correctly rounded under the default rounding mode
+#endif
+}
+
+// Round-to-nearest-even conversion of a 128-bit unsigned integer: the top 64
+// significant bits are converted with the bits shifted out below them folded
+// into bit 0 as a sticky bit (bit 0 lies below the rounding point, so it can
+// only break an exact tie, as those bits do).
+__host__ __device__ __forceinline__ double u128_to_double_rn(u128 x) {
+    const u64 hi = (u64)(x >> 64), lo = (u64)x;
+    if (hi == 0) return u64_to_double_rn(lo);
+#ifdef __CUDA_ARCH__
+    const int s = __clzll((long long)hi);
+#else
+    const int s = __builtin_clzll(hi);
+#endif
+    const u64 top = s ? (hi << s) | (lo >> (64 - s)) : hi;
+    const u64 below = s ? lo << s : lo;
+    const double t = u64_to_double_rn(top | (below != 0 ? 1ull : 0ull));
+    return ldexp(t, 64 - s);  // exact: a power-of-two scaling in range
+}
+
+__host__ __device__ __forceinline__ void finish_estimate(u64 s_lo, u64 s_hi, u64 closed, u64 m,
+                                                         u64 r, u64 batches,
+                                                         tc_estimate_t *out) {
+    const u128 S = ((u128)s_hi << 64) | s_lo;
+    const u128 N = S * (u128)m;
+    out->num_lo = (u64)N;
+    out->num_hi = (u64)(N >> 64);
+    out->r = r;
+    out->m = m;
+    out->n_closed = closed;
+    const u128 q = N / r;
+    const u64 rem = (u64)(N % r);
+    out->tau_hat = u128_to_double_rn(q) + (double)rem / (double)r;
+    out->sum_lo = s_lo;
+    out->sum_hi = s_hi;
+    out->batches = batches;
 }
 
 __host__ __device__ __forceinline__ u32 bits_for(u64 x) {

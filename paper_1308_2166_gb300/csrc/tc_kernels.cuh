@@ -483,6 +483,12 @@ static __global__ void finish_kernel(Control *ctl, const BatchAcc *acc, const u3
     ctl->epoch += 1;
 }
 
+// tc_estimate_async: the committed estimate as a tc_estimate_t record in
+// device memory (one thread; the same arithmetic as the host's tc_estimate).
+static __global__ void estimate_record_kernel(const Control *ctl, u64 r, tc_estimate_t *out) {
+    finish_estimate(ctl->est[0], ctl->est[1], ctl->est[2], ctl->est[3], r, ctl->batches, out);
+}
+
 // Median-of-means groups: CTA k sums group k = [k*r/g, (k+1)*r/g) into
 // out[2k], out[2k+1] (128-bit).
 constexpr int kReduceThreads = 256;

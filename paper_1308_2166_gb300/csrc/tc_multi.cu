@@ -34,6 +34,7 @@
 //   sweep       one thread per estimator of the participants only (roff).
 //   bw = bits of (max_k w_k) - 1, kb = bits of K-1, B = vertex id bits.
 #include <algorithm>
+#include <cstdint>
 #include <cstddef>
 #include <cstring>
 #include <new>
@@ -526,6 +527,19 @@ __global__ void mfinish_kernel(MStream *ms, const u64 *__restrict__ desc, u32 K,
     }
     if (out) write_record(out + (u64)k * kRecordWords, e, st);
     st.acc[0] = st.acc[1] = st.acc[2] = 0;
+}
+
+// tc_multi_estimates_async: every slot's estimate record (zero for an empty
+// slot), formed as tc_multi_estimate forms it on the host.
+__global__ void mestimate_kernel(const MStream *ms, u32 S, tc_estimate_t *out) {
+    const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const MStream &st = ms[s];
+    if (st.r == 0) {
+        out[s] = tc_estimate_t{};
+        return;
+    }
+    finish_estimate(st.est[0], st.est[1], st.est[2], st.m, st.r, st.batches, out + s);
 }
 
 __global__ void mgather_kernel(const MStream *ms, const u32 *slots, u32 Q, u64 *out) {
@@ -1153,29 +1167,16 @@ int tc_multi_estimate(tc_multi *M, uint32_t s, tc_estimate_t *out) {
     TCM_CUDA(cudaDeviceSynchronize());
     MStream h{};
     TCM_CUDA(cudaMemcpy(&h, M->ms + s, sizeof(MStream), cudaMemcpyDeviceToHost));
-    using u128 = unsigned __int128;
-    const u128 S = ((u128)h.est[1] << 64) | h.est[0];
-    const u128 N = S * (u128)h.m;
-    out->sum_lo = (u64)S;
-    out->sum_hi = (u64)(S >> 64);
-    out->num_lo = (u64)N;
-    out->num_hi = (u64)(N >> 64);
-    out->r = h.r;
-    out->m = h.m;
-    out->n_closed = h.est[2];
-    out->batches = h.batches;
-    const u128 q = N / h.r, rem = N % h.r;
-    out->tau_hat = (double)q + (double)rem / (double)h.r;
+    finish_estimate(h.est[0], h.est[1], h.est[2], h.m, h.r, h.batches, out);
     return TC_OK;
 }
 
-int tc_multi_estimates_async(tc_multi *M, uint64_t *d_out, void *cuda_stream) {
-    if (!M || !d_out) return TC_ERR_INVAL;
-    const unsigned char *est0 =
-        reinterpret_cast<const unsigned char *>(M->ms) + offsetof(MStream, est);
-    TCM_CUDA(cudaMemcpy2DAsync(d_out, 4 * sizeof(u64), est0, sizeof(MStream),
-                               4 * sizeof(u64), M->S, cudaMemcpyDeviceToDevice,
-                               (cudaStream_t)cuda_stream));
+int tc_multi_estimates_async(tc_multi *M, tc_estimate_t *d_out, void *cuda_stream) {
+    if (!M || !d_out || (reinterpret_cast<uintptr_t>(d_out) & 7)) return TC_ERR_INVAL;
+    mestimate_kernel<<<(M->S + 127) / 128, 128, 0, (cudaStream_t)cuda_stream>>>(M->ms, M->S,
+                                                                               d_out);
+    TCM_CUDA(cudaGetLastError());
+    M->launches += 1;
     return TC_OK;
 }
 

@@ -65,6 +65,7 @@ struct Req {
 
 struct Slot {
     u32 handle = 0;
+    u64 r = 0;  // the stream's estimators
     void *state = nullptr;
     u64 state_bytes = 0;
     bool used = false;
@@ -162,6 +163,13 @@ void tc_server::complete(const Req &q, int status, const u64 *rec) {
         c.sum_hi = rec[3];
         c.n_closed = rec[4];
         c.m = rec[5];
+        if (q.r) {
+            tc_estimate_t e;
+            finish_estimate(c.sum_lo, c.sum_hi, c.n_closed, c.m, q.r, c.batches, &e);
+            c.num_lo = e.num_lo;
+            c.num_hi = e.num_hi;
+            c.tau_hat = e.tau_hat;
+        }
     }
     c.t_submit_ns = q.t_submit;
     c.t_admit_ns = q.t_admit;
@@ -220,6 +228,7 @@ bool tc_server::admit() {
                 }
                 Slot &sl = slots[s];
                 sl.handle = q.handle;
+                sl.r = q.r;
                 sl.state = p;
                 sl.state_bytes = b;
                 sl.used = true;
@@ -312,6 +321,7 @@ bool tc_server::form_round() {
                     break;
                 }
                 qslots.push_back(s);
+                h.r = sl.r;
                 R.queries.push_back(std::move(h));
                 sl.q.pop_front();
                 continue;
@@ -334,6 +344,7 @@ bool tc_server::form_round() {
                 wait_seq = h.seq;
                 wait_ev = h.ev;
             }
+            h.r = sl.r;
             R.batches.push_back(std::move(h));
             sl.q.pop_front();
             break;

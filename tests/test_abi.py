@@ -6,6 +6,8 @@ tc_strerror, which touches no device state.
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -60,3 +62,51 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(tc, "_lib", None)
     with pytest.raises(RuntimeError):
         tc.load(str(tmp_path / "nope.so"))
+
+
+def _c_offsets(tmp_path, struct, fields):
+    """offsetof() of each field and sizeof(struct) as the C compiler lays out
+    the struct from include/tc.h."""
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "off.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tc.h"', 'int main(void) {']
+    for f in fields:
+        lines.append(f'  printf("%zu\\n", offsetof({struct}, {f}));')
+    lines.append(f'  printf("%zu\\n", sizeof({struct}));')
+    lines.append('  return 0; }')
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "off"
+    subprocess.check_call([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    vals = [int(x) for x in subprocess.check_output([str(exe)]).split()]
+    return vals[:-1], vals[-1]
+
+
+@pytest.mark.parametrize("struct,cls", [("tc_estimate_t", tc.tc_estimate_t),
+                                        ("tc_profile_t", tc.tc_profile_t),
+                                        ("tc_completion_t", tc.tc_completion_t),
+                                        ("tc_server_config_t", tc.tc_server_config_t),
+                                        ("tc_server_stats_t", tc.tc_server_stats_t)])
+def test_struct_layout_matches_header(tmp_path, struct, cls):
+    fields = [f for f, _ in cls._fields_]
+    offs, size = _c_offsets(tmp_path, struct, fields)
+    assert offs == [getattr(cls, f).offset for f in fields], struct
+    assert size == ctypes.sizeof(cls), struct
+
+
+def test_estimate_record_leads_with_problem_statement_fields():
+    # the problem statement's result first: N (128-bit), r, |E|, the closed
+    # count and tau_hat, then S and the batch count
+    names = [f for f, _ in tc.tc_estimate_t._fields_]
+    assert names[:6] == ["num_lo", "num_hi", "r", "m", "n_closed", "tau_hat"]
+    assert tc.ESTIMATE_BYTES == 72
+
+
+def test_completion_dtype_matches_struct():
+    import numpy as np
+    dt = tc._completion_dtype()
+    assert dt.itemsize == ctypes.sizeof(tc.tc_completion_t)
+    for name, _ in tc.tc_completion_t._fields_:
+        assert dt.fields[name][1] == getattr(tc.tc_completion_t, name).offset, name
+    assert np.dtype(dt.fields["tau_hat"][0]) == np.float64

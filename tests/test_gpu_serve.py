@@ -141,7 +141,8 @@ def _run_mix_many(srv, specs, plans, rng, chunk=7):
 
 
 def _alone(spec, plan, vertex_bits, bad=()):
-    """Expected (batches, S, closed, m) after each op of the plan, alone."""
+    """Expected (batches, S, closed, m, N, tau_hat) after each op of the plan,
+    alone."""
     r, seed, sid = spec
     ctx = tc.tc_create_ex(r, seed, sid, 4096, vertex_bits)
     out = []
@@ -150,7 +151,7 @@ def _alone(spec, plan, vertex_bits, bad=()):
             if op[0] == "b" and i not in bad:
                 tc.tc_process_batch(ctx, to_device(op[1]))
             e = tc.tc_estimate(ctx)
-            out.append((e["batches"], e["S"], e["n_closed"], e["m"]))
+            out.append((e["batches"], e["S"], e["n_closed"], e["m"], e["N"], e["tau_hat"]))
     finally:
         tc.tc_destroy(ctx)
     return out
@@ -175,7 +176,8 @@ def _check(where, done, specs, plans, vertex_bits, bad=None):
         else:
             assert c["status"] == tc.TC_OK, (s, i, c["status"])
         got = (int(c["batches"]), int(c["sum_lo"]) | (int(c["sum_hi"]) << 64),
-               int(c["n_closed"]), int(c["m"]))
+               int(c["n_closed"]), int(c["m"]), int(c["num_lo"]) | (int(c["num_hi"]) << 64),
+               float(c["tau_hat"]))
         # (a rejected batch reports the unchanged stream: the alone run skips it)
         assert got == expect[s][i], (s, i, got, expect[s][i])
 

@@ -40,7 +40,14 @@ def _host(outs):
 
 def test_noalloc_matches_allocating_rank_all_twice():
     keys = synth.finish(synth.chung_lu(1 << 14, 2.3, 30.0, 200000, seed=31), 1 << 14, seed=32)
-    calls = [(keys[:150001], 14), (keys[7:7 + tc.TC_NOALLOC_MAX_EDGES // 2], 32)]
+    big = synth.finish(synth.chung_lu(1 << 17, 2.3, 8.0, tc.TC_NOALLOC_MAX_EDGES, seed=33),
+                       1 << 17, seed=34)
+    # two calls in a row (the second finds the first's leftovers), then the
+    # largest accepted batch at 32-bit ids: both arc buffers full and the
+    # most look-back words (four 8-bit digit passes)
+    calls = [(keys[:150001], 14), (keys[7:7 + tc.TC_NOALLOC_MAX_EDGES // 2], 32),
+             (big, 32)]
+    assert big.size == tc.TC_NOALLOC_MAX_EDGES
     for W, vb in calls:
         d = _dev(W)
         ref = _outs(2 * W.size)
