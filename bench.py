@@ -2,17 +2,21 @@
 """Benchmark of the bulk neighborhood-sampling update on GB300.
 
 One step = one pass of the whole update over one batch of the synthetic
-stream (key build, both radix sorts, the fused Steps 1-3 sweep, batch
-bookkeeping) plus the 128-bit estimate reduction.  Default workload: R-MAT
-scale 20 (edge factor 16, (0.57, 0.19, 0.19, 0.05), about 15.7M edges),
-r = 2^20 estimators, w = 2^22 edges per batch; batches cycle through the
-stream with the estimator state carried on (steps beyond the stream's four
-batches replay it, which the update treats as new arrivals).
+stream (key build, both radix sorts and their directories, the fused
+Steps 1-3 sweep, batch bookkeeping) plus the estimate record of Lemma 3.1.
+Default workload: the large Chung-Lu stream (exponent 2.1, n = 2^25,
+expected degrees with mean 71.5 capped at 3e5, 1.2e9 edges in random order,
+drawn on the GPU), r = 2^24 estimators, w = 2^24 edges per batch.  Every
+step folds in a new batch of the stream (no batch is replayed): the warm-up
+steps, the timed steps, the end-to-end steps and the stage split take
+consecutive batches of one stream.  Short streams (the R-MAT scale-20 graph
+has 3.7 batches) are run as one stream after another, each on a fresh
+context, so that every context sees every edge once.
 
 `value` is device time (CUDA events on the launching stream) with every
-batch already resident in HBM; `e2e` is the same metric through the
-synchronous C-ABI call with pinned HOST batches, the H2D copy of each batch
-and the D2H read of each step's estimate inside the timed region.
+batch already resident in HBM; `e2e` is the same metric through the C-ABI
+host-input call with pinned HOST batches, the H2D copy of each batch and the
+D2H read of each step's estimate record inside the timed region.
 
 --impl reference times the CPU oracle (the plain numpy implementation the
 tests check the GPU against) on the host cores, on a bounded sample.
@@ -26,6 +30,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -41,12 +46,12 @@ if ROOT not in sys.path:
 METRIC = "edges/s (device-timed bulk estimator update)"
 UNIT = "edges/s"
 
-# ncu DRAM traffic of the dominant kernel, per algorithmic byte, with the
-# hash of the source it was taken on (profiles/ holds the capture summary).
-# Taken from profiles/onesweep_pass_rmat20.md: DRAM read + write of two arc
-# passes over their algorithmic bytes (writes largely stay in L2), valid
-# while the pass kernel's sources hash the same.
+# ncu DRAM traffic of a kernel per algorithmic byte, with the hash of the
+# sources it was measured on: the figure is reported only while the kernel's
+# sources hash the same (a changed kernel reports traffic null).
 TRAFFIC = {
+    # two rmat20 arc passes: 167.7 MB of DRAM read + write over 268.4 MB of
+    # algorithmic bytes (the passes' writes largely stay in L2)
     "onesweep_pass_kernel": {"src_hash": "1f2e5f68f12875e3",
                              "bytes_per_algorithmic_byte": 167.717888 / 268.435456},
 }
@@ -66,11 +71,17 @@ def _src_hash() -> str:
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=200)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    p.add_argument("--workload", choices=["rmat20", "tiny", "large", "multi512", "serve4096", "wsweep"], default="rmat20")
+    p.add_argument("--workload", choices=["large", "rmat20", "tiny", "multi512", "serve4096",
+                                          "wsweep", "accuracy"], default="large")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the extra keys of the default line (rmat20, multi512)")
+    p.add_argument("--stream-edges", type=int, default=None,
+                   help="large workload: edges of the generated stream (default the whole "
+                        "1.2e9; a smaller stream keeps profiler captures small)")
     p.add_argument("--e2e-steps", type=int, default=None)
     p.add_argument("--pipeline", choices=["on", "off"], default="on",
                    help="single stream: sort each batch beside the previous batch's sweep "
@@ -81,19 +92,6 @@ def _args():
                    help="A,E,R: fix the sort tuning (arc and Step-3 digit bits, ranking "
                         "1 match / 2 ballot / 3 atomic-or) instead of autotuning")
     return p.parse_args()
-
-
-def _workload(name):
-    import synth
-    cfg = dict(synth.WORKLOADS[name], name=name)
-    if name == "rmat20":
-        keys = synth.rmat20_single()
-    elif name == "large":
-        keys = synth.large_prefix(2)     # the first two batches of the 1.2e9-edge stream
-    else:
-        keys = synth.tiny_chung_lu()
-    cfg["m"] = int(keys.size)
-    return cfg, keys
 
 
 def _peaks():
@@ -153,28 +151,6 @@ class ClockSampler:
                 "samples": len(rows), "sm_mhz_min": min(r["sm"] for r in rows)}
 
 
-def _cpu_baseline(keys, cfg, budget_s=20.0):
-    """Time the oracle on the first batches of the same workload (full r, w)."""
-    from oracle import nbsi_bulk
-    import synth
-    ref = nbsi_bulk.BulkStream(cfg["r"], seed=cfg["seed"], vertex_bits=cfg["vertex_bits"])
-    done, t_all, cpu_all, nb = 0, 0.0, 0.0, 0
-    for W in synth.batches(keys, cfg["w"]):
-        t0, c0 = time.perf_counter(), time.process_time()
-        ref.process_batch(W)
-        t_all += time.perf_counter() - t0
-        cpu_all += time.process_time() - c0
-        done += W.size
-        nb += 1
-        if t_all >= budget_s:
-            break
-    return {"value": done / t_all, "unit": UNIT,
-            "cores": max(1, round(cpu_all / t_all)), "cores_available": os.cpu_count(),
-            "kind": "oracle",
-            "sample": f"first {nb} batch(es) ({done} edges) of the stream at r={cfg['r']}, "
-                      f"w={cfg['w']}, single process, {t_all:.1f} s"}
-
-
 def reduce_over_ranks(dist, t, units, device):
     """Whole-job timing of replicas: the slowest rank's time and the units
     (edges) of all ranks; (t, units) unchanged without a process group."""
@@ -188,36 +164,145 @@ def reduce_over_ranks(dist, t, units, device):
     return float(tt.item()), float(uu.item())
 
 
-def _l2_note(cfg, n_batches):
-    w, r = cfg["w"], cfg["r"]
-    ws = 8 * w + 2 * 16 * w + 2 * 8 * w + 28 * r
-    return (f"working set per step {ws / 2**20:.0f} MB (batch, arcs x2, edge keys x2, state) vs "
-            f"the 126 MB L2; each step reads a batch untouched for the previous "
-            f"{n_batches - 1} steps" if ws > 126 * 2**20 else
-            f"working set per step {ws / 2**20:.1f} MB fits in L2 (launch-bound case)")
+# ---------------------------------------------------------------------------
+# Algorithmic bytes of one batch (w edges into r estimators, B-bit ids)
+# ---------------------------------------------------------------------------
+
+def paper_layout_bytes(w: int, r: int, B: int) -> int:
+    """The minimal passes of the paper's layout: batch read 8w; arc sort
+    (histogram read 16w, ceil((B + bw)/8) 8-bit passes over 2w 16-byte
+    key moves: the arcs sorted on src and position); `edges` sort (histogram
+    read 8w, ceil(2B/8) passes of w keys, 24 bytes each once a u32 position
+    value has to ride beside the 2B key bits); 32-byte state read and
+    written once (64 r)."""
+    bw = max(1, (w - 1).bit_length())
+    pa = -(-(B + bw) // 8)
+    pe = -(-(2 * B) // 8)
+    e_bytes = 16 if 2 * B + bw <= 64 else 24
+    return 8 * w + (2 * w * 8 + pa * 2 * w * 16) + (w * 8 + pe * w * e_bytes) + 64 * r
 
 
-def _accuracy(tc, cfg, keys, dev_batches, rank):
-    """One pass over the whole stream on a fresh context (untimed): tau_hat
-    against the exact count stored in tests/golden/exact_tau.json (by a
-    script that calls only the CPU exact counter) when the generated stream
-    hashes the same, and the epsilon that Theorem 3.2's sample bound gives
-    for this r at delta = 0.05."""
-    import hashlib
-    import math
+def own_design_bytes(w: int, r: int, B: int, arc_digit_bits: int = 8,
+                     edge_digit_bits: int = 8) -> int:
+    """This design's minimal passes: key build (read 8w, write 2w arc keys
+    and w Step-3 keys, 24w); arc passes on the src bits only, each moving 2w
+    keys of 8 bytes in and out; Step-3 passes over the top of a 32-bit edge
+    hash (whole digits covering the bw - 2 bucket bits), w keys each; the
+    directory pass reads of the sorted Step-3 keys (8w); the 28-byte state
+    read and written once (56 r)."""
+    bw = max(1, (w - 1).bit_length())
+    hb = bw - 2 if bw > 3 else 1
+    pa = -(-B // arc_digit_bits)
+    pe = -(-hb // edge_digit_bits)
+    return 32 * w + pa * 2 * w * 16 + pe * w * 16 + 8 * w + 56 * r
+
+
+# ---------------------------------------------------------------------------
+# Single-stream workloads
+# ---------------------------------------------------------------------------
+
+def _single_workload(name, stream_edges=None):
+    """(cfg, streams, host_keys): streams is a list of device batch lists
+    (views of one int64 tensor per stream); host_keys the stream as numpy
+    uint64 when it was generated on the host (None for the large stream)."""
+    import torch
+    import synth
+    cfg = dict(synth.WORKLOADS[name], name=name)
+    w = cfg["w"]
+    if name == "large":
+        m = stream_edges or synth.LARGE_EDGES
+        dev = synth.large_stream_device(m)
+        host = None
+    else:
+        host = synth.rmat20_single() if name == "rmat20" else synth.tiny_chung_lu()
+        dev = torch.from_numpy(host.view(np.int64)).cuda()
+    n = int(dev.numel())
+    cfg["m"] = n
+    views = [dev[i:i + w] for i in range(0, n, w)]
+    return cfg, views, host
+
+
+class Schedule:
+    """Which (context, batch) each step folds: consecutive batches of one
+    stream, continued on a fresh context (same seed, stream id) once a short
+    stream is used up, so that no context ever sees an edge twice.  All
+    contexts are created up front."""
+
+    def __init__(self, tc, cfg, views, total_steps, rank, tuning, full_only=True):
+        self.tc = tc
+        # a stream's batches; a short last batch of the large stream is
+        # dropped so that every timed batch has the nominal w
+        self.views = [v for v in views if not full_only or v.numel() == cfg["w"]] \
+            if cfg["name"] == "large" else views
+        nb = len(self.views)
+        if cfg["name"] == "large" and total_steps > nb:
+            raise SystemExit(f"the large stream has {nb} batches; {total_steps} steps asked")
+        self.n_ctx = -(-total_steps // nb)
+        self.ctxs = []
+        for _ in range(self.n_ctx):
+            c = tc.tc_create_ex(cfg["r"], cfg["seed"], rank, cfg["w"], cfg["vertex_bits"])
+            tc.tc_tune(c, *tuning)
+            self.ctxs.append(c)
+        self.k = 0
+
+    def peek(self, j):
+        nb = len(self.views)
+        return self.ctxs[j // nb], self.views[j % nb]
+
+    def take(self):
+        ctx, b = self.peek(self.k)
+        self.k += 1
+        return ctx, b
+
+    def contexts(self, k0, k1):
+        """Contexts used by steps [k0, k1)."""
+        nb = len(self.views)
+        return self.ctxs[k0 // nb:(k1 - 1) // nb + 1]
+
+    def close(self):
+        for c in self.ctxs:
+            self.tc.tc_destroy(c)
+        self.ctxs = []
+
+
+def _sum_profiles(profs):
+    out = {}
+    for p in profs:
+        for k, v in p.items():
+            out[k] = out.get(k, 0) + v
+    return out
+
+
+def _accuracy(tc, cfg, views, host_keys, rank, est_last=None):
+    """tau_hat of one pass over the whole stream on a fresh context
+    (untimed), against the exact count stored in tests/golden/exact_tau.json
+    (written by a script that calls only the CPU exact counter) when the
+    generated stream hashes the same, and the epsilon that Theorem 3.2's
+    sample bound gives for this r at delta = 0.05.  The large stream has no
+    stored count: its exact count is out of reach of the machine's cores within
+    a run, so tau is reported unavailable."""
+    out = {"r": cfg["r"]}
+    if cfg["name"] == "large":
+        if est_last is not None:
+            out.update(tau_hat=est_last["tau_hat"], m=est_last["m"],
+                       n_closed=est_last["n_closed"], batches=est_last["batches"])
+        out["tau_exact"] = None
+        out["tau"] = ("unavailable: the exact count of the 1.2e9-edge graph is out of reach "
+                      "of the host's cores within a benchmark run")
+        return out
     ctx = tc.tc_create_ex(cfg["r"], cfg["seed"], rank, cfg["w"], cfg["vertex_bits"])
     try:
-        for b in dev_batches:
+        for b in views:
             tc.tc_process_batch(ctx, b)
         est = tc.tc_estimate(ctx)
     finally:
         tc.tc_destroy(ctx)
-    out = {"tau_hat": est["tau_hat"], "m": est["m"], "n_closed": est["n_closed"],
-           "r": cfg["r"], "batches": est["batches"]}
+    out.update(tau_hat=est["tau_hat"], m=est["m"], n_closed=est["n_closed"],
+               batches=est["batches"])
     path = os.path.join(ROOT, "tests", "golden", "exact_tau.json")
-    name = cfg.get("name")
-    gold = json.load(open(path)).get(name) if os.path.exists(path) and name else None
-    if gold and gold["keys_sha256"] == hashlib.sha256(keys.astype("<u8").tobytes()).hexdigest():
+    gold = json.load(open(path)).get(cfg["name"]) if os.path.exists(path) else None
+    if gold and host_keys is not None and \
+            gold["keys_sha256"] == hashlib.sha256(host_keys.astype("<u8").tobytes()).hexdigest():
         tau = gold["tau"]
         out["tau_exact"] = tau
         out["rel_error"] = abs(est["tau_hat"] - tau) / tau
@@ -226,26 +311,85 @@ def _accuracy(tc, cfg, keys, dev_batches, rank):
     return out
 
 
+def _cpu_baseline(cfg, host_sample, r_s, w_s, budget_s=20.0):
+    """Time the oracle on the first batches of a sample of the workload."""
+    from oracle import nbsi_bulk
+    import synth
+    ref = nbsi_bulk.BulkStream(r_s, seed=cfg["seed"], vertex_bits=cfg["vertex_bits"])
+    done, t_all, cpu_all, nb = 0, 0.0, 0.0, 0
+    for W in synth.batches(host_sample, w_s):
+        t0, c0 = time.perf_counter(), time.process_time()
+        ref.process_batch(W)
+        t_all += time.perf_counter() - t0
+        cpu_all += time.process_time() - c0
+        done += W.size
+        nb += 1
+        if t_all >= budget_s:
+            break
+    return {"value": done / t_all, "unit": UNIT,
+            "cores": max(1, round(cpu_all / t_all)), "cores_available": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"first {nb} batch(es) ({done} edges) of the stream at r={r_s}, "
+                      f"w={w_s}, single process, {t_all:.1f} s"}
+
+
+def _large_host_sample(n_edges, gen_seed=1):
+    """A random-order prefix of the large graph drawn on the host (numpy):
+    the first n_edges distinct endpoint samples of the same degree weights,
+    relabelled and shuffled (endpoint sampling draws edges independently, so
+    a prefix of the sample sequence is a prefix of a random-order stream)."""
+    import synth
+    n = 1 << 25
+    keys = synth.chung_lu(n, 2.1, 2 * synth.LARGE_EDGES / n, n_edges, seed=gen_seed,
+                          max_degree=3e5)
+    return synth.finish(keys, n, seed=gen_seed + 1000)
+
+
+def _reference_sample(workload):
+    """(cfg, host stream, r_s, w_s, scale) for the reference arm: the
+    workload's r:w ratio at 1/scale of its batch."""
+    import synth
+    cfg = dict(synth.WORKLOADS[workload], name=workload)
+    scale = {"large": 256, "rmat20": 64, "tiny": 1}[workload]
+    w_s, r_s = cfg["w"] // scale, max(1, cfg["r"] // scale)
+    return cfg, r_s, w_s, scale
+
+
 def run_reference(args, rank, world):
-    """CPU oracle on the host: one step = one batch of 2^16 edges with
-    r = 2^14 estimators (the workload's 1:4 ratio of r to w), state carried."""
+    """CPU oracle on the host: one step = one batch of the workload at 1/scale
+    of its batch size and estimator count (the same r:w ratio), state
+    carried, every batch a new one (consecutive batches of one stream)."""
     if rank != 0:
         return 0
     import synth
     from oracle import nbsi_bulk
-    cfg, keys = _workload(args.workload)
-    scale = 64 if args.workload == "rmat20" else 1
-    w_s, r_s = cfg["w"] // scale, max(1, cfg["r"] // scale)
+    workload = args.workload if args.workload in ("large", "rmat20", "tiny") else "large"
+    cfg, r_s, w_s, scale = _reference_sample(workload)
+    n_steps = args.warmup + args.steps
+    if workload == "large":
+        keys = _large_host_sample(n_steps * w_s)
+        graph = cfg["graph"] + f", m=1.2e9 (a random-order prefix of {keys.size} edges)"
+    else:
+        keys = synth.rmat20_single() if workload == "rmat20" else synth.tiny_chung_lu()
+        graph = cfg["graph"] + f", m={keys.size}"
     batches = synth.batches(keys, w_s)
+    nb = len(batches)
     ref = nbsi_bulk.BulkStream(r_s, seed=cfg["seed"], vertex_bits=cfg["vertex_bits"])
     k = 0
-    for _ in range(args.warmup):
-        ref.process_batch(batches[k % len(batches)])
+
+    def next_batch():
+        nonlocal k, ref
+        if k and k % nb == 0:    # a short stream is used up: a fresh stream again
+            ref = nbsi_bulk.BulkStream(r_s, seed=cfg["seed"], vertex_bits=cfg["vertex_bits"])
+        W = batches[k % nb]
         k += 1
+        return W
+
+    for _ in range(args.warmup):
+        ref.process_batch(next_batch())
     times, cpu, edges = [], 0.0, 0
     for _ in range(args.steps):
-        W = batches[k % len(batches)]
-        k += 1
+        W = next_batch()
         t0, c0 = time.perf_counter(), time.process_time()
         ref.process_batch(W)
         ref.closed_sum()
@@ -260,8 +404,8 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: {cfg['graph']}, m={cfg['m']}, "
-                               f"sampled at r={r_s}, w={w_s}", "r": r_s, "w": w_s},
+        "config": {"workload": f"{workload}: {graph}, sampled at r={r_s}, w={w_s}",
+                   "r": r_s, "w": w_s},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{args.steps} batches of {w_s} edges at r={r_s} "
                                    f"(the workload's r:w ratio, 1/{scale} of its batch)"},
@@ -271,10 +415,248 @@ def run_reference(args, rank, world):
     return 0
 
 
+def _time_single(tc, args, cfg, views, host_keys, rank, world, local_rank, dist, sh, stream,
+                 tuning, tune_table, with_e2e=True, with_clocks=True):
+    """Warm-up, timed, end-to-end and stage-split steps of one single-stream
+    workload on a Schedule; returns the result dict (not yet a JSON line)."""
+    import torch
+    r, w, B = cfg["r"], cfg["w"], cfg["vertex_bits"]
+    W, K = args.warmup, args.steps
+    nb_stream = len(views)
+    E = (args.e2e_steps or min(K, 20)) if with_e2e else 0
+    G = min(K, 20) if args.pipeline == "on" else 0
+    if cfg["name"] == "large":       # the stream's batches are shared by every leg
+        full = sum(1 for v in views if v.numel() == w)
+        spare = full - W - K
+        E = max(0, min(E, spare))
+        G = max(0, min(G, spare - E))
+    sched = Schedule(tc, cfg, views, W + K + E + G, rank, tuning)
+    rec = torch.zeros(tc.ESTIMATE_BYTES // 8, dtype=torch.int64, device="cuda")
+    process = (tc.tc_process_batch_ready_async if args.pipeline == "on"
+               else tc.tc_process_batch_async)
+
+    def step():
+        ctx, b = sched.take()
+        process(ctx, b, stream=sh)
+        tc.tc_estimate_async(ctx, rec, stream=sh)
+        return ctx, b.numel()
+
+    with torch.cuda.stream(stream):
+        for _ in range(W):
+            step()
+    for c in sched.contexts(0, max(1, W)):
+        tc.tc_sync(c)
+    torch.cuda.synchronize()
+
+    # ---- timed region: exactly K steps, events on the launching stream
+    k0 = sched.k
+    timed_ctx = sched.contexts(k0, k0 + K)
+    sampler = ClockSampler(local_rank) if (rank == 0 and with_clocks) else None
+    time.sleep(0.3 if sampler else 0)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for c in timed_ctx:
+        tc.tc_profile_begin(c)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+    edges, ws = 0, []
+    with torch.cuda.stream(stream):
+        evs[0].record(stream)
+        for j in range(K):
+            _, n = step()
+            edges += n
+            ws.append(n)
+            evs[j + 1].record(stream)
+    stream.synchronize()
+    torch.cuda.synchronize()
+    prof = _sum_profiles([tc.tc_profile_end(c) for c in timed_ctx])
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    for c in timed_ctx:
+        tc.tc_sync(c)
+    per_step = [evs[j].elapsed_time(evs[j + 1]) for j in range(K)]
+    t_ms, edges_all = reduce_over_ranks(dist, evs[0].elapsed_time(evs[-1]), edges, "cuda")
+    value = edges_all / (t_ms / 1e3)
+    last = tc.estimate_records(rec.cpu())[0]
+
+    # ---- end to end: pinned host batches through the C-ABI host-input call
+    e2e = None
+    if E:
+        kk = sched.k
+        pinned = []
+        for j in range(E):
+            _, b = sched.peek(kk + j)
+            t = torch.empty(b.numel(), dtype=torch.int64, pin_memory=True)
+            t.copy_(b)
+            pinned.append(t)
+        res_host = [torch.zeros(tc.ESTIMATE_BYTES // 8, dtype=torch.int64, pin_memory=True)
+                    for _ in range(4)]
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        e2e_edges = 0
+        with torch.cuda.stream(stream):
+            for j in range(E):
+                ctx, _ = sched.take()
+                hb = pinned[j]
+                tc.tc_process_batch_host_async(ctx, hb, stream=sh)
+                tc.tc_estimate_async(ctx, rec, stream=sh)
+                res_host[j % 4].copy_(rec, non_blocking=True)
+                e2e_edges += hb.numel()
+        stream.synchronize()
+        e2e_s, e2e_all = reduce_over_ranks(dist, time.perf_counter() - t0, e2e_edges, "cuda")
+        for c in sched.contexts(kk, kk + E):
+            tc.tc_sync(c)
+        last = tc.estimate_records(res_host[(E - 1) % 4])[0]
+        e2e = {"value": e2e_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * e2e_edges // E,
+               "d2h_bytes_per_step": tc.ESTIMATE_BYTES, "steps": E,
+               "how": "tc_process_batch_host_async from pinned host batches (each batch's "
+                      "copy overlaps the previous batch's update) + tc_estimate_async and a "
+                      "copy of its 72-byte record to pinned host memory every step; host "
+                      "wall clock; new batches of the stream"}
+        del pinned
+
+    # ---- stage split: pipelined, a batch's sort phase overlaps the previous
+    # batch's sweep, so per-stage times do not partition the step; a short
+    # stream-ordered pass after the timed run gives the split
+    if G:
+        kk = sched.k
+        cs = sched.contexts(kk, kk + G)
+        for c in cs:
+            tc.tc_sync(c)
+        torch.cuda.synchronize()
+        for c in cs:
+            tc.tc_profile_begin(c)
+        with torch.cuda.stream(stream):
+            for _ in range(G):
+                ctx, b = sched.take()
+                tc.tc_process_batch_async(ctx, b, stream=sh)
+                tc.tc_estimate_async(ctx, rec, stream=sh)
+        stream.synchronize()
+        sprof = _sum_profiles([tc.tc_profile_end(c) for c in cs])
+        stage_steps = G
+        stage_how = (f"stream-ordered pass of {G} new batches (tc_process_batch_async) after "
+                     "the timed run; the two sorts run side by side on two streams: "
+                     "ms_arc_sort = the arc passes with the Step-3 passes beside them, "
+                     "ms_dups = the arc directory, ms_edge_sort = what is left of the Step-3 "
+                     "branch (its directory and repeat check)")
+        torch.cuda.synchronize()
+        last = tc.estimate_records(rec.cpu())[0]
+    else:
+        sprof, stage_steps = prof, K
+        stage_how = "the timed run itself"
+    used = sched.k
+    sched.close()
+
+    peak, peak_kind = _peaks()
+    stages = {k2: sprof[k2] / stage_steps for k2 in ("ms_prep", "ms_arc_sort", "ms_edge_sort",
+                                                    "ms_dups", "ms_sweep", "ms_finish",
+                                                    "ms_estimate", "ms_sort_wall")}
+    # dominant kernel: the radix digit passes (both sorts side by side) or the
+    # fused Steps 1-3 sweep, by device time per step inside the timed region
+    ms_sort = prof["ms_sort_wall"]
+    ms_sweep = prof["ms_sweep"]
+    launched = max(1, prof["sort_pass_launches"] - prof["sort_pass_skipped"])
+    sort_gbs = prof["sort_pass_bytes"] / (ms_sort / 1e3) / 1e9 if ms_sort > 0 else 0.0
+    sort_roof = {
+        "kernel": "onesweep_pass_kernel (radix digit pass, arc and Step-3 sorts)",
+        "bound": "hbm", "achieved": sort_gbs, "peak": peak, "unit": "GB/s",
+        "frac": sort_gbs / peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
+        "bytes_per_launch": prof["sort_pass_bytes"] / launched,
+        "ms_per_launch": ms_sort / launched,
+        "ms_per_step": ms_sort / K,
+        "timing": "the arc and Step-3 sorts' passes run side by side on two CUDA streams: "
+                  "achieved = all passes' algorithmic bytes (16 B per key moved in and out) / "
+                  "the wall time from the first pass's start to the later sort's end (CUDA "
+                  "events on both streams, timed region)",
+        "traffic": None,
+    }
+    tr = TRAFFIC.get("onesweep_pass_kernel")
+    if tr and tr.get("src_hash") == _src_hash():
+        sort_roof["traffic"] = tr["bytes_per_algorithmic_byte"] * sort_roof["bytes_per_launch"]
+    sweep_bytes = 56 * r * K
+    sweep_gbs = sweep_bytes / (ms_sweep / 1e3) / 1e9 if ms_sweep > 0 else 0.0
+    sweep_roof = {
+        "kernel": "sweep_kernel (fused Steps 1-3 and the Lemma 3.1 sum)",
+        "bound": "hbm", "achieved": sweep_gbs, "peak": peak, "unit": "GB/s",
+        "frac": sweep_gbs / peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
+        "bytes_per_launch": 56 * r, "ms_per_launch": ms_sweep / K, "ms_per_step": ms_sweep / K,
+        "timing": "achieved = the 28-byte state read and written once per estimator (56 r "
+                  "bytes; the searches' probes are not algorithmic bytes) / the sweep's "
+                  "duration (CUDA events on the launching stream, timed region)",
+        "traffic": None,
+    }
+    if ms_sweep > ms_sort:
+        roofline, other = sweep_roof, sort_roof
+    else:
+        roofline, other = sort_roof, sweep_roof
+    roofline["share_of_step"] = roofline["ms_per_step"] / (t_ms / K) if t_ms else None
+    other["share_of_step"] = other["ms_per_step"] / (t_ms / K) if t_ms else None
+    paper_bytes = sum(paper_layout_bytes(x, r, B) for x in ws)
+    own_bytes = sum(own_design_bytes(x, r, B, tuning[0], tuning[1]) for x in ws)
+    t_s = t_ms / 1e3
+    from paper_1308_2166_gb300 import autotune
+    res = {
+        "value": value, "t_ms": t_ms, "edges": edges_all, "per_step": per_step,
+        "config": {
+            "workload": f"{cfg['name']}: {cfg['graph']}, m={cfg['m']}, r={r}, w={w}",
+            "pipeline": ("on: tc_process_batch_ready_async, batch k+1's sorts beside batch k's "
+                         "sweep" if args.pipeline == "on" else "off: tc_process_batch_async"),
+            "r": r, "w": w, "m": cfg["m"], "vertex_bits": B, "parallelism": f"replicas{world}",
+            "batches": {"stream": nb_stream, "warmup": W, "timed": K, "e2e": E, "stage_split": G,
+                        "used": used, "contexts": sched.n_ctx,
+                        "replayed": 0,
+                        "how": "every step folds a new batch of the stream; a short stream "
+                               "used up continues as a new stream on a fresh context"},
+            "sort_tuning": {"arc_digit_bits": tuning[0], "edge_digit_bits": tuning[1],
+                            "ranking": autotune.RANKINGS[tuning[2]],
+                            "table_ms": {f"{a}/{b}/{autotune.RANKINGS[c]}": round(v, 4)
+                                         for (a, b, c), v in sorted(tune_table.items())}},
+            "l2": "inputs larger than L2: every step reads a batch no earlier step touched "
+                  f"({8 * w / 2**20:.0f} MB) and a {28 * r / 2**20:.0f} MB state, with "
+                  f"{(48 * w) / 2**20:.0f} MB of sort buffers, against the 126 MB L2",
+        },
+        "updates_per_s": value * r,
+        "p50_ms": statistics.median(per_step),
+        "p99_ms": float(np.percentile(per_step, 99)),
+        "stage_ms_per_step": dict(stages, how=stage_how),
+        "step_hbm_frac": {
+            "paper_layout_min_bytes_per_step": paper_bytes / K,
+            "frac_paper_layout": paper_bytes / t_s / 1e9 / peak,
+            "own_min_bytes_per_step": own_bytes / K,
+            "frac_own": own_bytes / t_s / 1e9 / peak,
+            "how": "sum over the timed batches of each batch's minimal bytes at its own w "
+                   "(paper layout: 8w + 16w + ceil((B+bw)/8)*32w + 8w + ceil(2B/8)*w*(16|24) "
+                   "+ 64r; own design: 32w + ceil(B/8)*32w + ceil(hb/8)*16w + 8w + 56r) / the "
+                   "timed region / peak",
+        },
+        "roofline": roofline,
+        "roofline_other_kernel": other,
+        "gpu_launches": prof["launches"],
+        "clocks": clocks,
+        "e2e": e2e,
+        "estimate_last": last,
+    }
+    return res
+
+
+def _tuning(args, tc, views, cfg, sh):
+    from paper_1308_2166_gb300 import autotune
+    if args.sort_tuning:
+        return tuple(int(x) for x in args.sort_tuning.split(",")), {}
+    if args.no_autotune:
+        return (8, 8, 2), {}
+    # a few batches of the stream on scratch contexts (untimed; results do
+    # not depend on the tuning)
+    return autotune.tune(views[:2], cfg["r"], cfg["vertex_bits"], seed=cfg["seed"] + 99,
+                         reps=1, stream=sh)
+
+
 def run_gpu(args, rank, world, local_rank):
     import torch
     import paper_1308_2166_gb300 as tc
-    import synth
     from paper_1308_2166_gb300 import build
 
     torch.cuda.set_device(local_rank)
@@ -284,224 +666,80 @@ def run_gpu(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     build.build()
     tc.load()
-
-    cfg, keys = _workload(args.workload)
-    w, r = cfg["w"], cfg["r"]
-    host_batches = synth.batches(keys, w)
-    dev_batches = [torch.from_numpy(b.view(np.int64)).cuda() for b in host_batches]
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
-    from paper_1308_2166_gb300 import autotune
-    if args.sort_tuning:
-        tuning, tune_table = tuple(int(x) for x in args.sort_tuning.split(",")), {}
-    elif args.no_autotune:
-        tuning, tune_table = (8, 8, 2), {}
-    else:
-        tuning, tune_table = autotune.tune(dev_batches, r, cfg["vertex_bits"],
-                                           seed=cfg["seed"] + 99, reps=1, stream=sh)
-    ctx = tc.tc_create_ex(r, cfg["seed"], rank, w, cfg["vertex_bits"])
-    tc.tc_tune(ctx, *tuning)
-    est_words = torch.zeros(4, dtype=torch.int64, device="cuda")
-    nb = len(dev_batches)
 
-    # the batches sit in HBM before the run, so each can be handed to the
-    # pipelined call: its sort phase overlaps the previous batch's sweep
-    process = (tc.tc_process_batch_ready_async if args.pipeline == "on"
-               else tc.tc_process_batch_async)
-
-    def step(k):
-        process(ctx, dev_batches[k % nb], stream=sh)
-        tc.tc_estimate_async(ctx, est_words, stream=sh)
-        return dev_batches[k % nb].numel()
-
-    k = 0
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            step(k)
-            k += 1
-    tc.tc_sync(ctx)
+    t_gen = time.perf_counter()
+    cfg, views, host_keys = _single_workload(args.workload, args.stream_edges)
     torch.cuda.synchronize()
-
-    # ---- timed region: exactly K steps, events on the launching stream
-    sampler = ClockSampler(local_rank) if rank == 0 else None
-    time.sleep(0.3 if sampler else 0)
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    tc.tc_profile_begin(ctx)
-    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    edges = 0
-    with torch.cuda.stream(stream):
-        evs[0].record(stream)
-        for j in range(args.steps):
-            edges += step(k)
-            k += 1
-            evs[j + 1].record(stream)
-    stream.synchronize()
-    torch.cuda.synchronize()
-    prof = tc.tc_profile_end(ctx)
-    if dist:
-        dist.barrier()
-    clocks = sampler.stop() if sampler else None
-    tc.tc_sync(ctx)
-    per_step = [evs[j].elapsed_time(evs[j + 1]) for j in range(args.steps)]
-    t_ms, edges_all = reduce_over_ranks(dist, evs[0].elapsed_time(evs[-1]), edges, "cuda")
-    value = edges_all / (t_ms / 1e3)
-
-    # ---- end to end: pinned host batches through the C-ABI host-input call
-    e2e_steps = args.e2e_steps or min(args.steps, 40)
-    pinned = []
-    for b in host_batches:
-        t = torch.empty(b.size, dtype=torch.int64, pin_memory=True)
-        t.numpy()[:] = b.view(np.int64)
-        pinned.append(t)
-    if dist:
-        dist.barrier()
-    # each step: the pinned host batch goes in through the pipelined host-input
-    # call (its copy overlaps the previous batch's update) and the step's
-    # estimate words come back to pinned host memory
-    res_dev = torch.zeros(4, dtype=torch.int64, device="cuda")
-    res_host = [torch.zeros(4, dtype=torch.int64, pin_memory=True) for _ in range(4)]
-    for j in range(2):                   # untimed: both staging buffers in place
-        tc.tc_process_batch_host_async(ctx, pinned[k % nb], stream=sh)
-        k += 1
-    tc.tc_sync(ctx)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_edges = 0
-    with torch.cuda.stream(stream):
-        for j in range(e2e_steps):
-            hb = pinned[k % nb]
-            k += 1
-            tc.tc_process_batch_host_async(ctx, hb, stream=sh)
-            tc.tc_estimate_async(ctx, res_dev, stream=sh)
-            res_host[j % 4].copy_(res_dev, non_blocking=True)
-            e2e_edges += hb.numel()
-    stream.synchronize()
-    tc.tc_sync(ctx)
-    e2e_s, e2e_all = reduce_over_ranks(dist, time.perf_counter() - t0, e2e_edges, "cuda")
-    e2e_value = e2e_all / e2e_s
-
-    # ---- stage split: pipelined, a batch's sort phase overlaps the previous
-    # batch's sweep, so per-stage times do not partition the step; a short
-    # stream-ordered pass after the timed run gives the split
-    if args.pipeline == "on":
-        tc.tc_sync(ctx)
-        torch.cuda.synchronize()
-        stage_steps = min(args.steps, 20)
-        tc.tc_profile_begin(ctx)
-        with torch.cuda.stream(stream):
-            for j in range(stage_steps):
-                tc.tc_process_batch_async(ctx, dev_batches[k % nb], stream=sh)
-                tc.tc_estimate_async(ctx, est_words, stream=sh)
-                k += 1
-        stream.synchronize()
-        sprof = tc.tc_profile_end(ctx)
-        stage_how = (f"stream-ordered pass of {stage_steps} steps (tc_process_batch_async) "
-                     "after the timed run; the two sorts run side by side on two streams: "
-                     "ms_arc_sort = the arc passes with the Step-3 passes beside them, "
-                     "ms_dups = the arc directory, ms_edge_sort = what is left of the Step-3 "
-                     "branch (its directory and repeat check)")
-    else:
-        sprof, stage_steps = prof, args.steps
-        stage_how = "the timed run itself"
-
-    if rank != 0:
-        tc.tc_destroy(ctx)
-        if dist:
-            dist.destroy_process_group()
-        return 0
-
-    peak, peak_kind = _peaks()
-    ms_sort = prof["ms_sort_wall"]   # both sorts' passes, run side by side
-    # stream-ordered: the stages partition the step; pipelined: the sort
-    # phase runs on the library's own streams (ms_sort_wall), the rest on sh
-    stages = {k2: sprof[k2] / stage_steps for k2 in ("ms_prep", "ms_arc_sort", "ms_edge_sort",
-                                                    "ms_dups", "ms_sweep", "ms_finish",
-                                                    "ms_estimate", "ms_sort_wall")}
-    sort_gbs = prof["sort_pass_bytes"] / (ms_sort / 1e3) / 1e9 if ms_sort > 0 else 0.0
-    launched = max(1, prof["sort_pass_launches"] - prof["sort_pass_skipped"])
-    roofline = {
-        "kernel": "onesweep_pass_kernel (radix digit pass, arc and edge sorts)",
-        "bound": "hbm", "achieved": sort_gbs, "peak": peak, "unit": "GB/s",
-        "frac": sort_gbs / peak, "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
-        "bytes_per_launch": prof["sort_pass_bytes"] / launched,
-        "ms_per_launch": ms_sort / launched,
-        "timing": "the arc and edge sorts' passes run side by side on two CUDA streams: "
-                  "achieved = all passes' algorithmic bytes / the wall time from the first "
-                  "pass's start to the later sort's end (CUDA events on both streams)",
-        "traffic": None,
-        "share_of_step": ms_sort / t_ms if t_ms else None,
-        "limiter": "integer issue: the pass's ALU pipe is 69-71% busy while DRAM is ~20% busy "
-                   "(ncu, profiles/onesweep_pass_rmat20.md); HBM is the bound the pass's data "
-                   "movement allows, the fraction shows the distance to it",
-    }
-    tr = TRAFFIC.get("onesweep_pass_kernel")
-    if tr and tr.get("src_hash") == _src_hash():
-        roofline["traffic"] = tr["bytes_per_algorithmic_byte"] * roofline["bytes_per_launch"]
-    # algorithmic bytes of the whole step: this design's minimal passes (arcs
-    # on the src bits, Step-3 keys on the top bits of a 32-bit edge hash --
-    # whole 8-bit digits covering the bw - 2 bucket bits -- with the position
-    # packed below it) and the paper's layout (arcs sorted on src + position,
-    # the Step-3 `edges` array on (u, v), a u32 position value once
-    # 2B + bw > 64; 8-bit digits, 32-byte state read and written once)
-    bw = max(1, (w - 1).bit_length())
-    B = cfg["vertex_bits"]
-    pa = -(-B // 8)
-    pe = -(-(bw - 2 if bw > 3 else 1) // 8)
-    own_bytes = 32 * w + pa * 2 * w * 16 + pe * w * 16 + 8 * w + 2 * 28 * r
-    pe_p = -(-2 * B // 8)
-    e_bytes_p = 16 if 2 * B + bw <= 64 else 24
-    paper_bytes = 8 * w + (2 * w * 8 + (-(-(B + bw) // 8)) * 2 * w * 16) + \
-        (w * 8 + pe_p * w * e_bytes_p) + 64 * r
-    step_s = (t_ms / 1e3) / args.steps
+    gen_s = time.perf_counter() - t_gen
+    tuning, tune_table = _tuning(args, tc, views, cfg, sh)
+    res = _time_single(tc, args, cfg, views, host_keys, rank, world, local_rank, dist, sh,
+                       stream, tuning, tune_table)
+    K = args.steps
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": res["t_ms"] / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {
-            "workload": f"{args.workload}: {cfg['graph']}, m={cfg['m']}, r={r}, w={w}",
-            "pipeline": ("on: tc_process_batch_ready_async, batch k+1's sorts beside batch k's "
-                         "sweep" if args.pipeline == "on" else "off: tc_process_batch_async"),
-            "r": r, "w": w, "m": cfg["m"], "vertex_bits": B, "parallelism": f"replicas{world}",
-            "sort_tuning": {"arc_digit_bits": tuning[0], "edge_digit_bits": tuning[1],
-                            "ranking": autotune.RANKINGS[tuning[2]],
-                            "table_ms": {f"{a}/{b}/{autotune.RANKINGS[c]}": round(v, 4)
-                                         for (a, b, c), v in sorted(tune_table.items())}},
-            "l2": _l2_note(cfg, len(dev_batches)),
-        },
-        "updates_per_s": value * r,
-        "p50_ms": statistics.median(per_step),
-        "p99_ms": float(np.percentile(per_step, 99)),
-        "stage_ms_per_step": dict(stages, how=stage_how),
-        "step_hbm_frac": {
-            "own_min_bytes_per_step": own_bytes,
-            "frac_own": own_bytes / step_s / 1e9 / peak,
-            "paper_layout_min_bytes_per_step": paper_bytes,
-            "frac_paper_layout": paper_bytes / step_s / 1e9 / peak,
-        },
-        "roofline": roofline,
-        "gpu_launches": prof["launches"],
-        "clocks": clocks,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": w * 8,
-                "d2h_bytes_per_step": 32, "steps": e2e_steps,
-                "how": "tc_process_batch_host_async from pinned host batches (each batch's "
-                       "copy overlaps the previous batch's update) + tc_estimate_async and a "
-                       "copy of the 4 estimate words to pinned host memory every step; "
-                       "host wall clock"},
-        "estimate": _accuracy(tc, cfg, keys, dev_batches, rank),
-        "src_hash": _src_hash(),
+        "config": dict(res["config"], stream_gen_s=round(gen_s, 1)),
     }
-    tc.tc_destroy(ctx)
+    for k in ("updates_per_s", "p50_ms", "p99_ms", "stage_ms_per_step", "step_hbm_frac",
+              "roofline", "roofline_other_kernel", "gpu_launches", "clocks", "e2e"):
+        line[k] = res[k]
+    if rank == 0:
+        line["estimate"] = _accuracy(tc, cfg, views, host_keys, rank, res["estimate_last"])
+    line["src_hash"] = _src_hash()
+    del views
+    torch.cuda.empty_cache()
+    if rank == 0 and args.workload == "large" and not args.no_extras:
+        line["rmat20"] = _extra_rmat20(args, tc, rank, world, local_rank, sh, stream)
+        line["multi512"] = _extra_multi(args, tc, local_rank)
     if dist:
         dist.destroy_process_group()
+    if rank != 0:
+        return 0
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = _cpu_baseline(keys, cfg)
+        if cfg["name"] == "large":
+            # the first 2^22 edges of a random-order prefix of the same graph at
+            # r = 2^22 (the workload's r:w ratio at 1/4 of its batch)
+            sample = _large_host_sample(1 << 22)
+            line["cpu_baseline"] = _cpu_baseline(cfg, sample, 1 << 22, 1 << 22)
+        else:
+            line["cpu_baseline"] = _cpu_baseline(cfg, host_keys, cfg["r"], cfg["w"])
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_multi(args, rank, world, local_rank):
+def _extra_rmat20(args, tc, rank, world, local_rank, sh, stream):
+    """The R-MAT scale-20 single stream (r = 2^20, w = 2^22) as an extra key
+    of the default line: streams of 3.7 batches, each on a fresh context."""
+    import torch
+    cfg, views, host_keys = _single_workload("rmat20")
+    tuning, table = _tuning(args, tc, views, cfg, sh)
+    res = _time_single(tc, args, cfg, views, host_keys, rank, 1, local_rank, None, sh, stream,
+                       tuning, table, with_clocks=False)
+    out = {"value": res["value"], "unit": UNIT, "ms_per_step": res["t_ms"] / args.steps,
+           "config": res["config"], "e2e": res["e2e"], "roofline": res["roofline"],
+           "roofline_other_kernel": res["roofline_other_kernel"],
+           "step_hbm_frac": res["step_hbm_frac"], "stage_ms_per_step": res["stage_ms_per_step"],
+           "p50_ms": res["p50_ms"], "p99_ms": res["p99_ms"], "gpu_launches": res["gpu_launches"],
+           "estimate": _accuracy(tc, cfg, views, host_keys, rank)}
+    del views
+    torch.cuda.empty_cache()
+    return out
+
+
+def _extra_multi(args, tc, local_rank):
+    """The multi-stream bench (512 streams) as an extra key: its aggregate
+    edges/s and the ratio over back-to-back per-stream launches."""
+    line = run_multi(args, 0, 1, local_rank, emit=False)
+    keep = ("metric", "value", "unit", "ms_per_step", "config", "updates_per_s",
+            "batched_plain", "batched_pipelined", "back_to_back", "speedup_vs_back_to_back",
+            "identical_outputs", "gpu_launches")
+    return {k: line[k] for k in keep if k in line}
+
+
+def run_multi(args, rank, world, local_rank, emit=True):
     """512 independent Chung-Lu streams advanced round by round.
 
     Per-stream batch w_s = min(w_cap, len_s // rounds) so that every stream
@@ -663,6 +901,8 @@ def run_multi(args, rank, world, local_rank):
         "gpu_launches": launches_graph,
         "clocks": clocks,
     }
+    if not emit:
+        return line
     print(json.dumps(line), flush=True)
     return 0
 
@@ -940,7 +1180,7 @@ def run_wsweep(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     build.build()
     tc.load()
-    cfg, keys = _workload("rmat20")
+    cfg, _, keys = _single_workload("rmat20")
     r, vb = cfg["r"], cfg["vertex_bits"]
     dev = torch.from_numpy(keys.view(np.int64)).cuda()
     stream = torch.cuda.Stream()
@@ -996,6 +1236,74 @@ def run_wsweep(args, rank, world, local_rank):
     return 0
 
 
+def run_accuracy(args, rank, world, local_rank):
+    """Relative error of tau_hat against the exact count per configuration
+    and per r (the paper's Table 2 reports the mean deviation per r): for the
+    tiny Chung-Lu stream and the R-MAT scale-20 stream, one pass over the
+    whole stream at r = 2^10, 2^12, ..., up to the workload's r, for 5 Philox
+    seeds each; the mean over the seeds of |tau_hat - tau| / tau, beside the
+    epsilon that Theorem 3.2's sample bound gives at delta = 0.05.  The exact
+    counts come from tests/golden/exact_tau.json (written by a script that
+    calls only the CPU exact counter), used only when the generated stream
+    hashes the same.  The large stream has no exact count (out of reach of
+    the host's cores), so its row says tau unavailable."""
+    import torch
+    import paper_1308_2166_gb300 as tc
+    from paper_1308_2166_gb300 import build
+
+    torch.cuda.set_device(local_rank)
+    build.build()
+    tc.load()
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "exact_tau.json")))
+    seeds = (1, 2, 3, 4, 5)
+    table = {}
+    t0 = time.perf_counter()
+    for name, r_max in (("tiny", 1 << 10), ("rmat20", 1 << 20)):
+        cfg, views, keys = _single_workload(name)
+        g = gold.get(name)
+        if not g or g["keys_sha256"] != hashlib.sha256(keys.astype("<u8").tobytes()).hexdigest():
+            table[name] = {"tau": "unavailable: generated stream does not match the stored count"}
+            continue
+        tau = g["tau"]
+        rows = []
+        for lr in range(10, r_max.bit_length(), 2):
+            r = 1 << lr
+            errs, taus = [], []
+            for sd in seeds:
+                ctx = tc.tc_create_ex(r, sd, 0, cfg["w"], cfg["vertex_bits"])
+                try:
+                    for b in views:
+                        tc.tc_process_batch_async(ctx, b)
+                    e = tc.tc_estimate(ctx)
+                finally:
+                    tc.tc_destroy(ctx)
+                taus.append(e["tau_hat"])
+                errs.append(abs(e["tau_hat"] - tau) / tau)
+            rows.append({"r": r, "mean_rel_error": float(np.mean(errs)),
+                         "max_rel_error": float(np.max(errs)),
+                         "mean_tau_hat": float(np.mean(taus)),
+                         "thm32_eps_delta_0.05": math.sqrt(
+                             96.0 * g["m"] * g["max_degree"] / tau * math.log(1 / 0.05) / r)})
+        table[name] = {"tau_exact": tau, "m": g["m"], "w": cfg["w"], "seeds": list(seeds),
+                       "rows": rows}
+        del views
+        torch.cuda.empty_cache()
+    table["large"] = {"tau_exact": None,
+                      "tau": "unavailable: the exact count of the 1.2e9-edge graph is out of "
+                             "reach of the host's cores within a benchmark run"}
+    head = table["rmat20"]["rows"][-1] if "rows" in table.get("rmat20", {}) else {}
+    line = {"metric": "mean relative error of tau_hat vs the exact count (5 seeds)",
+            "value": head.get("mean_rel_error"), "unit": "fraction", "n_gpus": 1,
+            "steps": len(seeds), "warmup": 0, "ms_per_step": None, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": {"workload": "accuracy: tiny (Chung-Lu 2.3, m=32768) and rmat20 "
+                                   "(R-MAT scale 20) at r = 2^10 .. workload r, 5 seeds; "
+                                   "value = rmat20 at r = 2^20"},
+            "table": table, "seconds": round(time.perf_counter() - t0, 1)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = _args()
     rank = int(os.environ.get("RANK", "0"))
@@ -1009,6 +1317,8 @@ def main():
         return run_serve(args, rank, world, local_rank)
     if args.workload == "wsweep":
         return run_wsweep(args, rank, world, local_rank)
+    if args.workload == "accuracy":
+        return run_accuracy(args, rank, world, local_rank)
     return run_gpu(args, rank, world, local_rank)
 
 

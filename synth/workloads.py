@@ -50,6 +50,23 @@ def large_prefix(n_batches: int = 2, gen_seed: int = 1) -> np.ndarray:
     return finish(keys, n, seed=gen_seed + 1000)
 
 
+# Edges of the whole ``large`` stream (about 1.2e9, 71.5 batches of 2^24).
+LARGE_EDGES = 1_200_000_000
+
+
+def large_stream_device(m: int = LARGE_EDGES, gen_seed: int = 1, device: str = "cuda"):
+    """The ``large`` stream drawn on the GPU: Chung-Lu, exponent 2.1,
+    n = 2^25, expected degrees with mean 2 * 1.2e9 / 2^25 (about 71.5)
+    capped at 3e5, m distinct edges in random order (int64 tensor of packed
+    keys on `device`).  m defaults to the whole stream, so that every batch a
+    run folds in is a new one (no batch is replayed); a smaller m is a
+    shorter stream from the same degree weights, not a prefix of it."""
+    from .device import chung_lu_device
+    n = 1 << 25
+    return chung_lu_device(n, 2.1, 2 * LARGE_EDGES / n, m, seed=gen_seed, max_degree=3e5,
+                           device=device)
+
+
 def batches(keys: np.ndarray, w: int):
     """Split a stream into consecutive batches of w edges (last may be short)."""
     return [keys[i:i + w] for i in range(0, keys.size, w)]
