@@ -88,6 +88,8 @@ def _args():
                         "(tc_process_batch_ready_async) or fully stream-ordered")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the library's default sort tuning (8-bit digits, ballot ranking)")
+    p.add_argument("--sweep-blocks", type=int, default=0,
+                   help="estimator sweep blocks per SM (1..6) instead of autotuning")
     p.add_argument("--sort-tuning", default=None,
                    help="A,E,R: fix the sort tuning (arc and Step-3 digit bits, ranking "
                         "1 match / 2 ballot / 3 atomic-or) instead of autotuning")
@@ -228,7 +230,8 @@ class Schedule:
     stream is used up, so that no context ever sees an edge twice.  All
     contexts are created up front."""
 
-    def __init__(self, tc, cfg, views, total_steps, rank, tuning, full_only=True):
+    def __init__(self, tc, cfg, views, total_steps, rank, tuning, sweep_bps=0,
+                 full_only=True):
         self.tc = tc
         # a stream's batches; a short last batch of the large stream is
         # dropped so that every timed batch has the nominal w
@@ -242,6 +245,7 @@ class Schedule:
         for _ in range(self.n_ctx):
             c = tc.tc_create_ex(cfg["r"], cfg["seed"], rank, cfg["w"], cfg["vertex_bits"])
             tc.tc_tune(c, *tuning)
+            tc.tc_tune_sweep(c, sweep_bps)
             self.ctxs.append(c)
         self.k = 0
 
@@ -416,7 +420,8 @@ def run_reference(args, rank, world):
 
 
 def _time_single(tc, args, cfg, views, host_keys, rank, world, local_rank, dist, sh, stream,
-                 tuning, tune_table, with_e2e=True, with_clocks=True):
+                 tuning, tune_table, sweep_bps=6, sweep_table=None, with_e2e=True,
+                 with_clocks=True):
     """Warm-up, timed, end-to-end and stage-split steps of one single-stream
     workload on a Schedule; returns the result dict (not yet a JSON line)."""
     import torch
@@ -430,7 +435,7 @@ def _time_single(tc, args, cfg, views, host_keys, rank, world, local_rank, dist,
         spare = full - W - K
         E = max(0, min(E, spare))
         G = max(0, min(G, spare - E))
-    sched = Schedule(tc, cfg, views, W + K + E + G, rank, tuning)
+    sched = Schedule(tc, cfg, views, W + K + E + G, rank, tuning, sweep_bps)
     rec = torch.zeros(tc.ESTIMATE_BYTES // 8, dtype=torch.int64, device="cuda")
     process = (tc.tc_process_batch_ready_async if args.pipeline == "on"
                else tc.tc_process_batch_async)
@@ -614,6 +619,9 @@ def _time_single(tc, args, cfg, views, host_keys, rank, world, local_rank, dist,
                             "ranking": autotune.RANKINGS[tuning[2]],
                             "table_ms": {f"{a}/{b}/{autotune.RANKINGS[c]}": round(v, 4)
                                          for (a, b, c), v in sorted(tune_table.items())}},
+            "sweep_blocks_per_sm": {"value": sweep_bps,
+                                    "table_ms_per_batch": {str(k): round(v, 4) for k, v in
+                                                           sorted((sweep_table or {}).items())}},
             "l2": "inputs larger than L2: every step reads a batch no earlier step touched "
                   f"({8 * w / 2**20:.0f} MB) and a {28 * r / 2**20:.0f} MB state, with "
                   f"{(48 * w) / 2**20:.0f} MB of sort buffers, against the 126 MB L2",
@@ -643,15 +651,25 @@ def _time_single(tc, args, cfg, views, host_keys, rank, world, local_rank, dist,
 
 
 def _tuning(args, tc, views, cfg, sh):
+    """(sort tuning, its table, sweep blocks per SM, its table)."""
     from paper_1308_2166_gb300 import autotune
     if args.sort_tuning:
-        return tuple(int(x) for x in args.sort_tuning.split(",")), {}
-    if args.no_autotune:
-        return (8, 8, 2), {}
-    # a few batches of the stream on scratch contexts (untimed; results do
-    # not depend on the tuning)
-    return autotune.tune(views[:2], cfg["r"], cfg["vertex_bits"], seed=cfg["seed"] + 99,
-                         reps=1, stream=sh)
+        tuning, table = tuple(int(x) for x in args.sort_tuning.split(",")), {}
+    elif args.no_autotune:
+        tuning, table = (8, 8, 2), {}
+    else:
+        # a few batches of the stream on scratch contexts (untimed; results
+        # do not depend on the tuning)
+        tuning, table = autotune.tune(views[:2], cfg["r"], cfg["vertex_bits"],
+                                      seed=cfg["seed"] + 99, reps=1, stream=sh)
+    if args.sweep_blocks:
+        bps, stable = args.sweep_blocks, {}
+    elif args.no_autotune:
+        bps, stable = 6, {}
+    else:
+        bps, stable = autotune.tune_sweep(views[:6], cfg["r"], cfg["vertex_bits"], tuning,
+                                          seed=cfg["seed"] + 98, stream=sh)
+    return tuning, table, bps, stable
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -673,9 +691,9 @@ def run_gpu(args, rank, world, local_rank):
     cfg, views, host_keys = _single_workload(args.workload, args.stream_edges)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t_gen
-    tuning, tune_table = _tuning(args, tc, views, cfg, sh)
+    tuning, tune_table, bps, stable = _tuning(args, tc, views, cfg, sh)
     res = _time_single(tc, args, cfg, views, host_keys, rank, world, local_rank, dist, sh,
-                       stream, tuning, tune_table)
+                       stream, tuning, tune_table, bps, stable)
     K = args.steps
     line = {
         "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": K,
@@ -715,9 +733,9 @@ def _extra_rmat20(args, tc, rank, world, local_rank, sh, stream):
     of the default line: streams of 3.7 batches, each on a fresh context."""
     import torch
     cfg, views, host_keys = _single_workload("rmat20")
-    tuning, table = _tuning(args, tc, views, cfg, sh)
+    tuning, table, bps, stable = _tuning(args, tc, views, cfg, sh)
     res = _time_single(tc, args, cfg, views, host_keys, rank, 1, local_rank, None, sh, stream,
-                       tuning, table, with_clocks=False)
+                       tuning, table, bps, stable, with_clocks=False)
     out = {"value": res["value"], "unit": UNIT, "ms_per_step": res["t_ms"] / args.steps,
            "config": res["config"], "e2e": res["e2e"], "roofline": res["roofline"],
            "roofline_other_kernel": res["roofline_other_kernel"],
@@ -740,19 +758,27 @@ def _extra_multi(args, tc, local_rank):
 
 
 def run_multi(args, rank, world, local_rank, emit=True):
-    """512 independent Chung-Lu streams advanced round by round.
+    """512 independent Chung-Lu streams at their full lengths, advanced
+    together round by round (the batching configuration).
 
-    Per-stream batch w_s = min(w_cap, len_s // rounds) so that every stream
-    takes part in every round (streams of uneven length advance at uneven
-    rates); w_cap is picked by timing a few rounds of each candidate.  Three
-    ways to run the same rounds, on fresh state each, timed on the device:
-      back_to_back  one tc_process_batch_async per stream per round
-                    (a native loop over 512 single-stream contexts);
-      batched       one tc_multi_process_async per round;
+    Streams have m_s log-uniform in [1e4, 1e7] edges (about 7e8 in all),
+    r_s log-uniform in [2^10, 2^16] estimators, exponents in [2.1, 2.5].  A
+    stream is cut into T rounds of w_s = m_s // T edges, so every stream
+    takes part in every round and is used up by the last one; T (hence the
+    per-stream batch size) and the sort tuning are picked by timing a few
+    rounds of each candidate.  Rounds 0 .. T/2 - 1 run untimed, rounds T/2
+    .. T - 1 are timed: by then every stream has folded in half its edges,
+    so at most 1/(T/2 + 1) of its estimators replace their level-1 edge per
+    round.  Four ways to run the same rounds, each on fresh state:
       graph         the round captured once as a CUDA graph, replayed per
                     round after a device copy of that round's edges into the
-                    captured buffer (the copy is inside the timed region).
-    Outputs of the three are compared estimator by estimator at the end.
+                    captured buffer (the copy is inside the timed region);
+      batched       one tc_multi_process_async per round;
+      pipelined     tc_multi_process_ready_async (round k+1 sorted beside
+                    round k's sweep);
+      back_to_back  one tc_process_batch_async per stream per round (a
+                    native loop over 512 single-stream contexts).
+    Outputs of the four are compared estimator by estimator at the end.
     """
     import torch
     import paper_1308_2166_gb300 as tc
@@ -762,140 +788,159 @@ def run_multi(args, rank, world, local_rank, emit=True):
     torch.cuda.set_device(local_rank)
     build.build()
     tc.load()
-    S, T = 512, max(2, min(args.steps, 8))
-    caps = (2048, 4096, 8192, 16384)
-    streams, r, n = synth.multi_streams(S, per_stream_edges=T * max(caps), seed=1)
+    S = 512
+    t_gen = time.perf_counter()
+    streams, r, n = synth.multi_streams_device(S, seed=1)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t_gen
+    m = np.array([int(x.numel()) for x in streams], dtype=np.int64)
     B = int(max(1, int(n.max() - 1).bit_length()))
     seeds = np.arange(1, S + 1, dtype=np.uint64)
     sids = np.arange(S, dtype=np.uint32)
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
 
-    def rounds_for(cap):
-        ws = [min(cap, x.size // T) for x in streams]
+    def rounds_for(T):
+        ws = (m // T).astype(np.int64)
         offs = np.concatenate([[0], np.cumsum(ws)]).astype(np.uint64)
-        rounds, parts_all = [], []
-        for k in range(T):
-            parts = [streams[s][k * ws[s]:(k + 1) * ws[s]] for s in range(S)]
-            rounds.append(torch.from_numpy(np.concatenate(parts).view(np.int64)).cuda())
-            parts_all.append(parts)
-        return ws, offs, rounds, parts_all
+        rounds = [torch.cat([streams[s][k * ws[s]:(k + 1) * ws[s]] for s in range(S)])
+                  for k in range(T)]
+        return ws, offs, rounds
 
-    def time_batched(cap, nrounds, graph=False, tuning=None, ready=False):
-        ws, offs, rounds, _ = rounds_for(cap)
+    def run_batched(T, ws, offs, rounds, k_lo, k_hi, mode, tuning):
+        """Rounds 0 .. k_hi - 1 on a fresh engine; rounds k_lo .. k_hi - 1
+        timed.  Returns (engine, ms, launches in the timed rounds)."""
         M = tc.MultiStream(r, seeds, sids, w_max_round=int(offs[-1]), vertex_bits=B)
-        if tuning:
-            M.tune(*tuning)
+        M.tune(*tuning)
         buf = torch.empty_like(rounds[0])
-        if graph:
+        if mode == "graph":
             M.capture(buf, offs, sh)
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = 0
         with torch.cuda.stream(stream):
-            ev0.record(stream)
-            for k in range(nrounds):
-                if graph:
+            for k in range(k_hi):
+                if k == k_lo:
+                    stream.synchronize()
+                    l0 = M.launches()
+                    ev0.record(stream)
+                if mode == "graph":
                     buf.copy_(rounds[k], non_blocking=True)
                     M.replay(sh)
-                elif ready:
+                elif mode == "pipelined":   # every round's buffer is filled already
                     M.process_ready_async(rounds[k], offs, sh)
                 else:
                     M.process_async(rounds[k], offs, sh)
             ev1.record(stream)
         stream.synchronize()
-        ms = ev0.elapsed_time(ev1)
         errs = M.sync()
-        assert not errs.any(), "batched round rejected a stream"
-        return M, ms, int(offs[-1]) * nrounds, M.launches()
+        assert not errs.any(), "a round rejected a stream"
+        return M, ev0.elapsed_time(ev1), M.launches() - l0
 
-    tune, dtune = {}, {}
+    tune_T, tune_sort = {}, {}
+    cand_T = (16, 32, 64)
     if args.no_autotune:
-        cap, tuning = max(caps), (8, 8, 2)
+        T, tuning = 32, (8, 8, 2)
     else:
-        # autotune the per-stream batch cap on a few rounds (untimed for the result)
-        for cap in caps:
-            M, ms, edges, _ = time_batched(cap, 3)
-            tune[cap] = edges / (ms / 1e3)
+        # per-stream batch size: a few rounds (4..7) of each round count
+        for Tc in cand_T:
+            ws, offs, rounds = rounds_for(Tc)
+            M, ms, _ = run_batched(Tc, ws, offs, rounds, 4, 8, "batched", (8, 8, 2))
+            tune_T[Tc] = int(ws.sum()) * 4 / (ms / 1e3)
             M.close()
-        cap = max(tune, key=tune.get)
-        # then the sort tuning (digit widths, warp ranking) at that cap
+            del rounds
+        T = max(tune_T, key=tune_T.get)
+        ws, offs, rounds = rounds_for(T)
         for cand in ((8, 8, 2), (8, 8, 1), (8, 10, 2), (10, 8, 2), (10, 10, 2)):
-            M, ms, edges, _ = time_batched(cap, 3, tuning=cand)
-            dtune[cand] = edges / (ms / 1e3)
+            M, ms, _ = run_batched(T, ws, offs, rounds, 4, 8, "batched", cand)
+            tune_sort[cand] = int(ws.sum()) * 4 / (ms / 1e3)
             M.close()
-        tuning = max(dtune, key=dtune.get)
-    ws, offs, rounds, parts_all = rounds_for(cap)
-    edges_total = int(offs[-1]) * T
+        tuning = max(tune_sort, key=tune_sort.get)
+    ws, offs, rounds = rounds_for(T)
+    k_lo = T // 2
+    timed_rounds = T - k_lo
+    edges_timed = int(ws.sum()) * timed_rounds
 
-    sampler = ClockSampler(local_rank)
-    Mg, ms_graph, _, launches_graph = time_batched(cap, T, graph=True, tuning=tuning)
-    clocks = sampler.stop()
-    Mb, ms_batched, _, launches_b = time_batched(cap, T, graph=False, tuning=tuning)
-    Mp, ms_piped, _, _ = time_batched(cap, T, graph=False, tuning=tuning, ready=True)
+    sampler = ClockSampler(local_rank) if emit else None
+    Mg, ms_graph, launches_graph = run_batched(T, ws, offs, rounds, k_lo, T, "graph", tuning)
+    clocks = sampler.stop() if sampler else None
+    Mb, ms_batched, launches_b = run_batched(T, ws, offs, rounds, k_lo, T, "batched", tuning)
+    Mp, ms_piped, _ = run_batched(T, ws, offs, rounds, k_lo, T, "pipelined", tuning)
 
     # back to back: one single-stream context per stream
-    ctxs = [tc.tc_create_ex(int(r[s]), int(seeds[s]), int(sids[s]), max(1, ws[s]), B)
+    ctxs = [tc.tc_create_ex(int(r[s]), int(seeds[s]), int(sids[s]), max(1, int(ws[s])), B)
             for s in range(S)]
     for cx in ctxs:                      # the same sort tuning as the rounds
         tc.tc_tune(cx, *tuning)
-    dev_parts = []
-    for k in range(T):
-        base = rounds[k]
-        views, o = [], 0
+
+    def parts_of(k):
+        base, views, o = rounds[k], [], 0
         for s in range(S):
-            views.append(base[o:o + ws[s]])
-            o += ws[s]
-        dev_parts.append(views)
-    torch.cuda.synchronize()
+            views.append(base[o:o + int(ws[s])])
+            o += int(ws[s])
+        return views
+
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0 = time.perf_counter()
     with torch.cuda.stream(stream):
-        ev0.record(stream)
         for k in range(T):
-            tc.tc_process_batches_async(ctxs, dev_parts[k], sh)
+            if k == k_lo:
+                stream.synchronize()
+                ev0.record(stream)
+            tc.tc_process_batches_async(ctxs, parts_of(k), sh)
         ev1.record(stream)
     stream.synchronize()
     ms_b2b = ev0.elapsed_time(ev1)
+    for cx in ctxs:
+        tc.tc_sync(cx)
 
     identical = True
     for s in range(S):
         a = Mg.state(s)
-        b = Mb.state(s)
-        c = tc.tc_get_state(ctxs[s])
-        d = Mp.state(s)
-        for x, y, z, t in zip(a, b, c, d):
-            if not (np.array_equal(x, y) and np.array_equal(x, z) and np.array_equal(x, t)):
-                identical = False
+        for other in (Mb.state(s), Mp.state(s), tc.tc_get_state(ctxs[s])):
+            for x, y in zip(a, other):
+                if not np.array_equal(x, y):
+                    identical = False
     for cx in ctxs:
         tc.tc_destroy(cx)
     Mg.close()
     Mb.close()
     Mp.close()
-    val = edges_total / (ms_graph / 1e3)
+    del rounds
+    torch.cuda.empty_cache()
+    val = edges_timed / (ms_graph / 1e3)
+    per_round_launch = 5 + 1 + -(-B // tuning[0]) + -(-max(1, int(ws.max() - 1).bit_length() - 2)
+                                                       // tuning[1])
     line = {
         "metric": "aggregate edges/s, 512 streams advanced together (round = one CUDA graph)",
-        "value": val, "unit": UNIT, "n_gpus": 1, "steps": T, "warmup": 0,
-        "ms_per_step": ms_graph / T, "higher_is_better": True, "scaling": "weak",
+        "value": val, "unit": UNIT, "n_gpus": 1, "steps": timed_rounds, "warmup": k_lo,
+        "ms_per_step": ms_graph / timed_rounds, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": f"multi512: {S} Chung-Lu streams, gamma U[2.1,2.5], m log-uniform "
-                               f"[1e4,1e7], r log-uniform [2^10,2^16]; per-stream batch "
-                               f"min(w_cap, len/rounds)",
-                   "streams": S, "rounds": T, "w_cap": cap, "round_edges": int(offs[-1]),
-                   "estimators": int(r.sum()), "vertex_bits": B,
-                   "w_cap_table": {str(k): v for k, v in tune.items()},
+        "config": {"workload": f"multi512: {S} Chung-Lu streams, gamma U[2.1,2.5], m "
+                               f"log-uniform [1e4,1e7] (full lengths, {int(m.sum())} edges), "
+                               f"r log-uniform [2^10,2^16]; stream s cut into T rounds of "
+                               f"m_s // T edges, rounds T/2..T-1 timed",
+                   "streams": S, "rounds": T, "timed_rounds": timed_rounds,
+                   "round_edges": int(offs[-1]), "edges_total": int(m.sum()),
+                   "stream_edges_min_max": [int(m.min()), int(m.max())],
+                   "estimators": int(r.sum()), "vertex_bits": B, "stream_gen_s": round(gen_s, 1),
+                   "replacement_bound_timed": 1.0 / (k_lo + 1),
+                   "rounds_table": {str(k): v for k, v in tune_T.items()},
                    "sort_tuning": {"arc_digit_bits": tuning[0], "edge_digit_bits": tuning[1],
                                    "ranking": "match" if tuning[2] == 1 else "ballot",
                                    "table": {f"{a}/{b}/{'match' if c == 1 else 'ballot'}": v
-                                             for (a, b, c), v in dtune.items()}}},
-        "updates_per_s": float(sum(int(r[s2]) * ws[s2] for s2 in range(S))) * T / (ms_graph / 1e3),
-        "batched_plain": {"value": edges_total / (ms_batched / 1e3), "ms_per_round": ms_batched / T,
-                          "launches_per_round": launches_b / T},
-        "batched_pipelined": {"value": edges_total / (ms_piped / 1e3),
-                              "ms_per_round": ms_piped / T,
+                                             for (a, b, c), v in tune_sort.items()}}},
+        "updates_per_s": float((r.astype(np.float64) * ws).sum()) * timed_rounds /
+                         (ms_graph / 1e3),
+        "batched_plain": {"value": edges_timed / (ms_batched / 1e3),
+                          "ms_per_round": ms_batched / timed_rounds,
+                          "launches_per_round": launches_b / timed_rounds},
+        "batched_pipelined": {"value": edges_timed / (ms_piped / 1e3),
+                              "ms_per_round": ms_piped / timed_rounds,
                               "how": "tc_multi_process_ready_async: each round's sorts beside "
                                      "the previous round's sweep"},
-        "back_to_back": {"value": edges_total / (ms_b2b / 1e3), "ms_per_round": ms_b2b / T,
-                         "launches_per_round": sum(1 for w in ws if w) * (5 + -(-B // 8) + -(-2 * B // 8))},
+        "back_to_back": {"value": edges_timed / (ms_b2b / 1e3),
+                         "ms_per_round": ms_b2b / timed_rounds,
+                         "launches_per_round": S * (per_round_launch - 1)},
         "speedup_vs_back_to_back": ms_b2b / ms_graph,
         "identical_outputs": identical,
         "gpu_launches": launches_graph,
@@ -1051,6 +1096,8 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
     lat_q = (queries["t_done_ns"] - queries["t_submit_ns"]) / 1e6
     wait_b = (batches["t_admit_ns"] - batches["t_submit_ns"]) / 1e6
     serv_b = (batches["t_done_ns"] - batches["t_admit_ns"]) / 1e6
+    queue_b = (batches["t_round_ns"].astype(np.int64) - batches["t_admit_ns"].astype(np.int64)) / 1e6
+    round_b = (batches["t_done_ns"].astype(np.int64) - batches["t_round_ns"].astype(np.int64)) / 1e6
     pct = (lambda a, q: float(np.percentile(a, q)) if a.size else None)
     lags = np.asarray(lags) * 1e3
     extra = {}
@@ -1060,7 +1107,9 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
         extra = {"client_lag_ms": {"p50": pct(lags, 50), "p99": pct(lags, 99),
                                    "max": float(lags.max()) if lags.size else None},
                  "batch_wait_ms": {"p50": pct(wait_b, 50), "p99": pct(wait_b, 99)},
-                 "batch_service_ms": {"p50": pct(serv_b, 50), "p99": pct(serv_b, 99)}}
+                 "batch_service_ms": {"p50": pct(serv_b, 50), "p99": pct(serv_b, 99)},
+                 "batch_queue_ms": {"p50": pct(queue_b, 50), "p99": pct(queue_b, 99)},
+                 "batch_round_ms": {"p50": pct(round_b, 50), "p99": pct(round_b, 99)}}
         # where the slow batches sit in the phase (admission time, 50 ms bins)
         lat_all = (batches["t_done_ns"] - batches["t_submit_ns"]) / 1e6
         slow = lat_all > 5.0
@@ -1068,6 +1117,9 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
             at = (batches["t_admit_ns"][slow].astype(np.int64) - first) / 1e6
             bins, cnt = np.unique((at // 50).astype(np.int64), return_counts=True)
             extra["slow_batches"] = {"over_ms": 5.0, "count": int(slow.sum()),
+                                     "mean_ms": {"admission_wait": float(wait_b[slow].mean()),
+                                                 "round_queue": float(queue_b[slow].mean()),
+                                                 "round": float(round_b[slow].mean())},
                                      "admit_bins_50ms": {str(int(k) * 50): int(c)
                                                          for k, c in zip(bins[:20], cnt[:20])},
                                      "max_ms": float(lat_all.max()),
@@ -1086,6 +1138,8 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
         "max_round_edges": int(st1["max_round_edges"]),
         "max_round_streams": int(st1["max_round_streams"]),
         "admission_waits": int(st1["admission_waits"]),
+        "sched_gap_max_ms": st1["sched_gap_max_ns"] / 1e6,
+        "sched_gaps_over_5ms": int(st1["sched_gaps_over_5ms"] - st0["sched_gaps_over_5ms"]),
         "bytes_peak": int(st1["bytes_peak"]), "bytes_fixed": int(st1["bytes_fixed"]),
         "opens": int(st1["opens"]), "closes": int(st1["closes"]),
     }

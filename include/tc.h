@@ -217,7 +217,8 @@ int tc_profile_end(tc_ctx *c, tc_profile_t *out);
 
 /* Launch tuning of the two radix sorts (rankAll's arcs, Lemma 4.3; Step 3's
  * edges, Sec. 4.4).  arc_digit_bits / edge_digit_bits: 0 (automatic: 8-bit
- * digits over the live key bits, measured fastest), 8, 10 or 11.  ranking (how a warp
+ * digits over the live key bits, or 9-bit ones where they save a pass), 8,
+ * 9, 10 or 11.  ranking (how a warp
  * finds the lanes holding equal digits): 0 or 2 = one ballot per digit bit
  * (the default), 1 = one match.any per key, 3 = lanes OR their bit into a
  * shared-memory word per (warp, digit; 8-bit digits only, else match.any).
@@ -225,6 +226,25 @@ int tc_profile_end(tc_ctx *c, tc_profile_t *out);
  * afterwards.
  * Errors: TC_ERR_INVAL for other values. */
 int tc_tune(tc_ctx *c, uint32_t arc_digit_bits, uint32_t edge_digit_bits, uint32_t ranking);
+
+/* Launch shape of the estimator sweep (fused Steps 1-3): blocks of 256
+ * threads per SM, 1..6 (0 = 6, the default: one resident wave).  The sweep
+ * is bound by random DRAM reads and the digit passes by integer issue, so a
+ * wave of fewer blocks per SM leaves room for the next batch's sort passes
+ * to run beside it when batches are pipelined.  Results do not depend on
+ * it.  Applies to batches enqueued afterwards.  Errors: TC_ERR_INVAL. */
+int tc_tune_sweep(tc_ctx *c, uint32_t blocks_per_sm);
+
+/* Key of the 32-bit edge hash that orders the Step-3 lookup keys (Sec. 4.4's
+ * `edges` array, sorted here by hash bucket).  Results never depend on the
+ * key: a lookup checks every candidate against the batch itself.  Each
+ * context starts with a key drawn from the operating system's entropy
+ * source, so that no batch can be crafted to crowd its edges into a few
+ * hash runs (the repeat check and the lookups scan a run, so crowded runs
+ * would cost time quadratic in their length); a fixed key makes the bucket
+ * layout reproducible, for tests that build such runs on purpose.  Applies
+ * to batches enqueued afterwards.  Errors: TC_ERR_INVAL. */
+int tc_set_hash_key(tc_ctx *c, uint64_t key);
 
 /* Free the context and its device memory (NULL is a no-op). */
 void tc_destroy(tc_ctx *c);
@@ -332,6 +352,10 @@ int tc_multi_get_counters(tc_multi *M, uint32_t s, uint64_t *r, uint64_t *m,
 int tc_multi_tune(tc_multi *M, uint32_t arc_digit_bits, uint32_t edge_digit_bits,
                   uint32_t ranking);
 
+/* Key of the Step-3 edge hash for later rounds, as tc_set_hash_key (each
+ * engine starts with a random key). */
+int tc_multi_set_hash_key(tc_multi *M, uint64_t key);
+
 /* Library kernels launched by this object so far. */
 int tc_multi_launches(tc_multi *M, uint64_t *launches);
 
@@ -391,6 +415,10 @@ typedef struct {
      * tc_estimate_t; zero for open and close */
     uint64_t num_lo, num_hi;
     double tau_hat;
+    /* host steady-clock nanoseconds when the request's round was formed and
+     * enqueued (zero for an open): t_round - t_admit is the wait for a round
+     * slot, t_done - t_round the round itself */
+    uint64_t t_round_ns;
 } tc_completion_t;
 
 typedef struct {
@@ -401,6 +429,10 @@ typedef struct {
     uint64_t admission_waits;   /* head requests that had to wait for memory or a slot */
     uint64_t max_round_edges, max_round_streams;
     uint64_t bytes_budget, bytes_fixed, bytes_reserved, bytes_peak;
+    /* the longest stretch between two scheduler passes while work was in
+     * flight or waiting (beyond the scheduler's own bounded waits), and how
+     * many stretches exceeded 5 ms: stalls of the scheduler thread itself */
+    uint64_t sched_gap_max_ns, sched_gaps_over_5ms;
 } tc_server_stats_t;
 
 /* Errors: TC_ERR_INVAL (bad config; key bits as tc_multi_create with

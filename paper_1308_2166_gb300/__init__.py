@@ -39,7 +39,8 @@ EXPORTS = (
     "tc_server_close", "tc_server_poll", "tc_server_drain", "tc_server_stats",
     "tc_server_destroy", "tc_selftest_wait_timeout", "tc_save_size", "tc_save", "tc_load",
     "tc_process_batch_host_async", "tc_process_batch_ready_async",
-    "tc_multi_process_ready_async", "tc_server_submit_many",
+    "tc_multi_process_ready_async", "tc_server_submit_many", "tc_set_hash_key",
+    "tc_multi_set_hash_key", "tc_tune_sweep",
 )
 
 TC_REQ_OPEN, TC_REQ_BATCH, TC_REQ_QUERY, TC_REQ_CLOSE = 1, 2, 3, 4
@@ -105,13 +106,13 @@ class tc_completion_t(ctypes.Structure):
                 ("m", ctypes.c_uint64), ("t_submit_ns", ctypes.c_uint64),
                 ("t_admit_ns", ctypes.c_uint64), ("t_done_ns", ctypes.c_uint64),
                 ("num_lo", ctypes.c_uint64), ("num_hi", ctypes.c_uint64),
-                ("tau_hat", ctypes.c_double)]
+                ("tau_hat", ctypes.c_double), ("t_round_ns", ctypes.c_uint64)]
 
 
 _STATS_FIELDS = ("rounds", "kernel_launches", "batches", "rejected", "edges", "queries", "opens",
                  "closes", "streams_open", "requests_waiting", "admission_waits",
                  "max_round_edges", "max_round_streams", "bytes_budget", "bytes_fixed",
-                 "bytes_reserved", "bytes_peak")
+                 "bytes_reserved", "bytes_peak", "sched_gap_max_ns", "sched_gaps_over_5ms")
 
 
 class tc_server_stats_t(ctypes.Structure):
@@ -142,6 +143,9 @@ def load(path: str | None = None):
         "tc_profile_begin": (I, [P]),
         "tc_profile_end": (I, [P, ctypes.POINTER(tc_profile_t)]),
         "tc_tune": (I, [P, U32, U32, U32]),
+        "tc_set_hash_key": (I, [P, U64]),
+        "tc_tune_sweep": (I, [P, U32]),
+        "tc_multi_set_hash_key": (I, [P, U64]),
         "tc_estimate_mom": (I, [P, U32, ctypes.POINTER(U64), ctypes.POINTER(U64),
                                 ctypes.POINTER(U64), ctypes.POINTER(ctypes.c_double)]),
         "tc_get_state": (I, [P, P, P, P, P]),
@@ -301,6 +305,14 @@ def tc_profile_end(ctx: int) -> dict:
 
 def tc_tune(ctx: int, arc_digit_bits: int = 0, edge_digit_bits: int = 0, ranking: int = 0) -> None:
     _check(load().tc_tune(ctx, arc_digit_bits, edge_digit_bits, ranking), "tc_tune")
+
+
+def tc_tune_sweep(ctx: int, blocks_per_sm: int = 0) -> None:
+    _check(load().tc_tune_sweep(ctx, blocks_per_sm), "tc_tune_sweep")
+
+
+def tc_set_hash_key(ctx: int, key: int) -> None:
+    _check(load().tc_set_hash_key(ctx, key), "tc_set_hash_key")
 
 
 def tc_estimate_mom(ctx: int, g: int) -> dict:
@@ -519,6 +531,9 @@ class MultiStream:
         _check(load().tc_multi_tune(self.h, arc_digit_bits, edge_digit_bits, ranking),
                "tc_multi_tune")
 
+    def set_hash_key(self, key: int):
+        _check(load().tc_multi_set_hash_key(self.h, key), "tc_multi_set_hash_key")
+
     def launches(self) -> int:
         v = ctypes.c_uint64()
         _check(load().tc_multi_launches(self.h, ctypes.byref(v)), "tc_multi_launches")
@@ -548,7 +563,8 @@ def _completion_dtype():
             ("ticket", "<u8"), ("handle", "<u4"), ("kind", "<i4"), ("status", "<i4"),
             ("pad", "<u4"), ("batches", "<u8"), ("sum_lo", "<u8"), ("sum_hi", "<u8"),
             ("n_closed", "<u8"), ("m", "<u8"), ("t_submit_ns", "<u8"), ("t_admit_ns", "<u8"),
-            ("t_done_ns", "<u8"), ("num_lo", "<u8"), ("num_hi", "<u8"), ("tau_hat", "<f8")])
+            ("t_done_ns", "<u8"), ("num_lo", "<u8"), ("num_hi", "<u8"), ("tau_hat", "<f8"),
+            ("t_round_ns", "<u8")])
         assert COMPLETION_DTYPE.itemsize == ctypes.sizeof(tc_completion_t)
     return COMPLETION_DTYPE
 

@@ -2,6 +2,8 @@
 // per-batch launch sequence of bulkUpdateAll (Sec. 4), the estimate of
 // Lemma 3.1, stage timing and the standalone rankAll (Lemma 4.3).
 #include <algorithm>
+#include <chrono>
+#include <random>
 #include <atomic>
 #include <cstdint>
 #include <cstdio>
@@ -73,6 +75,7 @@ PassKernel select_pass(u32 bits, bool values, int rank) {
         return k;
     switch (bits) {
         TC_PASS_CASE(8)
+        TC_PASS_CASE(9)
         TC_PASS_CASE(10)
         default:
         TC_PASS_CASE(11)
@@ -81,7 +84,7 @@ PassKernel select_pass(u32 bits, bool values, int rank) {
 #undef TC_PASS_RANK
 }
 
-constexpr u32 kDigitChoices[3] = {8, 10, 11};
+constexpr u32 kDigitChoices[4] = {8, 9, 10, 11};
 
 int configure_kernels() {
     static bool done[64] = {false};
@@ -101,9 +104,30 @@ int configure_kernels() {
     return TC_OK;
 }
 
+}  // namespace
+
+// A fresh key for the Step-3 edge hash, from the OS's entropy source (with a
+// clock-based fallback where none is available).  Results never depend on it.
+u64 tc::random_hash_key() {
+    u64 k = 0;
+    try {
+        std::random_device rd;
+        k = ((u64)rd() << 32) ^ (u64)rd();
+    } catch (...) {
+    }
+    if (!k) k = (u64)std::chrono::steady_clock::now().time_since_epoch().count() *
+                0x9E3779B97F4A7C15ull;
+    return k;
+}
+
+namespace {
+
 // Digit width and pass count for `live` key bits: 8-bit digits unless
-// tc_tune forced another width (8-bit passes measured fastest on GB300: a
-// wider digit saves passes but each pass costs more than it saves).
+// tc_tune forced another width.  On GB300 the 8-bit passes measured fastest:
+// a wider digit saves passes but each pass costs more than it saves (at
+// 25-bit ids three 9-bit arc passes took 1.05 ms per batch against 0.95 ms
+// for four 8-bit ones, the last of which ranks one live bit; 10- and 11-bit
+// passes run at 2 or 3 blocks per SM for their shared-memory counters).
 u32 pick_digits(u32 live, u32 forced, int &passes) {
     const u32 bits = forced ? forced : 8;
     passes = (int)((live + bits - 1) / bits);
@@ -118,8 +142,9 @@ u32 hash_bucket_bits(u64 w) {
     return bw > 3 ? bw - 2 : 1;
 }
 
-BatchShape make_shape(u64 w, u32 B, u32 force_a = 0, u32 force_e = 0) {
+BatchShape make_shape(u64 w, u32 B, u32 force_a = 0, u32 force_e = 0, u64 hkey = 0) {
     BatchShape s{};
+    s.hkey = hkey;
     s.w = (u32)w;
     s.bw = bits_for(w - 1);
     s.B = B;
@@ -185,6 +210,8 @@ struct tc_ctx {
     u64 cap_w = 0;                           // scratch capacity in edges
     u32 force_bits_a = 0, force_bits_e = 0;  // tc_tune digit widths (0 = automatic)
     int rank_method = kRankBallot;           // tc_tune warp ranking method
+    u32 sweep_bps = kSweepBlocksPerSM;       // tc_tune_sweep: sweep blocks per SM
+    u64 hash_key = 0;                        // Step-3 edge hash key (random per context)
     cudaStream_t own = nullptr;
     // the edge sort runs on `side`, concurrently with the arc sort
     cudaStream_t side = nullptr;
@@ -204,8 +231,11 @@ struct tc_ctx {
         u64 *arcs[2] = {nullptr, nullptr};
         u64 *ekeys[2] = {nullptr, nullptr};
         unsigned char *zeroed = nullptr;  // BatchAcc, error word, SortPlan[2], look-back
-        DirEntry *adir = nullptr;         // per-vertex arc directory (ids < 2^kDirMaxBits)
+        DirEntry *adir = nullptr;         // tagged arc directory (ids < 2^kDirMaxBits; made
+                                          // by the first batch that needs it)
+        u32 *aoff = nullptr;              // dense arc offsets, 2^B + 1 (ids < 2^kDirMaxBits)
         DirEntry *edir = nullptr;         // Step-3 hash-bucket directory
+        u32 *efilt = nullptr;             // Step-3 filter masks (one per hash bucket)
     };
     Set set[2];
     int nsets = 1;
@@ -264,12 +294,16 @@ static void free_set(tc_ctx::Set &z, bool with_dir) {
         z.arcs[k] = z.ekeys[k] = nullptr;
     }
     cudaFree(z.edir);
+    cudaFree(z.efilt);
     cudaFree(z.zeroed);
     z.edir = nullptr;
+    z.efilt = nullptr;
     z.zeroed = nullptr;
     if (with_dir) {
         cudaFree(z.adir);
+        cudaFree(z.aoff);
         z.adir = nullptr;
+        z.aoff = nullptr;
     }
 }
 
@@ -294,13 +328,34 @@ static bool alloc_set(tc_ctx *c, tc_ctx::Set &z, u64 w) {
     const u64 nb = 1ull << hash_bucket_bits(w);
     ok &= ok && cudaMalloc(&z.edir, nb * sizeof(DirEntry)) == cudaSuccess;
     ok &= ok && cudaMemset(z.edir, 0, nb * sizeof(DirEntry)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&z.efilt, nb * sizeof(u32)) == cudaSuccess;
     ok &= ok && cudaMalloc(&z.zeroed, zb) == cudaSuccess;
-    if (ok && !z.adir && c->vertex_bits <= kDirMaxBits) {
+    if (ok && !z.aoff && c->vertex_bits <= kDirMaxBits) {
         const u64 nverts = 1ull << c->vertex_bits;
-        ok &= cudaMalloc(&z.adir, nverts * sizeof(DirEntry)) == cudaSuccess;
-        ok &= ok && cudaMemset(z.adir, 0, nverts * sizeof(DirEntry)) == cudaSuccess;
+        ok &= cudaMalloc(&z.aoff, (nverts + 1) * sizeof(u32)) == cudaSuccess;
     }
     return ok;
+}
+
+// How a batch of w edges finds its arc runs: the dense offsets when writing
+// all 2^B + 1 of them costs no more than one arc pass moves (2^B <= 8w), the
+// tagged directory for smaller batches, binary search beyond 2^kDirMaxBits ids.
+static int arc_dir_mode(u32 B, u64 w) {
+    if (B > kDirMaxBits) return kArcSearch;
+    return ((1ull << B) <= 8 * w) ? kArcDense : kArcTagged;
+}
+
+// The tagged directory of a set, made on first need (all tags 0: no entry
+// is valid for a batch, whose tags start at 1).
+static int ensure_tagged_dir(tc_ctx *c, tc_ctx::Set &z, cudaStream_t st) {
+    if (z.adir) return TC_OK;
+    const u64 nverts = 1ull << c->vertex_bits;
+    if (cudaMalloc(&z.adir, nverts * sizeof(DirEntry)) != cudaSuccess) {
+        cudaGetLastError();
+        return TC_ERR_NOMEM;
+    }
+    TC_CUDA(cudaMemsetAsync(z.adir, 0, nverts * sizeof(DirEntry), st));
+    return TC_OK;
 }
 
 static int ensure_scratch(tc_ctx *c, u64 w) {
@@ -346,9 +401,23 @@ static int map_device_error(u32 e) {
 static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool pipelined = false,
                          cudaEvent_t w_ready = nullptr) {
     const NvtxRange range("tc batch");
-    const BatchShape s = make_shape(w, c->vertex_bits, c->force_bits_a, c->force_bits_e);
+    const BatchShape s =
+        make_shape(w, c->vertex_bits, c->force_bits_a, c->force_bits_e, c->hash_key);
     const int b = c->nsets == 2 ? (int)(c->seq & 1) : 0;
-    const u32 tag = ++c->seq;
+    u32 tag = ++c->seq;
+    if (tag == 0) {
+        // the directory tags wrapped (after 2^32 batches): clear every tagged
+        // entry so that no stale entry can carry a reused tag, and skip tag 0
+        TC_CUDA(cudaDeviceSynchronize());
+        for (int k = 0; k < c->nsets; ++k) {
+            if (c->set[k].adir)
+                TC_CUDA(cudaMemset(c->set[k].adir, 0,
+                                   (sizeof(DirEntry) << c->vertex_bits)));
+            TC_CUDA(cudaMemset(c->set[k].edir, 0,
+                               (sizeof(DirEntry) << hash_bucket_bits(c->cap_w))));
+        }
+        tag = ++c->seq;
+    }
     tc_ctx::Set &z = c->set[b];
     BatchAcc *acc = reinterpret_cast<BatchAcc *>(z.zeroed);
     u32 *berr = reinterpret_cast<u32 *>(z.zeroed + kOffErr);
@@ -360,6 +429,11 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
     // the set's previous batch may have been swept on another stream
     TC_CUDA(cudaStreamWaitEvent(ms, c->ev_swept[b], 0));
     if (w_ready) TC_CUDA(cudaStreamWaitEvent(ms, w_ready, 0));
+    const int dmode = arc_dir_mode(c->vertex_bits, w);
+    if (dmode == kArcTagged) {
+        const int rc = ensure_tagged_dir(c, z, ms);
+        if (rc) return rc;
+    }
     const bool stages = !pipelined;
     if (stages) stamp(c, ms, kStart);
     TC_CUDA(cudaMemsetAsync(z.zeroed, 0, used, ms));
@@ -386,8 +460,9 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
             z.ekeys[0], z.ekeys[1], nullptr, nullptr, (u32)w, s.she + p * s.bits_e,
             live_bits(s.hs, s.bits_e, p), p, &plans[1], lbe + (u64)p * le, berr, c->ctl);
     const cudaEvent_t edge_end = mark(c, c->side);
+    TC_CUDA(cudaMemsetAsync(z.efilt, 0, (sizeof(u32) << s.hb), c->side));
     index_kernel<false><<<index_blocks(w), kIdxThreads, 0, c->side>>>(
-        z.ekeys[0], z.ekeys[1], &plans[1], s, z.edir, W, tag, berr);
+        z.ekeys[0], z.ekeys[1], &plans[1], s, z.edir, W, tag, berr, z.efilt);
     TC_CUDA(cudaEventRecord(c->ev_join, c->side));
     for (int p = 0; p < s.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, ms>>>(
@@ -396,7 +471,10 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
     const cudaEvent_t arc_end = mark(c, ms);
     if (sort_begin && edge_end && arc_end) c->spans.push_back({sort_begin, arc_end, edge_end});
     if (stages) stamp(c, ms, kArcSort);  // arc passes, with the edge passes beside them
-    if (z.adir)
+    if (dmode == kArcDense)
+        offsets_kernel<<<index_blocks(2 * w), kIdxThreads, 0, ms>>>(z.arcs[0], z.arcs[1],
+                                                                     &plans[0], s, z.aoff);
+    else if (dmode == kArcTagged)
         index_kernel<true><<<index_blocks(2 * w), kIdxThreads, 0, ms>>>(
             z.arcs[0], z.arcs[1], &plans[0], s, z.adir, W, tag, berr);
     if (stages) stamp(c, ms, kDups);  // the arc index, beside the rest of the edge branch
@@ -420,7 +498,9 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
     a.ekeys1 = z.ekeys[1];
     a.plans = plans;
     a.adir = z.adir;
+    a.aoff = z.aoff;
     a.edir = z.edir;
+    a.efilt = z.efilt;
     a.ctl = c->ctl;
     a.acc = acc;
     a.berr = berr;
@@ -428,17 +508,20 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
     a.s = s;
     a.key = make_uint2((u32)(c->seed & 0xFFFFFFFFu), (u32)(c->seed >> 32));
     a.stream = c->stream_id;
-    if (z.adir)
-        sweep_kernel<true><<<sweep_blocks(c->r, c->sm_count), kSweepThreads, 0, st>>>(a);
+    const unsigned sb = sweep_blocks(c->r, c->sm_count, c->sweep_bps);
+    if (dmode == kArcDense)
+        sweep_kernel<kArcDense><<<sb, kSweepThreads, 0, st>>>(a);
+    else if (dmode == kArcTagged)
+        sweep_kernel<kArcTagged><<<sb, kSweepThreads, 0, st>>>(a);
     else
-        sweep_kernel<false><<<sweep_blocks(c->r, c->sm_count), kSweepThreads, 0, st>>>(a);
+        sweep_kernel<kArcSearch><<<sb, kSweepThreads, 0, st>>>(a);
     stamp(c, st, kSweep);
     finish_kernel<<<1, 1, 0, st>>>(c->ctl, acc, berr, w);
     stamp(c, st, kFinish);
     // this set is free again once the sweep and bookkeeping have read it
     TC_CUDA(cudaEventRecord(c->ev_swept[b], st));
     TC_CUDA(cudaGetLastError());
-    c->launches += (z.adir ? 6 : 5) + (u64)s.npa + (u64)s.npe;
+    c->launches += (dmode != kArcSearch ? 6 : 5) + (u64)s.npa + (u64)s.npe;
     if (c->prof) {
         c->prof_batches += 1;
         c->prof_sort_launches += (u64)s.npa + (u64)s.npe;
@@ -496,6 +579,7 @@ int tc_create_ex(uint64_t r, uint64_t seed, uint32_t stream_id, uint64_t w_max,
     c->seed = seed;
     c->stream_id = stream_id;
     c->vertex_bits = vertex_bits;
+    c->hash_key = random_hash_key();
     bool ok = cudaGetDevice(&c->device) == cudaSuccess;
     ok &= ok && cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) ==
                     cudaSuccess;
@@ -739,8 +823,20 @@ int tc_get_state(tc_ctx *c, uint64_t *f1, uint64_t *f2, uint64_t *chi, uint32_t 
     return TC_OK;
 }
 
+int tc_tune_sweep(tc_ctx *c, uint32_t blocks_per_sm) {
+    if (!c || blocks_per_sm > kSweepBlocksPerSM) return TC_ERR_INVAL;
+    c->sweep_bps = blocks_per_sm ? blocks_per_sm : kSweepBlocksPerSM;
+    return TC_OK;
+}
+
+int tc_set_hash_key(tc_ctx *c, uint64_t key) {
+    if (!c) return TC_ERR_INVAL;
+    c->hash_key = key;
+    return TC_OK;
+}
+
 int tc_tune(tc_ctx *c, uint32_t arc_digit_bits, uint32_t edge_digit_bits, uint32_t ranking) {
-    auto ok_bits = [](uint32_t b) { return b == 0 || b == 8 || b == 10 || b == 11; };
+    auto ok_bits = [](uint32_t b) { return b == 0 || (b >= 8 && b <= 11); };
     if (!c || !ok_bits(arc_digit_bits) || !ok_bits(edge_digit_bits) || ranking > 3)
         return TC_ERR_INVAL;
     c->force_bits_a = arc_digit_bits;

@@ -144,6 +144,9 @@ __host__ __device__ __forceinline__ void finish_estimate(u64 s_lo, u64 s_hi, u64
     out->batches = batches;
 }
 
+// A fresh random key for the Step-3 edge hash (host; defined in tc_api.cu).
+u64 random_hash_key();
+
 __host__ __device__ __forceinline__ u32 bits_for(u64 x) {
     // number of bits needed to hold values 0..x (at least 1)
     u32 b = 1;

@@ -44,14 +44,19 @@ struct BatchShape {
     int npe;        // edge sort passes
     u32 bits_a;     // arc sort digit width
     u32 bits_e;     // edge sort digit width
+    u64 hkey;       // key of the Step-3 edge hash
 };
 
-// 32-bit mix of a packed edge (u << 32) | v for the Step-3 keys: the
-// finaliser of Steele, Lea and Flood's SplitMix64 (OOPSLA 2014, constants
-// as published by Vigna), high half.  Any fixed mix gives the same lookup
-// results -- a lookup verifies the edge itself -- a good one keeps the
-// buckets even whatever the degree distribution.
-__host__ __device__ __forceinline__ u32 edge_hash(u64 x) {
+// 32-bit keyed mix of a packed edge (u << 32) | v for the Step-3 keys: the
+// edge xor a 64-bit key, through the finaliser of Steele, Lea and Flood's
+// SplitMix64 (OOPSLA 2014, constants as published by Vigna), high half.
+// Any key gives the same lookup results -- a lookup verifies the edge
+// itself -- and a key drawn at random per context keeps the buckets even
+// whatever the batch: a batch crafted to pile its edges into a few runs of
+// equal sorted bits (which the repeat check and the lookups scan) would have
+// to know the key.
+__host__ __device__ __forceinline__ u32 edge_hash(u64 x, u64 key) {
+    x ^= key;
     x ^= x >> 30;
     x *= 0xbf58476d1ce4e5b9ull;
     x ^= x >> 27;
@@ -109,7 +114,7 @@ static __global__ void __launch_bounds__(kPrepThreads) prep_kernel(
                 atomicAdd(&h[p * ra + digit_bits(av, s.sha + p * s.bits_a, ma)], 1u);
             }
             if (build_edges) {
-                const u64 ek = ((u64)edge_hash(e) << s.bw) | j;
+                const u64 ek = ((u64)edge_hash(e, s.hkey) << s.bw) | j;
                 ekeys0[j] = ek;
                 for (int p = 0; p < s.npe; ++p)
                     atomicAdd(&he[p * re + digit_bits(ek, s.she + p * s.bits_e, me)], 1u);
@@ -186,10 +191,18 @@ constexpr int kIdxThreads = 256;
 constexpr int kIdxItems = 8;
 constexpr int kIdxTile = kIdxThreads * kIdxItems;
 
+// Step-3 filter: one 32-bit mask per hash bucket (the top hb bits of h),
+// bit (h >> (27 - hb)) & 31 set for every edge of the batch.  A closing pair
+// whose bit is clear has no edge in the batch, so its lookup stops there; at
+// about four edges per bucket, a pair with no edge sees its bit set about
+// one time in eight.  The mask array is zeroed before the pass that builds
+// it (index_kernel<false>).
+__device__ __forceinline__ u32 filter_bit(u64 h, u32 hb) { return 1u << ((h >> (27 - hb)) & 31); }
+
 template <bool kArcs>
 static __global__ void __launch_bounds__(kIdxThreads) index_kernel(
     const u64 *keys0, const u64 *keys1, const SortPlan *plan, BatchShape s, DirEntry *dir,
-    const u64 *__restrict__ W, u32 epoch, u32 *err) {
+    const u64 *__restrict__ W, u32 epoch, u32 *err, u32 *efilt = nullptr) {
     __shared__ u64 st[kIdxTile + 2];  // st[1 + i] = key t0 + i; st[0], st[kIdxTile + 1]: halo
     const u64 *__restrict__ K = plan_final_sel(plan) ? keys1 : keys0;
     const u64 n = kArcs ? 2ull * s.w : (u64)s.w;
@@ -238,10 +251,87 @@ static __global__ void __launch_bounds__(kIdxThreads) index_kernel(
             if (x >= nverts) continue;  // invalid batch (already flagged by the key build)
             if (x != prev) *reinterpret_cast<u64 *>(&dir[x].epoch) = (k << 32) | epoch;
             if (x != next) dir[x].end = (u32)(k + 1);
+            if constexpr (!kArcs) {
+                // the first key of its bucket in this tile ORs the bucket's
+                // filter bits of the keys that follow it in the tile
+                if (i == 0 || x != prev) {
+                    u32 mask = filter_bit(key >> s.bw, s.hb);
+                    for (int q = i + 1; q < kIdxTile && t0 + (u64)q < n; ++q) {
+                        const u64 kq = st[1 + q];
+                        if ((kq >> sh) != x) break;
+                        mask |= filter_bit(kq >> s.bw, s.hb);
+                    }
+                    atomicOr(efilt + x, mask);
+                }
+            }
         }
         __syncthreads();  // the tile is restaged next
     }
     if (dup) set_error(err, kErrInput);
+}
+
+// ---------------------------------------------------------------------------
+// Dense arc directory (CSR offsets): off[x] = the first index of the sorted
+// arcs whose src is >= x, for x in [0, 2^B], so that vertex x's arcs are
+// [off[x], off[x+1]) and deg_W(x) = off[x+1] - off[x] (Def. 4.2).  Every
+// entry is written every batch, so nothing is tagged or cleared: sorted key
+// k writes the entries of the vertices in (src(k-1), src(k)], and the entries
+// past the largest src get 2w.  4 bytes per vertex id, written whole: used
+// when 2^B <= 8w (the write then costs at most what one arc pass moves).
+// A run of more than 32 absent vertices is filled by the whole warp.
+// ---------------------------------------------------------------------------
+// A block stages tiles of kIdxTile sorted keys (plus the key before the
+// tile) in shared memory with coalesced loads, as index_kernel does, so each
+// thread's kIdxItems keys cost no dependent global load.
+static __global__ void __launch_bounds__(kIdxThreads) offsets_kernel(const u64 *keys0,
+                                                                    const u64 *keys1,
+                                                                    const SortPlan *plan,
+                                                                    BatchShape s, u32 *off) {
+    __shared__ u64 st[kIdxTile + 1];  // st[1 + i] = src of key t0 + i; st[0]: the key before
+    const u64 *__restrict__ K = plan_final_sel(plan) ? keys1 : keys0;
+    const u64 n = 2ull * s.w;
+    const u64 nv = 1ull << s.B;
+    const int tid = threadIdx.x, lane = tid & 31;
+    // entries past the largest src: every thread takes a share
+    const u64 x_last = __ldg(K + n - 1) >> s.sha;
+    const u64 stride = (u64)gridDim.x * kIdxThreads;
+    for (u64 v = x_last + 1 + (u64)blockIdx.x * kIdxThreads + tid; v <= nv; v += stride)
+        off[v] = (u32)n;
+    for (u64 t0 = (u64)blockIdx.x * kIdxTile; t0 < n; t0 += (u64)gridDim.x * kIdxTile) {
+#pragma unroll
+        for (int j = 0; j < kIdxItems; ++j) {
+            const u64 k = t0 + (u64)(j * kIdxThreads + tid);
+            st[1 + j * kIdxThreads + tid] = k < n ? __ldg(K + k) >> s.sha : 0ull;
+        }
+        if (tid == 0) st[0] = t0 ? __ldg(K + t0 - 1) >> s.sha : 0ull;
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kIdxItems; ++j) {
+            const int i = j * kIdxThreads + tid;
+            const u64 k = t0 + (u64)i;
+            u64 lo = 0, hi = 0;  // key k writes off[lo .. hi)
+            if (k < n) {
+                const u64 x = st[1 + i];
+                lo = k ? st[i] + 1 : 0;
+                hi = x + 1 < nv + 1 ? x + 1 : nv + 1;
+                if (lo > hi) lo = hi;  // unsorted keys (a timed-out sort): write nothing wrong
+            }
+            const bool longrun = hi - lo > 32;
+            if (!longrun)
+                for (u64 v = lo; v < hi; ++v) off[v] = (u32)k;
+            // a run of more than 32 absent vertices is filled by the whole warp
+            unsigned todo = __ballot_sync(0xFFFFFFFFu, longrun);
+            while (todo) {
+                const int src_lane = __ffs(todo) - 1;
+                todo &= todo - 1;
+                const u64 l2 = __shfl_sync(0xFFFFFFFFu, lo, src_lane);
+                const u64 h2 = __shfl_sync(0xFFFFFFFFu, hi, src_lane);
+                const u64 k2 = __shfl_sync(0xFFFFFFFFu, k, src_lane);
+                for (u64 v = l2 + lane; v < h2; v += 32) off[v] = (u32)k2;
+            }
+        }
+        __syncthreads();  // the tile is restaged next
+    }
 }
 
 // Blocks of an index launch over n keys.
@@ -304,8 +394,10 @@ struct SweepArgs {
     const u64 *arcs0, *arcs1;
     const u64 *ekeys0, *ekeys1;
     const SortPlan *plans;
-    const DirEntry *adir;         // null unless vertex ids < 2^kDirMaxBits
+    const DirEntry *adir;         // tagged arc directory (kArcTagged)
+    const u32 *aoff;              // dense arc offsets, 2^B + 1 entries (kArcDense)
     const DirEntry *edir;         // Step-3 hash buckets
+    const u32 *efilt;             // Step-3 filter masks, one per hash bucket
     Control *ctl;
     BatchAcc *acc;                // per-batch S / closed accumulator (zeroed)
     const u32 *berr;              // this batch's error word (zeroed)
@@ -327,8 +419,12 @@ __device__ __forceinline__ void closing_pair(u64 f1, u64 f2, u64 &gu, u64 &gv) {
     gv = x1 < x2 ? x2 : x1;
 }
 
+// How the sweep finds a vertex's arc run: binary search on the sorted arcs,
+// the tagged per-vertex directory, or the dense offsets.
+enum ArcDir : int { kArcSearch = 0, kArcTagged = 1, kArcDense = 2 };
+
 // One estimator: Steps 1-3 of Sec. 4 applied to its state in place.
-template <bool kDir>
+template <int kDir>
 __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 epoch,
                                           const DrawKey &dk, const u64 *__restrict__ arcs,
                                           const u64 *__restrict__ E, u64 &f1, u64 &f2, u64 &chi,
@@ -354,7 +450,12 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
     // (positions and indices are 32-bit: a batch has fewer than 2^29 arcs)
     const u64 u = f1 >> 32, v = f1 & kMask32;
     u32 su, eu, sv, ev;
-    if constexpr (kDir) {
+    if constexpr (kDir == kArcDense) {
+        eu = min(__ldg(a.aoff + u + 1), n_arcs);
+        su = min(__ldg(a.aoff + u), eu);
+        ev = min(__ldg(a.aoff + v + 1), n_arcs);
+        sv = min(__ldg(a.aoff + v), ev);
+    } else if constexpr (kDir == kArcTagged) {
         dir_segment32(a.adir, epoch, u, n_arcs, su, eu);
         dir_segment32(a.adir, epoch, v, n_arcs, sv, ev);
     } else {
@@ -398,9 +499,13 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
         u32 lo, hi;
         closing_pair(f1, f2, gu, gv);
         const u64 g = (gu << 32) | gv;
-        const u64 h = edge_hash(g);
+        const u64 h = edge_hash(g, s.hkey);
         const u64 hp = h >> (32 - s.hs);  // the sorted bits
-        dir_segment32(a.edir, epoch, h >> (32 - s.hb), s.w, lo, hi);
+        const u64 bucket = h >> (32 - s.hb);
+        // no edge of the batch has the pair's filter bit: nothing to look up
+        const bool maybe = (__ldg(a.efilt + bucket) & filter_bit(h, s.hb)) != 0;
+        if (maybe) dir_segment32(a.edir, epoch, bucket, s.w, lo, hi);
+        else lo = hi = 0;
         for (u32 k = lower_bound_idx32(E, lo, hi, hp << s.she); k < hi; ++k) {
             const u64 ek = __ldg(E + k);
             if ((ek >> s.she) != hp) break;
@@ -415,10 +520,9 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
 }
 
 // One estimator per thread and iteration (grid-stride over r; the grid is
-// sweep_blocks(r)).  kDir: arc segments from the vertex directory, else by
-// binary search on the sorted arcs.  Adds sum(chi over closed) and the
-// closed count of the new state into a.acc.
-template <bool kDir>
+// sweep_blocks(r)).  kDir (ArcDir): how arc segments are found.  Adds
+// sum(chi over closed) and the closed count of the new state into a.acc.
+template <int kDir>
 static __global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArgs a) {
     __shared__ u64 s_lo[kSweepThreads / 32], s_hi[kSweepThreads / 32], s_cnt[kSweepThreads / 32];
     if (ld_relaxed(a.berr)) return;  // rejected batch: state stays as it was
@@ -454,14 +558,16 @@ static __global__ void __launch_bounds__(kSweepThreads, 6) sweep_kernel(SweepArg
     }
 }
 
-// Blocks of a sweep over r estimators: at most one full wave (the 6 blocks
-// per SM the launch bounds allow), each thread then taking every
-// (blocks x threads)-th estimator.  One resident wave measured 3% faster
-// per batch than one block per 256 estimators at r = 2^20.
+// Blocks of a sweep over r estimators: at most one resident wave of
+// `per_sm` blocks per SM (6, the most the launch bounds allow, by default),
+// each thread then taking every (blocks x threads)-th estimator.  One
+// resident wave measured 3% faster per batch than one block per 256
+// estimators at r = 2^20.  A wave of fewer blocks per SM leaves room for the
+// next batch's sort passes to run beside the sweep (tc_tune_sweep).
 constexpr u32 kSweepBlocksPerSM = 6;
-inline unsigned sweep_blocks(u64 r, int sm_count) {
+inline unsigned sweep_blocks(u64 r, int sm_count, u32 per_sm = kSweepBlocksPerSM) {
     const u64 b = (r + kSweepThreads - 1) / kSweepThreads;
-    const u64 cap = (u64)kSweepBlocksPerSM * (u64)(sm_count > 0 ? sm_count : 1);
+    const u64 cap = (u64)per_sm * (u64)(sm_count > 0 ? sm_count : 1);
     return (unsigned)(b < cap ? b : cap);
 }
 

@@ -69,6 +69,9 @@ struct RoundShape {
     u32 he_sh;  // Step-3 bucket: sorted bits >> he_sh, 2^hE buckets
     u64 nba, nbe;   // 2^hA, 2^hE
     u64 pmul;   // pi: x -> x * pmul mod 2^B (pmul odd)
+    u64 hkey;   // key of the Step-3 edge hash
+    u32 fsh;    // Step-3 filter bit: (participant, hash) >> fsh & 31, the five
+                // bits below the bucket's
 };
 
 // pi(x): the vertex id bijection of the arc keys.
@@ -152,7 +155,7 @@ __global__ void __launch_bounds__(kMThreads) mprep_kernel(const u64 *__restrict_
             atomicAdd(&h[p * ra + digit_bits(au, rs.sha + p * rs.bits_a, ra - 1)], 1u);
             atomicAdd(&h[p * ra + digit_bits(av, rs.sha + p * rs.bits_a, ra - 1)], 1u);
         }
-        const u64 ek = mkey(rs, k, edge_hash(e), jl);
+        const u64 ek = mkey(rs, k, edge_hash(e, rs.hkey), jl);
         ekeys0[j] = ek;
         if (!rs.eko) evals0[j] = (u32)jl;
         for (int p = 0; p < rs.npe; ++p)
@@ -226,7 +229,7 @@ __global__ void __launch_bounds__(kIdxThreads) marc_index_kernel(const u64 *arcs
 __global__ void __launch_bounds__(kIdxThreads) mdups_kernel(
     const u64 *ekeys0, const u64 *ekeys1, const u32 *evals0, const u32 *evals1,
     const SortPlan *plans, const u64 *__restrict__ desc, RoundShape rs, u32 *perr,
-    DirEntry *edir, const u32 *tagp) {
+    DirEntry *edir, const u32 *tagp, u32 *efilt) {
     __shared__ u64 st[kIdxTile + 2];
     const Desc d = desc_view(desc, rs.K);
     const bool sel = plan_final_sel(&plans[1]) != 0;
@@ -245,6 +248,21 @@ __global__ void __launch_bounds__(kIdxThreads) mdups_kernel(
             if (i >= n) break;
             const u64 a = st[1 + ti];
             dir_mark(edir, rs.nbe, tag, n, i, a, st[ti], st[ti + 2], rs.she + rs.he_sh);
+            {
+                // Step-3 filter: the first key of its bucket in this tile ORs
+                // the bucket's filter bits of the keys that follow in the tile
+                const u32 fs = rs.she + rs.he_sh;
+                const u64 xb = a >> fs;
+                if (xb < rs.nbe && (ti == 0 || (st[ti] >> fs) != xb)) {
+                    u32 mask = 1u << ((mkey_prefix(rs, a) >> rs.fsh) & 31);
+                    for (int q = ti + 1; q < kIdxTile && t0 + (u64)q < n; ++q) {
+                        const u64 kq = st[1 + q];
+                        if ((kq >> fs) != xb) break;
+                        mask |= 1u << ((mkey_prefix(rs, kq) >> rs.fsh) & 31);
+                    }
+                    atomicOr(efilt + xb, mask);
+                }
+            }
             const u64 sa = mkey_sorted(rs, a), pa = mkey_prefix(rs, a);
             if (i + 1 >= n || mkey_sorted(rs, st[ti + 2]) != sa) continue;
             // a repeat shares the whole hash, so it lies in the run of equal
@@ -281,6 +299,7 @@ struct MSweepArgs {
     const u32 *gerr;     // round-wide error (a timed-out sort)
     const u32 *perr;     // each participant's error this round
     const DirEntry *adir, *edir;
+    const u32 *efilt;    // Step-3 filter masks, one per Step-3 bucket
     const u32 *tag;      // the round set's directory tag
     RoundShape rs;
 };
@@ -454,13 +473,16 @@ __global__ void __launch_bounds__(kMThreads, 7) msweep_kernel(MSweepArgs a) {
                 const u64 x2 = (a2 == a1 || a2 == b1) ? b2 : a2;
                 const u64 gu = x1 < x2 ? x1 : x2, gv = x1 < x2 ? x2 : x1;
                 const u64 gkey = (gu << 32) | gv;
-                const u64 probe = mkey(rs, k, edge_hash(gkey), 0);
+                const u64 probe = mkey(rs, k, edge_hash(gkey, rs.hkey), 0);
                 const u64 pp = mkey_prefix(rs, probe), ps = mkey_sorted(rs, probe);
                 const bool es = plan_final_sel(&a.plans[1]) != 0;
                 const u64 *E = es ? a.ekeys1 : a.ekeys0;
                 const u32 *EV = es ? a.evals1 : a.evals0;
-                u64 lo64, hi64;
-                dir_segment(a.edir, tag, ps >> rs.he_sh, rs.Wt, lo64, hi64);
+                u64 lo64 = 0, hi64 = 0;
+                // no key of the round has the pair's filter bit: no lookup
+                const u64 bucket = ps >> rs.he_sh;
+                if (__ldg(a.efilt + bucket) & (1u << ((pp >> rs.fsh) & 31)))
+                    dir_segment(a.edir, tag, bucket, rs.Wt, lo64, hi64);
                 const u32 qhi = (u32)hi64;
                 for (u32 q = lower_bound32(E, (u32)lo64, qhi, ps << rs.she); q < qhi; ++q) {
                     const u64 ek = __ldg(E + q);
@@ -675,7 +697,7 @@ u64 fib_multiplier(u32 B) {
 // Bytes of one round set's directories and tag word.
 u64 dir_bytes(u64 w_max_round) {
     return ((1ull << arc_dir_bits(w_max_round)) + (1ull << edge_dir_bits(w_max_round))) *
-               sizeof(DirEntry) + 256;
+               sizeof(DirEntry) + (1ull << edge_dir_bits(w_max_round)) * sizeof(u32) + 256;
 }
 
 // Participant error words at the end of the zeroed block, one per slot at most.
@@ -705,6 +727,7 @@ static void free_round_set(tc_multi::RoundSet &z) {
     cudaFree(z.zeroed);
     cudaFree(z.adir);
     cudaFree(z.edir);
+    cudaFree(z.efilt);
     cudaFree(z.tag);
     z = tc_multi::RoundSet{};
 }
@@ -726,6 +749,7 @@ static bool alloc_round_set(tc_multi::RoundSet &z, u64 w_max, u64 zeroed_bytes) 
     ok &= ok && cudaMemset(z.adir, 0, na * sizeof(DirEntry)) == cudaSuccess;
     ok &= ok && cudaMalloc(&z.edir, ne * sizeof(DirEntry)) == cudaSuccess;
     ok &= ok && cudaMemset(z.edir, 0, ne * sizeof(DirEntry)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&z.efilt, ne * sizeof(u32)) == cudaSuccess;
     const u32 one = 1;
     ok &= ok && cudaMalloc(&z.tag, 256) == cudaSuccess;
     ok &= ok && cudaMemcpy(z.tag, &one, sizeof(one), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -770,6 +794,7 @@ int multi_alloc(u32 S, u64 w_max_round, u32 vertex_bits, tc_multi **out, int set
     tc_multi *M = new (std::nothrow) tc_multi();
     if (!M) return TC_ERR_NOMEM;
     M->S = S;
+    M->hash_key = random_hash_key();
     M->B = vertex_bits;
     M->sb = sb;
     M->w_max = w_max_round;
@@ -884,7 +909,11 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u
     rs.he_sh = rs.kb + rs.hs - he;
     rs.nba = 1ull << ha;
     rs.nbe = 1ull << he;
+    // bucket = (participant, hash) >> (32 - hs + he_sh); the filter takes the
+    // five bits below (32 - hs + he_sh = 32 + kb - he >= 6 as he <= 26)
+    rs.fsh = 32 - rs.hs + rs.he_sh - 5;
     rs.pmul = fib_multiplier(rs.B);
+    rs.hkey = M->hash_key;
     const int b = M->nsets == 2 ? (int)(M->rseq & 1) : 0;
     M->rseq++;
     tc_multi::RoundSet &z = M->rset[b];
@@ -924,8 +953,10 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u
             z.ekeys[0], z.ekeys[1], rs.eko ? nullptr : z.evals[0], rs.eko ? nullptr : z.evals[1],
             (u32)Wt, rs.she + p * rs.bits_e, mlive(rs.hs + rs.kb, rs.bits_e, p), p, &plans[1],
             lbe + (u64)p * le, gerr, nullptr);
+    TCM_CUDA(cudaMemsetAsync(z.efilt, 0, rs.nbe * sizeof(u32), M->side));
     mdups_kernel<<<index_blocks(Wt), kIdxThreads, 0, M->side>>>(
-        z.ekeys[0], z.ekeys[1], z.evals[0], z.evals[1], plans, desc, rs, perr, z.edir, z.tag);
+        z.ekeys[0], z.ekeys[1], z.evals[0], z.evals[1], plans, desc, rs, perr, z.edir, z.tag,
+        z.efilt);
     TCM_CUDA(cudaEventRecord(M->ev_join, M->side));
     for (int p = 0; p < rs.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, ms>>>(
@@ -953,6 +984,7 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u
     a.perr = perr;
     a.adir = z.adir;
     a.edir = z.edir;
+    a.efilt = z.efilt;
     a.tag = z.tag;
     a.rs = rs;
     msweep_kernel<<<(unsigned)((R + kMThreads - 1) / kMThreads), kMThreads, 0, st>>>(a);
@@ -1042,6 +1074,12 @@ int tc_multi_tune(tc_multi *M, uint32_t arc_digit_bits, uint32_t edge_digit_bits
     M->force_a = arc_digit_bits;
     M->force_e = edge_digit_bits;
     M->rank = ranking == 1 ? kRankMatch : kRankBallot;
+    return TC_OK;
+}
+
+int tc_multi_set_hash_key(tc_multi *M, uint64_t key) {
+    if (!M) return TC_ERR_INVAL;
+    M->hash_key = key;
     return TC_OK;
 }
 

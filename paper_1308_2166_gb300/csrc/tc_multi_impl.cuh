@@ -54,6 +54,7 @@ struct tc_multi {
     tc::u64 w_max = 0;   // most edges one round carries
     tc::u32 force_a = 0, force_e = 0;
     int rank = 0;
+    tc::u64 hash_key = 0;                // Step-3 edge hash key (random per engine)
     tc::u64 *state = nullptr;            // state block of tc_multi_create's streams
     std::vector<tc::MStream> h_rec;      // host copy of each slot's static fields
     tc::MStream *ms = nullptr;           // device records, S
@@ -66,6 +67,7 @@ struct tc_multi {
         unsigned char *zeroed = nullptr;  // SortPlan[2], look-back, round error, participant errors
         tc::DirEntry *adir = nullptr;     // arc bucket directory
         tc::DirEntry *edir = nullptr;     // Step-3 bucket directory
+        tc::u32 *efilt = nullptr;         // Step-3 filter masks, one per Step-3 bucket
         tc::u32 *tag = nullptr;           // device word: the directories' current tag
     };
     RoundSet rset[2];

@@ -24,7 +24,7 @@
 //     permutation and is skipped (decided on the device from the
 //     histogram); ping-pong buffer selection follows on the device, so the
 //     host never needs the histogram.
-// Digit width (8, 10 or 11 bits) is a template parameter.
+// Digit width (8, 9, 10 or 11 bits) is a template parameter.
 // Look-back waits are bounded: after kSpinLimit rounds without progress the
 // CTA records kErrTimeout and proceeds (the batch is then rejected, never
 // hung).
@@ -245,7 +245,7 @@ __device__ __forceinline__ void rank_warp(Smem &S, const u64 (&keys)[kSortItems]
 // by plan_sel(plan, pass); `lookback` holds this pass's status words, tile-major
 // ([tiles][2^kBits]), zeroed before the pass.
 template <int kBits, bool kHasValues, int kRank>
-static __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits <= 8 ? 4 : 3))
+static __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits <= 9 ? 4 : 3))
     onesweep_pass_kernel(u64 *keys0, u64 *keys1, u32 *vals0, u32 *vals1, u32 n, u32 shift,
                          u32 live, int pass, SortPlan *plan, u32 *lookback, u32 *err,
                          Control *ctl) {

@@ -55,7 +55,7 @@ struct Req {
     u64 w = 0;
     u64 r = 0, seed = 0;
     u32 stream_id = 0;
-    u64 t_submit = 0, t_admit = 0;
+    u64 t_submit = 0, t_admit = 0, t_round = 0;
     u64 *d_edges = nullptr;  // device copy of an admitted batch
     u64 bytes = 0;           // budget bytes it holds until completion
     int ev = -1;             // copy event
@@ -173,6 +173,7 @@ void tc_server::complete(const Req &q, int status, const u64 *rec) {
     }
     c.t_submit_ns = q.t_submit;
     c.t_admit_ns = q.t_admit;
+    c.t_round_ns = q.t_round;
     c.t_done_ns = now();
     outbox.push_back(c);
 }
@@ -359,6 +360,12 @@ bool tc_server::form_round() {
     }
     for (u32 s : again) ready.push_back(s);
     if (items.empty() && qslots.empty() && R.closes.empty()) return false;
+    {
+        const u64 t = now();
+        for (Req &q : R.queries) q.t_round = t;
+        for (Req &q : R.batches) q.t_round = t;
+        for (Req &q : R.closes) q.t_round = t;
+    }
 
     const int b = (int)(round_no % (u64)nbuf);
     const u32 Q = (u32)qslots.size(), K = (u32)items.size();
@@ -487,7 +494,19 @@ void tc_server::fail_all(int code) {
 
 void tc_server::run() {
     cudaSetDevice(dev);
+    u64 t_prev = now();
     for (;;) {
+        {
+            // the longest stretch between two scheduler passes with work in
+            // flight or waiting: where the scheduler thread itself stalled
+            const u64 t = now();
+            if (!inflight.empty() || !pending.empty()) {
+                const u64 gap = t - t_prev;
+                if (gap > local.sched_gap_max_ns) local.sched_gap_max_ns = gap;
+                if (gap > 5000000) local.sched_gaps_over_5ms++;
+            }
+            t_prev = t;
+        }
         bool stopping;
         {
             std::lock_guard<std::mutex> lk(mu);
@@ -513,8 +532,14 @@ void tc_server::run() {
             publish();
             if (!progress && err == TC_OK) {
                 std::unique_lock<std::mutex> lk(mu);
-                cv_in.wait_for(lk, std::chrono::microseconds(inflight.empty() ? 500 : 10),
-                               [&] { return stop || !inbox.empty(); });
+                const auto budget = std::chrono::microseconds(inflight.empty() ? 500 : 10);
+                const u64 t_wait = now();
+                cv_in.wait_for(lk, budget, [&] { return stop || !inbox.empty(); });
+                // a wait up to its budget is the scheduler's own choice; only
+                // time beyond it (the thread not running) counts as a gap
+                const u64 waited = now() - t_wait;
+                const u64 allowed = (u64)std::chrono::nanoseconds(budget).count();
+                t_prev += waited < allowed ? waited : allowed;
             }
             continue;
         }

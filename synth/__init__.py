@@ -13,4 +13,5 @@ m from 1e4 to 1e9 edges.
 """
 from .graphs import chung_lu, rmat, finish, pack, unpack  # noqa: F401
 from .workloads import (WORKLOADS, LARGE_EDGES, tiny_chung_lu, rmat20_single, large_prefix,  # noqa: F401
-                        large_stream_device, batches, multi_streams)
+                        large_stream_device, batches, multi_streams,
+                        multi_streams_device)

@@ -98,3 +98,30 @@ def multi_streams(S: int = 512, per_stream_edges: int = 32768, seed: int = 1,
         rs.append(int(np.exp(lr[s])))
         ns.append(n)
     return streams, np.array(rs, dtype=np.uint64), np.array(ns, dtype=np.int64)
+
+
+def multi_streams_device(S: int = 512, seed: int = 1, m_range=(1e4, 1e7),
+                         r_range=(2 ** 10, 2 ** 16), gamma_range=(2.1, 2.5),
+                         mean_degree: float = 16.0, device: str = "cuda"):
+    """S independent Chung-Lu streams at their full lengths, drawn on the GPU.
+
+    Stream s has m_s edges, m_s log-uniform in m_range; r_s estimators,
+    log-uniform in r_range; exponent uniform in gamma_range; n_s =
+    max(64, 2 m_s / mean_degree) vertices.  Returns (streams, r, n): a list
+    of int64 device tensors of packed edges in arrival order, and numpy
+    arrays of r_s and n_s.
+    """
+    from .device import chung_lu_device
+    rng = np.random.default_rng(seed)
+    lm = rng.uniform(np.log(m_range[0]), np.log(m_range[1]), size=S)
+    lr = rng.uniform(np.log(r_range[0]), np.log(r_range[1]), size=S)
+    gam = rng.uniform(gamma_range[0], gamma_range[1], size=S)
+    streams, rs, ns = [], [], []
+    for s in range(S):
+        m = int(np.exp(lm[s]))
+        n = max(64, int(2 * m / mean_degree))
+        streams.append(chung_lu_device(n, float(gam[s]), 2.0 * m / n, m,
+                                       seed=seed * 100_003 + s, device=device))
+        rs.append(int(np.exp(lr[s])))
+        ns.append(n)
+    return streams, np.array(rs, dtype=np.uint64), np.array(ns, dtype=np.int64)

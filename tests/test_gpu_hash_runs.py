@@ -9,6 +9,11 @@ least every bit the library sorts on for these batch sizes (whole 8-bit
 digits covering about bits(w) - 2 bucket bits, or bw + 1 bits next to the
 participant index in a round of two).  Closing edges then sit at every place
 of runs of seven, and the GPU state must still match the oracle bit for bit.
+
+The mix is keyed (each context draws a random key, so that no batch can be
+crafted against it); these tests fix the key with tc_set_hash_key to build
+the runs, and one test checks that under a context's own random key the
+crafted batches no longer form long runs and the state still matches.
 """
 import numpy as np
 import pytest
@@ -21,6 +26,7 @@ pytestmark = pytest.mark.gpu
 
 VB = 20
 PREFIX_BITS = 16
+KEY = 0x243F6A8885A308D3   # the key the runs are built for
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -30,10 +36,11 @@ def _built():
     tc.load()
 
 
-def _mix_high(x):
-    """The library's Step-3 edge mix: SplitMix64's finaliser (Steele, Lea,
-    Flood, OOPSLA 2014), high 32 bits, on packed edges (u << 32) | v."""
-    x = np.asarray(x, dtype=np.uint64).copy()
+def _mix_high(x, key=KEY):
+    """The library's keyed Step-3 edge mix: SplitMix64's finaliser (Steele,
+    Lea, Flood, OOPSLA 2014), high 32 bits, on packed edges (u << 32) | v
+    xor the key."""
+    x = np.asarray(x, dtype=np.uint64) ^ np.uint64(key)
     x ^= x >> np.uint64(30)
     x *= np.uint64(0xBF58476D1CE4E5B9)
     x ^= x >> np.uint64(27)
@@ -83,6 +90,7 @@ def test_runs_of_equal_sorted_bits_single_stream():
         assert counts.min() >= 7 and not (counts % 7).any()   # runs of seven or more
     r, seed = 4096, 11
     ctx = tc.tc_create_ex(r, seed, 3, max(W.size for W in batches), VB)
+    tc.tc_set_hash_key(ctx, KEY)
     ref = nbsi_bulk.BulkStream(r, seed=seed, stream=3, vertex_bits=VB)
     try:
         for k, W in enumerate(batches):
@@ -104,6 +112,7 @@ def test_repeat_inside_a_run_is_rejected():
     members = np.flatnonzero(pre == pre[0])
     bad = np.concatenate([W, W[members[0]:members[0] + 1]])
     ctx = tc.tc_create_ex(256, 5, 0, bad.size, VB)
+    tc.tc_set_hash_key(ctx, KEY)
     ref = nbsi_bulk.BulkStream(256, seed=5, vertex_bits=VB)
     try:
         with pytest.raises(tc.TcError) as e:
@@ -125,6 +134,7 @@ def test_runs_of_equal_sorted_bits_in_a_round():
     seeds, sids = [21, 22], [0, 1]
     M = tc.MultiStream(r, seeds, sids, w_max_round=2 * max(x.size for x in A + B) + 8,
                        vertex_bits=VB)
+    M.set_hash_key(KEY)
     refs = [nbsi_bulk.BulkStream(r[s], seed=seeds[s], stream=sids[s], vertex_bits=VB)
             for s in range(2)]
     try:
@@ -147,3 +157,25 @@ def test_runs_of_equal_sorted_bits_in_a_round():
         assert int(refs[1].closed.sum()) > 100
     finally:
         M.close()
+
+
+def test_random_key_defeats_the_crafted_runs():
+    """Under a key the batch was not built for, the crafted edges spread over
+    the buckets (no run of seven is left), and a context with its own random
+    key -- the default -- still matches the oracle bit for bit."""
+    batches = _collision_batches(1)
+    other = 0x13198A2E03707344
+    for W in batches:
+        pre = _mix_high(W, other) >> np.uint64(32 - PREFIX_BITS)
+        _, counts = np.unique(pre, return_counts=True)
+        assert counts.max() < 7
+    r, seed = 4096, 11
+    ctx = tc.tc_create_ex(r, seed, 3, max(W.size for W in batches), VB)
+    ref = nbsi_bulk.BulkStream(r, seed=seed, stream=3, vertex_bits=VB)
+    try:
+        for k, W in enumerate(batches):
+            tc.tc_process_batch(ctx, to_device(W))
+            ref.process_batch(W)
+            assert_state_equal(tc.tc_get_state(ctx), ref.state_arrays(), f"batch {k}")
+    finally:
+        tc.tc_destroy(ctx)

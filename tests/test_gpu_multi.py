@@ -151,3 +151,67 @@ def test_captured_round_replays_match_oracle():
                 assert_state_equal(M.state(s), refs[s].state_arrays(), f"replay {rep} stream {s}")
     finally:
         M.close()
+
+
+def test_512_streams_sampled_against_oracle():
+    """The batching configuration's scale: 512 streams of uneven length and
+    estimator count (Chung-Lu, m log-uniform [1e3, 3e4], r log-uniform
+    [2^6, 2^12], 21-bit ids as in the 512-stream bench), each cut into 8
+    rounds of m_s // 8 edges, folded as CUDA-graph replays of one captured
+    round.  A sample of 24 streams (the longest, the shortest, the most and
+    fewest estimators, and random ones) must equal the oracle bit for bit
+    after the last round, and every stream must equal its single-stream run
+    and the engine's estimate records."""
+    import torch
+    S, T, VB = 512, 8, 21
+    rng = np.random.default_rng(512)
+    m = np.exp(rng.uniform(np.log(1e3), np.log(3e4), size=S)).astype(np.int64)
+    r = np.exp(rng.uniform(np.log(2 ** 6), np.log(2 ** 12), size=S)).astype(np.uint64)
+    seeds = rng.integers(1, 2**63, size=S, dtype=np.uint64)
+    sids = np.arange(S, dtype=np.uint32)
+    streams = []
+    for s in range(S):
+        n = max(64, int(m[s] // 8))
+        g = float(rng.uniform(2.1, 2.5))
+        streams.append(synth.finish(synth.chung_lu(n, g, 2.0 * m[s] / n, int(m[s]), seed=9000 + s),
+                                    n, seed=19000 + s))
+    ws = m // T
+    offs = np.concatenate([[0], np.cumsum(ws)]).astype(np.uint64)
+    rounds = [np.concatenate([streams[s][k * ws[s]:(k + 1) * ws[s]] for s in range(S)])
+              for k in range(T)]
+    M = tc.MultiStream(r, seeds, sids, w_max_round=int(offs[-1]), vertex_bits=VB)
+    st = torch.cuda.Stream()
+    try:
+        buf = torch.empty(int(offs[-1]), dtype=torch.int64, device="cuda")
+        M.capture(buf, offs, st.cuda_stream)
+        for k in range(T):
+            with torch.cuda.stream(st):
+                buf.copy_(to_device(rounds[k]), non_blocking=True)
+                M.replay(st.cuda_stream)
+            st.synchronize()
+        assert not M.sync().any()
+        sample = {int(np.argmax(m)), int(np.argmin(m)), int(np.argmax(r)), int(np.argmin(r))}
+        sample |= set(rng.choice(S, size=24 - len(sample), replace=False).tolist())
+        for s in sorted(sample):
+            ref = nbsi_bulk.BulkStream(int(r[s]), seed=int(seeds[s]), stream=int(sids[s]),
+                                       vertex_bits=VB)
+            for k in range(T):
+                ref.process_batch(streams[s][k * ws[s]:(k + 1) * ws[s]])
+            assert_state_equal(M.state(s), ref.state_arrays(), f"stream {s} vs oracle")
+            e = M.estimate(s)
+            assert e["S"] == ref.closed_sum() and e["m"] == ref.m == T * ws[s]
+        d = torch.zeros(S * tc.ESTIMATE_BYTES // 8, dtype=torch.int64, device="cuda")
+        M.estimates_async(d)
+        torch.cuda.synchronize()
+        recs = tc.estimate_records(d.cpu())
+        for s in range(S):
+            ctx = tc.tc_create_ex(int(r[s]), int(seeds[s]), int(sids[s]), int(ws[s]), VB)
+            try:
+                for k in range(T):
+                    tc.tc_process_batch(ctx, to_device(streams[s][k * ws[s]:(k + 1) * ws[s]]))
+                assert_state_equal(M.state(s), tc.tc_get_state(ctx), f"stream {s} vs alone")
+                assert recs[s] == tc.tc_estimate(ctx)
+            finally:
+                tc.tc_destroy(ctx)
+    finally:
+        M.close()
