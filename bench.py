@@ -77,15 +77,18 @@ def _args():
     p.add_argument("--workload", choices=["large", "rmat20", "tiny", "multi512", "serve4096",
                                           "wsweep", "accuracy"], default="large")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-clock-sampling", action="store_true",
+                   help="do not poll nvidia-smi during the timed phases (clocks reported null)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the extra keys of the default line (rmat20, multi512)")
     p.add_argument("--stream-edges", type=int, default=None,
                    help="large workload: edges of the generated stream (default the whole "
                         "1.2e9; a smaller stream keeps profiler captures small)")
     p.add_argument("--e2e-steps", type=int, default=None)
-    p.add_argument("--pipeline", choices=["on", "off"], default="on",
+    p.add_argument("--pipeline", choices=["auto", "on", "off"], default="auto",
                    help="single stream: sort each batch beside the previous batch's sweep "
-                        "(tc_process_batch_ready_async) or fully stream-ordered")
+                        "(tc_process_batch_ready_async), fully stream-ordered, or the faster "
+                        "of the two on a few untimed batches")
     p.add_argument("--no-autotune", action="store_true",
                    help="keep the library's default sort tuning (8-bit digits, ballot ranking)")
     p.add_argument("--sweep-blocks", type=int, default=0,
@@ -420,8 +423,8 @@ def run_reference(args, rank, world):
 
 
 def _time_single(tc, args, cfg, views, host_keys, rank, world, local_rank, dist, sh, stream,
-                 tuning, tune_table, sweep_bps=6, sweep_table=None, with_e2e=True,
-                 with_clocks=True):
+                 tuning, tune_table, sweep_bps=6, sweep_table=None, pipe="on", pipe_table=None,
+                 with_e2e=True, with_clocks=True):
     """Warm-up, timed, end-to-end and stage-split steps of one single-stream
     workload on a Schedule; returns the result dict (not yet a JSON line)."""
     import torch
@@ -429,7 +432,7 @@ def _time_single(tc, args, cfg, views, host_keys, rank, world, local_rank, dist,
     W, K = args.warmup, args.steps
     nb_stream = len(views)
     E = (args.e2e_steps or min(K, 20)) if with_e2e else 0
-    G = min(K, 20) if args.pipeline == "on" else 0
+    G = min(K, 20) if pipe == "on" else 0
     if cfg["name"] == "large":       # the stream's batches are shared by every leg
         full = sum(1 for v in views if v.numel() == w)
         spare = full - W - K
@@ -437,8 +440,7 @@ def _time_single(tc, args, cfg, views, host_keys, rank, world, local_rank, dist,
         G = max(0, min(G, spare - E))
     sched = Schedule(tc, cfg, views, W + K + E + G, rank, tuning, sweep_bps)
     rec = torch.zeros(tc.ESTIMATE_BYTES // 8, dtype=torch.int64, device="cuda")
-    process = (tc.tc_process_batch_ready_async if args.pipeline == "on"
-               else tc.tc_process_batch_async)
+    process = (tc.tc_process_batch_ready_async if pipe == "on" else tc.tc_process_batch_async)
 
     def step():
         ctx, b = sched.take()
@@ -607,8 +609,11 @@ def _time_single(tc, args, cfg, views, host_keys, rank, world, local_rank, dist,
         "value": value, "t_ms": t_ms, "edges": edges_all, "per_step": per_step,
         "config": {
             "workload": f"{cfg['name']}: {cfg['graph']}, m={cfg['m']}, r={r}, w={w}",
-            "pipeline": ("on: tc_process_batch_ready_async, batch k+1's sorts beside batch k's "
-                         "sweep" if args.pipeline == "on" else "off: tc_process_batch_async"),
+            "pipeline": {"mode": ("on: tc_process_batch_ready_async, batch k+1's sorts beside "
+                                  "batch k's sweep" if pipe == "on"
+                                  else "off: tc_process_batch_async, stream-ordered"),
+                         "chosen_by": args.pipeline,
+                         "table_ms_per_batch": pipe_table or {}},
             "r": r, "w": w, "m": cfg["m"], "vertex_bits": B, "parallelism": f"replicas{world}",
             "batches": {"stream": nb_stream, "warmup": W, "timed": K, "e2e": E, "stage_split": G,
                         "used": used, "contexts": sched.n_ctx,
@@ -669,7 +674,14 @@ def _tuning(args, tc, views, cfg, sh):
     else:
         bps, stable = autotune.tune_sweep(views[:6], cfg["r"], cfg["vertex_bits"], tuning,
                                           seed=cfg["seed"] + 98, stream=sh)
-    return tuning, table, bps, stable
+    if args.pipeline != "auto":
+        pipe, ptable = args.pipeline, {}
+    elif args.no_autotune:
+        pipe, ptable = "on", {}
+    else:
+        pipe, ptable = autotune.tune_pipeline(views[:6], cfg["r"], cfg["vertex_bits"], tuning,
+                                              bps, seed=cfg["seed"] + 97, stream=sh)
+    return tuning, table, bps, stable, pipe, ptable
 
 
 def run_gpu(args, rank, world, local_rank):
@@ -691,9 +703,9 @@ def run_gpu(args, rank, world, local_rank):
     cfg, views, host_keys = _single_workload(args.workload, args.stream_edges)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t_gen
-    tuning, tune_table, bps, stable = _tuning(args, tc, views, cfg, sh)
+    tuning, tune_table, bps, stable, pipe, ptable = _tuning(args, tc, views, cfg, sh)
     res = _time_single(tc, args, cfg, views, host_keys, rank, world, local_rank, dist, sh,
-                       stream, tuning, tune_table, bps, stable)
+                       stream, tuning, tune_table, bps, stable, pipe, ptable)
     K = args.steps
     line = {
         "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": K,
@@ -733,9 +745,9 @@ def _extra_rmat20(args, tc, rank, world, local_rank, sh, stream):
     of the default line: streams of 3.7 batches, each on a fresh context."""
     import torch
     cfg, views, host_keys = _single_workload("rmat20")
-    tuning, table, bps, stable = _tuning(args, tc, views, cfg, sh)
+    tuning, table, bps, stable, pipe, ptable = _tuning(args, tc, views, cfg, sh)
     res = _time_single(tc, args, cfg, views, host_keys, rank, 1, local_rank, None, sh, stream,
-                       tuning, table, bps, stable, with_clocks=False)
+                       tuning, table, bps, stable, pipe, ptable, with_clocks=False)
     out = {"value": res["value"], "unit": UNIT, "ms_per_step": res["t_ms"] / args.steps,
            "config": res["config"], "e2e": res["e2e"], "roofline": res["roofline"],
            "roofline_other_kernel": res["roofline_other_kernel"],
@@ -1125,6 +1137,36 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
                                      "max_ms": float(lat_all.max()),
                                      "w_mean": float(ws[slow].mean()),
                                      "r_mean": float(rs[slow].mean())}
+    # the rounds, rebuilt from the completions (one formation time per round)
+    if rate and batches.size:
+        tr = batches["t_round_ns"].astype(np.int64)
+        order = np.argsort(tr, kind="stable")
+        tr_s, w_s = tr[order], ws[order]
+        done_s = batches["t_done_ns"].astype(np.int64)[order]
+        starts = np.flatnonzero(np.r_[True, tr_s[1:] != tr_s[:-1]])
+        r_t = tr_s[starts]
+        r_n = np.diff(np.r_[starts, tr_s.size])
+        r_e = np.add.reduceat(w_s, starts)
+        r_d = np.maximum.reduceat(done_s, starts) - r_t
+        gaps = np.diff(r_t) / 1e6
+        lat_all2 = (batches["t_done_ns"] - batches["t_submit_ns"]) / 1e6
+        worst = int(batches["t_round_ns"][int(np.argmax(lat_all2))])
+        win = (r_t >= worst - 60_000_000) & (r_t <= worst + 20_000_000)
+        extra["rounds_rebuilt"] = {
+            "count": int(r_t.size),
+            "interval_ms": {"p50": pct(gaps, 50), "p99": pct(gaps, 99),
+                            "max": float(gaps.max()) if gaps.size else None},
+            "batches_per_round": {"p50": pct(r_n.astype(np.float64), 50),
+                                  "max": int(r_n.max())},
+            "edges_per_round": {"p50": pct(r_e, 50), "max": float(r_e.max())},
+            "round_ms": {"p50": pct(r_d / 1e6, 50), "p99": pct(r_d / 1e6, 99),
+                         "max": float(r_d.max() / 1e6)},
+            "around_worst_batch": [[round((t - worst) / 1e6, 3), int(nb), int(e), round(d / 1e6, 3)]
+                                   for t, nb, e, d in zip(r_t[win], r_n[win], r_e[win],
+                                                          r_d[win])][:120],
+            "around_worst_how": "[round formed, ms relative to the slowest batch's round; "
+                                "batches; edges; ms to its last completion]",
+        }
     return {**extra,
         "edges_per_s": float(ws.sum()) / span,
         "updates_per_s": float((ws * rs).sum()) / span,
@@ -1139,6 +1181,7 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
         "max_round_streams": int(st1["max_round_streams"]),
         "admission_waits": int(st1["admission_waits"]),
         "sched_gap_max_ms": st1["sched_gap_max_ns"] / 1e6,
+        "inflight_full_max_ms": st1["inflight_full_max_ns"] / 1e6,
         "sched_gaps_over_5ms": int(st1["sched_gaps_over_5ms"] - st0["sched_gaps_over_5ms"]),
         "bytes_peak": int(st1["bytes_peak"]), "bytes_fixed": int(st1["bytes_fixed"]),
         "opens": int(st1["opens"]), "closes": int(st1["closes"]),
@@ -1178,16 +1221,17 @@ def run_serve(args, rank, world, local_rank):
     gen_s = time.perf_counter() - t
     cfg = {"vertex_bits": 22, "budget_bytes": 120 << 30, "w_max_round": 1 << 23, "depth": 2}
     secs = max(3.0, min(20.0, args.steps / 10.0))
-    sampler = ClockSampler(local_rank)
+    sample = not args.no_clock_sampling
+    sampler = ClockSampler(local_rank) if sample else None
     sat = _serve_phase(tc, graphs, cfg, S, secs, cap_edges=3 * cfg["w_max_round"])
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler else None
     b2b = _serve_phase(tc, graphs, cfg, S, max(3.0, secs / 2), cap_edges=3 * cfg["w_max_round"],
                        max_round_streams=1)
     req_rate = 0.7 * sat["edges_per_s"] / max(1.0, sat["mean_batch"]) / 0.9
-    sampler = ClockSampler(local_rank)
+    sampler = ClockSampler(local_rank) if sample else None
     poi = _serve_phase(tc, graphs, cfg, S, secs, rate=req_rate)
     poi50 = _serve_phase(tc, graphs, cfg, S, secs, rate=req_rate * 5 / 7)
-    clocks_poisson = sampler.stop()
+    clocks_poisson = sampler.stop() if sampler else None
     line = {
         "metric": "aggregate edges/s served: 4096 concurrent streams, continuous batching",
         "value": sat["edges_per_s"], "unit": UNIT, "n_gpus": 1, "steps": sat["rounds"],

@@ -433,6 +433,9 @@ typedef struct {
      * flight or waiting (beyond the scheduler's own bounded waits), and how
      * many stretches exceeded 5 ms: stalls of the scheduler thread itself */
     uint64_t sched_gap_max_ns, sched_gaps_over_5ms;
+    /* the longest stretch with `depth` rounds in flight, i.e. the scheduler
+     * waiting for the GPU before it may form the next round */
+    uint64_t inflight_full_max_ns;
 } tc_server_stats_t;
 
 /* Errors: TC_ERR_INVAL (bad config; key bits as tc_multi_create with

@@ -117,3 +117,34 @@ def tune_sweep(dev_batches, r: int, vertex_bits: int, tuning, seed: int = 1, str
             tc_destroy(ctx)
     best = min(table, key=table.get)
     return best, table
+
+
+def tune_pipeline(dev_batches, r: int, vertex_bits: int, tuning, sweep_blocks: int = 0,
+                  seed: int = 1, stream: int = 0, warm: int = 2):
+    """Time whole batches stream-ordered (tc_process_batch_async) and
+    pipelined (tc_process_batch_ready_async: each batch's sorts beside the
+    previous batch's sweep) on scratch contexts; return ("on" | "off",
+    table of ms per batch).  Results are identical either way."""
+    import torch
+    w_max = max(int(b.numel()) for b in dev_batches)
+    st = torch.cuda.ExternalStream(stream) if stream else torch.cuda.current_stream()
+    table = {}
+    for mode, fn in (("off", tc_process_batch_async), ("on", tc_process_batch_ready_async)):
+        ctx = tc_create_ex(r, seed, 0, w_max, vertex_bits)
+        try:
+            tc_tune(ctx, *tuning)
+            tc_tune_sweep(ctx, sweep_blocks)
+            for b in dev_batches[:warm]:
+                fn(ctx, b, stream=stream)
+            tc_sync(ctx)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for b in dev_batches[warm:]:
+                fn(ctx, b, stream=stream)
+            e1.record(st)
+            st.synchronize()
+            tc_sync(ctx)
+            table[mode] = e0.elapsed_time(e1) / max(1, len(dev_batches) - warm)
+        finally:
+            tc_destroy(ctx)
+    return min(table, key=table.get), table

@@ -281,53 +281,112 @@ static __global__ void __launch_bounds__(kIdxThreads) index_kernel(
 // A run of more than 32 absent vertices is filled by the whole warp.
 // ---------------------------------------------------------------------------
 // A block stages tiles of kIdxTile sorted keys (plus the key before the
-// tile) in shared memory with coalesced loads, as index_kernel does, so each
-// thread's kIdxItems keys cost no dependent global load.
+// tile) in shared memory with coalesced loads, as index_kernel does.  The
+// tile owns the vertices (src of the key before it, src of its last key];
+// the entries past the largest src are written by every thread of the grid
+// before the tiles (they all get 2w).  When the tile's span fits a shared
+// array of kOffSpan entries, each run head marks its vertex with its index,
+// a block-wide suffix minimum carries every mark down over the absent
+// vertices below it, and the span is written with coalesced stores.  A
+// wider span (sparse ids) is filled warp by warp instead: each warp owns the
+// vertices below its 32 keys and fills them 32 at a time, lane l finding by
+// a five-step shuffle search how many of the warp's keys have src < v.
+constexpr u32 kOffSpan = 8192;
+constexpr u32 kOffNone = 0xFFFFFFFFu;
+
+__device__ __forceinline__ u32 block_suffix_min(u32 x, u32 *s_tmp) {
+    // exclusive suffix minimum over threads (thread t gets min of t+1 .. end)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    u32 inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u32 t = __shfl_down_sync(0xFFFFFFFFu, inc, o);
+        if (lane + o < 32) inc = min(inc, t);
+    }
+    if (lane == 0) s_tmp[warp] = inc;
+    __syncthreads();
+    u32 after = kOffNone;
+    for (int w2 = warp + 1; w2 < kIdxThreads / 32; ++w2) after = min(after, s_tmp[w2]);
+    __syncthreads();
+    const u32 next_lane = __shfl_down_sync(0xFFFFFFFFu, inc, 1);
+    return lane < 31 ? min(after, next_lane) : after;
+}
+
 static __global__ void __launch_bounds__(kIdxThreads) offsets_kernel(const u64 *keys0,
                                                                     const u64 *keys1,
                                                                     const SortPlan *plan,
                                                                     BatchShape s, u32 *off) {
-    __shared__ u64 st[kIdxTile + 1];  // st[1 + i] = src of key t0 + i; st[0]: the key before
+    __shared__ u32 st[kIdxTile + 1];  // st[1 + i] = src of key t0 + i; st[0]: the key before
+    __shared__ u32 mark[kOffSpan];
+    __shared__ u32 s_tmp[kIdxThreads / 32];
     const u64 *__restrict__ K = plan_final_sel(plan) ? keys1 : keys0;
     const u64 n = 2ull * s.w;
-    const u64 nv = 1ull << s.B;
+    const u32 nv = 1u << s.B;  // B <= kDirMaxBits here
     const int tid = threadIdx.x, lane = tid & 31;
-    // entries past the largest src: every thread takes a share
-    const u64 x_last = __ldg(K + n - 1) >> s.sha;
-    const u64 stride = (u64)gridDim.x * kIdxThreads;
-    for (u64 v = x_last + 1 + (u64)blockIdx.x * kIdxThreads + tid; v <= nv; v += stride)
-        off[v] = (u32)n;
+    {
+        const u64 xg = __ldg(K + n - 1) >> s.sha;  // the largest src
+        const u64 stride = (u64)gridDim.x * kIdxThreads;
+        for (u64 v = xg + 1 + (u64)blockIdx.x * kIdxThreads + tid; v <= nv; v += stride)
+            off[v] = (u32)n;
+    }
     for (u64 t0 = (u64)blockIdx.x * kIdxTile; t0 < n; t0 += (u64)gridDim.x * kIdxTile) {
 #pragma unroll
         for (int j = 0; j < kIdxItems; ++j) {
             const u64 k = t0 + (u64)(j * kIdxThreads + tid);
-            st[1 + j * kIdxThreads + tid] = k < n ? __ldg(K + k) >> s.sha : 0ull;
+            st[1 + j * kIdxThreads + tid] = k < n ? (u32)(__ldg(K + k) >> s.sha) : kOffNone;
         }
-        if (tid == 0) st[0] = t0 ? __ldg(K + t0 - 1) >> s.sha : 0ull;
+        if (tid == 0) st[0] = t0 ? (u32)(__ldg(K + t0 - 1) >> s.sha) : 0u;
         __syncthreads();
+        const u32 cnt = (u32)min((u64)kIdxTile, n - t0);
+        const u32 x_last = st[cnt];
+        const u32 vlo = t0 ? st[0] + 1 : 0u;
+        const u32 vhi = x_last < nv ? x_last + 1 : nv + 1;  // exclusive
+        const u32 span = vhi > vlo ? vhi - vlo : 0u;
+        if (span <= kOffSpan) {
+            for (u32 q = tid; q < span; q += kIdxThreads) mark[q] = kOffNone;
+            __syncthreads();
 #pragma unroll
-        for (int j = 0; j < kIdxItems; ++j) {
-            const int i = j * kIdxThreads + tid;
-            const u64 k = t0 + (u64)i;
-            u64 lo = 0, hi = 0;  // key k writes off[lo .. hi)
-            if (k < n) {
-                const u64 x = st[1 + i];
-                lo = k ? st[i] + 1 : 0;
-                hi = x + 1 < nv + 1 ? x + 1 : nv + 1;
-                if (lo > hi) lo = hi;  // unsorted keys (a timed-out sort): write nothing wrong
+            for (int j = 0; j < kIdxItems; ++j) {
+                const int i = j * kIdxThreads + tid;
+                if ((u32)i >= cnt) break;
+                const u32 x = st[1 + i];
+                const bool head = (t0 + (u64)i == 0) || x != st[i];
+                if (head && x >= vlo && x - vlo < span) mark[x - vlo] = (u32)(t0 + (u64)i);
             }
-            const bool longrun = hi - lo > 32;
-            if (!longrun)
-                for (u64 v = lo; v < hi; ++v) off[v] = (u32)k;
-            // a run of more than 32 absent vertices is filled by the whole warp
-            unsigned todo = __ballot_sync(0xFFFFFFFFu, longrun);
-            while (todo) {
-                const int src_lane = __ffs(todo) - 1;
-                todo &= todo - 1;
-                const u64 l2 = __shfl_sync(0xFFFFFFFFu, lo, src_lane);
-                const u64 h2 = __shfl_sync(0xFFFFFFFFu, hi, src_lane);
-                const u64 k2 = __shfl_sync(0xFFFFFFFFu, k, src_lane);
-                for (u64 v = l2 + lane; v < h2; v += 32) off[v] = (u32)k2;
+            __syncthreads();
+            // suffix minimum over the span: thread t takes a contiguous block
+            const u32 per = (span + kIdxThreads - 1) / kIdxThreads;
+            const u32 q0 = min(span, (u32)tid * per), q1 = min(span, q0 + per);
+            u32 m = kOffNone;
+            for (u32 q = q0; q < q1; ++q) m = min(m, mark[q]);
+            u32 carry = block_suffix_min(m, s_tmp);
+            for (u32 q = q1; q > q0; --q) {
+                carry = min(carry, mark[q - 1]);
+                mark[q - 1] = carry;
+            }
+            __syncthreads();
+            for (u32 q = tid; q < span; q += kIdxThreads) off[vlo + q] = mark[q];
+        } else {
+#pragma unroll
+            for (int j = 0; j < kIdxItems; ++j) {
+                const int i0 = j * kIdxThreads + (tid & ~31);  // the warp's first item
+                const u64 k0 = t0 + (u64)i0;
+                if (k0 >= n) break;  // warp-uniform
+                const u32 x = st[1 + i0 + lane];  // sorted across the lanes; past n: maximum
+                const u32 nvalid = (u32)min((u64)32, n - k0);
+                const u32 xl = __shfl_sync(0xFFFFFFFFu, x, nvalid - 1);
+                const u32 wlo = k0 ? st[i0] + 1 : 0u;
+                const u32 whi = xl < nv ? xl + 1 : nv + 1;  // exclusive
+                for (u32 cb = wlo; cb < whi; cb += 32) {    // warp-uniform bounds
+                    const u32 v = cb + lane;
+                    int pos = 0;  // lanes with src < v (at most nvalid - 1 while v <= xl)
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1) {
+                        const u32 probe = __shfl_sync(0xFFFFFFFFu, x, pos + step - 1);
+                        if (probe < v) pos += step;
+                    }
+                    if (v < whi) off[v] = (u32)(k0 + (u64)pos);
+                }
             }
         }
         __syncthreads();  // the tile is restaged next

@@ -70,8 +70,6 @@ struct RoundShape {
     u64 nba, nbe;   // 2^hA, 2^hE
     u64 pmul;   // pi: x -> x * pmul mod 2^B (pmul odd)
     u64 hkey;   // key of the Step-3 edge hash
-    u32 fsh;    // Step-3 filter bit: (participant, hash) >> fsh & 31, the five
-                // bits below the bucket's
 };
 
 // pi(x): the vertex id bijection of the arc keys.
@@ -229,7 +227,7 @@ __global__ void __launch_bounds__(kIdxThreads) marc_index_kernel(const u64 *arcs
 __global__ void __launch_bounds__(kIdxThreads) mdups_kernel(
     const u64 *ekeys0, const u64 *ekeys1, const u32 *evals0, const u32 *evals1,
     const SortPlan *plans, const u64 *__restrict__ desc, RoundShape rs, u32 *perr,
-    DirEntry *edir, const u32 *tagp, u32 *efilt) {
+    DirEntry *edir, const u32 *tagp) {
     __shared__ u64 st[kIdxTile + 2];
     const Desc d = desc_view(desc, rs.K);
     const bool sel = plan_final_sel(&plans[1]) != 0;
@@ -248,21 +246,6 @@ __global__ void __launch_bounds__(kIdxThreads) mdups_kernel(
             if (i >= n) break;
             const u64 a = st[1 + ti];
             dir_mark(edir, rs.nbe, tag, n, i, a, st[ti], st[ti + 2], rs.she + rs.he_sh);
-            {
-                // Step-3 filter: the first key of its bucket in this tile ORs
-                // the bucket's filter bits of the keys that follow in the tile
-                const u32 fs = rs.she + rs.he_sh;
-                const u64 xb = a >> fs;
-                if (xb < rs.nbe && (ti == 0 || (st[ti] >> fs) != xb)) {
-                    u32 mask = 1u << ((mkey_prefix(rs, a) >> rs.fsh) & 31);
-                    for (int q = ti + 1; q < kIdxTile && t0 + (u64)q < n; ++q) {
-                        const u64 kq = st[1 + q];
-                        if ((kq >> fs) != xb) break;
-                        mask |= 1u << ((mkey_prefix(rs, kq) >> rs.fsh) & 31);
-                    }
-                    atomicOr(efilt + xb, mask);
-                }
-            }
             const u64 sa = mkey_sorted(rs, a), pa = mkey_prefix(rs, a);
             if (i + 1 >= n || mkey_sorted(rs, st[ti + 2]) != sa) continue;
             // a repeat shares the whole hash, so it lies in the run of equal
@@ -299,7 +282,6 @@ struct MSweepArgs {
     const u32 *gerr;     // round-wide error (a timed-out sort)
     const u32 *perr;     // each participant's error this round
     const DirEntry *adir, *edir;
-    const u32 *efilt;    // Step-3 filter masks, one per Step-3 bucket
     const u32 *tag;      // the round set's directory tag
     RoundShape rs;
 };
@@ -478,11 +460,8 @@ __global__ void __launch_bounds__(kMThreads, 7) msweep_kernel(MSweepArgs a) {
                 const bool es = plan_final_sel(&a.plans[1]) != 0;
                 const u64 *E = es ? a.ekeys1 : a.ekeys0;
                 const u32 *EV = es ? a.evals1 : a.evals0;
-                u64 lo64 = 0, hi64 = 0;
-                // no key of the round has the pair's filter bit: no lookup
-                const u64 bucket = ps >> rs.he_sh;
-                if (__ldg(a.efilt + bucket) & (1u << ((pp >> rs.fsh) & 31)))
-                    dir_segment(a.edir, tag, bucket, rs.Wt, lo64, hi64);
+                u64 lo64, hi64;
+                dir_segment(a.edir, tag, ps >> rs.he_sh, rs.Wt, lo64, hi64);
                 const u32 qhi = (u32)hi64;
                 for (u32 q = lower_bound32(E, (u32)lo64, qhi, ps << rs.she); q < qhi; ++q) {
                     const u64 ek = __ldg(E + q);
@@ -697,11 +676,17 @@ u64 fib_multiplier(u32 B) {
 // Bytes of one round set's directories and tag word.
 u64 dir_bytes(u64 w_max_round) {
     return ((1ull << arc_dir_bits(w_max_round)) + (1ull << edge_dir_bits(w_max_round))) *
-               sizeof(DirEntry) + (1ull << edge_dir_bits(w_max_round)) * sizeof(u32) + 256;
+               sizeof(DirEntry) + 256;
 }
 
 // Participant error words at the end of the zeroed block, one per slot at most.
 u64 perr_bytes(u32 S) { return ((u64)S * 4 + 255) & ~255ull; }
+
+// Rounds a set's directory tags may serve before the set is cleared: each
+// round advances the 32-bit tag (skipping 0), so well before it could come
+// back to a value still held by a stale entry, every entry is reset to tag 0
+// and the tag restarts at 1.
+constexpr u64 kTagRoundsMax = 0xFFFFFF00ull;
 
 // Per-stream state block bytes (f1, f2, chi, flags), padded to 256 bytes.
 u64 state_bytes(u64 r) { return (28 * r + 255) & ~255ull; }
@@ -727,7 +712,6 @@ static void free_round_set(tc_multi::RoundSet &z) {
     cudaFree(z.zeroed);
     cudaFree(z.adir);
     cudaFree(z.edir);
-    cudaFree(z.efilt);
     cudaFree(z.tag);
     z = tc_multi::RoundSet{};
 }
@@ -735,6 +719,21 @@ static void free_round_set(tc_multi::RoundSet &z) {
 // Allocate one set of round scratch: the sort buffers, the zeroed block,
 // the two directories (tag 0 everywhere) and the tag word (1: the first
 // round's tag).  On failure the set is freed and false returned.
+// Before a set's tag could wrap: wait for the device, reset every directory
+// entry of the set to tag 0 and its tag word to 1.
+static int clear_tags_if_due(tc_multi *M, int b) {
+    if (M->set_rounds[b] < kTagRoundsMax) return TC_OK;
+    tc_multi::RoundSet &z = M->rset[b];
+    const u64 na = 1ull << arc_dir_bits(M->w_max), ne = 1ull << edge_dir_bits(M->w_max);
+    const u32 one = 1;
+    TCM_CUDA(cudaDeviceSynchronize());
+    TCM_CUDA(cudaMemset(z.adir, 0, na * sizeof(DirEntry)));
+    TCM_CUDA(cudaMemset(z.edir, 0, ne * sizeof(DirEntry)));
+    TCM_CUDA(cudaMemcpy(z.tag, &one, sizeof(one), cudaMemcpyHostToDevice));
+    M->set_rounds[b] = 0;
+    return TC_OK;
+}
+
 static bool alloc_round_set(tc_multi::RoundSet &z, u64 w_max, u64 zeroed_bytes) {
     bool ok = true;
     for (int k = 0; k < 2 && ok; ++k) {
@@ -749,7 +748,6 @@ static bool alloc_round_set(tc_multi::RoundSet &z, u64 w_max, u64 zeroed_bytes) 
     ok &= ok && cudaMemset(z.adir, 0, na * sizeof(DirEntry)) == cudaSuccess;
     ok &= ok && cudaMalloc(&z.edir, ne * sizeof(DirEntry)) == cudaSuccess;
     ok &= ok && cudaMemset(z.edir, 0, ne * sizeof(DirEntry)) == cudaSuccess;
-    ok &= ok && cudaMalloc(&z.efilt, ne * sizeof(u32)) == cudaSuccess;
     const u32 one = 1;
     ok &= ok && cudaMalloc(&z.tag, 256) == cudaSuccess;
     ok &= ok && cudaMemcpy(z.tag, &one, sizeof(one), cudaMemcpyHostToDevice) == cudaSuccess;
@@ -909,14 +907,20 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u
     rs.he_sh = rs.kb + rs.hs - he;
     rs.nba = 1ull << ha;
     rs.nbe = 1ull << he;
-    // bucket = (participant, hash) >> (32 - hs + he_sh); the filter takes the
-    // five bits below (32 - hs + he_sh = 32 + kb - he >= 6 as he <= 26)
-    rs.fsh = 32 - rs.hs + rs.he_sh - 5;
     rs.pmul = fib_multiplier(rs.B);
     rs.hkey = M->hash_key;
     const int b = M->nsets == 2 ? (int)(M->rseq & 1) : 0;
     M->rseq++;
     tc_multi::RoundSet &z = M->rset[b];
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    TCM_CUDA(cudaStreamIsCapturing(st, &cap));
+    if (cap == cudaStreamCaptureStatusNone) {
+        const int rc = clear_tags_if_due(M, b);
+        if (rc) return rc;
+    } else {
+        M->graph_set = b;
+    }
+    M->set_rounds[b]++;
     SortPlan *plans = reinterpret_cast<SortPlan *>(z.zeroed);
     u32 *lb = reinterpret_cast<u32 *>(z.zeroed + 2 * sizeof(SortPlan));
     const u64 la = mlookback(2 * Wt, rs.bits_a), le = mlookback(Wt, rs.bits_e);
@@ -953,10 +957,8 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u
             z.ekeys[0], z.ekeys[1], rs.eko ? nullptr : z.evals[0], rs.eko ? nullptr : z.evals[1],
             (u32)Wt, rs.she + p * rs.bits_e, mlive(rs.hs + rs.kb, rs.bits_e, p), p, &plans[1],
             lbe + (u64)p * le, gerr, nullptr);
-    TCM_CUDA(cudaMemsetAsync(z.efilt, 0, rs.nbe * sizeof(u32), M->side));
     mdups_kernel<<<index_blocks(Wt), kIdxThreads, 0, M->side>>>(
-        z.ekeys[0], z.ekeys[1], z.evals[0], z.evals[1], plans, desc, rs, perr, z.edir, z.tag,
-        z.efilt);
+        z.ekeys[0], z.ekeys[1], z.evals[0], z.evals[1], plans, desc, rs, perr, z.edir, z.tag);
     TCM_CUDA(cudaEventRecord(M->ev_join, M->side));
     for (int p = 0; p < rs.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, ms>>>(
@@ -984,7 +986,6 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u
     a.perr = perr;
     a.adir = z.adir;
     a.edir = z.edir;
-    a.efilt = z.efilt;
     a.tag = z.tag;
     a.rs = rs;
     msweep_kernel<<<(unsigned)((R + kMThreads - 1) / kMThreads), kMThreads, 0, st>>>(a);
@@ -1172,6 +1173,9 @@ int tc_multi_capture(tc_multi *M, const uint64_t *d_edges, const uint64_t *offse
 
 int tc_multi_replay(tc_multi *M, void *cuda_stream) {
     if (!M || !M->gexec) return TC_ERR_INVAL;
+    const int rc = clear_tags_if_due(M, M->graph_set);
+    if (rc) return rc;
+    M->set_rounds[M->graph_set]++;
     TCM_CUDA(cudaGraphLaunch(M->gexec, (cudaStream_t)cuda_stream));
     M->launches += M->graph_launches;
     return TC_OK;

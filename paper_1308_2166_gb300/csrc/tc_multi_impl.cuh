@@ -67,10 +67,11 @@ struct tc_multi {
         unsigned char *zeroed = nullptr;  // SortPlan[2], look-back, round error, participant errors
         tc::DirEntry *adir = nullptr;     // arc bucket directory
         tc::DirEntry *edir = nullptr;     // Step-3 bucket directory
-        tc::u32 *efilt = nullptr;         // Step-3 filter masks, one per Step-3 bucket
         tc::u32 *tag = nullptr;           // device word: the directories' current tag
     };
     RoundSet rset[2];
+    tc::u64 set_rounds[2] = {0, 0};      // rounds (replays included) on each set's tags
+    int graph_set = 0;                   // the set a captured round uses
     int nsets = 1;
     tc::u32 rseq = 0;                    // rounds enqueued: set parity
     tc::u64 zeroed_bytes = 0;

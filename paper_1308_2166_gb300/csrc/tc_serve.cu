@@ -495,7 +495,19 @@ void tc_server::fail_all(int code) {
 void tc_server::run() {
     cudaSetDevice(dev);
     u64 t_prev = now();
+    u64 t_full = 0;  // since when `depth` rounds have been in flight (0: not full)
     for (;;) {
+        {
+            // the longest stretch with every round slot busy: the scheduler
+            // waiting for the GPU to finish a round
+            const u64 t = now();
+            if ((int)inflight.size() >= depth) {
+                if (!t_full) t_full = t;
+                if (t - t_full > local.inflight_full_max_ns) local.inflight_full_max_ns = t - t_full;
+            } else {
+                t_full = 0;
+            }
+        }
         {
             // the longest stretch between two scheduler passes with work in
             // flight or waiting: where the scheduler thread itself stalled
