@@ -499,6 +499,16 @@ def _time_single(tc, args, cfg, views, host_keys, rank, world, local_rank, dist,
             pinned.append(t)
         res_host = [torch.zeros(tc.ESTIMATE_BYTES // 8, dtype=torch.int64, pin_memory=True)
                     for _ in range(4)]
+        # the host link as this machine gives it: one pinned batch copied alone
+        probe = torch.empty_like(sched.peek(kk)[1])
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record()
+        probe.copy_(pinned[0], non_blocking=True)
+        p1.record()
+        torch.cuda.synchronize()
+        h2d_gbs = pinned[0].numel() * 8 / (p0.elapsed_time(p1) / 1e3) / 1e9
+        del probe
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -519,6 +529,7 @@ def _time_single(tc, args, cfg, views, host_keys, rank, world, local_rank, dist,
         last = tc.estimate_records(res_host[(E - 1) % 4])[0]
         e2e = {"value": e2e_all / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * e2e_edges // E,
                "d2h_bytes_per_step": tc.ESTIMATE_BYTES, "steps": E,
+               "h2d_gbs_one_batch": h2d_gbs,
                "how": "tc_process_batch_host_async from pinned host batches (each batch's "
                       "copy overlaps the previous batch's update) + tc_estimate_async and a "
                       "copy of its 72-byte record to pinned host memory every step; host "
@@ -1166,6 +1177,10 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
                                                           r_d[win])][:120],
             "around_worst_how": "[round formed, ms relative to the slowest batch's round; "
                                 "batches; edges; ms to its last completion]",
+            "around_slowest_round": [[round((t - int(r_t[int(np.argmax(r_d))])) / 1e6, 3), int(nb),
+                                      int(e), round(d / 1e6, 3)]
+                                     for t, nb, e, d in zip(r_t, r_n, r_e, r_d)
+                                     if -30e6 <= t - int(r_t[int(np.argmax(r_d))]) <= 100e6][:160],
         }
     return {**extra,
         "edges_per_s": float(ws.sum()) / span,
@@ -1182,6 +1197,8 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
         "admission_waits": int(st1["admission_waits"]),
         "sched_gap_max_ms": st1["sched_gap_max_ns"] / 1e6,
         "inflight_full_max_ms": st1["inflight_full_max_ns"] / 1e6,
+        "pool_reserved_high": int(st1["pool_reserved_high"]),
+        "pool_used_high": int(st1["pool_used_high"]),
         "sched_gaps_over_5ms": int(st1["sched_gaps_over_5ms"] - st0["sched_gaps_over_5ms"]),
         "bytes_peak": int(st1["bytes_peak"]), "bytes_fixed": int(st1["bytes_fixed"]),
         "opens": int(st1["opens"]), "closes": int(st1["closes"]),

@@ -436,6 +436,9 @@ typedef struct {
     /* the longest stretch with `depth` rounds in flight, i.e. the scheduler
      * waiting for the GPU before it may form the next round */
     uint64_t inflight_full_max_ns;
+    /* the server's memory pool (stream state and batch copies): physical
+     * memory it holds and the most it had in use at once, high-water marks */
+    uint64_t pool_reserved_high, pool_used_high;
 } tc_server_stats_t;
 
 /* Errors: TC_ERR_INVAL (bad config; key bits as tc_multi_create with

@@ -234,8 +234,7 @@ struct tc_ctx {
         DirEntry *adir = nullptr;         // tagged arc directory (ids < 2^kDirMaxBits; made
                                           // by the first batch that needs it)
         u32 *aoff = nullptr;              // dense arc offsets, 2^B + 1 (ids < 2^kDirMaxBits)
-        DirEntry *edir = nullptr;         // Step-3 hash-bucket directory
-        u32 *efilt = nullptr;             // Step-3 filter masks (one per hash bucket)
+        uint2 *bdir = nullptr;            // Step-3 buckets {first index, filter mask}, 2^hb + 1
     };
     Set set[2];
     int nsets = 1;
@@ -293,11 +292,9 @@ static void free_set(tc_ctx::Set &z, bool with_dir) {
         cudaFree(z.ekeys[k]);
         z.arcs[k] = z.ekeys[k] = nullptr;
     }
-    cudaFree(z.edir);
-    cudaFree(z.efilt);
+    cudaFree(z.bdir);
     cudaFree(z.zeroed);
-    z.edir = nullptr;
-    z.efilt = nullptr;
+    z.bdir = nullptr;
     z.zeroed = nullptr;
     if (with_dir) {
         cudaFree(z.adir);
@@ -326,9 +323,7 @@ static bool alloc_set(tc_ctx *c, tc_ctx::Set &z, u64 w) {
         ok &= ok && cudaMalloc(&z.ekeys[k], w * sizeof(u64)) == cudaSuccess;
     }
     const u64 nb = 1ull << hash_bucket_bits(w);
-    ok &= ok && cudaMalloc(&z.edir, nb * sizeof(DirEntry)) == cudaSuccess;
-    ok &= ok && cudaMemset(z.edir, 0, nb * sizeof(DirEntry)) == cudaSuccess;
-    ok &= ok && cudaMalloc(&z.efilt, nb * sizeof(u32)) == cudaSuccess;
+    ok &= ok && cudaMalloc(&z.bdir, (nb + 1) * sizeof(uint2)) == cudaSuccess;
     ok &= ok && cudaMalloc(&z.zeroed, zb) == cudaSuccess;
     if (ok && !z.aoff && c->vertex_bits <= kDirMaxBits) {
         const u64 nverts = 1ull << c->vertex_bits;
@@ -409,13 +404,10 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
         // the directory tags wrapped (after 2^32 batches): clear every tagged
         // entry so that no stale entry can carry a reused tag, and skip tag 0
         TC_CUDA(cudaDeviceSynchronize());
-        for (int k = 0; k < c->nsets; ++k) {
+        for (int k = 0; k < c->nsets; ++k)
             if (c->set[k].adir)
                 TC_CUDA(cudaMemset(c->set[k].adir, 0,
                                    (sizeof(DirEntry) << c->vertex_bits)));
-            TC_CUDA(cudaMemset(c->set[k].edir, 0,
-                               (sizeof(DirEntry) << hash_bucket_bits(c->cap_w))));
-        }
         tag = ++c->seq;
     }
     tc_ctx::Set &z = c->set[b];
@@ -460,9 +452,8 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
             z.ekeys[0], z.ekeys[1], nullptr, nullptr, (u32)w, s.she + p * s.bits_e,
             live_bits(s.hs, s.bits_e, p), p, &plans[1], lbe + (u64)p * le, berr, c->ctl);
     const cudaEvent_t edge_end = mark(c, c->side);
-    TC_CUDA(cudaMemsetAsync(z.efilt, 0, (sizeof(u32) << s.hb), c->side));
-    index_kernel<false><<<index_blocks(w), kIdxThreads, 0, c->side>>>(
-        z.ekeys[0], z.ekeys[1], &plans[1], s, z.edir, W, tag, berr, z.efilt);
+    step3_index_kernel<<<index_blocks(w), kIdxThreads, 0, c->side>>>(
+        z.ekeys[0], z.ekeys[1], &plans[1], s, z.bdir, W, berr);
     TC_CUDA(cudaEventRecord(c->ev_join, c->side));
     for (int p = 0; p < s.npa; ++p)
         ka.fn<<<(unsigned)ta, ka.threads, ka.smem, ms>>>(
@@ -499,8 +490,7 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
     a.plans = plans;
     a.adir = z.adir;
     a.aoff = z.aoff;
-    a.edir = z.edir;
-    a.efilt = z.efilt;
+    a.bdir = z.bdir;
     a.ctl = c->ctl;
     a.acc = acc;
     a.berr = berr;

@@ -19,8 +19,8 @@
 //                   keys sharing its top hs bits, and so does a repeat.
 //     adir          per-vertex directory over the sorted arcs (vertex ids
 //                   < 2^kDirMaxBits), epoch-tagged;
-//     edir          directory of the 2^hb hash buckets (top hb bits of h)
-//                   over the sorted Step-3 keys, epoch-tagged.
+//     bdir          dense directory of the 2^hb hash buckets (top hb bits of
+//                   h) over the sorted Step-3 keys: {first index, filter mask}.
 //   bw = bits of w-1, B = vertex id bits, hb = bucket bits (about w/4
 //   buckets), she = bw + 32 - hs the first sorted bit of a Step-3 key.
 #pragma once
@@ -191,18 +191,10 @@ constexpr int kIdxThreads = 256;
 constexpr int kIdxItems = 8;
 constexpr int kIdxTile = kIdxThreads * kIdxItems;
 
-// Step-3 filter: one 32-bit mask per hash bucket (the top hb bits of h),
-// bit (h >> (27 - hb)) & 31 set for every edge of the batch.  A closing pair
-// whose bit is clear has no edge in the batch, so its lookup stops there; at
-// about four edges per bucket, a pair with no edge sees its bit set about
-// one time in eight.  The mask array is zeroed before the pass that builds
-// it (index_kernel<false>).
-__device__ __forceinline__ u32 filter_bit(u64 h, u32 hb) { return 1u << ((h >> (27 - hb)) & 31); }
-
 template <bool kArcs>
 static __global__ void __launch_bounds__(kIdxThreads) index_kernel(
     const u64 *keys0, const u64 *keys1, const SortPlan *plan, BatchShape s, DirEntry *dir,
-    const u64 *__restrict__ W, u32 epoch, u32 *err, u32 *efilt = nullptr) {
+    const u64 *__restrict__ W, u32 epoch, u32 *err) {
     __shared__ u64 st[kIdxTile + 2];  // st[1 + i] = key t0 + i; st[0], st[kIdxTile + 1]: halo
     const u64 *__restrict__ K = plan_final_sel(plan) ? keys1 : keys0;
     const u64 n = kArcs ? 2ull * s.w : (u64)s.w;
@@ -251,19 +243,6 @@ static __global__ void __launch_bounds__(kIdxThreads) index_kernel(
             if (x >= nverts) continue;  // invalid batch (already flagged by the key build)
             if (x != prev) *reinterpret_cast<u64 *>(&dir[x].epoch) = (k << 32) | epoch;
             if (x != next) dir[x].end = (u32)(k + 1);
-            if constexpr (!kArcs) {
-                // the first key of its bucket in this tile ORs the bucket's
-                // filter bits of the keys that follow it in the tile
-                if (i == 0 || x != prev) {
-                    u32 mask = filter_bit(key >> s.bw, s.hb);
-                    for (int q = i + 1; q < kIdxTile && t0 + (u64)q < n; ++q) {
-                        const u64 kq = st[1 + q];
-                        if ((kq >> sh) != x) break;
-                        mask |= filter_bit(kq >> s.bw, s.hb);
-                    }
-                    atomicOr(efilt + x, mask);
-                }
-            }
         }
         __syncthreads();  // the tile is restaged next
     }
@@ -393,6 +372,144 @@ static __global__ void __launch_bounds__(kIdxThreads) offsets_kernel(const u64 *
     }
 }
 
+// ---------------------------------------------------------------------------
+// Dense Step-3 bucket directory with the filter inside: one 8-byte entry per
+// hash bucket b (the top hb bits of h), {first index of the sorted Step-3
+// keys whose bucket is >= b, mask}, for b in [0, 2^hb] (entry 2^hb = {w, 0}).
+// Bucket b's keys are [entry b, entry b+1); the mask has bit
+// (h >> (27 - hb)) & 31 set for each of them, so that a closing pair whose
+// bit is clear has no edge in the batch and its lookup ends at that one load
+// (about four edges per bucket: a pair with no edge sees its bit set about
+// one time in eight).  Written whole every batch, like the arc offsets: a
+// tile owns the buckets (bucket of the key before it, bucket of its last
+// key]; when that span fits the shared arrays, run heads mark their bucket's
+// first index and every key ORs its bit into its bucket's mask (the last
+// owned bucket's keys past the tile are read from global memory), a suffix
+// minimum carries each first index down over empty buckets, and the span is
+// written with coalesced stores; a wider span is written head by head.  The
+// same pass does the in-batch repeat check: a repeated edge has the repeated
+// hash, so it lies in the run of keys sharing the sorted hash bits that
+// follows (almost always empty), where the edges with the whole hash are
+// compared.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ u32 filter_bit(u64 h, u32 hb) { return 1u << ((h >> (27 - hb)) & 31); }
+
+constexpr u32 kBucketSpan = 3072;  // tiles average 512 buckets (4 keys per bucket)
+
+static __global__ void __launch_bounds__(kIdxThreads) step3_index_kernel(
+    const u64 *keys0, const u64 *keys1, const SortPlan *plan, BatchShape s, uint2 *bdir,
+    const u64 *__restrict__ W, u32 *err) {
+    __shared__ u64 st[kIdxTile + 2];  // st[1 + i] = key t0 + i; st[0], st[kIdxTile + 1]: halo
+    __shared__ u32 soff[kBucketSpan], smask[kBucketSpan];
+    __shared__ u32 s_tmp[kIdxThreads / 32];
+    const u64 *__restrict__ K = plan_final_sel(plan) ? keys1 : keys0;
+    const u64 n = s.w;
+    const u32 nb = 1u << s.hb;
+    const u32 sh = s.bw + 32 - s.hb;  // key -> bucket
+    const u64 pmask = (1ull << s.bw) - 1;
+    const int tid = threadIdx.x;
+    {
+        // the buckets past the last key's: every thread takes a share
+        const u64 bg = __ldg(K + n - 1) >> sh;
+        const u64 stride = (u64)gridDim.x * kIdxThreads;
+        for (u64 b = bg + 1 + (u64)blockIdx.x * kIdxThreads + tid; b <= nb; b += stride)
+            bdir[b] = make_uint2((u32)n, 0u);
+    }
+    bool dup = false;
+    for (u64 t0 = (u64)blockIdx.x * kIdxTile; t0 < n; t0 += (u64)gridDim.x * kIdxTile) {
+#pragma unroll
+        for (int j = 0; j < kIdxItems; ++j) {
+            const u64 k = t0 + (u64)(j * kIdxThreads + tid);
+            st[1 + j * kIdxThreads + tid] = k < n ? __ldg(K + k) : ~0ull;
+        }
+        if (tid == 0) st[0] = t0 ? __ldg(K + t0 - 1) : 0ull;
+        if (tid == 1) st[kIdxTile + 1] = t0 + kIdxTile < n ? __ldg(K + t0 + kIdxTile) : ~0ull;
+        __syncthreads();
+        const u32 cnt = (u32)min((u64)kIdxTile, n - t0);
+        const u64 b_last = st[cnt] >> sh;
+        const u64 blo = t0 ? (st[0] >> sh) + 1 : 0;
+        const u64 bhi = b_last < nb ? b_last + 1 : (u64)nb + 1;  // exclusive
+        const u32 span = bhi > blo ? (u32)(bhi - blo) : 0u;
+        const bool fits = span <= kBucketSpan;
+        if (fits)
+            for (u32 q = tid; q < span; q += kIdxThreads) {
+                soff[q] = 0xFFFFFFFFu;
+                smask[q] = 0u;
+            }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kIdxItems; ++j) {
+            const int i = j * kIdxThreads + tid;
+            const u64 k = t0 + (u64)i;
+            if (k >= n) break;
+            const u64 key = st[1 + i];
+            const u64 b = key >> sh;
+            // repeat check: the run of equal sorted bits that follows
+            {
+                const u64 hp = key >> s.she, h = key >> s.bw;
+                u64 e = 0;
+                bool have_e = false;
+                for (u64 q = k + 1; q < n; ++q) {
+                    const u64 kq = (q - t0 < (u64)kIdxTile + 1) ? st[1 + (q - t0)] : __ldg(K + q);
+                    if ((kq >> s.she) != hp) break;
+                    if ((kq >> s.bw) != h) continue;
+                    if (!have_e) {
+                        e = __ldg(W + (key & pmask));
+                        have_e = true;
+                    }
+                    dup |= __ldg(W + (kq & pmask)) == e;
+                }
+            }
+            if (b < blo || b >= bhi) continue;  // a bucket begun in an earlier tile
+            const bool head = (k == 0) || (st[i] >> sh) != b;
+            if (fits) {
+                if (head) soff[b - blo] = (u32)k;
+                atomicOr(&smask[b - blo], filter_bit(key >> s.bw, s.hb));
+            } else if (head) {
+                // wide span: this head writes its bucket (mask from its keys)
+                // and the empty buckets below it
+                u32 mask = 0;
+                for (u64 q = k; q < n; ++q) {
+                    const u64 kq = (q - t0 < (u64)kIdxTile + 1) ? st[1 + (q - t0)] : __ldg(K + q);
+                    if ((kq >> sh) != b) break;
+                    mask |= filter_bit(kq >> s.bw, s.hb);
+                }
+                const u64 bprev = k ? (st[i] >> sh) + 1 : 0;
+                for (u64 q = bprev; q < b; ++q) bdir[q] = make_uint2((u32)k, 0u);
+                bdir[b] = make_uint2((u32)k, mask);
+            }
+        }
+        __syncthreads();
+        if (fits && span) {
+            // the last owned bucket's keys past the tile
+            if (tid == 0 && b_last < nb) {
+                u32 mask = 0;
+                for (u64 q = t0 + cnt; q < n; ++q) {
+                    const u64 kq = __ldg(K + q);
+                    if ((kq >> sh) != b_last) break;
+                    mask |= filter_bit(kq >> s.bw, s.hb);
+                }
+                smask[span - 1] |= mask;
+            }
+            // suffix minimum of the first indices over the span (blocked per thread)
+            const u32 per = (span + kIdxThreads - 1) / kIdxThreads;
+            const u32 q0 = min(span, (u32)tid * per), q1 = min(span, q0 + per);
+            u32 m = 0xFFFFFFFFu;
+            for (u32 q = q0; q < q1; ++q) m = min(m, soff[q]);
+            u32 carry = block_suffix_min(m, s_tmp);
+            for (u32 q = q1; q > q0; --q) {
+                carry = min(carry, soff[q - 1]);
+                soff[q - 1] = carry;
+            }
+            __syncthreads();
+            for (u32 q = tid; q < span; q += kIdxThreads)
+                bdir[blo + q] = make_uint2(soff[q], smask[q]);
+        }
+        __syncthreads();  // the tile is restaged next
+    }
+    if (dup) set_error(err, kErrInput);
+}
+
 // Blocks of an index launch over n keys.
 inline unsigned index_blocks(u64 n) {
     const u64 b = (n + kIdxTile - 1) / kIdxTile;
@@ -455,8 +572,7 @@ struct SweepArgs {
     const SortPlan *plans;
     const DirEntry *adir;         // tagged arc directory (kArcTagged)
     const u32 *aoff;              // dense arc offsets, 2^B + 1 entries (kArcDense)
-    const DirEntry *edir;         // Step-3 hash buckets
-    const u32 *efilt;             // Step-3 filter masks, one per hash bucket
+    const uint2 *bdir;            // Step-3 buckets: {first key index, filter mask}, 2^hb + 1
     Control *ctl;
     BatchAcc *acc;                // per-batch S / closed accumulator (zeroed)
     const u32 *berr;              // this batch's error word (zeroed)
@@ -562,9 +678,13 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
         const u64 hp = h >> (32 - s.hs);  // the sorted bits
         const u64 bucket = h >> (32 - s.hb);
         // no edge of the batch has the pair's filter bit: nothing to look up
-        const bool maybe = (__ldg(a.efilt + bucket) & filter_bit(h, s.hb)) != 0;
-        if (maybe) dir_segment32(a.edir, epoch, bucket, s.w, lo, hi);
-        else lo = hi = 0;
+        const uint2 e0 = __ldg(a.bdir + bucket);
+        if (e0.y & filter_bit(h, s.hb)) {
+            hi = min(__ldg(a.bdir + bucket + 1).x, s.w);
+            lo = min(e0.x, hi);
+        } else {
+            lo = hi = 0;
+        }
         for (u32 k = lower_bound_idx32(E, lo, hi, hp << s.she); k < hi; ++k) {
             const u64 ek = __ldg(E + k);
             if ((ek >> s.she) != hp) break;

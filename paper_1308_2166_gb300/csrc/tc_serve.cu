@@ -831,6 +831,11 @@ int tc_server_stats(tc_server *S, tc_server_stats_t *out) {
     *out = S->stats;
     out->bytes_budget = S->cfg.budget_bytes;
     out->bytes_fixed = S->fixed;
+    unsigned long long v = 0;  // the runtime reports these attributes as 64-bit values
+    if (cudaMemPoolGetAttribute(S->pool, cudaMemPoolAttrReservedMemHigh, &v) == cudaSuccess)
+        out->pool_reserved_high = (uint64_t)v;
+    if (cudaMemPoolGetAttribute(S->pool, cudaMemPoolAttrUsedMemHigh, &v) == cudaSuccess)
+        out->pool_used_high = (uint64_t)v;
     return TC_OK;
 }
 
