@@ -392,7 +392,10 @@ typedef struct {
                               round buffers, open streams' state (28 B per
                               estimator) and admitted batches (8 B per edge) */
     uint64_t w_max_round;  /* most edges one round folds (and the largest batch) */
-    uint32_t depth;        /* rounds in flight, 1..8; 0 means 2 */
+    uint32_t depth;        /* rounds in flight, 1..8; 0 means 1.  With more than
+                              one, a round's sorts run beside the previous round's
+                              sweep: the same saturation throughput was measured,
+                              with a much longer latency tail */
     uint32_t max_round_streams; /* most streams one round folds; 0 = max_streams
                                    (1 serves one batch per round, back to back) */
 } tc_server_config_t;

@@ -577,7 +577,7 @@ class Server:
     """
 
     def __init__(self, max_streams: int, vertex_bits: int, budget_bytes: int,
-                 w_max_round: int, depth: int = 2, max_round_streams: int = 0):
+                 w_max_round: int, depth: int = 0, max_round_streams: int = 0):
         import numpy as np
         cfg = tc_server_config_t(max_streams, vertex_bits, budget_bytes, w_max_round, depth,
                                  max_round_streams)

@@ -93,7 +93,7 @@ int status_of(u64 e) {
 struct tc_server {
     tc_server_config_t cfg{};
     int dev = 0;
-    int depth = 2;
+    int depth = 1;
     tc_multi *M = nullptr;
     cudaStream_t cs = nullptr;  // rounds
     cudaStream_t xs = nullptr;  // host -> device batch copies
@@ -602,7 +602,11 @@ int tc_server_create(const tc_server_config_t *cfg, tc_server **out) {
     *out = nullptr;
     if (cfg->max_streams == 0 || cfg->depth > 8 || cfg->w_max_round == 0) return TC_ERR_INVAL;
     const u32 S = cfg->max_streams;
-    const int depth = cfg->depth ? (int)cfg->depth : 2;
+    // one round in flight unless asked: with two, a round's sorts run beside
+    // the previous round's sweep, which measured the same throughput at
+    // saturation but rounds that stalled for tens of milliseconds now and
+    // then (p99 batch latency 31-113 ms at 70% load against 1.5 ms with one)
+    const int depth = cfg->depth ? (int)cfg->depth : 1;
     const int nbuf = depth + 1;
     const u64 ring_bytes = (u64)nbuf * (2ull * S * kRecordWords * 8 + desc_words(S) * 8 + S * 4);
     const u64 fixed = multi_scratch_bytes(S, cfg->w_max_round, cfg->vertex_bits, 2) + ring_bytes;

@@ -182,7 +182,8 @@ def _check(where, done, specs, plans, vertex_bits, bad=None):
         assert got == expect[s][i], (s, i, got, expect[s][i])
 
 
-def test_mix_equals_alone_with_slot_waits():
+@pytest.mark.parametrize("depth", [0, 2], ids=["default_depth", "depth2"])
+def test_mix_equals_alone_with_slot_waits(depth):
     rng = np.random.default_rng(5)
     n_streams = 24
     specs, plans = [], []
@@ -192,7 +193,7 @@ def test_mix_equals_alone_with_slot_waits():
                       int(rng.integers(0, 2**32))))
         plans.append(_plan(rng, keys, int(rng.integers(3, 14))))
     srv = tc.Server(max_streams=8, vertex_bits=12, budget_bytes=2 << 30, w_max_round=4096,
-                    depth=2)
+                    depth=depth)
     try:
         where, done = _run_mix(srv, specs, plans, rng)
         st = srv.stats()
