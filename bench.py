@@ -49,21 +49,26 @@ UNIT = "edges/s"
 # ncu DRAM traffic of a kernel per algorithmic byte, with the hash of the
 # sources it was measured on: the figure is reported only while the kernel's
 # sources hash the same (a changed kernel reports traffic null).
+# Keyed by (kernel, workload): how much of a pass's output L2 still holds
+# when the next pass reads it depends on the sizes.
 TRAFFIC = {
-    # two rmat20 arc passes: 167.7 MB of DRAM read + write over 268.4 MB of
-    # algorithmic bytes (the passes' writes largely stay in L2)
-    "onesweep_pass_kernel": {"src_hash": "1f2e5f68f12875e3",
-                             "bytes_per_algorithmic_byte": 167.717888 / 268.435456},
+    # r = w = 2^24, batch 4 of the stream: 3 Step-3 passes + 4 arc passes,
+    # 2643.9 MB of DRAM read + write over 2952.9 MB of algorithmic bytes
+    ("onesweep_pass_kernel", "large"): {"src_hash": "dc37046c1501b761",
+                                        "bytes_per_algorithmic_byte": 2643.9 / 2952.9},
 }
 
-# Sources the sort pass kernel is built from.
-_SORT_SOURCES = ("tc_common.cuh", "tc_onesweep.cuh")
+# Sources each kernel is built from.
+_SOURCES = {
+    "onesweep_pass_kernel": ("tc_common.cuh", "tc_onesweep.cuh"),
+    "sweep_kernel": ("tc_common.cuh", "tc_kernels.cuh"),
+}
 
 
-def _src_hash() -> str:
+def _src_hash(kernel: str = "onesweep_pass_kernel") -> str:
     h = hashlib.sha256()
     cs = os.path.join(ROOT, "paper_1308_2166_gb300", "csrc")
-    for f in _SORT_SOURCES:
+    for f in _SOURCES[kernel]:
         h.update(open(os.path.join(cs, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -77,6 +82,8 @@ def _args():
     p.add_argument("--workload", choices=["large", "rmat20", "tiny", "multi512", "serve4096",
                                           "wsweep", "accuracy"], default="large")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--serve-depth", type=int, default=1,
+                   help="serving: rounds in flight at once (1 = one round after another)")
     p.add_argument("--no-clock-sampling", action="store_true",
                    help="do not poll nvidia-smi during the timed phases (clocks reported null)")
     p.add_argument("--no-extras", action="store_true",
@@ -591,8 +598,8 @@ def _time_single(tc, args, cfg, views, host_keys, rank, world, local_rank, dist,
                   "events on both streams, timed region)",
         "traffic": None,
     }
-    tr = TRAFFIC.get("onesweep_pass_kernel")
-    if tr and tr.get("src_hash") == _src_hash():
+    tr = TRAFFIC.get(("onesweep_pass_kernel", cfg["name"]))
+    if tr and tr.get("src_hash") == _src_hash("onesweep_pass_kernel"):
         sort_roof["traffic"] = tr["bytes_per_algorithmic_byte"] * sort_roof["bytes_per_launch"]
     sweep_bytes = 56 * r * K
     sweep_gbs = sweep_bytes / (ms_sweep / 1e3) / 1e9 if ms_sweep > 0 else 0.0
@@ -1236,7 +1243,8 @@ def run_serve(args, rank, world, local_rank):
         del keys
         torch.cuda.empty_cache()
     gen_s = time.perf_counter() - t
-    cfg = {"vertex_bits": 22, "budget_bytes": 120 << 30, "w_max_round": 1 << 23, "depth": 2}
+    cfg = {"vertex_bits": 22, "budget_bytes": 120 << 30, "w_max_round": 1 << 23,
+           "depth": args.serve_depth}
     secs = max(3.0, min(20.0, args.steps / 10.0))
     sample = not args.no_clock_sampling
     sampler = ClockSampler(local_rank) if sample else None
@@ -1355,7 +1363,8 @@ def run_accuracy(args, rank, world, local_rank):
     """Relative error of tau_hat against the exact count per configuration
     and per r (the paper's Table 2 reports the mean deviation per r): for the
     tiny Chung-Lu stream and the R-MAT scale-20 stream, one pass over the
-    whole stream at r = 2^10, 2^12, ..., up to the workload's r, for 5 Philox
+    whole stream at r = 2^6 .. 2^18 (tiny, whose own r is 2^10) and 2^10 .. 2^22
+    (rmat20, own r 2^20) in steps of 4x, for 5 Philox
     seeds each; the mean over the seeds of |tau_hat - tau| / tau, beside the
     epsilon that Theorem 3.2's sample bound gives at delta = 0.05.  The exact
     counts come from tests/golden/exact_tau.json (written by a script that
@@ -1373,7 +1382,8 @@ def run_accuracy(args, rank, world, local_rank):
     seeds = (1, 2, 3, 4, 5)
     table = {}
     t0 = time.perf_counter()
-    for name, r_max in (("tiny", 1 << 10), ("rmat20", 1 << 20)):
+    # r from well below to 4x past each workload's own r (tiny 2^10, rmat20 2^20)
+    for name, lr_lo, lr_hi in (("tiny", 6, 18), ("rmat20", 10, 22)):
         cfg, views, keys = _single_workload(name)
         g = gold.get(name)
         if not g or g["keys_sha256"] != hashlib.sha256(keys.astype("<u8").tobytes()).hexdigest():
@@ -1381,7 +1391,7 @@ def run_accuracy(args, rank, world, local_rank):
             continue
         tau = g["tau"]
         rows = []
-        for lr in range(10, r_max.bit_length(), 2):
+        for lr in range(lr_lo, lr_hi + 1, 2):
             r = 1 << lr
             errs, taus = [], []
             for sd in seeds:
@@ -1406,14 +1416,14 @@ def run_accuracy(args, rank, world, local_rank):
     table["large"] = {"tau_exact": None,
                       "tau": "unavailable: the exact count of the 1.2e9-edge graph is out of "
                              "reach of the host's cores within a benchmark run"}
-    head = table["rmat20"]["rows"][-1] if "rows" in table.get("rmat20", {}) else {}
+    head = next((x for x in table.get("rmat20", {}).get("rows", []) if x["r"] == 1 << 20), {})
     line = {"metric": "mean relative error of tau_hat vs the exact count (5 seeds)",
             "value": head.get("mean_rel_error"), "unit": "fraction", "n_gpus": 1,
             "steps": len(seeds), "warmup": 0, "ms_per_step": None, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
             "config": {"workload": "accuracy: tiny (Chung-Lu 2.3, m=32768) and rmat20 "
-                                   "(R-MAT scale 20) at r = 2^10 .. workload r, 5 seeds; "
-                                   "value = rmat20 at r = 2^20"},
+                                   "(R-MAT scale 20) at r = 2^6 .. 2^18 and 2^10 .. 2^22, 5 "
+                                   "seeds; value = rmat20 at its own r = 2^20"},
             "table": table, "seconds": round(time.perf_counter() - t0, 1)}
     print(json.dumps(line), flush=True)
     return 0

@@ -520,9 +520,13 @@ int tc_save(tc_ctx *c, void *buf, uint64_t size);
 
 /* Create a context from a blob (scratch for batches of up to w_max edges,
  * as tc_create_ex).  TC_ERR_INVAL if the header is not a version-1 blob,
- * `size` is short, a flag word has bits other than TC_FLAG_CLOSED, or the
- * stored S and closed count disagree with the state; TC_ERR_NOMEM,
- * TC_ERR_CUDA as tc_create_ex. */
+ * `size` is short, a flag word has bits other than TC_FLAG_CLOSED, a tuple
+ * is not one the update can reach (with |E| = 0 every tuple empty; else f1
+ * an edge u < v < 2^vertex_bits, f2 empty with chi = 0 or another such
+ * edge sharing an endpoint with f1 with chi >= 1, closed only with f2), or
+ * the stored S and
+ * closed count disagree with the state; TC_ERR_NOMEM, TC_ERR_CUDA as
+ * tc_create_ex. */
 int tc_load(const void *buf, uint64_t size, uint64_t w_max, tc_ctx **out);
 
 /* Self-test of the bounded device-side waits (no counterpart in the paper;

@@ -234,6 +234,7 @@ struct tc_ctx {
         DirEntry *adir = nullptr;         // tagged arc directory (ids < 2^kDirMaxBits; made
                                           // by the first batch that needs it)
         u32 *aoff = nullptr;              // dense arc offsets, 2^B + 1 (ids < 2^kDirMaxBits)
+        uint4 *pdir = nullptr;            // the same packed, packed_groups(2^B)
         uint2 *bdir = nullptr;            // Step-3 buckets {first index, filter mask}, 2^hb + 1
     };
     Set set[2];
@@ -299,8 +300,10 @@ static void free_set(tc_ctx::Set &z, bool with_dir) {
     if (with_dir) {
         cudaFree(z.adir);
         cudaFree(z.aoff);
+        cudaFree(z.pdir);
         z.adir = nullptr;
         z.aoff = nullptr;
+        z.pdir = nullptr;
     }
 }
 
@@ -328,6 +331,7 @@ static bool alloc_set(tc_ctx *c, tc_ctx::Set &z, u64 w) {
     if (ok && !z.aoff && c->vertex_bits <= kDirMaxBits) {
         const u64 nverts = 1ull << c->vertex_bits;
         ok &= cudaMalloc(&z.aoff, (nverts + 1) * sizeof(u32)) == cudaSuccess;
+        ok &= ok && cudaMalloc(&z.pdir, packed_groups(nverts) * sizeof(uint4)) == cudaSuccess;
     }
     return ok;
 }
@@ -462,10 +466,12 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
     const cudaEvent_t arc_end = mark(c, ms);
     if (sort_begin && edge_end && arc_end) c->spans.push_back({sort_begin, arc_end, edge_end});
     if (stages) stamp(c, ms, kArcSort);  // arc passes, with the edge passes beside them
-    if (dmode == kArcDense)
+    if (dmode == kArcDense) {
         offsets_kernel<<<index_blocks(2 * w), kIdxThreads, 0, ms>>>(z.arcs[0], z.arcs[1],
                                                                      &plans[0], s, z.aoff);
-    else if (dmode == kArcTagged)
+        pack_offsets_kernel<<<pack_blocks(c->vertex_bits, c->sm_count), kIdxThreads, 0, ms>>>(
+            z.aoff, 1u << c->vertex_bits, z.pdir);
+    } else if (dmode == kArcTagged)
         index_kernel<true><<<index_blocks(2 * w), kIdxThreads, 0, ms>>>(
             z.arcs[0], z.arcs[1], &plans[0], s, z.adir, W, tag, berr);
     if (stages) stamp(c, ms, kDups);  // the arc index, beside the rest of the edge branch
@@ -490,6 +496,7 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
     a.plans = plans;
     a.adir = z.adir;
     a.aoff = z.aoff;
+    a.pdir = z.pdir;
     a.bdir = z.bdir;
     a.ctl = c->ctl;
     a.acc = acc;
@@ -511,7 +518,7 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
     // this set is free again once the sweep and bookkeeping have read it
     TC_CUDA(cudaEventRecord(c->ev_swept[b], st));
     TC_CUDA(cudaGetLastError());
-    c->launches += (dmode != kArcSearch ? 6 : 5) + (u64)s.npa + (u64)s.npe;
+    c->launches += (dmode == kArcDense ? 7 : dmode == kArcTagged ? 6 : 5) + (u64)s.npa + (u64)s.npe;
     if (c->prof) {
         c->prof_batches += 1;
         c->prof_sort_launches += (u64)s.npa + (u64)s.npe;
@@ -1178,19 +1185,46 @@ extern "C" int tc_load(const void *buf, uint64_t size, uint64_t w_max, tc_ctx **
         return TC_ERR_INVAL;
     const u64 r = h.r;
     const unsigned char *p = static_cast<const unsigned char *>(buf) + sizeof(h);
-    // the committed estimate must be the one the state gives (Lemma 3.1's
-    // S over the closed estimators): a cheap check against a damaged blob
+    // Every tuple must be one the update can reach (Sec. 3): before the first
+    // edge all are empty; after it, f1 is an edge of the stream model (u < v,
+    // ids below 2^B), f2 is empty or another such edge sharing an endpoint
+    // with f1, with chi >= 1, and only a tuple with f2 can be closed.  The
+    // sweep indexes the vertex directories by f1's endpoints, so a blob
+    // outside these is refused here rather than read out of bounds there.
+    // The committed estimate must also be the one the state gives (Lemma
+    // 3.1's S over the closed estimators).
+    const u64 id_lim = h.vertex_bits >= 32 ? (1ull << 32) : (1ull << h.vertex_bits);
+    auto edge_ok = [id_lim](u64 e) {
+        const u64 u = e >> 32, v = e & 0xFFFFFFFFull;
+        return u < v && v < id_lim;
+    };
     using u128 = unsigned __int128;
     u128 S = 0;
     u64 closed = 0;
     for (u64 i = 0; i < r; ++i) {
+        u64 f1, f2, chi;
         u32 fl;
+        std::memcpy(&f1, p + 8 * i, 8);
+        std::memcpy(&f2, p + 8 * r + 8 * i, 8);
+        std::memcpy(&chi, p + 16 * r + 8 * i, 8);
         std::memcpy(&fl, p + 24 * r + 4 * i, 4);
         if (fl & ~TC_FLAG_CLOSED) return TC_ERR_INVAL;
+        if (h.m == 0) {
+            if (f1 != kEmpty || f2 != kEmpty || chi != 0 || fl != 0) return TC_ERR_INVAL;
+            continue;
+        }
+        if (!edge_ok(f1)) return TC_ERR_INVAL;
+        if (f2 == kEmpty) {
+            // chi turns positive exactly when the first f2 is drawn
+            if ((fl & TC_FLAG_CLOSED) || chi != 0) return TC_ERR_INVAL;
+        } else {
+            const u64 a1 = f1 >> 32, b1 = f1 & 0xFFFFFFFFull;
+            const u64 a2 = f2 >> 32, b2 = f2 & 0xFFFFFFFFull;
+            const bool adjacent = a1 == a2 || a1 == b2 || b1 == a2 || b1 == b2;
+            if (!edge_ok(f2) || f2 == f1 || !adjacent || chi == 0) return TC_ERR_INVAL;
+        }
         if (fl & TC_FLAG_CLOSED) {
-            u64 x;
-            std::memcpy(&x, p + 16 * r + 8 * i, 8);
-            S += x;
+            S += chi;
             ++closed;
         }
     }

@@ -18,7 +18,10 @@
 //                   bits): every edge lies in its hash bucket, in the run of
 //                   keys sharing its top hs bits, and so does a repeat.
 //     adir          per-vertex directory over the sorted arcs (vertex ids
-//                   < 2^kDirMaxBits), epoch-tagged;
+//                   < 2^kDirMaxBits), epoch-tagged, for batches with
+//                   2^B > 8w; otherwise
+//     aoff, pdir    the dense CSR offsets of the sorted arcs (2^B + 1 u32)
+//                   and the same packed 12 vertices to 16 bytes;
 //     bdir          dense directory of the 2^hb hash buckets (top hb bits of
 //                   h) over the sorted Step-3 keys: {first index, filter mask}.
 //   bw = bits of w-1, B = vertex id bits, hb = bucket bits (about w/4
@@ -373,6 +376,69 @@ static __global__ void __launch_bounds__(kIdxThreads) offsets_kernel(const u64 *
 }
 
 // ---------------------------------------------------------------------------
+// Packed arc offsets: the dense offsets again, in 16 bytes per group of
+// kPackVerts vertices, {off[x0], then for j < kPackVerts the byte
+// off[x0 + j + 1] - off[x0]}, x0 = kPackVerts * g, so that one load gives a
+// vertex's whole run [off[x], off[x+1]).  A group with more than 255 arcs
+// (one holding a high-degree vertex) is marked kPackWide and its lookups
+// read the offsets themselves.  At 2^25 ids this is 45 MB against the
+// offsets' 128 MB: it stays in L2 beside the Step-3 bucket directory through
+// the sweep, whose two degree lookups per estimator would otherwise be
+// random DRAM reads.  One thread per group; a block stages its groups'
+// offsets in shared memory with coalesced loads.
+// ---------------------------------------------------------------------------
+constexpr u32 kPackVerts = 12;
+constexpr u32 kPackWide = 0xFFFFFFFFu;  // offsets are below 2^30: never a base
+
+__host__ __device__ constexpr u64 packed_groups(u64 nv) { return (nv + kPackVerts - 1) / kPackVerts; }
+
+static __global__ void __launch_bounds__(kIdxThreads) pack_offsets_kernel(const u32 *off, u32 nv,
+                                                                         uint4 *pdir) {
+    __shared__ u32 so[kIdxThreads * kPackVerts + 1];
+    const u32 ng = (u32)packed_groups(nv);
+    for (u32 t0 = blockIdx.x * kIdxThreads; t0 < ng; t0 += gridDim.x * kIdxThreads) {
+        const u32 x0 = t0 * kPackVerts;
+        for (u32 q = threadIdx.x; q <= kIdxThreads * kPackVerts; q += kIdxThreads)
+            so[q] = __ldg(off + min(x0 + q, nv));  // off has nv + 1 entries
+        __syncthreads();
+        const u32 g = t0 + threadIdx.x;
+        if (g < ng) {
+            const u32 *o = so + threadIdx.x * kPackVerts;
+            const u32 base = o[0];
+            uint4 e = make_uint4(kPackWide, 0u, 0u, 0u);
+            if (o[kPackVerts] - base <= 255u) {
+                u32 wd[3] = {0u, 0u, 0u};
+#pragma unroll
+                for (u32 j = 0; j < kPackVerts; ++j) wd[j >> 2] |= (o[j + 1] - base) << (8 * (j & 3));
+                e = make_uint4(base, wd[0], wd[1], wd[2]);
+            }
+            pdir[g] = e;
+        }
+        __syncthreads();  // the groups' offsets are restaged next
+    }
+}
+
+// Byte j of a packed entry's run ends (j < kPackVerts).
+__device__ __forceinline__ u32 pack_end(const uint4 &q, u32 j) {
+    const u32 wd = j < 4 ? q.y : (j < 8 ? q.z : q.w);
+    return (wd >> (8 * (j & 3))) & 0xFFu;
+}
+
+// Run [start, end) of vertex x (< nv) in the sorted arcs, clamped to the n arcs.
+__device__ __forceinline__ void packed_segment(const uint4 *pdir, const u32 *off, u32 x, u32 n,
+                                               u32 &start, u32 &end) {
+    const u32 g = x / kPackVerts, j = x - g * kPackVerts;
+    const uint4 q = __ldg(pdir + g);
+    if (q.x != kPackWide) {
+        end = min(q.x + pack_end(q, j), n);
+        start = min(j ? q.x + pack_end(q, j - 1) : q.x, end);
+    } else {
+        end = min(__ldg(off + x + 1), n);
+        start = min(__ldg(off + x), end);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Dense Step-3 bucket directory with the filter inside: one 8-byte entry per
 // hash bucket b (the top hb bits of h), {first index of the sorted Step-3
 // keys whose bucket is >= b, mask}, for b in [0, 2^hb] (entry 2^hb = {w, 0}).
@@ -516,6 +582,14 @@ inline unsigned index_blocks(u64 n) {
     return (unsigned)(b < 152 * 8 ? (b ? b : 1) : 152 * 8);
 }
 
+// Blocks of a pack_offsets_kernel launch over 2^B vertex ids: one group per
+// thread, at most 8 waves' worth of blocks per SM (grid-stride beyond).
+inline unsigned pack_blocks(u32 B, int sm_count) {
+    const u64 b = (packed_groups(1ull << B) + kIdxThreads - 1) / kIdxThreads;
+    const u64 cap = 8ull * (u64)(sm_count > 0 ? sm_count : 1);
+    return (unsigned)(b < cap ? b : cap);
+}
+
 // ---------------------------------------------------------------------------
 // 128-bit sums (Lemma 3.1's S can exceed 64 bits).
 // ---------------------------------------------------------------------------
@@ -572,6 +646,7 @@ struct SweepArgs {
     const SortPlan *plans;
     const DirEntry *adir;         // tagged arc directory (kArcTagged)
     const u32 *aoff;              // dense arc offsets, 2^B + 1 entries (kArcDense)
+    const uint4 *pdir;            // the same packed, packed_groups(2^B) entries (kArcDense)
     const uint2 *bdir;            // Step-3 buckets: {first key index, filter mask}, 2^hb + 1
     Control *ctl;
     BatchAcc *acc;                // per-batch S / closed accumulator (zeroed)
@@ -626,10 +701,8 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
     const u64 u = f1 >> 32, v = f1 & kMask32;
     u32 su, eu, sv, ev;
     if constexpr (kDir == kArcDense) {
-        eu = min(__ldg(a.aoff + u + 1), n_arcs);
-        su = min(__ldg(a.aoff + u), eu);
-        ev = min(__ldg(a.aoff + v + 1), n_arcs);
-        sv = min(__ldg(a.aoff + v), ev);
+        packed_segment(a.pdir, a.aoff, (u32)u, n_arcs, su, eu);
+        packed_segment(a.pdir, a.aoff, (u32)v, n_arcs, sv, ev);
     } else if constexpr (kDir == kArcTagged) {
         dir_segment32(a.adir, epoch, u, n_arcs, su, eu);
         dir_segment32(a.adir, epoch, v, n_arcs, sv, ev);

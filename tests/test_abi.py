@@ -110,3 +110,32 @@ def test_completion_dtype_matches_struct():
     for name, _ in tc.tc_completion_t._fields_:
         assert dt.fields[name][1] == getattr(tc.tc_completion_t, name).offset, name
     assert np.dtype(dt.fields["tau_hat"][0]) == np.float64
+
+
+def test_load_refuses_unreachable_tuples_on_the_host(lib):
+    """tc_load checks a blob's tuples on the host before it creates a
+    context, so these refusals need no GPU."""
+    import numpy as np
+    r, B = 4, 12
+    empty = (1 << 64) - 1
+
+    def blob(m, f1, f2, chi, fl):
+        hdr = np.zeros(16, dtype=np.uint64)
+        hdr[:11] = [0x3145544154534354, 1, r, 7, 0, B, m, 1 if m else 0, 0, 0, 0]
+        return (hdr.tobytes() + np.array(f1, dtype=np.uint64).tobytes()
+                + np.array(f2, dtype=np.uint64).tobytes()
+                + np.array(chi, dtype=np.uint64).tobytes()
+                + np.array(fl, dtype=np.uint32).tobytes())
+
+    e = (1 << 32) | 2
+    bad = [
+        blob(0, [e, empty, empty, empty], [empty] * 4, [0] * 4, [0] * 4),   # edge before |E| > 0
+        blob(10, [empty, e, e, e], [empty] * 4, [0] * 4, [0] * 4),          # empty f1 after
+        blob(10, [(1 << 32) | (1 << B)] + [e] * 3, [empty] * 4, [0] * 4, [0] * 4),
+        blob(10, [e] * 4, [(3 << 32) | 4] + [empty] * 3, [1, 0, 0, 0], [0] * 4),
+        blob(10, [e] * 4, [empty] * 4, [2, 0, 0, 0], [0] * 4),
+    ]
+    for b in bad:
+        h = ctypes.c_void_p()
+        assert lib.tc_load(b, len(b), 4096, ctypes.byref(h)) == tc.TC_ERR_INVAL
+        assert not h.value

@@ -80,3 +80,50 @@ def test_damaged_blob_is_refused():
     bad[128 + 24 * 64] |= 2                         # a flag bit that does not exist
     with pytest.raises(tc.TcError):
         tc.tc_load(bytes(bad), 4096)
+
+
+def test_unreachable_tuples_are_refused():
+    """A blob whose tuples the update cannot reach is refused before any of
+    its vertex ids could index a directory."""
+    r, B = 64, 12
+    ctx = tc.tc_create_ex(r, 1, 0, 4096, B)
+    try:
+        tc.tc_process_batch(ctx, to_device(synth.tiny_chung_lu()[:4096]))
+        blob = bytes(tc.tc_save(ctx))
+    finally:
+        tc.tc_destroy(ctx)
+    f1 = np.frombuffer(blob[128:128 + 8 * r], dtype=np.uint64)
+    f2 = np.frombuffer(blob[128 + 8 * r:128 + 16 * r], dtype=np.uint64)
+    chi = np.frombuffer(blob[128 + 16 * r:128 + 24 * r], dtype=np.uint64)
+    fl = np.frombuffer(blob[128 + 24 * r:], dtype=np.uint32)
+    with_f2 = int(np.flatnonzero((f2 != tc.TC_EMPTY_EDGE) & (fl == 0))[0])
+    without_f2 = np.flatnonzero(f2 == tc.TC_EMPTY_EDGE)
+
+    def patched(i, f1v=None, f2v=None, chiv=None, flv=None):
+        b = bytearray(blob)
+        for off, arr, val, size in ((128, f1, f1v, 8), (128 + 8 * r, f2, f2v, 8),
+                                    (128 + 16 * r, chi, chiv, 8), (128 + 24 * r, fl, flv, 4)):
+            if val is not None:
+                b[off + size * i:off + size * (i + 1)] = \
+                    np.array([val], dtype=np.uint64 if size == 8 else np.uint32).tobytes()
+        return bytes(b)
+
+    u, v = int(f1[with_f2]) >> 32, int(f1[with_f2]) & 0xFFFFFFFF
+    a, b = [x for x in range(4) if x not in (u, v)][:2]
+    cases = [
+        patched(with_f2, f1v=(u << 32) | (1 << B)),             # id beyond 2^B
+        patched(with_f2, f1v=tc.TC_EMPTY_EDGE),                 # empty f1 once |E| > 0
+        patched(with_f2, f1v=(5 << 32) | 3),                    # u > v
+        patched(with_f2, f2v=int(f1[with_f2])),                 # f2 = f1
+        patched(with_f2, f2v=(a << 32) | b),                    # f2 not adjacent to f1
+        patched(with_f2, chiv=0),                               # f2 drawn from no neighbour
+    ]
+    if without_f2.size:
+        i = int(without_f2[0])
+        cases += [patched(i, chiv=3), patched(i, flv=1)]       # chi or closed without f2
+    for bad in cases:
+        with pytest.raises(tc.TcError) as e:
+            tc.tc_load(bad, 4096)
+        assert e.value.code == tc.TC_ERR_INVAL
+    ok = tc.tc_load(blob, 4096)
+    tc.tc_destroy(ok)

@@ -106,3 +106,76 @@ def test_every_sort_tuning_gives_identical_states(vertex_bits):
             assert_state_equal(tc.tc_get_state(ctx), exp, f"tuning {cand}")
         finally:
             tc.tc_destroy(ctx)
+
+
+def _packed_directory_stream(seed=0):
+    """Batch 0 puts 300 arcs into the group of vertices 60..71 (a hub), exactly
+    255 into 84..95 and 256 into 96..107 (the packed offsets keep up to 255
+    arcs per group of 12 ids), and arcs on every id of the last, partial group
+    4092..4095 of the 2^12 ids; later batches are random edges over all ids."""
+    rng = np.random.default_rng(seed)
+    n, w = 1 << 12, 4096
+    designed = set()
+
+    def others(k, avoid):
+        pool = np.setdiff1d(np.arange(120, 4092), avoid)
+        return rng.choice(pool, size=k, replace=False)
+
+    for x in others(300, []):
+        designed.add((63, int(x)))
+    for x in others(200, []):
+        designed.add((84, int(x)))
+    for x in others(55, []):
+        designed.add((95, int(x)))
+    for x in others(256, []):
+        designed.add((96, int(x)))
+    for a in range(4092, 4096):
+        for x in others(5, []):
+            designed.add((int(x), a))
+    designed.add((4092, 4095))
+    special = set(range(60, 72)) | set(range(84, 108)) | set(range(4092, 4096))
+    edges = set(designed)
+    batch0 = list(designed)
+    while len(batch0) < w:
+        u, v = sorted(int(t) for t in rng.integers(0, n, 2))
+        if u == v or (u, v) in edges or u in special or v in special:
+            continue
+        edges.add((u, v))
+        batch0.append((u, v))
+    rest = []
+    # triangles through the hubs: (hub, x) in batch 0, then (x, y) and (hub, y)
+    for hub in (63, 84, 96):
+        nb = np.array(sorted(b for a, b in designed if a == hub))
+        made = 0
+        while made < 100:
+            x, y = int(rng.choice(nb)), int(rng.integers(120, 4092))
+            e1, e2 = (min(x, y), max(x, y)), (hub, y)
+            if x == y or e1 in edges or e2 in edges:
+                continue
+            edges.update((e1, e2))
+            rest += [e1, e2]
+            made += 1
+    while len(rest) < 3 * w:
+        u, v = sorted(int(t) for t in rng.integers(0, n, 2))
+        if u == v or (u, v) in edges:
+            continue
+        edges.add((u, v))
+        rest.append((u, v))
+    rng.shuffle(batch0)
+    rng.shuffle(rest)
+    pairs = np.array(batch0 + rest, dtype=np.uint64)
+    keys = (pairs[:, 0] << np.uint64(32)) | pairs[:, 1]
+    # the groups the test is about have the arc counts it claims
+    ids = np.concatenate([pairs[:w, 0], pairs[:w, 1]]).astype(np.int64)
+    per_group = np.bincount(ids // 12, minlength=(n + 11) // 12)
+    assert per_group[5] == 300 and per_group[7] == 255 and per_group[8] == 256
+    assert np.all(np.bincount(ids, minlength=n)[4092:4096] > 0)
+    return keys, w
+
+
+def test_packed_arc_offsets_wide_and_boundary_groups():
+    """Dense arc offsets (2^12 ids <= 8w): the packed entries, the groups too
+    wide to pack and the partial last group all give the oracle's states."""
+    keys, w = _packed_directory_stream()
+    _run_pair(keys, 4096, [w] * 4, seed=31, vertex_bits=12)
+    _run_pair(keys, 999, [w // 2] * 8, seed=32, vertex_bits=12)
