@@ -442,14 +442,17 @@ __device__ __forceinline__ void packed_segment(const uint4 *pdir, const u32 *off
 // Dense Step-3 bucket directory with the filter inside: one 8-byte entry per
 // hash bucket b (the top hb bits of h), {first index of the sorted Step-3
 // keys whose bucket is >= b, mask}, for b in [0, 2^hb] (entry 2^hb = {w, 0}).
-// Bucket b's keys are [entry b, entry b+1); the mask has bit
-// (h >> (27 - hb)) & 31 set for each of them, so that a closing pair whose
-// bit is clear has no edge in the batch and its lookup ends at that one load
-// (about four edges per bucket: a pair with no edge sees its bit set about
-// one time in eight).  Written whole every batch, like the arc offsets: a
-// tile owns the buckets (bucket of the key before it, bucket of its last
-// key]; when that span fits the shared arrays, run heads mark their bucket's
-// first index and every key ORs its bit into its bucket's mask (the last
+// Bucket b's keys are [entry b, entry b+1); the mask has two bits set for
+// each of them, bit (h >> (27 - hb)) & 31 (the five hash bits below the
+// bucket's) and bit (h * 0x9E3779B1) >> 27 (a multiplicative rehash, so the
+// pair stays independent-ish where hb leaves few bits below the bucket), so
+// that a closing pair missing either of its bits has no edge in the batch
+// and its lookup ends at that one load (about four edges per bucket: a pair
+// with no edge passes about one time in twenty, against one in eight with a
+// single bit).  Written whole every batch, like the arc offsets: a tile owns
+// the buckets (bucket of the key before it, bucket of its last key]; when
+// that span fits the shared arrays, run heads mark their bucket's first
+// index and every key ORs its bits into its bucket's mask (the last
 // owned bucket's keys past the tile are read from global memory), a suffix
 // minimum carries each first index down over empty buckets, and the span is
 // written with coalesced stores; a wider span is written head by head.  The
@@ -458,7 +461,9 @@ __device__ __forceinline__ void packed_segment(const uint4 *pdir, const u32 *off
 // follows (almost always empty), where the edges with the whole hash are
 // compared.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ u32 filter_bit(u64 h, u32 hb) { return 1u << ((h >> (27 - hb)) & 31); }
+__device__ __forceinline__ u32 filter_bits(u64 h, u32 hb) {
+    return (1u << ((h >> (27 - hb)) & 31)) | (1u << (((u32)h * 0x9E3779B1u) >> 27));
+}
 
 constexpr u32 kBucketSpan = 3072;  // tiles average 512 buckets (4 keys per bucket)
 
@@ -530,7 +535,7 @@ static __global__ void __launch_bounds__(kIdxThreads) step3_index_kernel(
             const bool head = (k == 0) || (st[i] >> sh) != b;
             if (fits) {
                 if (head) soff[b - blo] = (u32)k;
-                atomicOr(&smask[b - blo], filter_bit(key >> s.bw, s.hb));
+                atomicOr(&smask[b - blo], filter_bits(key >> s.bw, s.hb));
             } else if (head) {
                 // wide span: this head writes its bucket (mask from its keys)
                 // and the empty buckets below it
@@ -538,7 +543,7 @@ static __global__ void __launch_bounds__(kIdxThreads) step3_index_kernel(
                 for (u64 q = k; q < n; ++q) {
                     const u64 kq = (q - t0 < (u64)kIdxTile + 1) ? st[1 + (q - t0)] : __ldg(K + q);
                     if ((kq >> sh) != b) break;
-                    mask |= filter_bit(kq >> s.bw, s.hb);
+                    mask |= filter_bits(kq >> s.bw, s.hb);
                 }
                 const u64 bprev = k ? (st[i] >> sh) + 1 : 0;
                 for (u64 q = bprev; q < b; ++q) bdir[q] = make_uint2((u32)k, 0u);
@@ -553,7 +558,7 @@ static __global__ void __launch_bounds__(kIdxThreads) step3_index_kernel(
                 for (u64 q = t0 + cnt; q < n; ++q) {
                     const u64 kq = __ldg(K + q);
                     if ((kq >> sh) != b_last) break;
-                    mask |= filter_bit(kq >> s.bw, s.hb);
+                    mask |= filter_bits(kq >> s.bw, s.hb);
                 }
                 smask[span - 1] |= mask;
             }
@@ -750,9 +755,11 @@ __device__ __forceinline__ void sweep_one(const SweepArgs &a, u64 i, u64 m, u32 
         const u64 h = edge_hash(g, s.hkey);
         const u64 hp = h >> (32 - s.hs);  // the sorted bits
         const u64 bucket = h >> (32 - s.hb);
-        // no edge of the batch has the pair's filter bit: nothing to look up
+        // no edge of the batch has both of the pair's filter bits: nothing to
+        // look up
         const uint2 e0 = __ldg(a.bdir + bucket);
-        if (e0.y & filter_bit(h, s.hb)) {
+        const u32 fb = filter_bits(h, s.hb);
+        if ((e0.y & fb) == fb) {
             hi = min(__ldg(a.bdir + bucket + 1).x, s.w);
             lo = min(e0.x, hi);
         } else {
