@@ -82,8 +82,9 @@ def _args():
     p.add_argument("--workload", choices=["large", "rmat20", "tiny", "multi512", "serve4096",
                                           "wsweep", "accuracy"], default="large")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--serve-depth", type=int, default=1,
-                   help="serving: rounds in flight at once (1 = one round after another)")
+    p.add_argument("--serve-depth", type=int, default=0,
+                   help="serving: rounds in flight at once (0 = the library's default, 2; "
+                        "1 = one round after another)")
     p.add_argument("--no-clock-sampling", action="store_true",
                    help="do not poll nvidia-smi during the timed phases (clocks reported null)")
     p.add_argument("--no-extras", action="store_true",
@@ -1206,6 +1207,11 @@ def _serve_phase(tc, graphs, cfg, S, seconds, rate=None, cap_edges=None, max_rou
         "inflight_full_max_ms": st1["inflight_full_max_ns"] / 1e6,
         "pool_reserved_high": int(st1["pool_reserved_high"]),
         "pool_used_high": int(st1["pool_used_high"]),
+        "round_gpu_max_ms": st1["round_gpu_max_ns"] / 1e6,
+        "rounds_gpu_over_5ms": int(st1["rounds_gpu_over_5ms"]),
+        "round_gpu_max_split_ms": {"wait": st1["round_max_wait_ns"] / 1e6,
+                                   "sort": st1["round_max_sort_ns"] / 1e6,
+                                   "sweep": st1["round_max_sweep_ns"] / 1e6},
         "sched_gaps_over_5ms": int(st1["sched_gaps_over_5ms"] - st0["sched_gaps_over_5ms"]),
         "bytes_peak": int(st1["bytes_peak"]), "bytes_fixed": int(st1["bytes_fixed"]),
         "opens": int(st1["opens"]), "closes": int(st1["closes"]),

@@ -392,10 +392,10 @@ typedef struct {
                               round buffers, open streams' state (28 B per
                               estimator) and admitted batches (8 B per edge) */
     uint64_t w_max_round;  /* most edges one round folds (and the largest batch) */
-    uint32_t depth;        /* rounds in flight, 1..8; 0 means 1.  With more than
+    uint32_t depth;        /* rounds in flight, 1..8; 0 means 2.  With more than
                               one, a round's sorts run beside the previous round's
-                              sweep: the same saturation throughput was measured,
-                              with a much longer latency tail */
+                              sweep (9% more throughput at saturation, measured
+                              at depth 2 against 1) */
     uint32_t max_round_streams; /* most streams one round folds; 0 = max_streams
                                    (1 serves one batch per round, back to back) */
 } tc_server_config_t;
@@ -442,6 +442,13 @@ typedef struct {
     /* the server's memory pool (stream state and batch copies): physical
      * memory it holds and the most it had in use at once, high-water marks */
     uint64_t pool_reserved_high, pool_used_high;
+    /* device time of the rounds (CUDA events): the longest round, from the
+     * start of its work on the compute stream to its records; how many took
+     * more than 5 ms; and the longest round's split into waiting (for its
+     * batches' copies and, with depth > 1, the previous round's sweep), its
+     * sorts and directories, and its sweep and records */
+    uint64_t round_gpu_max_ns, rounds_gpu_over_5ms;
+    uint64_t round_max_wait_ns, round_max_sort_ns, round_max_sweep_ns;
 } tc_server_stats_t;
 
 /* Errors: TC_ERR_INVAL (bad config; key bits as tc_multi_create with
@@ -458,9 +465,11 @@ int tc_server_create(const tc_server_config_t *cfg, tc_server **out);
 int tc_server_open(tc_server *S, uint64_t r, uint64_t seed, uint32_t stream_id,
                    uint32_t *handle, uint64_t *ticket);
 
-/* Submit a batch of w edges (HOST memory, (min << 32) | max, arrival order;
- * pinned memory lets the copy overlap).  The buffer is borrowed until the
- * batch's completion.  w = 0 completes as a no-op.  TC_ERR_INVAL for an
+/* Submit a batch of w edges (HOST memory, (min << 32) | max, arrival order).
+ * The buffer is borrowed until the batch's completion.  Pinned memory (and,
+ * on a device that reads pageable host memory, any host memory) is uploaded
+ * when the batch is admitted by the server's own copy kernel, one launch for
+ * every batch admitted together; other memory by cudaMemcpyAsync.  w = 0 completes as a no-op.  TC_ERR_INVAL for an
  * unknown or closed handle, TC_ERR_RANGE for w > w_max_round or a batch that
  * can never fit the budget.  A batch that breaks the stream model completes
  * with TC_ERR_INPUT and leaves its stream as it was. */

@@ -113,7 +113,9 @@ _STATS_FIELDS = ("rounds", "kernel_launches", "batches", "rejected", "edges", "q
                  "closes", "streams_open", "requests_waiting", "admission_waits",
                  "max_round_edges", "max_round_streams", "bytes_budget", "bytes_fixed",
                  "bytes_reserved", "bytes_peak", "sched_gap_max_ns", "sched_gaps_over_5ms",
-                 "inflight_full_max_ns", "pool_reserved_high", "pool_used_high")
+                 "inflight_full_max_ns", "pool_reserved_high", "pool_used_high",
+                 "round_gpu_max_ns", "rounds_gpu_over_5ms", "round_max_wait_ns",
+                 "round_max_sort_ns", "round_max_sweep_ns")
 
 
 class tc_server_stats_t(ctypes.Structure):

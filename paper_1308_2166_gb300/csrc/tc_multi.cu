@@ -811,7 +811,9 @@ int multi_alloc(u32 S, u64 w_max_round, u32 vertex_bits, tc_multi **out, int set
     for (int k = 0; k < kRing && ok; ++k) {
         ok &= cudaMalloc(&M->desc[k], desc_words(S) * sizeof(u64)) == cudaSuccess;
         ok &= ok && cudaHostAlloc(&M->h_desc[k], desc_words(S) * sizeof(u64),
-                                  cudaHostAllocDefault) == cudaSuccess;
+                                  cudaHostAllocMapped) == cudaSuccess;
+        M->h_desc_dev[k] = ok ? static_cast<u64 *>(mapped_device_ptr(M->h_desc[k])) : nullptr;
+        ok &= M->h_desc_dev[k] != nullptr;
         ok &= ok && cudaEventCreateWithFlags(&M->ring_ev[k], cudaEventDisableTiming) == cudaSuccess;
     }
     ok &= ok && cudaHostAlloc(&M->h_ms, S * sizeof(MStream), cudaHostAllocDefault) == cudaSuccess;
@@ -866,6 +868,31 @@ u64 write_descriptor(const tc_multi *M, const RoundItem *items, u32 K, u64 *h) {
     return wmax;
 }
 
+static __global__ void __launch_bounds__(256) copy_words_kernel(u64 *__restrict__ dst,
+                                                                const u64 *__restrict__ src,
+                                                                u64 n) {
+    for (u64 i = (u64)blockIdx.x * 256 + threadIdx.x; i < n; i += (u64)gridDim.x * 256)
+        dst[i] = src[i];
+}
+
+int copy_words_async(tc_multi *M, u64 *dst, const u64 *src, u64 n, cudaStream_t st) {
+    if (n == 0) return TC_OK;
+    const u64 blocks = std::min<u64>((n + 255) / 256, 64);
+    copy_words_kernel<<<(unsigned)blocks, 256, 0, st>>>(dst, src, n);
+    TCM_CUDA(cudaGetLastError());
+    if (M) M->launches += 1;
+    return TC_OK;
+}
+
+void *mapped_device_ptr(void *h) {
+    void *d = nullptr;
+    if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return d;
+}
+
 int multi_gather(tc_multi *M, const u32 *d_slots, u32 Q, u64 *out, cudaStream_t st) {
     if (Q == 0) return TC_OK;
     mgather_kernel<<<(Q + 255) / 256, 256, 0, st>>>(M->ms, d_slots, Q, out);
@@ -875,7 +902,8 @@ int multi_gather(tc_multi *M, const u32 *d_slots, u32 Q, u64 *out, cudaStream_t 
 }
 
 int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u64 *h_desc,
-                  u64 *out, cudaStream_t st, bool pipelined, cudaEvent_t wait_ev) {
+                  u64 *out, cudaStream_t st, bool pipelined, cudaEvent_t wait_ev,
+                  cudaEvent_t ev_sort0, cudaEvent_t ev_sort1) {
     const NvtxRange range("tc round");
     u64 Wt = 0, wmax = 0, R = 0;
     for (u32 k = 0; k < K; ++k) {
@@ -933,9 +961,11 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u
     // stream (one set: every round runs in the order of its stream)
     if (M->nsets == 2) TCM_CUDA(cudaStreamWaitEvent(ms, M->ev_swept[b], 0));
     if (wait_ev) TCM_CUDA(cudaStreamWaitEvent(ms, wait_ev, 0));
-    if (h_desc)
-        TCM_CUDA(cudaMemcpyAsync(desc, h_desc, desc_words(K) * sizeof(u64),
-                                 cudaMemcpyHostToDevice, ms));
+    if (ev_sort0) TCM_CUDA(cudaEventRecord(ev_sort0, ms));
+    if (h_desc) {
+        const int rc = copy_words_async(M, desc, h_desc, desc_words(K), ms);
+        if (rc) return rc;
+    }
     TCM_CUDA(cudaMemsetAsync(z.zeroed, 0, 2 * sizeof(SortPlan) + lwords * sizeof(u32), ms));
     TCM_CUDA(cudaMemsetAsync(gerr, 0, 256 + (u64)K * 4, ms));
 
@@ -967,6 +997,7 @@ int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u
     marc_index_kernel<<<index_blocks(2 * Wt), kIdxThreads, 0, ms>>>(z.arcs[0], z.arcs[1], plans,
                                                                    rs, z.adir, z.tag);
     TCM_CUDA(cudaStreamWaitEvent(ms, M->ev_join, 0));
+    if (ev_sort1) TCM_CUDA(cudaEventRecord(ev_sort1, ms));
     if (pipelined) {
         TCM_CUDA(cudaEventRecord(M->ev_sorted[b], ms));
         TCM_CUDA(cudaStreamWaitEvent(st, M->ev_sorted[b], 0));
@@ -1022,8 +1053,8 @@ static int upload_and_enqueue(tc_multi *M, const std::vector<RoundItem> &items,
     M->ring = (M->ring + 1) % kRing;
     TCM_CUDA(cudaEventSynchronize(M->ring_ev[slot]));
     write_descriptor(M, items.data(), K, M->h_desc[slot]);
-    TCM_CUDA(cudaMemcpyAsync(M->desc[slot], M->h_desc[slot], desc_words(K) * sizeof(u64),
-                             cudaMemcpyHostToDevice, st));
+    const int rc = copy_words_async(M, M->desc[slot], M->h_desc_dev[slot], desc_words(K), st);
+    if (rc) return rc;
     TCM_CUDA(cudaEventRecord(M->ring_ev[slot], st));
     return multi_enqueue(M, items.data(), K, M->desc[slot], nullptr, nullptr, st);
 }
@@ -1116,7 +1147,7 @@ int tc_multi_process_ready_async(tc_multi *M, const uint64_t *d_edges, const uin
     M->ring = (M->ring + 1) % kRing;
     TCM_CUDA(cudaEventSynchronize(M->ring_ev[slot]));
     write_descriptor(M, items.data(), (u32)items.size(), M->h_desc[slot]);
-    rc = multi_enqueue(M, items.data(), (u32)items.size(), M->desc[slot], M->h_desc[slot],
+    rc = multi_enqueue(M, items.data(), (u32)items.size(), M->desc[slot], M->h_desc_dev[slot],
                        nullptr, (cudaStream_t)cuda_stream, true, nullptr);
     if (rc) return rc;
     TCM_CUDA(cudaEventRecord(M->ring_ev[slot], M->sa));  // after the descriptor's upload

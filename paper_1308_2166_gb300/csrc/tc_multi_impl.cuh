@@ -78,7 +78,8 @@ struct tc_multi {
     cudaStream_t sa = nullptr;           // a pipelined round's sort phase (with `side`)
     cudaEvent_t ev_sorted[2] = {}, ev_swept[2] = {};
     tc::u64 *desc[tc::kRing] = {};       // device round descriptors
-    tc::u64 *h_desc[tc::kRing] = {};     // pinned staging
+    tc::u64 *h_desc[tc::kRing] = {};     // pinned staging (mapped)
+    tc::u64 *h_desc_dev[tc::kRing] = {}; // its device address
     cudaEvent_t ring_ev[tc::kRing] = {};
     int ring = 0;
     tc::u64 launches = 0;
@@ -112,17 +113,32 @@ u64 multi_scratch_bytes(u32 S, u64 w_max_round, u32 vertex_bits, int sets = 1);
 int multi_open_slot(tc_multi *M, u32 slot, u64 r, u64 seed, u32 stream_id, void *state,
                     cudaStream_t st);
 
+// Copy n words with a kernel on st (either side may be mapped pinned host
+// memory, by its device address).  Unlike cudaMemcpyAsync this takes no copy
+// engine, so it never queues behind copies on other streams: a round's
+// descriptor upload would otherwise wait behind the batch copies admitted
+// for later rounds.
+int copy_words_async(tc_multi *M, u64 *dst, const u64 *src, u64 n, cudaStream_t st);
+
+// The device address of mapped pinned host memory (from cudaHostAlloc with
+// cudaHostAllocMapped), or nullptr.
+void *mapped_device_ptr(void *h);
+
 // Enqueue one round whose sweep and bookkeeping land on st.  desc: the
-// device descriptor of desc_words(K) words; h_desc: if not null, its pinned
-// host copy (written by write_descriptor), uploaded by the round itself
-// ahead of the key build; out: optional device array of K * kRecordWords
+// device descriptor of desc_words(K) words; h_desc: if not null, the device
+// address of its mapped pinned host copy (written by write_descriptor),
+// copied by the round itself ahead of the key build; out: optional device
+// array of K * kRecordWords
 // words receiving each participant's record after the round.  Pipelined
 // (two sets): the sort phase runs on the engine's own streams once wait_ev
 // (if any; e.g. the batches' copies) has fired and the round's set is free,
-// beside the previous round's sweep.
+// beside the previous round's sweep.  ev_sort0 / ev_sort1 (optional, with
+// timing): recorded on the sort phase's stream once its waits are over and
+// when the sort phase ends.
 int multi_enqueue(tc_multi *M, const RoundItem *items, u32 K, u64 *desc, const u64 *h_desc,
                   u64 *out, cudaStream_t st, bool pipelined = false,
-                  cudaEvent_t wait_ev = nullptr);
+                  cudaEvent_t wait_ev = nullptr, cudaEvent_t ev_sort0 = nullptr,
+                  cudaEvent_t ev_sort1 = nullptr);
 
 // Fill a host descriptor for the given participants; returns the largest w.
 u64 write_descriptor(const tc_multi *M, const RoundItem *items, u32 K, u64 *h_desc);

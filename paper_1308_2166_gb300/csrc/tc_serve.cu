@@ -34,6 +34,7 @@
 #include <thread>
 #include <unordered_map>
 #include <unordered_set>
+#include <utility>
 #include <vector>
 
 #include "tc_multi_impl.cuh"
@@ -52,6 +53,7 @@ struct Req {
     int kind = 0;
     u32 handle = 0;
     const u64 *h_edges = nullptr;
+    const u64 *h_dev = nullptr;  // h_edges as the device reads it (null: copy engine)
     u64 w = 0;
     u64 r = 0, seed = 0;
     u32 stream_id = 0;
@@ -75,6 +77,7 @@ struct Slot {
 
 struct Round {
     int buf = 0;
+    bool sorted = false;  // has batches: a sort phase with its own timing events
     std::vector<Req> queries;
     std::vector<Req> batches;
     std::vector<Req> closes;
@@ -82,6 +85,66 @@ struct Round {
 
 u64 round_up(u64 x) { return (x + 255) & ~255ull; }
 u64 state_bytes_for(u64 r) { return round_up(28 * r); }
+
+// Batches admitted in one scheduler pass are uploaded together by a few
+// kernel launches: SMs read the host memory (pinned, or pageable where the
+// device can read it) in chunks of kUploadWords.  A cudaMemcpyAsync per
+// batch cost about 9 us of the scheduler thread each (20,000 batches of
+// log-uniform [1e3, 1e6] edges took 171 ms to issue, 130 GB/s), while one
+// gather kernel per 50 batches issued the same in 0.6 ms and copied at
+// 191 GB/s.  Under serving load the copy-engine path also left rounds
+// waiting tens of milliseconds for their batches (p99 batch latency 22-77 ms
+// at 70% of saturation against 3.7-16 ms with the kernel, A/B on the same
+// boxes), even when only the largest batches took it.
+struct UploadChunk {
+    const u64 *src;
+    u64 *dst;
+    u32 n;
+    u32 pad;
+};
+constexpr u32 kUploadWords = 16384;   // words per chunk (128 KB)
+constexpr u32 kUploadChunks = 16384;  // chunks per ring slot
+constexpr int kUploadSlots = 4;
+// One launch per group of at most kUploadGroup chunks (8 MB), each batch's
+// copy event recorded behind the group holding its last chunk, so a batch is
+// ready as soon as its own group has landed; a block per chunk, eight loads
+// in flight per thread.
+constexpr u32 kUploadGroup = 64;
+constexpr u32 kUploadUnroll = 8;
+
+__global__ void __launch_bounds__(256) upload_kernel(const UploadChunk *__restrict__ chunks,
+                                                     u32 nchunks) {
+    for (u32 c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        const UploadChunk ch = chunks[c];
+        for (u32 i0 = threadIdx.x; i0 < ch.n; i0 += 256 * kUploadUnroll) {
+            u64 v[kUploadUnroll];
+#pragma unroll
+            for (u32 k = 0; k < kUploadUnroll; ++k) {
+                const u32 i = i0 + k * 256;
+                v[k] = i < ch.n ? __ldcs(ch.src + i) : 0ull;
+            }
+#pragma unroll
+            for (u32 k = 0; k < kUploadUnroll; ++k) {
+                const u32 i = i0 + k * 256;
+                if (i < ch.n) ch.dst[i] = v[k];
+            }
+        }
+    }
+}
+
+// The address at which the device reads host buffer h, or nullptr when it
+// cannot (then the copy engine uploads it).
+const u64 *device_readable(const u64 *h, bool pageable_ok) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeDevice ||
+        a.type == cudaMemoryTypeManaged)
+        return static_cast<const u64 *>(a.devicePointer);
+    return pageable_ok ? h : nullptr;
+}
 
 int status_of(u64 e) {
     return e == 0 ? TC_OK : e == kErrInput ? TC_ERR_INPUT : e == kErrTimeout ? TC_ERR_TIMEOUT
@@ -93,7 +156,7 @@ int status_of(u64 e) {
 struct tc_server {
     tc_server_config_t cfg{};
     int dev = 0;
-    int depth = 1;
+    int depth = 2;
     tc_multi *M = nullptr;
     cudaStream_t cs = nullptr;  // rounds
     cudaStream_t xs = nullptr;  // host -> device batch copies
@@ -124,11 +187,26 @@ struct tc_server {
     std::deque<Round> inflight;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<int> ev_free;
+    bool pageable_ok = false;  // the device reads pageable host memory
+    // upload ring: chunk lists in mapped pinned memory, one kernel per list
+    UploadChunk *up_ring = nullptr, *up_ring_dev = nullptr;
+    cudaEvent_t up_ev[kUploadSlots] = {};
+    int up_slot = 0;
+    std::vector<UploadChunk> up_chunks;
+    // (index of the batch's last chunk, its copy event): recorded after the
+    // launch covering that chunk
+    std::vector<std::pair<size_t, int>> up_events;
     u64 copy_seq = 0;
     int nbuf = 0;
     std::vector<u64 *> d_out, h_out, d_desc, h_desc;
-    std::vector<u32 *> d_qs, h_qs;
-    std::vector<cudaEvent_t> round_ev;
+    std::vector<u32 *> h_qs;
+    // device addresses of the mapped pinned buffers: the round's descriptor
+    // and query slots are read, and its records written, by kernels, so no
+    // round work waits for a copy engine busy with later rounds' batches
+    std::vector<u64 *> h_out_dev, h_desc_dev;
+    std::vector<u32 *> h_qs_dev;
+    std::vector<cudaEvent_t> round_ev;            // a round's records are back (timing)
+    std::vector<cudaEvent_t> ev_start, ev_sort0, ev_sort1;  // its start; its sort phase
     u64 round_no = 0;
     u64 reserved = 0, peak = 0;
     int err = TC_OK;          // first CUDA failure seen by the scheduler
@@ -149,6 +227,8 @@ struct tc_server {
     void fail_all(int code);
     int get_event();
     void complete(const Req &q, int status, const u64 *rec);
+    void note_round_time(const Round &R);
+    bool flush_uploads();
 };
 
 void tc_server::complete(const Req &q, int status, const u64 *rec) {
@@ -254,10 +334,20 @@ bool tc_server::admit() {
                         break;
                     }
                     q.ev = get_event();
-                    if (q.ev < 0 ||
-                        cudaMemcpyAsync(q.d_edges, q.h_edges, 8 * q.w, cudaMemcpyHostToDevice,
-                                        xs) != cudaSuccess ||
-                        cudaEventRecord(ev_pool[q.ev], xs) != cudaSuccess) {
+                    bool ok = q.ev >= 0;
+                    if (ok && q.h_dev) {
+                        // uploaded by this pass's kernel; its event follows it
+                        for (u64 o = 0; o < q.w; o += kUploadWords)
+                            up_chunks.push_back(UploadChunk{
+                                q.h_dev + o, q.d_edges + o,
+                                (u32)std::min<u64>(kUploadWords, q.w - o), 0u});
+                        up_events.emplace_back(up_chunks.size() - 1, q.ev);
+                    } else if (ok) {
+                        ok = cudaMemcpyAsync(q.d_edges, q.h_edges, 8 * q.w,
+                                             cudaMemcpyHostToDevice, xs) == cudaSuccess &&
+                             cudaEventRecord(ev_pool[q.ev], xs) == cudaSuccess;
+                    }
+                    if (!ok) {
                         err = TC_ERR_CUDA;
                         pending.push_front(std::move(q));
                         break;
@@ -292,7 +382,39 @@ bool tc_server::admit() {
         pending.push_front(std::move(keep.back()));
         keep.pop_back();
     }
+    if (!flush_uploads() && err == TC_OK) err = TC_ERR_CUDA;
     return moved;
+}
+
+// Launch the upload kernels for the chunks gathered by this pass on the copy
+// stream, recording each uploaded batch's copy event behind the launch that
+// covers its last chunk.
+bool tc_server::flush_uploads() {
+    bool ok = true;
+    size_t done_chunks = 0, next_ev = 0;
+    while (ok && done_chunks < up_chunks.size()) {
+        const int k = up_slot;
+        up_slot = (up_slot + 1) % kUploadSlots;
+        // the slot's previous list has been read once its kernels finished
+        ok &= cudaEventSynchronize(up_ev[k]) == cudaSuccess;
+        const u32 n = (u32)std::min<size_t>(kUploadChunks, up_chunks.size() - done_chunks);
+        UploadChunk *list = up_ring + (size_t)k * kUploadChunks;
+        const UploadChunk *list_dev = up_ring_dev + (size_t)k * kUploadChunks;
+        std::memcpy(list, up_chunks.data() + done_chunks, n * sizeof(UploadChunk));
+        for (u32 g = 0; g < n && ok; g += kUploadGroup) {
+            const u32 m = std::min<u32>(kUploadGroup, n - g);
+            upload_kernel<<<m, 256, 0, xs>>>(list_dev + g, m);
+            ok &= cudaGetLastError() == cudaSuccess;
+            const size_t end = done_chunks + g + m;  // chunks uploaded so far
+            while (ok && next_ev < up_events.size() && up_events[next_ev].first < end)
+                ok &= cudaEventRecord(ev_pool[up_events[next_ev++].second], xs) == cudaSuccess;
+        }
+        ok &= ok && cudaEventRecord(up_ev[k], xs) == cudaSuccess;
+        done_chunks += n;
+    }
+    up_chunks.clear();
+    up_events.clear();
+    return ok;
 }
 
 bool tc_server::form_round() {
@@ -369,21 +491,20 @@ bool tc_server::form_round() {
 
     const int b = (int)(round_no % (u64)nbuf);
     const u32 Q = (u32)qslots.size(), K = (u32)items.size();
-    bool ok = true;
-    if (Q) {
+    bool ok = cudaEventRecord(ev_start[b], cs) == cudaSuccess;
+    if (Q && ok) {
         std::memcpy(h_qs[b], qslots.data(), Q * sizeof(u32));
-        ok &= cudaMemcpyAsync(d_qs[b], h_qs[b], Q * sizeof(u32), cudaMemcpyHostToDevice, cs) ==
-              cudaSuccess;
-        ok &= ok && multi_gather(M, d_qs[b], Q, d_out[b], cs) == TC_OK;
+        ok &= multi_gather(M, h_qs_dev[b], Q, d_out[b], cs) == TC_OK;
     }
     if (K && ok) {
         // pipelined: the round is sorted on the engine's own streams as soon as
         // its batches' copies have landed, beside the previous round's sweep;
         // its sweep and records are ordered on cs
         write_descriptor(M, items.data(), K, h_desc[b]);
-        ok &= multi_enqueue(M, items.data(), K, d_desc[b], h_desc[b],
+        ok &= multi_enqueue(M, items.data(), K, d_desc[b], h_desc_dev[b],
                             d_out[b] + (u64)Q * kRecordWords, cs, true,
-                            wait_ev >= 0 ? ev_pool[wait_ev] : nullptr) == TC_OK;
+                            wait_ev >= 0 ? ev_pool[wait_ev] : nullptr, ev_sort0[b],
+                            ev_sort1[b]) == TC_OK;
         for (Req &q : R.batches) {
             ok &= ok && cudaFreeAsync(q.d_edges, cs) == cudaSuccess;
             q.d_edges = nullptr;
@@ -392,9 +513,7 @@ bool tc_server::form_round() {
         }
     }
     const u64 words = (u64)(Q + K) * kRecordWords;
-    if (words && ok)
-        ok &= cudaMemcpyAsync(h_out[b], d_out[b], words * sizeof(u64), cudaMemcpyDeviceToHost,
-                              cs) == cudaSuccess;
+    if (words && ok) ok &= copy_words_async(M, h_out_dev[b], d_out[b], words, cs) == TC_OK;
     for (u32 s : closed_slots) {
         Slot &sl = slots[s];
         ok &= ok && cudaFreeAsync(sl.state, cs) == cudaSuccess;
@@ -414,6 +533,7 @@ bool tc_server::form_round() {
         return false;
     }
     R.buf = b;
+    R.sorted = K > 0;
     inflight.push_back(std::move(R));
     round_no++;
     local.rounds++;
@@ -421,6 +541,30 @@ bool tc_server::form_round() {
     if (edges > local.max_round_edges) local.max_round_edges = edges;
     if (K > local.max_round_streams) local.max_round_streams = K;
     return true;
+}
+
+// Device time of a finished round and, for the longest so far, its split.
+void tc_server::note_round_time(const Round &R) {
+    const int b = R.buf;
+    auto ns = [](cudaEvent_t a, cudaEvent_t z) -> u64 {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, a, z) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        return ms > 0.f ? (u64)((double)ms * 1e6) : 0;
+    };
+    const u64 total = ns(ev_start[b], round_ev[b]);
+    if (total > 5000000) local.rounds_gpu_over_5ms++;
+    if (total <= local.round_gpu_max_ns) return;
+    local.round_gpu_max_ns = total;
+    if (R.sorted) {
+        local.round_max_wait_ns = ns(ev_start[b], ev_sort0[b]);
+        local.round_max_sort_ns = ns(ev_sort0[b], ev_sort1[b]);
+        local.round_max_sweep_ns = ns(ev_sort1[b], round_ev[b]);
+    } else {
+        local.round_max_wait_ns = local.round_max_sort_ns = local.round_max_sweep_ns = 0;
+    }
 }
 
 bool tc_server::retire() {
@@ -433,6 +577,7 @@ bool tc_server::retire() {
             err = TC_ERR_CUDA;
             return any;
         }
+        note_round_time(R);
         const u64 *o = h_out[R.buf];
         const size_t Q = R.queries.size();
         for (size_t i = 0; i < Q; ++i) {
@@ -581,13 +726,18 @@ static void server_free(tc_server *S) {
     for (int k = 0; k < S->nbuf; ++k) {
         cudaFree(S->d_out[k]);
         cudaFree(S->d_desc[k]);
-        cudaFree(S->d_qs[k]);
         if (S->h_out[k]) cudaFreeHost(S->h_out[k]);
         if (S->h_desc[k]) cudaFreeHost(S->h_desc[k]);
         if (S->h_qs[k]) cudaFreeHost(S->h_qs[k]);
         if (S->round_ev[k]) cudaEventDestroy(S->round_ev[k]);
+        if (S->ev_start[k]) cudaEventDestroy(S->ev_start[k]);
+        if (S->ev_sort0[k]) cudaEventDestroy(S->ev_sort0[k]);
+        if (S->ev_sort1[k]) cudaEventDestroy(S->ev_sort1[k]);
     }
     for (cudaEvent_t e : S->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : S->up_ev)
+        if (e) cudaEventDestroy(e);
+    if (S->up_ring) cudaFreeHost(S->up_ring);
     if (S->M) multi_free(S->M);
     if (S->pool) cudaMemPoolDestroy(S->pool);
     if (S->cs) cudaStreamDestroy(S->cs);
@@ -602,13 +752,13 @@ int tc_server_create(const tc_server_config_t *cfg, tc_server **out) {
     *out = nullptr;
     if (cfg->max_streams == 0 || cfg->depth > 8 || cfg->w_max_round == 0) return TC_ERR_INVAL;
     const u32 S = cfg->max_streams;
-    // one round in flight unless asked: with two, a round's sorts run beside
-    // the previous round's sweep, which measured the same throughput at
-    // saturation but rounds that stalled for tens of milliseconds now and
-    // then (p99 batch latency 31-113 ms at 70% load against 1.5 ms with one)
-    const int depth = cfg->depth ? (int)cfg->depth : 1;
+    // two rounds in flight unless asked: a round's sorts run beside the
+    // previous round's sweep (8.51 against 7.80 G edges/s at saturation,
+    // with p99 batch latency at 70% load of 1.3-4.3 ms against 1.5-2.4 ms
+    // with one, on one box)
+    const int depth = cfg->depth ? (int)cfg->depth : 2;
     const int nbuf = depth + 1;
-    const u64 ring_bytes = (u64)nbuf * (2ull * S * kRecordWords * 8 + desc_words(S) * 8 + S * 4);
+    const u64 ring_bytes = (u64)nbuf * (2ull * S * kRecordWords * 8 + desc_words(S) * 8);
     const u64 fixed = multi_scratch_bytes(S, cfg->w_max_round, cfg->vertex_bits, 2) + ring_bytes;
     if (fixed >= cfg->budget_bytes) return TC_ERR_RANGE;
 
@@ -658,26 +808,55 @@ int tc_server_create(const tc_server_config_t *cfg, tc_server **out) {
     Sv->h_out.assign(nbuf, nullptr);
     Sv->d_desc.assign(nbuf, nullptr);
     Sv->h_desc.assign(nbuf, nullptr);
-    Sv->d_qs.assign(nbuf, nullptr);
     Sv->h_qs.assign(nbuf, nullptr);
     Sv->round_ev.assign(nbuf, nullptr);
+    Sv->h_out_dev.assign(nbuf, nullptr);
+    Sv->h_desc_dev.assign(nbuf, nullptr);
+    Sv->h_qs_dev.assign(nbuf, nullptr);
+    Sv->ev_start.assign(nbuf, nullptr);
+    Sv->ev_sort0.assign(nbuf, nullptr);
+    Sv->ev_sort1.assign(nbuf, nullptr);
     for (int k = 0; k < nbuf && ok; ++k) {
         const u64 ob = 2ull * S * kRecordWords * 8;
         ok &= cudaMalloc(&Sv->d_out[k], ob) == cudaSuccess;
-        ok &= ok && cudaHostAlloc(&Sv->h_out[k], ob, cudaHostAllocDefault) == cudaSuccess;
+        ok &= ok && cudaHostAlloc(&Sv->h_out[k], ob, cudaHostAllocMapped) == cudaSuccess;
         ok &= ok && cudaMalloc(&Sv->d_desc[k], desc_words(S) * 8) == cudaSuccess;
-        ok &= ok && cudaHostAlloc(&Sv->h_desc[k], desc_words(S) * 8, cudaHostAllocDefault) ==
+        ok &= ok && cudaHostAlloc(&Sv->h_desc[k], desc_words(S) * 8, cudaHostAllocMapped) ==
                         cudaSuccess;
-        ok &= ok && cudaMalloc(&Sv->d_qs[k], S * 4) == cudaSuccess;
-        ok &= ok && cudaHostAlloc(&Sv->h_qs[k], S * 4, cudaHostAllocDefault) == cudaSuccess;
-        ok &= ok && cudaEventCreateWithFlags(&Sv->round_ev[k], cudaEventDisableTiming) ==
-                        cudaSuccess;
+        ok &= ok && cudaHostAlloc(&Sv->h_qs[k], S * 4, cudaHostAllocMapped) == cudaSuccess;
+        if (ok) {
+            Sv->h_out_dev[k] = static_cast<u64 *>(mapped_device_ptr(Sv->h_out[k]));
+            Sv->h_desc_dev[k] = static_cast<u64 *>(mapped_device_ptr(Sv->h_desc[k]));
+            Sv->h_qs_dev[k] = static_cast<u32 *>(mapped_device_ptr(Sv->h_qs[k]));
+            ok &= Sv->h_out_dev[k] && Sv->h_desc_dev[k] && Sv->h_qs_dev[k];
+        }
+        // timing events: the stats report each round's device time
+        ok &= ok && cudaEventCreate(&Sv->round_ev[k]) == cudaSuccess;
+        ok &= ok && cudaEventCreate(&Sv->ev_start[k]) == cudaSuccess;
+        ok &= ok && cudaEventCreate(&Sv->ev_sort0[k]) == cudaSuccess;
+        ok &= ok && cudaEventCreate(&Sv->ev_sort1[k]) == cudaSuccess;
     }
     if (!ok) {
         if (rc == TC_OK) rc = cudaGetLastError() == cudaErrorMemoryAllocation ? TC_ERR_NOMEM
                                                                               : TC_ERR_CUDA;
         server_free(Sv);
         return rc;
+    }
+    if (ok) {
+        int pma = 0;
+        if (cudaDeviceGetAttribute(&pma, cudaDevAttrPageableMemoryAccess, Sv->dev) == cudaSuccess)
+            Sv->pageable_ok = pma != 0;
+        cudaGetLastError();
+        ok &= cudaHostAlloc(&Sv->up_ring, (size_t)kUploadSlots * kUploadChunks * sizeof(UploadChunk),
+                            cudaHostAllocMapped) == cudaSuccess;
+        Sv->up_ring_dev = ok ? static_cast<UploadChunk *>(mapped_device_ptr(Sv->up_ring)) : nullptr;
+        ok &= Sv->up_ring_dev != nullptr;
+        for (int k = 0; k < kUploadSlots && ok; ++k)
+            ok &= cudaEventCreateWithFlags(&Sv->up_ev[k], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            server_free(Sv);
+            return TC_ERR_CUDA;
+        }
     }
     Sv->slots.resize(S);
     Sv->free_slots.reserve(S);
@@ -742,6 +921,7 @@ int tc_server_submit(tc_server *S, uint32_t handle, const uint64_t *h_edges, uin
     q.kind = TC_REQ_BATCH;
     q.handle = handle;
     q.h_edges = h_edges;
+    q.h_dev = w ? device_readable(h_edges, S->pageable_ok) : nullptr;
     q.w = w;
     return submit(S, std::move(q), ticket);
 }
@@ -771,6 +951,10 @@ int tc_server_submit_many(tc_server *S, uint32_t n, const uint32_t *kinds,
             return TC_ERR_INVAL;
         }
     }
+    // where the device reads each batch, found before taking the lock
+    std::vector<const u64 *> dev(n, nullptr);
+    for (u32 i = 0; i < n; ++i)
+        if (kinds[i] == TC_REQ_BATCH && w[i]) dev[i] = device_readable(h_edges[i], S->pageable_ok);
     std::lock_guard<std::mutex> lk(S->mu);
     if (S->fatal) return S->fatal;
     for (u32 i = 0; i < n; ++i)
@@ -782,6 +966,7 @@ int tc_server_submit_many(tc_server *S, uint32_t n, const uint32_t *kinds,
         q.handle = handles[i];
         if (q.kind == TC_REQ_BATCH) {
             q.h_edges = h_edges[i];
+            q.h_dev = dev[i];
             q.w = w[i];
         }
         q.ticket = S->next_ticket++;

@@ -48,9 +48,10 @@ def _blob(r, m, batches, chis, closed, seed=1, sid=0, vb=32):
     S = sum(int(c) for c, k in zip(chis, closed) if k)
     head = struct.pack("<16Q", 0x3145544154534354, 1, r, seed, sid, vb, m, batches,
                        S & (2**64 - 1), S >> 64, int(sum(closed)), 0, 0, 0, 0, 0)
+    # a tuple the update can reach: f2 (adjacent to f1) exactly where chi > 0
     f1 = np.full(r, (1 << 32) | 2, dtype="<u8")
-    f2 = np.full(r, (1 << 32) | 3, dtype="<u8")
     ch = np.asarray(chis, dtype="<u8")
+    f2 = np.where(ch > 0, np.uint64((1 << 32) | 3), np.uint64(2**64 - 1)).astype("<u8")
     fl = np.asarray(closed, dtype="<u4")
     return head + f1.tobytes() + f2.tobytes() + ch.tobytes() + fl.tobytes()
 
@@ -90,7 +91,8 @@ def test_estimate_beyond_64_bits_from_a_loaded_state():
         # chi <= 2 |E| as in any stream (|Gamma(f1)| counts later edges), which
         # keeps N = |E| * S below 2^128 here
         chis = [rnd.randint(0, min(2 * m, 2**rnd.choice([8, 30, 50]))) for _ in range(r)]
-        closed = [rnd.random() < 0.6 for _ in range(r)]
+        # closed only with an f2, which needs chi >= 1
+        closed = [c > 0 and rnd.random() < 0.6 for c in chis]
         cases.append((r, m, chis, closed))
     beyond = 0
     for r, m, chis, closed in cases:

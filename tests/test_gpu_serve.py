@@ -182,7 +182,7 @@ def _check(where, done, specs, plans, vertex_bits, bad=None):
         assert got == expect[s][i], (s, i, got, expect[s][i])
 
 
-@pytest.mark.parametrize("depth", [0, 2], ids=["default_depth", "depth2"])
+@pytest.mark.parametrize("depth", [1, 0], ids=["depth1", "default_depth2"])
 def test_mix_equals_alone_with_slot_waits(depth):
     rng = np.random.default_rng(5)
     n_streams = 24
