@@ -93,7 +93,7 @@ u64 state_bytes_for(u64 r) { return round_up(28 * r); }
 // log-uniform [1e3, 1e6] edges took 171 ms to issue, 130 GB/s), while one
 // gather kernel per 50 batches issued the same in 0.6 ms and copied at
 // 191 GB/s.  Under serving load the copy-engine path also left rounds
-// waiting tens of milliseconds for their batches (p99 batch latency 22-77 ms
+// waiting tens of milliseconds for their batches (p99 batch latency 8-82 ms
 // at 70% of saturation against 3.7-16 ms with the kernel, A/B on the same
 // boxes), even when only the largest batches took it.
 struct UploadChunk {
