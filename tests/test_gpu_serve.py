@@ -294,3 +294,79 @@ def test_rejected_batch_and_errors():
     finally:
         srv.destroy()
     _check(where, done, specs, plans, 12, bad={1: (i_bad,)})
+
+
+def _alone_w(spec, plan, vertex_bits, w_max):
+    """_alone for batches of up to w_max edges."""
+    r, seed, sid = spec
+    ctx = tc.tc_create_ex(r, seed, sid, w_max, vertex_bits)
+    out = []
+    try:
+        for op in plan:
+            if op[0] == "b":
+                tc.tc_process_batch(ctx, to_device(op[1]))
+            e = tc.tc_estimate(ctx)
+            out.append((e["batches"], e["S"], e["n_closed"], e["m"], e["N"], e["tau_hat"]))
+    finally:
+        tc.tc_destroy(ctx)
+    return out
+
+
+def test_many_streams_through_fewer_slots():
+    """512 streams through 128 slots at the default depth, batches of up to
+    20,000 edges submitted in chunks: every request completes once and OK,
+    each stream's counters advance batch by batch, and 32 sampled streams
+    equal their runs alone bit for bit."""
+    rng = np.random.default_rng(23)
+    base = [_graph(5000 + g, n_lo=3000, n_hi=40000) for g in range(32)]
+    n_streams, w_max = 512, 20000
+    specs, plans = [], []
+    for s in range(n_streams):
+        keys = base[int(rng.integers(0, len(base)))]
+        start = int(rng.integers(0, max(1, keys.size // 2)))
+        window = keys[start:]
+        specs.append((int(round(2 ** rng.uniform(4, 12))), int(rng.integers(0, 2**63)),
+                      int(rng.integers(0, 2**32))))
+        plan, cur = [], 0
+        for _ in range(int(rng.integers(4, 12))):
+            if rng.random() < 0.1 or cur >= window.size:
+                plan.append(("q",))
+            else:
+                w = int(min(round(10 ** rng.uniform(0, np.log10(w_max))), window.size - cur))
+                plan.append(("b", window[cur:cur + w].copy()))
+                cur += w
+        plan.append(("c",))
+        plans.append(plan)
+    srv = tc.Server(max_streams=128, vertex_bits=16, budget_bytes=4 << 30, w_max_round=1 << 20)
+    try:
+        where, done = _run_mix_many(srv, specs, plans, rng, chunk=64)
+        st = srv.stats()
+    finally:
+        srv.destroy()
+    assert len(done) == len(where), "every request completes exactly once"
+    assert st["opens"] == n_streams and st["closes"] == n_streams
+    assert st["max_round_streams"] <= 128 and st["rejected"] == 0
+    per = {s: [] for s in range(n_streams)}
+    for t, (s, i) in where.items():
+        c = done[t]
+        assert c["status"] == tc.TC_OK, (s, i, c["status"])
+        if i >= 0 and plans[s][i][0] != "c":
+            per[s].append((i, int(c["batches"]), int(c["m"])))
+    for s, rows in per.items():
+        rows.sort()
+        nb = m = 0
+        for i, b, mm in rows:
+            if plans[s][i][0] == "b":
+                nb += 1
+                m += plans[s][i][1].size
+            assert (b, mm) == (nb, m), (s, i)
+    for s in rng.choice(n_streams, size=32, replace=False):
+        exp = _alone_w(specs[s], plans[s], 16, w_max)
+        for t, (s2, i) in where.items():
+            if s2 != s or i < 0 or plans[s][i][0] == "c":
+                continue
+            c = done[t]
+            got = (int(c["batches"]), int(c["sum_lo"]) | (int(c["sum_hi"]) << 64),
+                   int(c["n_closed"]), int(c["m"]), int(c["num_lo"]) | (int(c["num_hi"]) << 64),
+                   float(c["tau_hat"]))
+            assert got == exp[i], (s, i, got, exp[i])
