@@ -461,6 +461,11 @@ __device__ __forceinline__ void packed_segment(const uint4 *pdir, const u32 *off
 // follows (almost always empty), where the edges with the whole hash are
 // compared.
 // ---------------------------------------------------------------------------
+// The 32-bit hash of a Step-3 key (its bits above the bw position bits).
+__device__ __forceinline__ u32 key_hash(u64 key, u32 bw) {
+    return __funnelshift_r((u32)key, (u32)(key >> 32), bw);
+}
+
 __device__ __forceinline__ u32 filter_bits(u64 h, u32 hb) {
     return (1u << ((h >> (27 - hb)) & 31)) | (1u << (((u32)h * 0x9E3779B1u) >> 27));
 }
@@ -508,22 +513,30 @@ static __global__ void __launch_bounds__(kIdxThreads) step3_index_kernel(
                 smask[q] = 0u;
             }
         __syncthreads();
+        // per key, all in 32 bits: h is the key's hash (its bits above the
+        // bw position bits), the sorted bits are the top hs of h, the bucket
+        // the top hb, and positions and indices are below 2^29
+        const u32 n32 = (u32)n, t32 = (u32)t0;
+        const u32 sh_s = 32 - s.hs, sh_b = 32 - s.hb;
+        const u32 blo32 = (u32)blo, bhi32 = (u32)bhi;
 #pragma unroll
         for (int j = 0; j < kIdxItems; ++j) {
             const int i = j * kIdxThreads + tid;
-            const u64 k = t0 + (u64)i;
-            if (k >= n) break;
+            const u32 k = t32 + (u32)i;
+            if (k >= n32) break;
             const u64 key = st[1 + i];
-            const u64 b = key >> sh;
+            const u32 h = key_hash(key, s.bw);
+            const u32 b = h >> sh_b;
             // repeat check: the run of equal sorted bits that follows
             {
-                const u64 hp = key >> s.she, h = key >> s.bw;
+                const u32 hp = h >> sh_s;
                 u64 e = 0;
                 bool have_e = false;
-                for (u64 q = k + 1; q < n; ++q) {
-                    const u64 kq = (q - t0 < (u64)kIdxTile + 1) ? st[1 + (q - t0)] : __ldg(K + q);
-                    if ((kq >> s.she) != hp) break;
-                    if ((kq >> s.bw) != h) continue;
+                for (u32 q = k + 1; q < n32; ++q) {
+                    const u64 kq = (q - t32 < (u32)kIdxTile + 1) ? st[1 + (q - t32)] : __ldg(K + q);
+                    const u32 hq = key_hash(kq, s.bw);
+                    if ((hq >> sh_s) != hp) break;
+                    if (hq != h) continue;
                     if (!have_e) {
                         e = __ldg(W + (key & pmask));
                         have_e = true;
@@ -531,23 +544,24 @@ static __global__ void __launch_bounds__(kIdxThreads) step3_index_kernel(
                     dup |= __ldg(W + (kq & pmask)) == e;
                 }
             }
-            if (b < blo || b >= bhi) continue;  // a bucket begun in an earlier tile
-            const bool head = (k == 0) || (st[i] >> sh) != b;
+            if (b < blo32 || b >= bhi32) continue;  // a bucket begun in an earlier tile
+            const bool head = (k == 0) || (key_hash(st[i], s.bw) >> sh_b) != b;
             if (fits) {
-                if (head) soff[b - blo] = (u32)k;
-                atomicOr(&smask[b - blo], filter_bits(key >> s.bw, s.hb));
+                if (head) soff[b - blo32] = k;
+                atomicOr(&smask[b - blo32], filter_bits(h, s.hb));
             } else if (head) {
                 // wide span: this head writes its bucket (mask from its keys)
                 // and the empty buckets below it
                 u32 mask = 0;
-                for (u64 q = k; q < n; ++q) {
-                    const u64 kq = (q - t0 < (u64)kIdxTile + 1) ? st[1 + (q - t0)] : __ldg(K + q);
-                    if ((kq >> sh) != b) break;
-                    mask |= filter_bits(kq >> s.bw, s.hb);
+                for (u32 q = k; q < n32; ++q) {
+                    const u64 kq = (q - t32 < (u32)kIdxTile + 1) ? st[1 + (q - t32)] : __ldg(K + q);
+                    const u32 hq = key_hash(kq, s.bw);
+                    if ((hq >> sh_b) != b) break;
+                    mask |= filter_bits(hq, s.hb);
                 }
-                const u64 bprev = k ? (st[i] >> sh) + 1 : 0;
-                for (u64 q = bprev; q < b; ++q) bdir[q] = make_uint2((u32)k, 0u);
-                bdir[b] = make_uint2((u32)k, mask);
+                const u32 bprev = k ? (key_hash(st[i], s.bw) >> sh_b) + 1 : 0u;
+                for (u32 q = bprev; q < b; ++q) bdir[q] = make_uint2(k, 0u);
+                bdir[b] = make_uint2(k, mask);
             }
         }
         __syncthreads();
