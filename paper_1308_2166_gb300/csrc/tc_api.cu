@@ -472,8 +472,8 @@ static int enqueue_batch(tc_ctx *c, const u64 *W, u64 w, cudaStream_t st, bool p
         pack_offsets_kernel<<<pack_blocks(c->vertex_bits, c->sm_count), kIdxThreads, 0, ms>>>(
             z.aoff, 1u << c->vertex_bits, z.pdir);
     } else if (dmode == kArcTagged)
-        index_kernel<true><<<index_blocks(2 * w), kIdxThreads, 0, ms>>>(
-            z.arcs[0], z.arcs[1], &plans[0], s, z.adir, W, tag, berr);
+        index_kernel<<<index_blocks(2 * w), kIdxThreads, 0, ms>>>(z.arcs[0], z.arcs[1],
+                                                                   &plans[0], s, z.adir, tag);
     if (stages) stamp(c, ms, kDups);  // the arc index, beside the rest of the edge branch
     TC_CUDA(cudaStreamWaitEvent(ms, c->ev_join, 0));
     if (stages) stamp(c, ms, kEdgeSort);  // what is left of the edge passes and their index

@@ -181,32 +181,29 @@ __device__ __forceinline__ u32 lower_bound_idx32(const u64 *__restrict__ a, u32 
 }
 
 // ---------------------------------------------------------------------------
-// Directories over the two sorted arrays, plus the in-batch repeat check.
-// For the arcs, x = src; for the Step-3 keys, x = the smaller endpoint.  The
-// first element of a run writes (epoch, start), the last one writes end.
+// Tagged arc directory (batches with 2^B > 8w, vertex ids below 2^kDirMaxBits):
+// per vertex x = src, the first arc of its run writes (epoch, start) and the
+// last one writes end; entries of other vertices keep an older epoch and read
+// as empty.  A block stages tiles of kIdxTile sorted keys (plus one key either
+// side) in shared memory with coalesced loads, then each thread examines
+// kIdxItems keys of the tile at a stride of the block.  (The Step-3 bucket
+// directory and the repeat check are step3_index_kernel's.)
 // ---------------------------------------------------------------------------
-// kArcs: the arc directory (after the arc sort); else the Step-3 bucket
-// directory and the in-batch repeat check (after the edge sort).  The two
-// run on the streams of their sorts.  A block stages tiles of kIdxTile keys
-// (plus one key either side) in shared memory with coalesced loads, then
-// each thread examines kIdxItems keys of the tile at a stride of the block.
 constexpr int kIdxThreads = 256;
 constexpr int kIdxItems = 8;
 constexpr int kIdxTile = kIdxThreads * kIdxItems;
 
-template <bool kArcs>
-static __global__ void __launch_bounds__(kIdxThreads) index_kernel(
-    const u64 *keys0, const u64 *keys1, const SortPlan *plan, BatchShape s, DirEntry *dir,
-    const u64 *__restrict__ W, u32 epoch, u32 *err) {
+static __global__ void __launch_bounds__(kIdxThreads) index_kernel(const u64 *keys0,
+                                                                  const u64 *keys1,
+                                                                  const SortPlan *plan,
+                                                                  BatchShape s, DirEntry *dir,
+                                                                  u32 epoch) {
     __shared__ u64 st[kIdxTile + 2];  // st[1 + i] = key t0 + i; st[0], st[kIdxTile + 1]: halo
     const u64 *__restrict__ K = plan_final_sel(plan) ? keys1 : keys0;
-    const u64 n = kArcs ? 2ull * s.w : (u64)s.w;
-    const u64 nverts = kArcs ? (1ull << s.B) : (1ull << s.hb);
-    // key -> directory slot: arcs by src; Step-3 keys by hash bucket
-    const u32 sh = kArcs ? s.sha : s.bw + 32 - s.hb;
-    const u64 pmask = (1ull << s.bw) - 1;
+    const u64 n = 2ull * s.w;
+    const u64 nverts = 1ull << s.B;
+    const u32 sh = s.sha;  // key -> src
     const int tid = threadIdx.x;
-    bool dup = false;
     for (u64 t0 = (u64)blockIdx.x * kIdxTile; t0 < n; t0 += (u64)gridDim.x * kIdxTile) {
 #pragma unroll
         for (int j = 0; j < kIdxItems; ++j) {
@@ -221,35 +218,15 @@ static __global__ void __launch_bounds__(kIdxThreads) index_kernel(
             const int i = j * kIdxThreads + tid;
             const u64 k = t0 + (u64)i;
             if (k >= n) break;
-            const u64 key = st[1 + i];
-            const u64 x = key >> sh;
+            const u64 x = st[1 + i] >> sh;
             const u64 prev = k ? st[i] >> sh : ~0ull;
             const u64 next = k + 1 < n ? st[i + 2] >> sh : ~0ull;
-            if constexpr (!kArcs) {
-                // a repeated edge has the repeated hash, so it lies in the run
-                // of keys sharing the sorted hash bits that follows (almost
-                // always empty): compare the edges whose whole hash matches
-                const u64 hp = key >> s.she, h = key >> s.bw;
-                u64 e = 0;
-                bool have_e = false;
-                for (u64 q = k + 1; q < n; ++q) {
-                    const u64 kq = __ldg(K + q);
-                    if ((kq >> s.she) != hp) break;
-                    if ((kq >> s.bw) != h) continue;
-                    if (!have_e) {
-                        e = __ldg(W + (key & pmask));
-                        have_e = true;
-                    }
-                    dup |= __ldg(W + (kq & pmask)) == e;
-                }
-            }
             if (x >= nverts) continue;  // invalid batch (already flagged by the key build)
             if (x != prev) *reinterpret_cast<u64 *>(&dir[x].epoch) = (k << 32) | epoch;
             if (x != next) dir[x].end = (u32)(k + 1);
         }
         __syncthreads();  // the tile is restaged next
     }
-    if (dup) set_error(err, kErrInput);
 }
 
 // ---------------------------------------------------------------------------
